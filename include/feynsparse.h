@@ -1,0 +1,230 @@
+/*
+ * feynsparse: selected computational-basis output amplitudes of a quantum
+ * circuit as a reduced Feynman sum over histories, on one NVIDIA B300
+ * (sm_103a).  C ABI; every entry point returns an int status (FS_OK = 0,
+ * negative on error) and leaves a message for fs_last_error() on failure.
+ *
+ * The method is that of "Fewer Histories, Faster Paths" (Larssen, Pennati,
+ * Asgrim, Peng, Markidis):
+ *   - the transition amplitude <out|U_m ... U_1|in> (Eq. 1) of a sparse input
+ *     |psi> = sum_in c_in |in> is sum_in c_in alpha^{in,out} (Eq. 2);
+ *   - alpha is the sum over histories (Eqs. 3-5), reduced to a sum over the
+ *     2^A assignments of artificial sources placed by a backward
+ *     output-to-input sweep (Sec. IV-A, Eq. 7);
+ *   - histories are evaluated with prefix/root/suffix checkpoints
+ *     (Sec. IV-C, Algorithm 2) at cuts autotuned on Eq. 8;
+ *   - invalid histories are pruned exactly and, when eps > 0, branches
+ *     whose running |amplitude| falls below eps are dropped (Sec. IV-A,
+ *     Observation 3).
+ *
+ * Conventions.
+ *   Qubit q is bit q of a bit string (qubit 0 = least significant); at most
+ *   FS_MAX_QUBITS qubits.  A bit string is passed as 2 uint64_t words (word 0
+ *   holds qubits 0..63).  Matrices are indexed [output value][input value];
+ *   for two targets the local value is bit(q[0]) + 2*bit(q[1]).
+ *   H = [[1,1],[1,-1]]/sqrt2, X, Y = [[0,-i],[i,0]], Z = diag(1,-1),
+ *   S = diag(1,i), T = diag(1,e^{i pi/4}), P(t) = diag(1,e^{it}),
+ *   RX(t) = [[c,-is],[-is,c]], RY(t) = [[c,-s],[s,c]],
+ *   RZ(t) = diag(e^{-it/2},e^{it/2}), RZZ(t) = diag(e^{-it/2}, e^{it/2},
+ *   e^{it/2}, e^{-it/2}), c = cos(t/2), s = sin(t/2).
+ *   Controls (ctrl_mask / ctrl_val, value 0 = negative control) are allowed
+ *   on X (CNOT, Toffoli, MCX), Z (CZ, MCZ), P (controlled phase), S and T.
+ *
+ * Gate roles (Sec. II-A): H, RX, RY branch; X, Y, SWAP are deterministic;
+ * Z, S, T, P, RZ, RZZ are wire-preserving; explicit U1/U2 matrices are
+ * classified by their exact zero pattern (diagonal: wire-preserving; one
+ * nonzero per column: deterministic; otherwise branching).  A branching
+ * input whose wire is the circuit input wire of that qubit (no earlier gate
+ * acted on the qubit except as a wire-preserving gate or a control) is a
+ * natural source and takes its value from the input bit string; every other
+ * branching input is an artificial source, numbered in the order the
+ * backward sweep meets it.
+ */
+#ifndef FEYNSPARSE_H
+#define FEYNSPARSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FS_API __attribute__((visibility("default")))
+#else
+#define FS_API
+#endif
+
+#define FS_MAX_QUBITS 128
+
+/* status codes */
+#define FS_OK 0
+#define FS_ERR_INVALID (-1)        /* bad argument (null pointer, index out of range, ...) */
+#define FS_ERR_UNSUPPORTED (-2)    /* unknown gate kind or controls on a kind that takes none */
+#define FS_ERR_TOO_MANY_QUBITS (-3)
+#define FS_ERR_NONUNITARY (-4)     /* explicit matrix with |U^+U - I| > 1e-12 */
+#define FS_ERR_NOMEM (-5)
+#define FS_ERR_CUDA (-6)           /* a CUDA runtime call failed; see fs_last_error() */
+#define FS_ERR_TIMEOUT (-7)        /* reserved: a bounded device wait gave up */
+#define FS_ERR_BAD_PROGRAM (-8)    /* the device found an opcode it does not know */
+#define FS_ERR_TOO_LARGE (-9)      /* 2^A histories cannot be enumerated (A > 62) or
+                                      the work exceeds the library's index range */
+#define FS_ERR_STATE (-10)         /* call out of order (e.g. run before plan) */
+
+/* gate kinds */
+enum {
+    FS_H = 0, FS_X = 1, FS_Y = 2, FS_Z = 3, FS_S = 4, FS_T = 5, FS_P = 6,
+    FS_RX = 7, FS_RY = 8, FS_RZ = 9, FS_RZZ = 10, FS_SWAP = 11, FS_U1 = 12, FS_U2 = 13
+};
+
+/* One gate.  n_q targets in q[]; controls as 128-bit masks; theta for the
+ * parametrised kinds; m[] = re/im interleaved row-major matrix for U1 (2x2,
+ * 8 doubles) and U2 (4x4, 32 doubles). */
+typedef struct fs_gate {
+    uint32_t kind;
+    uint32_t n_q;
+    uint32_t q[2];
+    uint64_t ctrl_mask[2];
+    uint64_t ctrl_val[2];
+    double theta;
+    double m[32];
+} fs_gate;
+
+typedef struct fs_circuit fs_circuit;   /* opaque, owned by the library */
+typedef struct fs_batch fs_batch;       /* opaque, owned by the library */
+
+/* Result of the analysis (Sec. IV-A) and of the autotuned partition
+ * (Sec. IV-C).  Cuts c1 <= c2 are positions in evaluation (output-to-input)
+ * order: the prefix is evaluation positions [0, c1), the root [c1, c2), the
+ * suffix [c2, n_gates). */
+typedef struct fs_analysis {
+    uint32_t n_qubits;
+    uint32_t n_gates;
+    uint32_t n_branch_vars;    /* branching inputs: natural + artificial */
+    uint32_t n_natural;
+    uint32_t A;                /* artificial sources */
+    uint32_t n_wp, n_det, n_br;/* gate role counts */
+    int32_t c1, c2;            /* autotuned cuts (for the request size last planned,
+                                  or for a single output when none was) */
+    uint32_t G_p, G_r, G_s;
+    uint32_t A_p, A_r, A_s;
+    uint64_t gateops_lo, gateops_hi;  /* Eq. 8 at (c1, c2), 128-bit */
+    uint32_t max_ap, min_apr;  /* the autotuner's memory / parallelism constraints */
+} fs_analysis;
+
+/* Options of a batch.  split: 0 = autotuned, 1 = fixed cuts (c1, c2 applied
+ * to every job), 2 = no checkpoints (Algorithm 1: a single region). */
+typedef struct fs_options {
+    uint32_t split;
+    int32_t c1, c2;
+    uint64_t table_budget_bytes;   /* checkpoint-table memory bound (0: 4 GiB) */
+    uint64_t min_items;            /* parallelism floor for (prefix, root) items (0: 2^19) */
+} fs_options;
+
+/* Counters of one job after a run. */
+typedef struct fs_stats {
+    uint64_t candidates;      /* S * M * 2^A */
+    uint64_t completed;       /* leaves that reached the input boundary */
+    uint64_t valid;           /* completed leaves with chi = 1 */
+    uint64_t gate_visits;     /* gates evaluated (Eq. 8 per pair in exact mode) */
+    uint64_t table_entries;   /* checkpoint entries written */
+    int32_t c1, c2;
+    uint32_t A_p, A_r, A_s;
+} fs_stats;
+
+/* Thread-local message of the last failing call on this thread. */
+FS_API const char* fs_last_error(void);
+
+/* Library version string. */
+FS_API const char* fs_version(void);
+
+/* Copies n_gates gates (host memory) into a new circuit on n_qubits qubits,
+ * validates them (qubit indices, controls, unitarity of U1/U2 to 1e-12),
+ * classifies their roles and places the artificial sources.  The gates are
+ * in circuit order (the first gate acts first).  *out receives a handle to
+ * free with fs_circuit_destroy.  Follows the statement of the problem
+ * (Sec. II, Eq. 1) and the analysis of Sec. IV-A. */
+FS_API int fs_circuit_create(const fs_gate* gates, size_t n_gates, uint32_t n_qubits,
+                      fs_circuit** out);
+
+FS_API int fs_circuit_destroy(fs_circuit* c);
+
+/* Analysis for the basis input input_bits (2 words, host): fills *out with
+ * the branching-variable and artificial-source counts and the autotuned
+ * partition for one output; also makes input_bits the circuit's input
+ * (S = 1, coefficient 1) until fs_set_input replaces it.  Sec. IV-A/IV-C. */
+FS_API int fs_analyze(fs_circuit* c, const uint64_t* input_bits, fs_analysis* out);
+
+/* Lists the branching variables in backward-sweep order: per entry the gate
+ * index (circuit order), the qubit, and the artificial source id or -1 for a
+ * natural source.  Arrays of capacity cap (host); *count receives the total
+ * (entries beyond cap are not written). */
+FS_API int fs_branch_vars(const fs_circuit* c, int32_t* gate_index, int32_t* qubit, int32_t* source,
+                   size_t cap, size_t* count);
+
+/* Sparse input state sum_k coeffs[k] |support[k]> (Eq. 2): S bit strings of 2
+ * words and S complex coefficients (re, im), host memory, copied. */
+FS_API int fs_set_input(fs_circuit* c, const uint64_t* support_bits, const double* coeffs, size_t S);
+
+/* Amplitudes <out|C|psi> of n_out requested outputs (n_out x 2 words, host)
+ * into amp_out (2*n_out doubles, re/im, host, caller-owned), with threshold
+ * eps (0 = exact).  Synchronous: plans, copies to the device, runs the
+ * kernels on the default stream and copies back.  Device memory is
+ * allocated and freed inside the call. */
+FS_API int fs_amplitudes(fs_circuit* c, const uint64_t* outputs, size_t n_out, double eps,
+                  double* amp_out);
+
+/* ---- batches: many circuits and outputs in one persistent launch ---- */
+
+FS_API int fs_batch_create(fs_batch** out);
+FS_API int fs_batch_destroy(fs_batch* b);
+
+/* Batch options (may be NULL for defaults); call before fs_batch_plan. */
+FS_API int fs_batch_set_options(fs_batch* b, const fs_options* opt);
+
+/* Adds a job: circuit c (its current input state), n_out outputs (host,
+ * copied), threshold eps.  *job_id receives the job's index; its amplitudes
+ * occupy amp_out[2*offset .. 2*(offset+n_out)) where offset is the sum of
+ * n_out over earlier jobs. */
+FS_API int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, size_t n_out,
+                 double eps, uint32_t* job_id);
+
+/* Compiles every job (programs, autotuned cuts, tile queue) and reports the
+ * device workspace size in bytes (256-byte aligned sub-buffers). */
+FS_API int fs_batch_plan(fs_batch* b, size_t* workspace_bytes);
+
+/* Copies the planned static data (programs, bit strings, tile list) into the
+ * caller's device workspace d_ws (at least workspace_bytes, 256-byte
+ * aligned) on stream (a cudaStream_t, NULL = legacy default stream).
+ * Asynchronous; the host arrays stay owned by the batch. */
+FS_API int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Enqueues one evaluation of every job on stream: counter reset, prefix
+ * expansion (checkpoint table), persistent history kernel over the atomic
+ * tile queue, fixed-order reduction into d_amp_out (device, 2 * total
+ * outputs doubles).  Asynchronous and free of host synchronisation, so it
+ * can be captured into a CUDA graph.  Requires fs_batch_upload on the same
+ * workspace first. */
+FS_API int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream);
+
+/* Waits for stream, reads the device error word and the per-job counters
+ * (fs_stats array of capacity cap, host) of the last run. */
+FS_API int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size_t cap);
+
+/* Total outputs over the jobs added so far. */
+FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
+
+/* Number of kernel launches fs_batch_run enqueues. */
+FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
+
+/* Average duration of the history kernel of the last fs_batch_run that
+ * recorded events (enabled by fs_batch_time_kernels), in milliseconds. */
+FS_API int fs_batch_time_kernels(fs_batch* b, int enable);
+FS_API int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* reduce_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEYNSPARSE_H */

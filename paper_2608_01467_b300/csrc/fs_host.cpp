@@ -1,0 +1,879 @@
+// Host side of the library: circuit validation and gate matrices, the
+// reduced-history analysis (Sec. IV-A), the evaluation-order program
+// compiler, the Eq. 8 autotuner (Sec. IV-C) and the batch planner that lays
+// out one device workspace for many jobs (Sec. IV-D, Observations 5-6).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/feynsparse.h"
+#include "fs_internal.h"
+
+using cd = std::complex<double>;
+using u128 = unsigned __int128;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(FS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+enum Role { WP = 0, DET = 1, BR = 2 };
+
+struct GateInfo {
+    uint32_t kind = 0;
+    int k = 1;                  // targets
+    int q[2] = {0, 0};
+    uint64_t cm[2] = {0, 0}, cv[2] = {0, 0};
+    double theta = 0;
+    cd u[16];                   // base matrix on the targets, u[out * dim + in]
+    Role role = WP;
+    int src[2] = {-2, -2};      // artificial source id, -1 natural, -2 not a branching input
+};
+
+struct Bits { uint64_t w[2] = {0, 0}; };
+
+}  // namespace
+
+struct fs_circuit {
+    uint32_t n = 0;
+    std::vector<GateInfo> g;
+    int A = 0, n_natural = 0, n_bvars = 0;
+    int n_wp = 0, n_det = 0, n_br = 0;
+    std::vector<Bits> in_bits{Bits{}};
+    std::vector<cd> in_coef{cd(1, 0)};
+};
+
+namespace {
+
+// ------------------------------------------------------------------ gates
+
+bool controllable(uint32_t k) { return k == FS_X || k == FS_Z || k == FS_P || k == FS_S || k == FS_T; }
+
+int build_matrix(const fs_gate& in, GateInfo& g)
+{
+    const double t = in.theta, c = std::cos(t / 2.0), s = std::sin(t / 2.0);
+    const double h = std::sqrt(0.5);
+    for (auto& v : g.u) v = 0.0;
+    g.k = 1;
+    switch (in.kind) {
+    case FS_H: g.u[0] = h; g.u[1] = h; g.u[2] = h; g.u[3] = -h; g.role = BR; break;
+    case FS_X: g.u[1] = 1; g.u[2] = 1; g.role = DET; break;
+    case FS_Y: g.u[1] = cd(0, -1); g.u[2] = cd(0, 1); g.role = DET; break;
+    case FS_Z: g.u[0] = 1; g.u[3] = -1; g.role = WP; break;
+    case FS_S: g.u[0] = 1; g.u[3] = cd(0, 1); g.role = WP; break;
+    case FS_T: g.u[0] = 1; g.u[3] = cd(std::cos(M_PI / 4.0), std::sin(M_PI / 4.0)); g.role = WP; break;
+    case FS_P: g.u[0] = 1; g.u[3] = cd(std::cos(t), std::sin(t)); g.role = WP; break;
+    case FS_RX: g.u[0] = c; g.u[1] = cd(0, -s); g.u[2] = cd(0, -s); g.u[3] = c; g.role = BR; break;
+    case FS_RY: g.u[0] = c; g.u[1] = -s; g.u[2] = s; g.u[3] = c; g.role = BR; break;
+    case FS_RZ: g.u[0] = cd(c, -s); g.u[3] = cd(c, s); g.role = WP; break;
+    case FS_RZZ:
+        g.k = 2;
+        g.u[0] = cd(c, -s); g.u[5] = cd(c, s); g.u[10] = cd(c, s); g.u[15] = cd(c, -s);
+        g.role = WP;
+        break;
+    case FS_SWAP:
+        g.k = 2;
+        g.u[0] = 1; g.u[1 * 4 + 2] = 1; g.u[2 * 4 + 1] = 1; g.u[15] = 1;
+        g.role = DET;
+        break;
+    case FS_U1:
+    case FS_U2: {
+        const int dim = in.kind == FS_U1 ? 2 : 4;
+        g.k = in.kind == FS_U1 ? 1 : 2;
+        for (int i = 0; i < dim * dim; ++i) g.u[i] = cd(in.m[2 * i], in.m[2 * i + 1]);
+        double dev = 0;   // max |U^+U - I|
+        for (int a = 0; a < dim; ++a)
+            for (int b = 0; b < dim; ++b) {
+                cd acc = 0;
+                for (int r = 0; r < dim; ++r) acc += std::conj(g.u[r * dim + a]) * g.u[r * dim + b];
+                dev = std::max(dev, std::abs(acc - cd(a == b ? 1.0 : 0.0)));
+            }
+        if (!(dev <= 1e-12)) return fail(FS_ERR_NONUNITARY, "explicit matrix is not unitary (|U^+U-I| = %g)", dev);
+        // roles from the exact zero pattern
+        bool diag = true, perm = true;
+        for (int col = 0; col < dim; ++col) {
+            int nz = 0;
+            for (int row = 0; row < dim; ++row)
+                if (g.u[row * dim + col] != cd(0, 0)) { ++nz; if (row != col) diag = false; }
+            if (nz != 1) perm = false;
+        }
+        g.role = diag ? WP : (perm ? DET : BR);
+        break;
+    }
+    default:
+        return fail(FS_ERR_UNSUPPORTED, "unknown gate kind %u", in.kind);
+    }
+    return FS_OK;
+}
+
+// ------------------------------------------------------------------ analysis
+
+// Natural vs artificial branching inputs, then artificial-source ids in
+// backward-sweep order (Sec. IV-A).  A qubit's input wire runs until the
+// first gate that may change its value (deterministic or branching target);
+// a branching gate at exactly that point reads the input bit (natural
+// source).  Every other branching input gets the next id as the sweep goes
+// from the output back to the input.
+void analyze_circuit(fs_circuit& C)
+{
+    const int G = (int)C.g.size();
+    std::vector<int> first_write(C.n, G);
+    for (int i = 0; i < G; ++i) {
+        const GateInfo& g = C.g[i];
+        if (g.role == WP) continue;
+        for (int t = 0; t < g.k; ++t)
+            if (first_write[g.q[t]] == G) first_write[g.q[t]] = i;
+    }
+    C.A = C.n_natural = C.n_bvars = C.n_wp = C.n_det = C.n_br = 0;
+    for (int i = G - 1; i >= 0; --i) {
+        GateInfo& g = C.g[i];
+        (g.role == WP ? C.n_wp : g.role == DET ? C.n_det : C.n_br)++;
+        g.src[0] = g.src[1] = -2;
+        if (g.role != BR) continue;
+        const int lo = (g.k == 2 && g.q[1] < g.q[0]) ? 1 : 0;
+        for (int j = 0; j < g.k; ++j) {
+            const int t = (j == 0) ? lo : 1 - lo;
+            ++C.n_bvars;
+            if (first_write[g.q[t]] == i) { g.src[t] = -1; ++C.n_natural; }
+            else g.src[t] = C.A++;
+        }
+    }
+}
+
+// Sources among the ops at evaluation positions [0, e) for every e.
+std::vector<int> source_prefix(const fs_circuit& C)
+{
+    const int G = (int)C.g.size();
+    std::vector<int> pre(G + 1, 0);
+    for (int e = 0; e < G; ++e) {
+        const GateInfo& g = C.g[G - 1 - e];
+        int a = 0;
+        if (g.role == BR)
+            for (int t = 0; t < g.k; ++t) a += g.src[t] >= 0;
+        pre[e + 1] = pre[e] + a;
+    }
+    return pre;
+}
+
+u128 eq8(uint64_t Gp, uint64_t Gr, uint64_t Gs, int Ap, int Ar, int As)
+{
+    // 2^Ap (Gp + 2^Ar (Gr + 2^As Gs))
+    const u128 one = 1;
+    return (one << Ap) * ((u128)Gp + (one << Ar) * ((u128)Gr + (one << As) * (u128)Gs));
+}
+
+struct Split {
+    int c1 = 0, c2 = 0, Ap = 0, Ar = 0, As = 0;
+    u128 cost = 0;
+};
+
+Split split_at(const fs_circuit& C, const std::vector<int>& pre, int c1, int c2)
+{
+    const int G = (int)C.g.size();
+    Split s;
+    s.c1 = c1; s.c2 = c2;
+    s.Ap = pre[c1]; s.Ar = pre[c2] - pre[c1]; s.As = pre[G] - pre[c2];
+    s.cost = eq8((uint64_t)c1, (uint64_t)(c2 - c1), (uint64_t)(G - c2), s.Ap, s.Ar, s.As);
+    return s;
+}
+
+// Autotuned partition: minimum of Eq. 8 over all cuts 0 <= c1 <= c2 <= G,
+// subject to the checkpoint table fitting (Ap <= max_ap) and enough
+// (prefix, root) items for the GPU (Ap + Ar >= min(min_apr, A)) and within
+// index range (Ap + Ar <= max_apr).  Ties: smallest c1, then smallest c2.
+bool autotune(const fs_circuit& C, int max_ap, int min_apr, int max_apr, Split& best)
+{
+    const int G = (int)C.g.size();
+    const std::vector<int> pre = source_prefix(C);
+    const int need = std::min(min_apr, C.A);
+    bool found = false;
+    for (int c1 = 0; c1 <= G && pre[c1] <= max_ap; ++c1) {
+        for (int c2 = c1; c2 <= G; ++c2) {
+            const int apr = pre[c2];
+            if (apr < need) continue;
+            if (apr > max_apr) break;
+            const Split s = split_at(C, pre, c1, c2);
+            if (!found || s.cost < best.cost) { best = s; found = true; }
+        }
+    }
+    return found;
+}
+
+int ilog2_floor(uint64_t v) { int r = -1; while (v) { v >>= 1; ++r; } return r; }
+int ilog2_ceil(uint64_t v) { int r = 0; while ((1ull << r) < v && r < 63) ++r; return r; }
+
+// ------------------------------------------------------------------ program
+
+struct Program {
+    std::vector<fs::Op> ops;
+    std::vector<uint32_t> masks;
+    std::vector<double2> fac;
+};
+
+uint32_t push_fac(Program& P, std::initializer_list<cd> v)
+{
+    const uint32_t off = (uint32_t)P.fac.size();
+    for (const cd& z : v) P.fac.push_back(make_double2(z.real(), z.imag()));
+    return off;
+}
+
+uint32_t push_mask(Program& P, int W, const uint64_t m[2], const uint64_t v[2])
+{
+    const uint32_t off = (uint32_t)P.masks.size();
+    for (int j = 0; j < W; ++j) P.masks.push_back((uint32_t)(m[j >> 1] >> (32 * (j & 1))));
+    for (int j = 0; j < W; ++j) P.masks.push_back((uint32_t)(v[j >> 1] >> (32 * (j & 1))));
+    return off;
+}
+
+// Emits the ops in evaluation (output-to-input) order.  An artificial source
+// with id k in a region whose ids are [k0, k0 + a) takes bit a - 1 - (k - k0)
+// of that region's enumeration word: the first source met is the most
+// significant bit, so a cut subtree is a contiguous range of h.
+void compile(const fs_circuit& C, int W, const Split& sp, Program& P)
+{
+    const int G = (int)C.g.size();
+    P.ops.clear(); P.masks.clear(); P.fac.clear();
+    P.ops.reserve(G);
+    auto region_bit = [&](int e, int k) -> int {
+        int k0, a;
+        if (e < sp.c1) { k0 = 0; a = sp.Ap; }
+        else if (e < sp.c2) { k0 = sp.Ap; a = sp.Ar; }
+        else { k0 = sp.Ap + sp.Ar; a = sp.As; }
+        return a - 1 - (k - k0);
+    };
+    for (int e = 0; e < G; ++e) {
+        const GateInfo& g = C.g[G - 1 - e];
+        fs::Op op;
+        std::memset(&op, 0, sizeof op);
+        op.q0 = (uint8_t)g.q[0];
+        op.q1 = (uint8_t)(g.k == 2 ? g.q[1] : 0);
+        op.s0 = op.s1 = -1;
+        const bool ctl = (g.cm[0] | g.cm[1]) != 0;
+        const int dim = g.k == 1 ? 2 : 4;
+        if (g.role == WP) {
+            if (g.kind == FS_Z || g.kind == FS_S || g.kind == FS_T || g.kind == FS_P) {
+                if (ctl) {
+                    uint64_t m[2] = {g.cm[0], g.cm[1]}, v[2] = {g.cv[0], g.cv[1]};
+                    m[g.q[0] >> 6] |= 1ull << (g.q[0] & 63);
+                    v[g.q[0] >> 6] |= 1ull << (g.q[0] & 63);
+                    op.aux2 = push_mask(P, W, m, v);
+                    if (g.kind == FS_Z) op.code = fs::OP_MCNEG;
+                    else { op.code = fs::OP_MCPH; op.aux = push_fac(P, {g.u[3]}); }
+                } else if (g.kind == FS_Z) {
+                    op.code = fs::OP_NEG1;
+                } else {
+                    op.code = fs::OP_PH1;
+                    op.aux = push_fac(P, {g.u[3]});
+                }
+            } else if (g.k == 1) {
+                op.code = fs::OP_DIAG1;
+                op.aux = push_fac(P, {g.u[0], g.u[3]});
+            } else {
+                op.code = fs::OP_DIAG2;
+                op.aux = push_fac(P, {g.u[0], g.u[5], g.u[10], g.u[15]});
+            }
+        } else if (g.role == DET) {
+            if (g.kind == FS_X) {
+                if (ctl) {
+                    op.code = fs::OP_MCX;
+                    op.aux2 = push_mask(P, W, g.cm, g.cv);
+                } else {
+                    op.code = fs::OP_X;
+                }
+            } else if (g.kind == FS_SWAP) {
+                op.code = fs::OP_SWAP;
+            } else if (g.k == 1) {
+                // antidiagonal: output o came from input 1 - o
+                op.code = fs::OP_PERM1;
+                op.aux = push_fac(P, {g.u[0 * 2 + 1], g.u[1 * 2 + 0]});
+            } else {
+                op.code = fs::OP_PERM2;
+                cd f[4];
+                uint32_t packed = 0;
+                for (int o = 0; o < 4; ++o) {
+                    int in = 0;
+                    for (int c = 0; c < 4; ++c)
+                        if (g.u[o * 4 + c] != cd(0, 0)) { in = c; break; }
+                    f[o] = g.u[o * 4 + in];
+                    packed |= (uint32_t)in << (2 * o);
+                }
+                op.aux = push_fac(P, {f[0], f[1], f[2], f[3]});
+                op.aux2 = packed;
+            }
+        } else {
+            if (g.src[0] >= 0) op.s0 = (int8_t)region_bit(e, g.src[0]);
+            if (g.k == 2 && g.src[1] >= 0) op.s1 = (int8_t)region_bit(e, g.src[1]);
+            if (g.kind == FS_H) {
+                op.code = fs::OP_H;
+            } else if (g.k == 1) {
+                op.code = fs::OP_BR1;
+                op.aux = push_fac(P, {g.u[0], g.u[1], g.u[2], g.u[3]});
+            } else {
+                op.code = fs::OP_BR2;
+                op.aux = (uint32_t)P.fac.size();
+                for (int i = 0; i < 16; ++i) P.fac.push_back(make_double2(g.u[i].real(), g.u[i].imag()));
+            }
+        }
+        (void)dim;
+        P.ops.push_back(op);
+    }
+}
+
+int words_for(uint32_t n) { const int w = (int)((n + 31) / 32); return w <= 1 ? 1 : (w == 2 ? 2 : 4); }
+
+// ------------------------------------------------------------------ batch
+
+struct Job {
+    fs_circuit* c = nullptr;
+    std::vector<Bits> outs;
+    std::vector<Bits> ins;
+    std::vector<cd> coef;
+    double eps = 0;
+    // plan
+    Split sp;
+    Program prog;
+    int W = 1;
+    uint64_t pairs = 0, n_tiles = 0, table_entries = 0, n_partials = 0;
+    int log2_ipp = 0, log2_spp = 0;
+    // offsets in the workspace
+    size_t o_ops = 0, o_masks = 0, o_fac = 0, o_outs = 0, o_ins = 0, o_coef = 0, o_table = 0, o_part = 0;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct fs_batch {
+    std::vector<Job> jobs;
+    fs_options opt{};
+    bool planned = false, uploaded = false;
+    size_t ws_bytes = 0;
+    size_t o_jobs = 0, o_pbegin = 0, o_obegin = 0, o_tiles = 0, o_stats = 0, o_counter = 0, o_err = 0;
+    size_t static_bytes = 0, dyn_begin = 0;
+    std::vector<unsigned char> host_static;
+    std::vector<uint2> tiles;
+    uint64_t total_prefix = 0, total_out = 0;
+    int grid = 0;
+    void* uploaded_ws = nullptr;
+    bool timing = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ev_recorded = false;
+    ~fs_batch()
+    {
+        for (auto& e : ev) if (e) cudaEventDestroy(e);
+    }
+};
+
+extern "C" {
+
+const char* fs_last_error(void) { return g_err.c_str(); }
+
+const char* fs_version(void) { return "feynsparse 0.1 (sm_103a)"; }
+
+int fs_circuit_create(const fs_gate* gates, size_t n_gates, uint32_t n_qubits, fs_circuit** out)
+{
+    if (!out) return fail(FS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n_qubits == 0) return fail(FS_ERR_INVALID, "n_qubits must be >= 1");
+    if (n_qubits > FS_MAX_QUBITS) return fail(FS_ERR_TOO_MANY_QUBITS, "n_qubits %u > %d", n_qubits, FS_MAX_QUBITS);
+    if (n_gates && !gates) return fail(FS_ERR_INVALID, "gates is NULL");
+    if (n_gates > (1u << 24)) return fail(FS_ERR_TOO_LARGE, "too many gates");
+    std::unique_ptr<fs_circuit> C(new (std::nothrow) fs_circuit);
+    if (!C) return fail(FS_ERR_NOMEM, "out of host memory");
+    C->n = n_qubits;
+    C->g.resize(n_gates);
+    const uint64_t valid_mask[2] = {n_qubits >= 64 ? ~0ull : ((1ull << n_qubits) - 1),
+                                    n_qubits >= 128 ? ~0ull : (n_qubits > 64 ? ((1ull << (n_qubits - 64)) - 1) : 0ull)};
+    for (size_t i = 0; i < n_gates; ++i) {
+        const fs_gate& in = gates[i];
+        GateInfo& g = C->g[i];
+        g.kind = in.kind;
+        const int rc = build_matrix(in, g);
+        if (rc) return fail(rc, "gate %zu: %s", i, g_err.c_str());
+        const uint32_t want_q = (in.kind == FS_RZZ || in.kind == FS_SWAP || in.kind == FS_U2) ? 2u : 1u;
+        if (in.n_q != want_q) return fail(FS_ERR_INVALID, "gate %zu: kind %u takes %u target(s), n_q = %u", i, in.kind, want_q, in.n_q);
+        for (uint32_t t = 0; t < want_q; ++t)
+            if (in.q[t] >= n_qubits) return fail(FS_ERR_INVALID, "gate %zu: qubit %u out of range", i, in.q[t]);
+        if (want_q == 2 && in.q[0] == in.q[1]) return fail(FS_ERR_INVALID, "gate %zu: repeated target qubit", i);
+        g.q[0] = (int)in.q[0];
+        g.q[1] = want_q == 2 ? (int)in.q[1] : 0;
+        g.cm[0] = in.ctrl_mask[0]; g.cm[1] = in.ctrl_mask[1];
+        g.cv[0] = in.ctrl_val[0]; g.cv[1] = in.ctrl_val[1];
+        g.theta = in.theta;
+        if ((g.cm[0] | g.cm[1]) && !controllable(in.kind))
+            return fail(FS_ERR_UNSUPPORTED, "gate %zu: controls are allowed on X, Z, P, S, T only", i);
+        if ((g.cm[0] & ~valid_mask[0]) || (g.cm[1] & ~valid_mask[1]))
+            return fail(FS_ERR_INVALID, "gate %zu: control qubit out of range", i);
+        if ((g.cv[0] & ~g.cm[0]) || (g.cv[1] & ~g.cm[1]))
+            return fail(FS_ERR_INVALID, "gate %zu: control value outside the control mask", i);
+        for (uint32_t t = 0; t < want_q; ++t)
+            if ((g.cm[g.q[t] >> 6] >> (g.q[t] & 63)) & 1ull)
+                return fail(FS_ERR_INVALID, "gate %zu: a target is also a control", i);
+    }
+    analyze_circuit(*C);
+    *out = C.release();
+    return FS_OK;
+}
+
+int fs_circuit_destroy(fs_circuit* c)
+{
+    delete c;
+    return FS_OK;
+}
+
+static int check_bits(const fs_circuit* c, const uint64_t* b, const char* what)
+{
+    const uint32_t n = c->n;
+    const uint64_t hi0 = n >= 64 ? 0 : ~((1ull << n) - 1);
+    const uint64_t hi1 = n >= 128 ? 0 : (n <= 64 ? ~0ull : ~((1ull << (n - 64)) - 1));
+    if ((b[0] & hi0) || (b[1] & hi1)) return fail(FS_ERR_INVALID, "%s has bits beyond qubit %u", what, n - 1);
+    return FS_OK;
+}
+
+int fs_analyze(fs_circuit* c, const uint64_t* input_bits, fs_analysis* out)
+{
+    if (!c || !input_bits || !out) return fail(FS_ERR_INVALID, "NULL argument");
+    if (int rc = check_bits(c, input_bits, "input")) return rc;
+    c->in_bits.assign(1, Bits{});
+    c->in_bits[0].w[0] = input_bits[0];
+    c->in_bits[0].w[1] = input_bits[1];
+    c->in_coef.assign(1, cd(1, 0));
+    std::memset(out, 0, sizeof *out);
+    out->n_qubits = c->n;
+    out->n_gates = (uint32_t)c->g.size();
+    out->n_branch_vars = (uint32_t)c->n_bvars;
+    out->n_natural = (uint32_t)c->n_natural;
+    out->A = (uint32_t)c->A;
+    out->n_wp = (uint32_t)c->n_wp;
+    out->n_det = (uint32_t)c->n_det;
+    out->n_br = (uint32_t)c->n_br;
+    // one output, default budget
+    const int max_ap = ilog2_floor((4ull << 30) / 32);
+    const int min_apr = ilog2_ceil(1ull << 19);
+    Split s;
+    if (!autotune(*c, max_ap, min_apr, 40, s)) return fail(FS_ERR_TOO_LARGE, "no admissible partition");
+    out->c1 = s.c1; out->c2 = s.c2;
+    const int G = (int)c->g.size();
+    out->G_p = (uint32_t)s.c1; out->G_r = (uint32_t)(s.c2 - s.c1); out->G_s = (uint32_t)(G - s.c2);
+    out->A_p = (uint32_t)s.Ap; out->A_r = (uint32_t)s.Ar; out->A_s = (uint32_t)s.As;
+    out->gateops_lo = (uint64_t)s.cost;
+    out->gateops_hi = (uint64_t)(s.cost >> 64);
+    out->max_ap = (uint32_t)max_ap;
+    out->min_apr = (uint32_t)min_apr;
+    return FS_OK;
+}
+
+int fs_branch_vars(const fs_circuit* c, int32_t* gate_index, int32_t* qubit, int32_t* source,
+                   size_t cap, size_t* count)
+{
+    if (!c || !count) return fail(FS_ERR_INVALID, "NULL argument");
+    size_t k = 0;
+    for (int i = (int)c->g.size() - 1; i >= 0; --i) {
+        const GateInfo& g = c->g[i];
+        if (g.role != BR) continue;
+        const int lo = (g.k == 2 && g.q[1] < g.q[0]) ? 1 : 0;
+        for (int j = 0; j < g.k; ++j) {
+            const int t = (j == 0) ? lo : 1 - lo;
+            if (k < cap) {
+                if (gate_index) gate_index[k] = i;
+                if (qubit) qubit[k] = g.q[t];
+                if (source) source[k] = g.src[t];
+            }
+            ++k;
+        }
+    }
+    *count = k;
+    return FS_OK;
+}
+
+int fs_set_input(fs_circuit* c, const uint64_t* support_bits, const double* coeffs, size_t S)
+{
+    if (!c || (S && (!support_bits || !coeffs))) return fail(FS_ERR_INVALID, "NULL argument");
+    if (S == 0) return fail(FS_ERR_INVALID, "empty input support");
+    if (S > (1u << 20)) return fail(FS_ERR_TOO_LARGE, "input support too large");
+    std::vector<Bits> b(S);
+    std::vector<cd> co(S);
+    for (size_t i = 0; i < S; ++i) {
+        if (int rc = check_bits(c, support_bits + 2 * i, "input support")) return rc;
+        b[i].w[0] = support_bits[2 * i];
+        b[i].w[1] = support_bits[2 * i + 1];
+        co[i] = cd(coeffs[2 * i], coeffs[2 * i + 1]);
+    }
+    c->in_bits.swap(b);
+    c->in_coef.swap(co);
+    return FS_OK;
+}
+
+int fs_batch_create(fs_batch** out)
+{
+    if (!out) return fail(FS_ERR_INVALID, "out is NULL");
+    *out = new (std::nothrow) fs_batch;
+    if (!*out) return fail(FS_ERR_NOMEM, "out of host memory");
+    return FS_OK;
+}
+
+int fs_batch_destroy(fs_batch* b)
+{
+    delete b;
+    return FS_OK;
+}
+
+int fs_batch_set_options(fs_batch* b, const fs_options* opt)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (opt) {
+        if (opt->split > 2) return fail(FS_ERR_INVALID, "split must be 0, 1 or 2");
+        b->opt = *opt;
+    } else {
+        std::memset(&b->opt, 0, sizeof b->opt);
+    }
+    b->planned = b->uploaded = false;
+    return FS_OK;
+}
+
+int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, size_t n_out, double eps,
+                 uint32_t* job_id)
+{
+    if (!b || !c || (n_out && !outputs)) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!(eps >= 0.0) || std::isinf(eps)) return fail(FS_ERR_INVALID, "eps must be finite and >= 0");
+    if (n_out > (1u << 26)) return fail(FS_ERR_TOO_LARGE, "too many outputs in one job");
+    if (b->jobs.size() >= 4096) return fail(FS_ERR_TOO_LARGE, "too many jobs in one batch");
+    Job j;
+    j.c = c;
+    j.outs.resize(n_out);
+    for (size_t i = 0; i < n_out; ++i) {
+        if (int rc = check_bits(c, outputs + 2 * i, "output")) return rc;
+        j.outs[i].w[0] = outputs[2 * i];
+        j.outs[i].w[1] = outputs[2 * i + 1];
+    }
+    j.ins = c->in_bits;
+    j.coef = c->in_coef;
+    j.eps = eps;
+    b->jobs.push_back(std::move(j));
+    if (job_id) *job_id = (uint32_t)(b->jobs.size() - 1);
+    b->planned = b->uploaded = false;
+    return FS_OK;
+}
+
+int fs_batch_total_outputs(const fs_batch* b, size_t* n)
+{
+    if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
+    size_t t = 0;
+    for (const Job& j : b->jobs) t += j.outs.size();
+    *n = t;
+    return FS_OK;
+}
+
+int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
+{
+    if (!b || !workspace_bytes) return fail(FS_ERR_INVALID, "NULL argument");
+    const uint64_t budget = b->opt.table_budget_bytes ? b->opt.table_budget_bytes : (4ull << 30);
+    const uint64_t min_items = b->opt.min_items ? b->opt.min_items : (1ull << 19);
+    // table budget shared by the jobs in proportion to their pair counts
+    uint64_t all_pairs = 0;
+    for (Job& j : b->jobs) all_pairs += (uint64_t)j.outs.size() * j.ins.size();
+    b->tiles.clear();
+    b->total_prefix = 0;
+    b->total_out = 0;
+    struct TileCost { double cost; uint32_t job; };
+    std::vector<TileCost> order;
+    for (size_t ji = 0; ji < b->jobs.size(); ++ji) {
+        Job& j = b->jobs[ji];
+        const fs_circuit& C = *j.c;
+        if (C.A > 62) return fail(FS_ERR_TOO_LARGE, "job %zu: A = %d artificial sources: 2^A histories cannot be enumerated", ji, C.A);
+        j.W = words_for(C.n);
+        j.pairs = (uint64_t)j.outs.size() * j.ins.size();
+        const int G = (int)C.g.size();
+        const std::vector<int> pre = source_prefix(C);
+        if (b->opt.split == 1) {
+            const int c1 = b->opt.c1, c2 = b->opt.c2;
+            if (c1 < 0 || c2 < c1 || c2 > G) return fail(FS_ERR_INVALID, "job %zu: fixed cuts (%d, %d) outside [0, %d]", ji, c1, c2, G);
+            j.sp = split_at(C, pre, c1, c2);
+        } else if (b->opt.split == 2) {
+            j.sp = split_at(C, pre, 0, 0);
+        } else {
+            const uint64_t share = all_pairs ? (uint64_t)((long double)budget * j.pairs / all_pairs) : budget;
+            const uint64_t per_pair = j.pairs ? share / (j.pairs * sizeof(fs::Entry)) : share;
+            const int max_ap = per_pair ? std::min(ilog2_floor(per_pair), 40) : 0;
+            const int min_apr = j.pairs ? ilog2_ceil((min_items + j.pairs - 1) / j.pairs) : 0;
+            const int max_apr = std::max(0, 40 - ilog2_ceil(std::max<uint64_t>(j.pairs, 1)));
+            if (!autotune(C, max_ap, min_apr, max_apr, j.sp))
+                return fail(FS_ERR_TOO_LARGE, "job %zu: no partition fits the table budget", ji);
+        }
+        if (j.sp.Ap + j.sp.Ar + ilog2_ceil(std::max<uint64_t>(j.pairs, 1)) > 40)
+            return fail(FS_ERR_TOO_LARGE, "job %zu: too many (prefix, root) items", ji);
+        compile(C, j.W, j.sp, j.prog);
+        j.log2_ipp = j.sp.Ap + j.sp.Ar;
+        j.log2_spp = std::max(0, j.log2_ipp - fs::TILE_LOG2);
+        j.table_entries = j.pairs << j.sp.Ap;
+        j.n_partials = j.pairs << j.log2_spp;
+        const uint64_t items = j.pairs << j.log2_ipp;
+        j.n_tiles = (items + fs::TILE - 1) / fs::TILE;
+        if (j.n_tiles >= (1ull << 32)) return fail(FS_ERR_TOO_LARGE, "job %zu: too many tiles", ji);
+        b->total_prefix += j.table_entries;
+        b->total_out += j.outs.size();
+        // predicted cost of one tile (Eq. 8 per item): G_r + 2^As G_s
+        const double tile_cost = (double)(j.sp.c2 - j.sp.c1) + std::ldexp((double)(G - j.sp.c2), j.sp.As);
+        order.push_back({tile_cost, (uint32_t)ji});
+    }
+    // longest-processing-time order: the most expensive tiles are handed out first
+    std::stable_sort(order.begin(), order.end(), [](const TileCost& a, const TileCost& x) { return a.cost > x.cost; });
+    uint64_t ntile_total = 0;
+    for (auto& t : order) ntile_total += b->jobs[t.job].n_tiles;
+    if (ntile_total >= (1ull << 32)) return fail(FS_ERR_TOO_LARGE, "too many tiles in the batch");
+    b->tiles.reserve(ntile_total);
+    for (auto& t : order)
+        for (uint64_t k = 0; k < b->jobs[t.job].n_tiles; ++k) b->tiles.push_back(make_uint2(t.job, (uint32_t)k));
+
+    // workspace layout: static part first (uploaded once), then the dynamic part
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
+    const size_t nj = b->jobs.size();
+    b->o_jobs = take(nj * sizeof(fs::JobDev));
+    b->o_pbegin = take(nj * sizeof(uint64_t));
+    b->o_obegin = take(nj * sizeof(uint64_t));
+    b->o_tiles = take(b->tiles.size() * sizeof(uint2));
+    for (Job& j : b->jobs) {
+        j.o_ops = take(j.prog.ops.size() * sizeof(fs::Op));
+        j.o_masks = take(j.prog.masks.size() * sizeof(uint32_t));
+        j.o_fac = take(j.prog.fac.size() * sizeof(double2));
+        j.o_outs = take(j.outs.size() * 16);
+        j.o_ins = take(j.ins.size() * 16);
+        j.o_coef = take(j.coef.size() * sizeof(double2));
+    }
+    b->static_bytes = off;
+    b->dyn_begin = off;
+    b->o_stats = take(nj * 4 * sizeof(unsigned long long));
+    b->o_counter = take(sizeof(unsigned int));
+    b->o_err = take(sizeof(uint32_t));
+    const size_t zero_end = off;
+    (void)zero_end;
+    for (Job& j : b->jobs) {
+        j.o_table = take(j.table_entries * sizeof(fs::Entry));
+        j.o_part = take(j.n_partials * sizeof(double2));
+    }
+    b->ws_bytes = off;
+    *workspace_bytes = off;
+    b->planned = true;
+    b->uploaded = false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    b->grid = fs::history_grid_size(dev);
+    return FS_OK;
+}
+
+int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
+{
+    if (!b || !d_ws) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    if (ws_bytes < b->ws_bytes) return fail(FS_ERR_INVALID, "workspace of %zu bytes < %zu needed", ws_bytes, b->ws_bytes);
+    if (((uintptr_t)d_ws) & 255) return fail(FS_ERR_INVALID, "workspace must be 256-byte aligned");
+    unsigned char* base = (unsigned char*)d_ws;
+    std::vector<unsigned char>& H = b->host_static;
+    H.assign(b->static_bytes, 0);
+    const size_t nj = b->jobs.size();
+    std::vector<fs::JobDev> jd(nj);
+    std::vector<uint64_t> pbegin(nj), obegin(nj);
+    uint64_t pacc = 0, oacc = 0;
+    for (size_t ji = 0; ji < nj; ++ji) {
+        Job& j = b->jobs[ji];
+        fs::JobDev& d = jd[ji];
+        std::memset(&d, 0, sizeof d);
+        d.ops = (const fs::Op*)(base + j.o_ops);
+        d.masks = (const uint32_t*)(base + j.o_masks);
+        d.fac = (const double2*)(base + j.o_fac);
+        d.outs = (const uint32_t*)(base + j.o_outs);
+        d.ins = (const uint32_t*)(base + j.o_ins);
+        d.coef = (const double2*)(base + j.o_coef);
+        d.table = (fs::Entry*)(base + j.o_table);
+        d.partials = (double2*)(base + j.o_part);
+        d.stats = (unsigned long long*)(base + b->o_stats) + 4 * ji;
+        d.G = (int32_t)j.c->g.size();
+        d.c1 = j.sp.c1; d.c2 = j.sp.c2;
+        d.Ap = j.sp.Ap; d.Ar = j.sp.Ar; d.As = j.sp.As;
+        d.W = j.W;
+        d.S = (int32_t)j.ins.size();
+        d.M = (int32_t)j.outs.size();
+        d.log2_ipp = j.log2_ipp;
+        d.log2_spp = j.log2_spp;
+        d.n_pairs = j.pairs;
+        d.prefix_begin = pacc;
+        d.out_begin = oacc;
+        d.n_tiles = j.n_tiles;
+        d.eps2 = j.eps * j.eps;
+        pbegin[ji] = pacc;
+        obegin[ji] = oacc;
+        pacc += j.table_entries;
+        oacc += j.outs.size();
+        std::memcpy(&H[j.o_ops], j.prog.ops.data(), j.prog.ops.size() * sizeof(fs::Op));
+        std::memcpy(&H[j.o_masks], j.prog.masks.data(), j.prog.masks.size() * sizeof(uint32_t));
+        std::memcpy(&H[j.o_fac], j.prog.fac.data(), j.prog.fac.size() * sizeof(double2));
+        for (size_t i = 0; i < j.outs.size(); ++i) std::memcpy(&H[j.o_outs + 16 * i], j.outs[i].w, 16);
+        for (size_t i = 0; i < j.ins.size(); ++i) std::memcpy(&H[j.o_ins + 16 * i], j.ins[i].w, 16);
+        for (size_t i = 0; i < j.coef.size(); ++i) {
+            const double2 v = make_double2(j.coef[i].real(), j.coef[i].imag());
+            std::memcpy(&H[j.o_coef + sizeof(double2) * i], &v, sizeof v);
+        }
+    }
+    if (nj) {
+        std::memcpy(&H[b->o_jobs], jd.data(), nj * sizeof(fs::JobDev));
+        std::memcpy(&H[b->o_pbegin], pbegin.data(), nj * sizeof(uint64_t));
+        std::memcpy(&H[b->o_obegin], obegin.data(), nj * sizeof(uint64_t));
+    }
+    if (!b->tiles.empty()) std::memcpy(&H[b->o_tiles], b->tiles.data(), b->tiles.size() * sizeof(uint2));
+    if (b->static_bytes)
+        CUDA_TRY(cudaMemcpyAsync(d_ws, H.data(), b->static_bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    // the host staging copy must outlive the asynchronous copy
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    b->uploaded_ws = d_ws;
+    b->uploaded = true;
+    return FS_OK;
+}
+
+int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
+{
+    if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
+    *n = 3;   // prefix, history, reduce
+    return FS_OK;
+}
+
+int fs_batch_time_kernels(fs_batch* b, int enable)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (enable && !b->ev[0])
+        for (auto& e : b->ev) CUDA_TRY(cudaEventCreate(&e));
+    b->timing = enable != 0;
+    b->ev_recorded = false;
+    return FS_OK;
+}
+
+int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* reduce_ms)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (!b->ev_recorded) return fail(FS_ERR_STATE, "no timed run recorded");
+    CUDA_TRY(cudaEventSynchronize(b->ev[3]));
+    float a = 0, h = 0, r = 0;
+    CUDA_TRY(cudaEventElapsedTime(&a, b->ev[0], b->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&h, b->ev[1], b->ev[2]));
+    CUDA_TRY(cudaEventElapsedTime(&r, b->ev[2], b->ev[3]));
+    if (prefix_ms) *prefix_ms = a;
+    if (history_ms) *history_ms = h;
+    if (reduce_ms) *reduce_ms = r;
+    return FS_OK;
+}
+
+int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
+{
+    if (!b || !d_ws || (!d_amp_out && b->total_out)) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "fs_batch_upload on this workspace must come first");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = (unsigned char*)d_ws;
+    const int nj = (int)b->jobs.size();
+    const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
+    CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
+    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[0], s));
+    CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
+                               (uint32_t*)(base + b->o_err), s));
+    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));
+    CUDA_TRY(fs::launch_history(jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
+                                (unsigned int*)(base + b->o_counter), (uint32_t*)(base + b->o_err), b->grid, s));
+    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[2], s));
+    CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
+                               (double2*)d_amp_out, s));
+    if (b->timing) {
+        CUDA_TRY(cudaEventRecord(b->ev[3], s));
+        b->ev_recorded = true;
+    }
+    return FS_OK;
+}
+
+int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size_t cap)
+{
+    if (!b || !d_ws) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "no run on this workspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nj = b->jobs.size();
+    std::vector<unsigned long long> st(4 * nj + 1, 0);
+    uint32_t err = 0;
+    unsigned char* base = (unsigned char*)d_ws;
+    if (nj) CUDA_TRY(cudaMemcpyAsync(st.data(), base + b->o_stats, 4 * nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&err, base + b->o_err, sizeof err, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    if (err & fs::DEV_ERR_BAD_OPCODE) return fail(FS_ERR_BAD_PROGRAM, "device found an unknown opcode");
+    if (stats) {
+        for (size_t ji = 0; ji < nj && ji < cap; ++ji) {
+            const Job& j = b->jobs[ji];
+            fs_stats& o = stats[ji];
+            std::memset(&o, 0, sizeof o);
+            const int A = j.c->A;
+            const int lp = ilog2_ceil(std::max<uint64_t>(j.pairs, 1));
+            o.candidates = (A + lp < 64) ? (j.pairs << A) : ~0ull;
+            o.completed = st[4 * ji + 0];
+            o.valid = st[4 * ji + 1];
+            o.gate_visits = st[4 * ji + 2];
+            o.table_entries = st[4 * ji + 3];
+            o.c1 = j.sp.c1; o.c2 = j.sp.c2;
+            o.A_p = (uint32_t)j.sp.Ap; o.A_r = (uint32_t)j.sp.Ar; o.A_s = (uint32_t)j.sp.As;
+        }
+    }
+    return FS_OK;
+}
+
+int fs_amplitudes(fs_circuit* c, const uint64_t* outputs, size_t n_out, double eps, double* amp_out)
+{
+    if (!c || (n_out && (!outputs || !amp_out))) return fail(FS_ERR_INVALID, "NULL argument");
+    if (n_out == 0) return FS_OK;
+    fs_batch b;
+    if (int rc = fs_batch_add(&b, c, outputs, n_out, eps, nullptr)) return rc;
+    size_t ws = 0;
+    if (int rc = fs_batch_plan(&b, &ws)) return rc;
+    void* d_ws = nullptr;
+    double* d_amp = nullptr;
+    cudaError_t e = cudaMalloc(&d_ws, ws ? ws : 256);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    e = cudaMalloc((void**)&d_amp, 2 * n_out * sizeof(double));
+    if (e != cudaSuccess) { cudaFree(d_ws); return cuda_fail(e, "cudaMalloc(amplitudes)"); }
+    int rc = fs_batch_upload(&b, d_ws, ws ? ws : 256, nullptr);
+    if (!rc) rc = fs_batch_run(&b, d_ws, d_amp, nullptr);
+    if (!rc) rc = fs_batch_finish(&b, d_ws, nullptr, nullptr, 0);
+    if (!rc) {
+        e = cudaMemcpy(amp_out, d_amp, 2 * n_out * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpy(amplitudes)");
+    }
+    cudaFree(d_amp);
+    cudaFree(d_ws);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal layout shared by the host compiler (fs_host.cpp) and the CUDA
+// kernels (fs_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace fs {
+
+// Opcodes of the evaluation-order program.  Every op moves the state from
+// the output side of one gate to its input side (the backward sweep of
+// Sec. IV-A) and multiplies the gate's matrix element into the running
+// amplitude.
+enum OpCode : uint8_t {
+    OP_X = 1,     // flip q0                                   (unit factor)
+    OP_MCX,       // flip q0 when (st & mask) == val            (unit factor)
+    OP_SWAP,      // exchange q0 and q1                         (unit factor)
+    OP_PERM1,     // o = bit q0: amp *= fac[aux + o]; flip q0   (Y, antidiagonal U1)
+    OP_PERM2,     // o = local 2-bit value: in = perm(o), amp *= fac[aux + o]
+    OP_DIAG1,     // amp *= fac[aux + bit q0]                   (RZ, diagonal U1)
+    OP_PH1,       // if bit q0: amp *= fac[aux]                 (S, T, P)
+    OP_NEG1,      // if bit q0: amp = -amp                      (Z)
+    OP_MCPH,      // if (st & mask) == val: amp *= fac[aux]     (controlled P/S/T)
+    OP_MCNEG,     // if (st & mask) == val: amp = -amp          (CZ, MCZ)
+    OP_DIAG2,     // amp *= fac[aux + bit q0 + 2 bit q1]        (RZZ, diagonal U2)
+    OP_H,         // branching H: i = source; amp *= (o & i) ? -1/sqrt2 : 1/sqrt2
+    OP_BR1,       // branching 1-qubit: amp *= fac[aux + 2 o + i]; q0 = i
+    OP_BR2,       // branching 2-qubit: amp *= fac[aux + 4 o + i]; (q0, q1) = i
+    OP_LAST
+};
+
+// 16-byte op.  s0/s1: bit index of the artificial source in the region's
+// enumeration word h (-1: natural source, value read from the input bit
+// string).  aux: factor offset (double2 units).  aux2: mask offset (u32
+// units, W mask words then W value words) or, for OP_PERM2, the packed
+// inverse permutation (2 bits per output value).
+struct Op {
+    uint8_t code, q0, q1, flags;
+    int8_t s0, s1;
+    uint16_t pad;
+    uint32_t aux;
+    uint32_t aux2;
+};
+static_assert(sizeof(Op) == 16, "Op must be 16 bytes");
+
+// One checkpoint-table entry (Algorithm 2: propagated state sigma_p and
+// partial amplitude beta_p after the prefix).  An entry whose prefix was cut
+// (bottom) carries a NaN real part.
+struct Entry {
+    uint32_t st[4];
+    double2 amp;
+};
+static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
+
+// Per-job descriptor in device memory.
+struct JobDev {
+    const Op* ops;
+    const uint32_t* masks;
+    const double2* fac;
+    const uint32_t* outs;      // M x 4 words
+    const uint32_t* ins;       // S x 4 words
+    const double2* coef;       // S
+    Entry* table;              // pairs x 2^Ap
+    double2* partials;         // pairs x spp
+    unsigned long long* stats; // [completed, valid, visits, entries]
+    int32_t G, c1, c2;
+    int32_t Ap, Ar, As;
+    int32_t W, S, M;
+    int32_t log2_ipp;          // Ap + Ar
+    int32_t log2_spp;          // max(0, log2_ipp - TILE_LOG2)
+    int32_t pad0;
+    uint64_t n_pairs;          // S * M
+    uint64_t prefix_begin;     // offset of this job in the flat prefix index space
+    uint64_t out_begin;        // offset of this job's outputs in amp_out
+    uint64_t n_tiles;
+    double eps2;               // eps^2 (0: exact)
+};
+
+constexpr int TILE_LOG2 = 8;             // items per tile = threads per CTA
+constexpr int TILE = 1 << TILE_LOG2;
+constexpr int REDUCE_THREADS = 128;
+
+// Device error word values.
+constexpr uint32_t DEV_ERR_BAD_OPCODE = 1;
+
+// Launch entry points (fs_kernels.cu).
+cudaError_t launch_prefix(const JobDev* d_jobs, const uint64_t* d_job_prefix_begin, int n_jobs,
+                          uint64_t total_prefix, uint32_t* d_err, cudaStream_t s);
+cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
+                           unsigned int* d_counter, uint32_t* d_err, int grid, cudaStream_t s);
+cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
+                          uint64_t total_out, double2* d_amp, cudaStream_t s);
+int history_grid_size(int device);
+
+}  // namespace fs

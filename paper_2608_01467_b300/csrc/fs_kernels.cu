@@ -1,0 +1,494 @@
+// CUDA kernels of the reduced-history path (sm_103a).
+//
+//   prefix_kernel   -- Algorithm 2, prefix region: for every (pair, h_p) walk
+//                      the output-side gates backward from b_out and write the
+//                      checkpoint (sigma_p, beta_p) into the table.
+//   history_kernel  -- Algorithm 2, root and suffix regions: a persistent
+//                      kernel pulls 256-item tiles off an atomic queue (the
+//                      device form of the server-worker balancer, Sec. IV-D);
+//                      each thread advances one (h_p, h_r) checkpoint through
+//                      the root and loops h_s over the suffix, checks chi at
+//                      the input boundary and accumulates beta_s.
+//   reduce_kernel   -- fixed-order sums of the per-tile partials and of the
+//                      sparse-input terms (Eq. 2) into the amplitudes.
+//
+// All arithmetic on amplitudes is FP64.  The complex product is
+// re = fma(a.re, b.re, -(a.im b.im)), im = fma(a.re, b.im, a.im b.re) with
+// explicit round-to-nearest intrinsics, so every history's amplitude is the
+// same double the host-side definition gives when it multiplies the same
+// factors in the same (backward) order.
+#include "fs_internal.h"
+
+namespace fs {
+
+namespace {
+
+constexpr double RSQRT2 = 0.70710678118654757;   // sqrt(0.5) rounded to nearest
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)),
+                        __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+}
+
+// Sign flip on the integer pipe (exact).
+__device__ __forceinline__ double dneg(double x)
+{
+    return __hiloint2double(__double2hiint(x) ^ 0x80000000, __double2loint(x));
+}
+
+__device__ __forceinline__ double2 ldf(const double2* p)
+{
+    return __ldg(p);
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t word_of(const uint32_t (&st)[W], uint32_t q)
+{
+    uint32_t v = st[0];
+#pragma unroll
+    for (int j = 1; j < W; ++j) v = ((q >> 5) == (uint32_t)j) ? st[j] : v;
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t getbit(const uint32_t (&st)[W], uint32_t q)
+{
+    return (word_of<W>(st, q) >> (q & 31)) & 1u;
+}
+
+template <int W>
+__device__ __forceinline__ void xorbit(uint32_t (&st)[W], uint32_t q, uint32_t v)
+{
+    const uint32_t m = v << (q & 31);
+#pragma unroll
+    for (int j = 0; j < W; ++j) st[j] ^= ((q >> 5) == (uint32_t)j) ? m : 0u;
+}
+
+template <int W>
+__device__ __forceinline__ bool match(const uint32_t (&st)[W], const uint32_t* __restrict__ m)
+{
+    uint32_t d = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) d |= (st[j] & __ldg(m + j)) ^ __ldg(m + W + j);
+    return d == 0;
+}
+
+template <int W>
+__device__ __forceinline__ bool same(const uint32_t (&a)[W], const uint32_t (&b)[W])
+{
+    uint32_t d = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) d |= a[j] ^ b[j];
+    return d == 0;
+}
+
+// Evaluates the ops at evaluation positions [e0, e1) (one region of
+// Algorithm 2, i.e. AdvanceCheckpoint).  h is the region's enumeration word
+// (the op's s0/s1 give the bit of each artificial source), bin the input bit
+// string (natural sources and the chi test).  Returns -1 when the region
+// completes; otherwise the history is cut (bottom: an exactly zero factor,
+// or |beta| < eps right after an artificial source) and the return value is
+// the lowest h bit assigned so far (nbits if none), so that every h sharing
+// the bits at and above it is known to be cut too.
+template <int W>
+__device__ int run_ops(const JobDev& J, int e0, int e1, uint32_t (&st)[W], double2& amp,
+                       uint64_t h, int nbits, const uint32_t (&bin)[W],
+                       unsigned long long& visits, uint32_t* err)
+{
+    int low = nbits;
+    const uint4* __restrict__ ops = reinterpret_cast<const uint4*>(J.ops);
+    const double2* __restrict__ fac = J.fac;
+    const uint32_t* __restrict__ masks = J.masks;
+    for (int e = e0; e < e1; ++e) {
+        const uint4 raw = __ldg(ops + e);
+        const uint32_t code = raw.x & 0xFFu;
+        const uint32_t q0 = (raw.x >> 8) & 0xFFu;
+        const uint32_t q1 = (raw.x >> 16) & 0xFFu;
+        const int s0 = (int)(int8_t)(raw.y & 0xFFu);
+        const int s1 = (int)(int8_t)((raw.y >> 8) & 0xFFu);
+        const uint32_t aux = raw.z, aux2 = raw.w;
+        bool srcop = false, zero = false;
+        switch (code) {
+        case OP_X:
+            xorbit<W>(st, q0, 1u);
+            break;
+        case OP_MCX:
+            if (match<W>(st, masks + aux2)) xorbit<W>(st, q0, 1u);
+            break;
+        case OP_SWAP: {
+            const uint32_t d = getbit<W>(st, q0) ^ getbit<W>(st, q1);
+            xorbit<W>(st, q0, d);
+            xorbit<W>(st, q1, d);
+            break;
+        }
+        case OP_PERM1: {
+            const uint32_t o = getbit<W>(st, q0);
+            amp = cmul(amp, ldf(fac + aux + o));
+            xorbit<W>(st, q0, 1u);
+            break;
+        }
+        case OP_PERM2: {
+            const uint32_t o = getbit<W>(st, q0) | (getbit<W>(st, q1) << 1);
+            const uint32_t i = (aux2 >> (2 * o)) & 3u;
+            amp = cmul(amp, ldf(fac + aux + o));
+            xorbit<W>(st, q0, (o ^ i) & 1u);
+            xorbit<W>(st, q1, ((o ^ i) >> 1) & 1u);
+            break;
+        }
+        case OP_DIAG1:
+            amp = cmul(amp, ldf(fac + aux + getbit<W>(st, q0)));
+            break;
+        case OP_PH1:
+            if (getbit<W>(st, q0)) amp = cmul(amp, ldf(fac + aux));
+            break;
+        case OP_NEG1:
+            if (getbit<W>(st, q0)) amp = make_double2(dneg(amp.x), dneg(amp.y));
+            break;
+        case OP_MCPH:
+            if (match<W>(st, masks + aux2)) amp = cmul(amp, ldf(fac + aux));
+            break;
+        case OP_MCNEG:
+            if (match<W>(st, masks + aux2)) amp = make_double2(dneg(amp.x), dneg(amp.y));
+            break;
+        case OP_DIAG2:
+            amp = cmul(amp, ldf(fac + aux + (getbit<W>(st, q0) | (getbit<W>(st, q1) << 1))));
+            break;
+        case OP_H: {
+            const uint32_t o = getbit<W>(st, q0);
+            uint32_t i;
+            if (s0 >= 0) { i = (uint32_t)(h >> s0) & 1u; srcop = true; low = s0; }
+            else i = getbit<W>(bin, q0);
+            const double hv = (o & i) ? -RSQRT2 : RSQRT2;
+            amp = make_double2(__dmul_rn(amp.x, hv), __dmul_rn(amp.y, hv));
+            xorbit<W>(st, q0, o ^ i);
+            break;
+        }
+        case OP_BR1: {
+            const uint32_t o = getbit<W>(st, q0);
+            uint32_t i;
+            if (s0 >= 0) { i = (uint32_t)(h >> s0) & 1u; srcop = true; low = s0; }
+            else i = getbit<W>(bin, q0);
+            const double2 f = ldf(fac + aux + 2 * o + i);
+            zero = (f.x == 0.0) & (f.y == 0.0);
+            amp = cmul(amp, f);
+            xorbit<W>(st, q0, o ^ i);
+            break;
+        }
+        case OP_BR2: {
+            const uint32_t o = getbit<W>(st, q0) | (getbit<W>(st, q1) << 1);
+            uint32_t i0, i1;
+            if (s0 >= 0) { i0 = (uint32_t)(h >> s0) & 1u; srcop = true; low = min(low, s0); }
+            else i0 = getbit<W>(bin, q0);
+            if (s1 >= 0) { i1 = (uint32_t)(h >> s1) & 1u; srcop = true; low = min(low, s1); }
+            else i1 = getbit<W>(bin, q1);
+            const uint32_t i = i0 | (i1 << 1);
+            const double2 f = ldf(fac + aux + 4 * o + i);
+            zero = (f.x == 0.0) & (f.y == 0.0);
+            amp = cmul(amp, f);
+            xorbit<W>(st, q0, (o ^ i) & 1u);
+            xorbit<W>(st, q1, ((o ^ i) >> 1) & 1u);
+            break;
+        }
+        default:
+            atomicOr(err, DEV_ERR_BAD_OPCODE);
+            zero = true;
+            break;
+        }
+        const bool cut = zero ||
+            (srcop && J.eps2 > 0.0 && __fma_rn(amp.x, amp.x, __dmul_rn(amp.y, amp.y)) < J.eps2);
+        if (cut) {
+            visits += (unsigned long long)(e - e0 + 1);
+            return low;
+        }
+    }
+    visits += (unsigned long long)(e1 - e0);
+    return -1;
+}
+
+template <int W>
+__device__ __forceinline__ void load_bits(const uint32_t* __restrict__ p, uint32_t (&st)[W])
+{
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < W; ++j) st[j] = a[j];
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ int find_job(const uint64_t* __restrict__ begin, int n_jobs, uint64_t idx)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(begin + mid) <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- prefix
+
+template <int W>
+__device__ void prefix_one(const JobDev& J, uint64_t local, uint32_t* err,
+                           unsigned long long& visits, unsigned long long& entries)
+{
+    const uint64_t pair = local >> J.Ap;
+    const uint64_t hp = local & ((1ull << J.Ap) - 1ull);
+    const uint64_t o = pair / (uint64_t)J.S;
+    const uint64_t s = pair - o * (uint64_t)J.S;
+    uint32_t st[W], bin[W];
+    load_bits<W>(J.outs + 4 * o, st);
+    load_bits<W>(J.ins + 4 * s, bin);
+    double2 amp = make_double2(1.0, 0.0);
+    const int r = run_ops<W>(J, 0, J.c1, st, amp, hp, J.Ap, bin, visits, err);
+    Entry e;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) e.st[j] = j < W ? st[j] : 0u;
+    e.amp = amp;
+    if (r >= 0) e.amp.x = __longlong_as_double(0x7ff8000000000000ll);   // bottom
+    else entries += 1;
+    uint4* dst = reinterpret_cast<uint4*>(J.table + local);
+    dst[0] = make_uint4(e.st[0], e.st[1], e.st[2], e.st[3]);
+    reinterpret_cast<double2*>(dst + 1)[0] = e.amp;
+}
+
+__global__ void __launch_bounds__(256) prefix_kernel(const JobDev* __restrict__ jobs,
+                                                     const uint64_t* __restrict__ begin, int n_jobs,
+                                                     uint64_t total, uint32_t* err)
+{
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (uint64_t)gridDim.x * blockDim.x) {
+        const bool any = __any_sync(0xffffffffu, idx < total);
+        if (!any) break;
+        unsigned long long visits = 0, entries = 0;
+        int j = 0;
+        if (idx < total) {
+            j = find_job(begin, n_jobs, idx);
+            const JobDev& J = jobs[j];
+            const uint64_t local = idx - J.prefix_begin;
+            if (J.W == 1) prefix_one<1>(J, local, err, visits, entries);
+            else if (J.W == 2) prefix_one<2>(J, local, err, visits, entries);
+            else prefix_one<4>(J, local, err, visits, entries);
+        }
+        // counter flush: one atomic per warp when the warp lies in one job,
+        // otherwise one per lane
+        const unsigned act = __ballot_sync(0xffffffffu, idx < total);
+        const unsigned same_job = __match_any_sync(0xffffffffu, idx < total ? j : -1);
+        if (act == 0xffffffffu && same_job == 0xffffffffu) {
+            const unsigned long long v = warp_sum_u64(visits), en = warp_sum_u64(entries);
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&jobs[j].stats[2], v);
+                atomicAdd(&jobs[j].stats[3], en);
+            }
+        } else if (idx < total) {
+            if (visits) atomicAdd(&jobs[j].stats[2], visits);
+            if (entries) atomicAdd(&jobs[j].stats[3], entries);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- history
+
+template <int W>
+__device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err, double2* s_warp)
+{
+    const uint64_t item = tile * TILE + threadIdx.x;
+    const uint64_t n_items = J.n_pairs << J.log2_ipp;
+    const bool active = item < n_items;
+    double2 acc = make_double2(0.0, 0.0);
+    unsigned long long completed = 0, valid = 0, visits = 0;
+    uint64_t pair = 0, local = 0;
+    if (active) {
+        pair = item >> J.log2_ipp;
+        local = item & ((1ull << J.log2_ipp) - 1ull);
+        const uint64_t hp = local >> J.Ar;
+        const uint64_t hr = local & ((1ull << J.Ar) - 1ull);
+        const uint64_t o = pair / (uint64_t)J.S;
+        const uint64_t s = pair - o * (uint64_t)J.S;
+        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << J.Ap) + hp);
+        const uint4 sv = __ldg(ent);
+        const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+        if (!isnan(a0.x)) {
+            uint32_t st[W], bin[W];
+            const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+            for (int j = 0; j < W; ++j) st[j] = tmp[j];
+            load_bits<W>(J.ins + 4 * s, bin);
+            double2 amp = a0;
+            const int r = run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err);
+            if (r < 0) {
+                const uint64_t ns = 1ull << J.As;
+                uint64_t hs = 0;
+                while (hs < ns) {
+                    uint32_t st2[W];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) st2[j] = st[j];
+                    double2 amp2 = amp;
+                    const int r2 = run_ops<W>(J, J.c2, J.G, st2, amp2, hs, J.As, bin, visits, err);
+                    if (r2 < 0) {
+                        ++completed;
+                        if (same<W>(st2, bin)) {
+                            ++valid;
+                            acc.x += amp2.x;
+                            acc.y += amp2.y;
+                        }
+                        ++hs;
+                    } else {
+                        hs = ((hs >> r2) + 1ull) << r2;
+                    }
+                }
+            }
+        }
+    }
+    // counters: one atomic per warp
+    completed = warp_sum_u64(completed);
+    valid = warp_sum_u64(valid);
+    visits = warp_sum_u64(visits);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0 && (completed | valid | visits)) {
+        atomicAdd(&J.stats[0], completed);
+        atomicAdd(&J.stats[1], valid);
+        atomicAdd(&J.stats[2], visits);
+    }
+    // fixed-order segmented reduction: a segment is one pair's items in the tile
+    const int seg_log2 = J.log2_ipp < TILE_LOG2 ? J.log2_ipp : TILE_LOG2;
+    if (seg_log2 < 5) {
+        const int seg = 1 << seg_log2;
+        for (int off = seg >> 1; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (active && (lane & (seg - 1)) == 0) J.partials[pair] = acc;
+    } else {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) s_warp[warp] = acc;
+        __syncthreads();
+        const int wps = 1 << (seg_log2 - 5);          // warps per segment
+        const int nseg = TILE >> seg_log2;
+        if ((int)threadIdx.x < nseg) {
+            const uint64_t first = tile * TILE + (uint64_t)threadIdx.x * (1ull << seg_log2);
+            if (first < n_items) {
+                double2 t = s_warp[threadIdx.x * wps];
+                for (int k = 1; k < wps; ++k) {
+                    t.x += s_warp[threadIdx.x * wps + k].x;
+                    t.y += s_warp[threadIdx.x * wps + k].y;
+                }
+                const uint64_t p = first >> J.log2_ipp;
+                const uint64_t l = first & ((1ull << J.log2_ipp) - 1ull);
+                J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = t;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TILE) history_kernel(const JobDev* __restrict__ jobs,
+                                                       const uint2* __restrict__ tiles, uint64_t n_tiles,
+                                                       unsigned int* counter, uint32_t* err)
+{
+    __shared__ unsigned int s_tile;
+    __shared__ double2 s_warp[TILE / 32];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+        __syncthreads();
+        const unsigned int t = s_tile;
+        __syncthreads();
+        if ((uint64_t)t >= n_tiles) break;
+        const uint2 td = tiles[t];
+        const JobDev& J = jobs[td.x];
+        if (J.W == 1) history_tile<1>(J, td.y, err, s_warp);
+        else if (J.W == 2) history_tile<2>(J, td.y, err, s_warp);
+        else history_tile<4>(J, td.y, err, s_warp);
+    }
+}
+
+// ---------------------------------------------------------------- reduce
+
+__global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
+                                                                const uint64_t* __restrict__ begin,
+                                                                int n_jobs, uint64_t total, double2* amp_out)
+{
+    __shared__ double2 s_red[REDUCE_THREADS];
+    for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const int j = find_job(begin, n_jobs, g);
+        const JobDev& J = jobs[j];
+        const uint64_t o = g - J.out_begin;
+        double2 amp = make_double2(0.0, 0.0);
+        const uint64_t nslots = 1ull << J.log2_spp;
+        for (int s = 0; s < J.S; ++s) {
+            const uint64_t base = ((o * (uint64_t)J.S + (uint64_t)s) << J.log2_spp);
+            double2 t = make_double2(0.0, 0.0);
+            for (uint64_t k = threadIdx.x; k < nslots; k += REDUCE_THREADS) {
+                const double2 v = J.partials[base + k];
+                t.x += v.x;
+                t.y += v.y;
+            }
+            s_red[threadIdx.x] = t;
+            __syncthreads();
+            for (int w = REDUCE_THREADS / 2; w >= 1; w >>= 1) {
+                if ((int)threadIdx.x < w) {
+                    s_red[threadIdx.x].x += s_red[threadIdx.x + w].x;
+                    s_red[threadIdx.x].y += s_red[threadIdx.x + w].y;
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const double2 w2 = cmul(__ldg(J.coef + s), s_red[0]);
+                amp.x += w2.x;
+                amp.y += w2.y;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) amp_out[g] = amp;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prefix(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
+                          uint64_t total, uint32_t* d_err, cudaStream_t s)
+{
+    if (total == 0) return cudaSuccess;
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > 148ull * 64) blocks = 148ull * 64;
+    prefix_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_begin, n_jobs, total, d_err);
+    return cudaGetLastError();
+}
+
+int history_grid_size(int device)
+{
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, history_kernel, TILE, 0);
+    if (sms <= 0) sms = 148;
+    if (per_sm <= 0) per_sm = 1;
+    return sms * per_sm;
+}
+
+cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
+                           unsigned int* d_counter, uint32_t* d_err, int grid, cudaStream_t s)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
+    history_kernel<<<grid, TILE, 0, s>>>(d_jobs, d_tiles, n_tiles, d_counter, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
+                          uint64_t total_out, double2* d_amp, cudaStream_t s)
+{
+    if (total_out == 0) return cudaSuccess;
+    uint64_t blocks = total_out < 148ull * 16 ? total_out : 148ull * 16;
+    reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp);
+    return cudaGetLastError();
+}
+
+}  // namespace fs

@@ -1,0 +1,278 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Exact mode: every amplitude within 1e-12 absolute + 1e-10 relative of the
+oracle; structure counters (completed and valid histories, gate visits)
+bit-exact.  Threshold mode: the device multiplies the same factors in the
+same order as the oracle (bit-identical partial amplitudes), so the pruning
+decisions and leaf counts must agree exactly."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import (Gate, SplitMix64, aa_workload, four_qubit_figure, qaoa_workload, qft,
+                       qft_workload, quantum_walk, qw_workload, random_small_circuit,
+                       three_qubit_example)
+from oracle import closed_forms, dense, feynman
+import paper_2608_01467_b300 as fs
+
+pytestmark = pytest.mark.gpu
+
+ATOL, RTOL = 1e-12, 1e-10
+
+
+def close(got, want):
+    got = np.asarray(got, complex)
+    want = np.asarray(want, complex)
+    err = np.abs(got - want)
+    bad = err > ATOL + RTOL * np.abs(want)
+    assert not bad.any(), f"max err {err.max():.3e} at {np.argmax(err)}"
+
+
+def run_batch(jobs, split="auto", c1=0, c2=0, **kw):
+    """jobs: list of (workloads.Circuit, inputs, outputs, eps)."""
+    b = fs.Batch(split=split, c1=c1, c2=c2, **kw)
+    circs = []
+    for circ, inputs, outputs, eps in jobs:
+        C = fs.Circuit(circ)
+        C.set_input(inputs)
+        circs.append(C)
+        b.add(C, outputs, eps)
+    b.plan()
+    b.allocate()
+    b.upload()
+    b.run()
+    stats = b.finish()
+    amp = b.amp.cpu().numpy()
+    return [amp[s] for s in b.job_slices()], stats, b
+
+
+def oracle_counts(circ, inputs, outputs, eps=0.0, c1=0, c2=0):
+    a, cnt = feynman.run(circ, inputs, outputs, eps=eps, c1=c1, c2=c2, threads=8)
+    return a, cnt
+
+
+def test_three_qubit_example_and_fig2():
+    c = three_qubit_example()
+    (a,), st, _ = run_batch([(c, [(0, 1.0)], list(range(8)), 0.0)])
+    want = np.zeros(8, complex)
+    want[0] = math.sqrt(0.5)
+    want[7] = 1j * math.sqrt(0.5)
+    close(a, want)
+    assert st[0]["valid"] == 2 and st[0]["completed"] == 8
+    f = four_qubit_figure()
+    for b_in in range(16):
+        (a,), st, _ = run_batch([(f, [(b_in, 1.0)], list(range(16)), 0.0)])
+        o, cnt = oracle_counts(f, [(b_in, 1.0)], list(range(16)))
+        close(a, o)
+        assert st[0]["valid"] == int(cnt["valid"].sum())
+        assert st[0]["completed"] == int(cnt["completed"].sum())
+
+
+def test_qft8_all_outputs_closed_form():
+    w = qft_workload(8)
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    x = w.meta["x"]
+    close(a, [closed_forms.qft_amplitude(8, x, y) for y in range(256)])
+    assert st[0]["completed"] == 256 and st[0]["valid"] == 256 and st[0]["candidates"] == 256
+
+
+@pytest.mark.parametrize("n,G,seed", [(3, 12, 1), (4, 20, 2), (6, 30, 3), (7, 40, 4),
+                                      (33, 60, 5), (40, 80, 6), (70, 100, 7), (128, 120, 8)])
+def test_random_circuits_every_gate_kind(n, G, seed):
+    c = random_small_circuit(n, G, 100 + seed)
+    an = feynman.analyze(c)
+    if an["A"] > 20:
+        pytest.skip(f"A = {an['A']}")
+    rng = SplitMix64(seed)
+    ins = [(rng.bits(n), complex(0.6, 0.0)), (rng.bits(n), complex(0.0, 0.8))]
+    if n <= 7:
+        outs = list(range(1 << n))
+    else:
+        # outputs reachable from the inputs: take dense-free random strings plus
+        # the single-history ends of deterministic runs
+        outs = [rng.bits(n) for _ in range(40)]
+    (a,), st, _ = run_batch([(c, ins, outs, 0.0)])
+    o, cnt = oracle_counts(c, ins, outs)
+    close(a, o)
+    assert st[0]["completed"] == int(cnt["completed"].sum())
+    assert st[0]["valid"] == int(cnt["valid"].sum())
+    if n <= 7:
+        close(a, dense.amplitudes(c, ins, outs))
+
+
+def test_random_circuit_nonzero_outputs_wide_registers():
+    """Outputs with nonzero amplitude on 40/70/128-qubit registers: the
+    outputs are read off the dense simulation of the few active qubits."""
+    for n in (40, 70, 128):
+        rng = SplitMix64(n)
+        act = sorted({rng.below(n) for _ in range(6)})
+        while len(act) < 5:
+            act.append((act[-1] + 1) % n)
+            act = sorted(set(act))
+        small = random_small_circuit(len(act), 24, 900 + n)
+        gates = []
+        for g in small.gates:
+            gates.append(Gate(g.kind, tuple(act[q] for q in g.qubits),
+                              tuple((act[q], v) for q, v in g.controls), g.theta, g.matrix))
+        from workloads import Circuit as WC
+        big = WC(n, gates, f"embed{n}")
+        base = rng.bits(n)
+        for q in act:
+            base &= ~(1 << q)
+        outs = []
+        for y in range(1 << len(act)):
+            v = base
+            for j, q in enumerate(act):
+                v |= ((y >> j) & 1) << q
+            outs.append(v)
+        (a,), st, _ = run_batch([(big, [(base, 1.0)], outs, 0.0)])
+        o, _ = oracle_counts(big, [(base, 1.0)], outs)
+        close(a, o)
+        d = dense.amplitudes(small, [(0, 1.0)], list(range(1 << len(act))))
+        close(a, d)
+        assert abs(np.sum(np.abs(a) ** 2) - 1) < 1e-12
+
+
+def test_aa_fig8_ablation_rows_agree():
+    w = aa_workload(n=4, iters=3, seed=11, all_outputs=True)
+    outs = w.outputs[:10]
+    want = dense.amplitudes(w.circuit, w.inputs, outs)
+    G = len(w.circuit.gates)
+    res = {}
+    for name, kw in (("none", dict(split="none")),
+                     ("thirds", dict(split="fixed", c1=G // 3, c2=2 * G // 3)),
+                     ("auto", dict(split="auto"))):
+        (a,), st, _ = run_batch([(w.circuit, w.inputs, outs, 0.0)], **kw)
+        close(a, want)
+        assert st[0]["valid"] == 10 * (1 << 24)
+        res[name] = st[0]
+    # gate visits follow Eq. 8 at the chosen cuts
+    for name, st in res.items():
+        (_, cost) = feynman.region_counts(w.circuit, st["c1"], st["c2"])
+        assert st["gate_visits"] == 10 * cost
+
+
+def test_qaoa8_exact_vs_dense_and_oracle_counts():
+    w = qaoa_workload(8, 2, n_out=64, seed=31)
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    close(a, dense.amplitudes(w.circuit, w.inputs, w.outputs))
+    assert st[0]["completed"] == 64 * (1 << 16) == st[0]["valid"]
+    cost = feynman.region_counts(w.circuit, st["c1"], st["c2"])[1]
+    assert st[0]["gate_visits"] == 64 * cost
+
+
+def test_qaoa16_full_size_sampled_outputs():
+    """QAOA p=2 on the 16-qubit graph of the benchmark family (A = 32):
+    a sample of requested outputs against the dense state vector."""
+    w = qaoa_workload(16, 2, n_out=1024)
+    outs = w.outputs[:3]
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, outs, 0.0)])
+    close(a, dense.amplitudes(w.circuit, w.inputs, outs))
+    assert st[0]["valid"] == 3 * (1 << 32)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 0.02, 0.1])
+def test_threshold_pruning_matches_oracle(eps):
+    w = qaoa_workload(8, 2, n_out=48, seed=41)
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, eps)])
+    o, cnt = oracle_counts(w.circuit, w.inputs, w.outputs, eps=eps)
+    close(a, o)
+    assert st[0]["completed"] == int(cnt["completed"].sum())
+    assert st[0]["valid"] == int(cnt["valid"].sum())
+
+
+def test_qw_small_vs_offset_walk():
+    w = qw_workload(steps=6, n_out=64, pos_bits=8)
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    s = math.sqrt(0.5)
+    close(a, [closed_forms.walk_amplitude(6, w.meta["p0"], y, s, 1j * s, 8) for y in w.outputs])
+    o, cnt = oracle_counts(w.circuit, w.inputs, w.outputs)
+    assert st[0]["valid"] == int(cnt["valid"].sum())
+    assert st[0]["completed"] == int(cnt["completed"].sum())
+
+
+def test_qw100_full_config_all_outputs():
+    """100-qubit walk, T = 16, 4096 outputs (the benchmark request): every
+    amplitude against the offset-space walk; norm 1 over the reachable
+    outputs; unreachable ones exactly zero; a sample of outputs against the
+    oracle's history counts."""
+    w = qw_workload()
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    s = math.sqrt(0.5)
+    want = [closed_forms.walk_amplitude(16, w.meta["p0"], y, s, 1j * s, 96) for y in w.outputs]
+    close(a, want)
+    r = w.meta["reachable"]
+    assert abs(np.sum(np.abs(a[:r]) ** 2) - 1) < 1e-12
+    assert np.all(a[r:] == 0)
+    assert st[0]["completed"] == 2 * 4096 * (1 << 15)
+    sample = [w.outputs[0], w.outputs[17], w.outputs[r + 5]]
+    _, cnt = oracle_counts(w.circuit, w.inputs, sample)
+    b2, st2, _ = run_batch([(w.circuit, w.inputs, sample, 0.0)])
+    assert st2[0]["valid"] == int(cnt["valid"].sum())
+
+
+def test_mixed_batch_one_launch():
+    """Jobs of different register widths and sizes in one persistent launch."""
+    j1 = qft_workload(8)
+    j2 = qaoa_workload(8, 2, n_out=32, seed=2)
+    j3 = qw_workload(steps=5, n_out=40, pos_bits=8)
+    c4 = random_small_circuit(70, 60, 77)
+    rng = SplitMix64(4)
+    j4 = (c4, [(rng.bits(70), 1.0)], [rng.bits(70) for _ in range(20)], 0.0)
+    jobs = [(j1.circuit, j1.inputs, j1.outputs, 0.0), (j2.circuit, j2.inputs, j2.outputs, 0.0),
+            (j3.circuit, j3.inputs, j3.outputs, 0.0), j4,
+            (j2.circuit, j2.inputs, [], 0.0)]
+    amps, st, b = run_batch(jobs)
+    for (circ, ins, outs, eps), a in zip(jobs, amps):
+        if not outs:
+            assert len(a) == 0
+            continue
+        o, _ = oracle_counts(circ, ins, outs)
+        close(a, o)
+
+
+def test_deterministic_and_host_path_bitwise():
+    w = qaoa_workload(8, 2, n_out=40, seed=9)
+    (a1,), _, b = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    b.run()
+    b.finish()
+    a2 = b.amp.cpu().numpy()
+    assert np.array_equal(a1, a2)
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    a3 = C.amplitudes(w.outputs)
+    assert np.array_equal(a1, a3)
+
+
+def test_cuda_graph_capture_of_run():
+    w = qaoa_workload(8, 2, n_out=40, seed=10)
+    (a1,), _, b = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    b.amp.zero_()
+    with torch.cuda.graph(g, stream=s):
+        b.run(stream=s)
+    for _ in range(3):
+        b.amp.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(b.amp.cpu().numpy(), a1)
+
+
+def test_edge_cases_ragged_and_empty():
+    c = qft(3)
+    (a,), st, _ = run_batch([(c, [(5, 1.0)], [0, 1, 2, 3, 4], 0.0)])
+    close(a, [closed_forms.qft_amplitude(3, 5, y) for y in range(5)])
+    # no outputs at all
+    amps, st, _ = run_batch([(c, [(5, 1.0)], [], 0.0)])
+    assert len(amps[0]) == 0
+    # empty circuit: identity
+    from workloads import Circuit as WC
+    e = WC(5, [], "empty")
+    (a,), st, _ = run_batch([(e, [(9, 1.0)], [9, 8], 0.0)])
+    close(a, [1.0, 0.0])
+    # host convenience call with zero outputs
+    C = fs.Circuit(c)
+    assert len(C.amplitudes([])) == 0

@@ -1,0 +1,182 @@
+"""Host-side tests of the library (no GPU needed): the C ABI loads and
+exports every declared symbol, the host analysis is bit-exact against the
+oracle's, the autotuner picks the oracle's argmin of Eq. 8, argument errors
+are reported with the documented codes."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from workloads import (Gate, Circuit as WCircuit, SplitMix64, aa_workload, amplitude_amplification,
+                       four_qubit_figure, qaoa_maxcut, qaoa_workload, qft, quantum_walk,
+                       qw_workload, random_small_circuit, three_qubit_example)
+from oracle import feynman
+import paper_2608_01467_b300 as fs
+from paper_2608_01467_b300 import _lib
+from paper_2608_01467_b300.build import LIB, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def setup_module(module):
+    build()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "feynsparse.h")).read()
+    return sorted(set(re.findall(r"FS_API\s+[\w\s\*]*?\b(fs_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 20
+    L = ctypes.CDLL(LIB)
+    for n in names:
+        assert hasattr(L, n), n
+    # and only those (plus nothing else called fs_*)
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if " T fs_" in ln})
+    assert exported == names
+    assert set(_lib.exported_symbols()) == set(names)
+
+
+def test_version_and_last_error():
+    L = _lib.load()
+    assert b"sm_103a" in L.fs_version()
+    h = ctypes.c_void_p()
+    rc = L.fs_circuit_create(None, 3, 2, ctypes.byref(h))
+    assert rc == -1
+    assert b"NULL" in L.fs_last_error()
+
+
+CIRCUITS = [
+    four_qubit_figure(), three_qubit_example(), qft(8), qft(12),
+    amplitude_amplification(12, 3, 0xA5C), amplitude_amplification(6, 3, 17),
+    amplitude_amplification(4, 3, 0),
+    qaoa_maxcut(16, 2, SplitMix64(1))[0], qaoa_maxcut(24, 3, SplitMix64(2))[0],
+    quantum_walk(16), quantum_walk(6, pos_bits=8),
+] + [random_small_circuit(n, g, s) for n, g, s in
+     [(3, 10, 1), (5, 30, 2), (7, 40, 3), (40, 80, 4), (70, 120, 5), (128, 150, 6)]]
+
+
+@pytest.mark.parametrize("idx", range(len(CIRCUITS)))
+def test_analysis_bit_exact_vs_oracle(idx):
+    c = CIRCUITS[idx]
+    o = feynman.analyze(c)
+    C = fs.Circuit(c)
+    a = C.analyze(0)
+    assert a["A"] == o["A"]
+    assert a["n_gates"] == len(c.gates)
+    roles = o["roles"]
+    assert a["n_wp"] == roles.count("WP") and a["n_det"] == roles.count("DET") and a["n_br"] == roles.count("BR")
+    # branching variables: same gates, same qubits, same source ids (backward order)
+    want = []
+    for gi in range(len(c.gates) - 1, -1, -1):
+        if roles[gi] != "BR":
+            continue
+        g = c.gates[gi]
+        tq = list(g.qubits)
+        order = sorted(range(len(tq)), key=lambda j: tq[j])
+        for j in order:
+            want.append((gi, tq[j], o["src"][gi][j]))
+    assert C.branch_vars() == want
+    assert a["n_natural"] == sum(1 for w in want if w[2] == -1)
+
+
+@pytest.mark.parametrize("idx", [0, 1, 2, 5, 6, 7, 10, 12, 13])
+def test_autotune_matches_oracle_argmin(idx):
+    c = CIRCUITS[idx]
+    a = fs.Circuit(c).analyze(0)
+    c1, c2, cost = feynman.autotune(c, max_ap=a["max_ap"], min_apr=a["min_apr"])
+    assert (a["c1"], a["c2"]) == (c1, c2)
+    assert a["gateops"] == cost
+    (Gp, Gr, Gs, Ap, Ar, As), cost2 = feynman.region_counts(c, c1, c2)
+    assert (a["G_p"], a["G_r"], a["G_s"], a["A_p"], a["A_r"], a["A_s"]) == (Gp, Gr, Gs, Ap, Ar, As)
+
+
+def test_table1_counts_through_the_abi():
+    assert fs.Circuit(qft(8)).analyze(0x3C)["A"] == 0
+    assert fs.Circuit(amplitude_amplification(12, 3, 77)).analyze(0)["A"] == 72
+    assert fs.Circuit(qaoa_maxcut(20, 2, SplitMix64(5))[0]).analyze(0)["A"] == 40
+    assert fs.Circuit(quantum_walk(16)).analyze(0)["A"] == 15
+
+
+def _err(gates, n):
+    with pytest.raises(_lib.FsError) as e:
+        fs.Circuit(gates=gates, n_qubits=n)
+    return e.value.code
+
+
+def test_argument_errors():
+    assert _err([Gate("H", (3,))], 3) == -1                                  # qubit out of range
+    assert _err([Gate("H", (0,))], 129) == -3                                # too many qubits
+    assert _err([Gate("U1", (0,), (), 0.0, (1, 1, 0, 1))], 2) == -4          # not unitary
+    assert _err([Gate("SWAP", (1, 1))], 2) == -1                             # repeated target
+    assert _err([Gate("X", (0,), ((0, 1),))], 2) == -1                       # target is a control
+    assert _err([Gate("X", (0,), ((5, 1),))], 3) == -1                       # control out of range
+    g = _lib.fs_gate()
+    g.kind = 1
+    g.n_q = 1
+    g.ctrl_mask[0] = 2
+    g.ctrl_val[0] = 4                                                        # value outside mask
+    h = ctypes.c_void_p()
+    assert _lib.load().fs_circuit_create((_lib.fs_gate * 1)(g), 1, 3, ctypes.byref(h)) == -1
+    g2 = _lib.fs_gate()
+    g2.kind = 0
+    g2.n_q = 1
+    g2.ctrl_mask[0] = 2                                                      # controlled H
+    assert _lib.load().fs_circuit_create((_lib.fs_gate * 1)(g2), 1, 3, ctypes.byref(h)) == -2
+    g3 = _lib.fs_gate()
+    g3.kind = 99
+    g3.n_q = 1
+    assert _lib.load().fs_circuit_create((_lib.fs_gate * 1)(g3), 1, 3, ctypes.byref(h)) == -2
+
+
+def test_bits_beyond_n_rejected():
+    C = fs.Circuit(qft(4))
+    with pytest.raises(_lib.FsError):
+        C.analyze(1 << 5)
+    with pytest.raises(_lib.FsError):
+        C.set_input([(1 << 4, 1.0)])
+    b = fs.Batch()
+    with pytest.raises(_lib.FsError):
+        b.add(C, [1 << 7])
+
+
+def test_plan_rejects_unenumerable_A():
+    C = fs.Circuit(amplitude_amplification(12, 3, 5))
+    b = fs.Batch()
+    b.add(C, [0, 1])
+    with pytest.raises(_lib.FsError) as e:
+        b.plan()
+    assert e.value.code == -9
+
+
+def test_plan_layout_and_fixed_split_errors():
+    w = qaoa_workload(8, 2, n_out=16, seed=3)
+    C = fs.Circuit(w.circuit)
+    b = fs.Batch(split="fixed", c1=5, c2=3)
+    b.add(C, w.outputs)
+    with pytest.raises(_lib.FsError):
+        b.plan()
+    b2 = fs.Batch()
+    b2.add(C, w.outputs)
+    b2.add(C, [])                      # empty job is allowed
+    n = b2.plan()
+    assert n > 0 and n % 256 == 0
+    assert b2.total_outputs == 16
+    assert b2.launch_count() == 3
+
+
+def test_run_before_upload_is_a_state_error():
+    C = fs.Circuit(qft(3))
+    b = fs.Batch()
+    b.add(C, [0, 1])
+    b.plan()
+    L = _lib.load()
+    rc = L.fs_batch_run(b._h, ctypes.c_void_p(256), ctypes.c_void_p(512), None)
+    assert rc == -10
