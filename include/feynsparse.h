@@ -127,7 +127,8 @@ typedef struct fs_stats {
     uint64_t candidates;      /* S * M * 2^A */
     uint64_t completed;       /* leaves that reached the input boundary */
     uint64_t valid;           /* completed leaves with chi = 1 */
-    uint64_t gate_visits;     /* gates evaluated (Eq. 8 per pair in exact mode) */
+    uint64_t gate_visits;     /* gates evaluated, all kernels (Eq. 8 per pair in exact mode) */
+    uint64_t history_visits;  /* of which in the root and suffix (history kernel) */
     uint64_t table_entries;   /* checkpoint entries written */
     int32_t c1, c2;
     uint32_t A_p, A_r, A_s;
@@ -212,6 +213,10 @@ FS_API int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream
  * (fs_stats array of capacity cap, host) of the last run. */
 FS_API int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size_t cap);
 
+/* Bytes fs_batch_upload copies host-to-device (programs, bit strings,
+ * descriptors, tile list) for the planned batch. */
+FS_API int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes);
+
 /* Total outputs over the jobs added so far. */
 FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
 
@@ -222,6 +227,23 @@ FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
  * recorded events (enabled by fs_batch_time_kernels), in milliseconds. */
 FS_API int fs_batch_time_kernels(fs_batch* b, int enable);
 FS_API int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* reduce_ms);
+
+/* Per-region opcode histogram of a planned job: counts[r * FS_N_OPCODES + k]
+ * for region r (0 prefix, 1 root, 2 suffix) and opcode k, into a host array
+ * of 3 * FS_N_OPCODES uint32_t.  Opcode numbering is the library's internal
+ * one (1 = X, 2 = MCX, 3 = SWAP, 4 = PERM1, 5 = PERM2, 6 = DIAG1, 7 = PH1,
+ * 8 = NEG1, 9 = MCPH, 10 = MCNEG, 11 = DIAG2, 12 = H, 13 = BR1, 14 = BR2);
+ * used to count algorithmic work for throughput reports. */
+#define FS_N_OPCODES 16
+FS_API int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* counts);
+
+/* Register width (32-bit words: 1, 2 or 4) of a planned job's state. */
+FS_API int fs_batch_job_words(const fs_batch* b, uint32_t job, uint32_t* words);
+
+/* Measures, on the current device, the sustained FP64 FMA rate (FMA/s) and
+ * the 32-bit integer logic rate (ops/s) with short probe kernels, and
+ * reports the SM count.  Allocates and frees 256 bytes of device memory. */
+FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms);
 
 #ifdef __cplusplus
 }

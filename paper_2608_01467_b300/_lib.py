@@ -48,6 +48,7 @@ class fs_options(ctypes.Structure):
 class fs_stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("valid", ctypes.c_uint64), ("gate_visits", ctypes.c_uint64),
+                ("history_visits", ctypes.c_uint64),
                 ("table_entries", ctypes.c_uint64), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
                 ("A_p", ctypes.c_uint32), ("A_r", ctypes.c_uint32), ("A_s", ctypes.c_uint32)]
 
@@ -75,11 +76,18 @@ SIGNATURES = {
     "fs_batch_run": (ctypes.c_int, [vp, vp, vp, vp]),
     "fs_batch_finish": (ctypes.c_int, [vp, vp, vp, P(fs_stats), ctypes.c_size_t]),
     "fs_batch_total_outputs": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
+    "fs_batch_upload_bytes": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
     "fs_batch_launch_count": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
     "fs_batch_time_kernels": (ctypes.c_int, [vp, ctypes.c_int]),
     "fs_batch_kernel_ms": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float),
                                           P(ctypes.c_float)]),
+    "fs_batch_op_histogram": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
+    "fs_batch_job_words": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
+    "fs_probe_peaks": (ctypes.c_int, [P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32)]),
 }
+N_OPCODES = 16
+OPCODES = {1: "X", 2: "MCX", 3: "SWAP", 4: "PERM1", 5: "PERM2", 6: "DIAG1", 7: "PH1", 8: "NEG1",
+           9: "MCPH", 10: "MCNEG", 11: "DIAG2", 12: "H", 13: "BR1", 14: "BR2"}
 
 _lib = None
 

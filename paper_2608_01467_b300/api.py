@@ -188,6 +188,11 @@ class Batch:
         check(_lib.load().fs_batch_total_outputs(self._h, ctypes.byref(n)))
         return n.value
 
+    def static_bytes(self) -> int:
+        n = ctypes.c_size_t(0)
+        check(_lib.load().fs_batch_upload_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
     def allocate(self, device="cuda"):
         import torch
         self._raw = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
@@ -224,6 +229,21 @@ class Batch:
         check(_lib.load().fs_batch_kernel_ms(self._h, ctypes.byref(a), ctypes.byref(h), ctypes.byref(r)))
         return a.value, h.value, r.value
 
+    def op_histogram(self, job: int):
+        """{region: {opname: count}} of a planned job (regions prefix/root/suffix)."""
+        arr = (ctypes.c_uint32 * (3 * _lib.N_OPCODES))()
+        check(_lib.load().fs_batch_op_histogram(self._h, job, arr))
+        out = {}
+        for r, name in enumerate(("prefix", "root", "suffix")):
+            out[name] = {_lib.OPCODES[k]: arr[r * _lib.N_OPCODES + k]
+                         for k in _lib.OPCODES if arr[r * _lib.N_OPCODES + k]}
+        return out
+
+    def job_words(self, job: int) -> int:
+        w = ctypes.c_uint32(0)
+        check(_lib.load().fs_batch_job_words(self._h, job, ctypes.byref(w)))
+        return w.value
+
     def job_slices(self):
         off = 0
         out = []
@@ -231,6 +251,13 @@ class Batch:
             out.append(slice(off, off + m))
             off += m
         return out
+
+
+def probe_peaks():
+    """Measured FP64 FMA/s, 32-bit integer ops/s and SM count of the current device."""
+    d, i, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    check(_lib.load().fs_probe_peaks(ctypes.byref(d), ctypes.byref(i), ctypes.byref(n)))
+    return {"dfma_per_s": d.value, "int_ops_per_s": i.value, "sms": n.value}
 
 
 def amplitudes(circuit, inputs, outputs, eps: float = 0.0) -> np.ndarray:

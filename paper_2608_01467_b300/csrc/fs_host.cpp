@@ -585,6 +585,14 @@ int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, size_t n_o
     return FS_OK;
 }
 
+int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes)
+{
+    if (!b || !bytes) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    *bytes = b->static_bytes;
+    return FS_OK;
+}
+
 int fs_batch_total_outputs(const fs_batch* b, size_t* n)
 {
     if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
@@ -673,7 +681,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     }
     b->static_bytes = off;
     b->dyn_begin = off;
-    b->o_stats = take(nj * 4 * sizeof(unsigned long long));
+    b->o_stats = take(nj * fs::STATS_PER_JOB * sizeof(unsigned long long));
     b->o_counter = take(sizeof(unsigned int));
     b->o_err = take(sizeof(uint32_t));
     const size_t zero_end = off;
@@ -717,7 +725,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.coef = (const double2*)(base + j.o_coef);
         d.table = (fs::Entry*)(base + j.o_table);
         d.partials = (double2*)(base + j.o_part);
-        d.stats = (unsigned long long*)(base + b->o_stats) + 4 * ji;
+        d.stats = (unsigned long long*)(base + b->o_stats) + fs::STATS_PER_JOB * ji;
         d.G = (int32_t)j.c->g.size();
         d.c1 = j.sp.c1; d.c2 = j.sp.c2;
         d.Ap = j.sp.Ap; d.Ar = j.sp.Ar; d.As = j.sp.As;
@@ -823,10 +831,10 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
     if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "no run on this workspace");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nj = b->jobs.size();
-    std::vector<unsigned long long> st(4 * nj + 1, 0);
+    std::vector<unsigned long long> st(fs::STATS_PER_JOB * nj + 1, 0);
     uint32_t err = 0;
     unsigned char* base = (unsigned char*)d_ws;
-    if (nj) CUDA_TRY(cudaMemcpyAsync(st.data(), base + b->o_stats, 4 * nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    if (nj) CUDA_TRY(cudaMemcpyAsync(st.data(), base + b->o_stats, fs::STATS_PER_JOB * nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(&err, base + b->o_err, sizeof err, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
@@ -839,14 +847,49 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
             const int A = j.c->A;
             const int lp = ilog2_ceil(std::max<uint64_t>(j.pairs, 1));
             o.candidates = (A + lp < 64) ? (j.pairs << A) : ~0ull;
-            o.completed = st[4 * ji + 0];
-            o.valid = st[4 * ji + 1];
-            o.gate_visits = st[4 * ji + 2];
-            o.table_entries = st[4 * ji + 3];
+            const unsigned long long* q = &st[fs::STATS_PER_JOB * ji];
+            o.completed = q[0];
+            o.valid = q[1];
+            o.gate_visits = q[2] + q[4];
+            o.history_visits = q[2];
+            o.table_entries = q[3];
             o.c1 = j.sp.c1; o.c2 = j.sp.c2;
             o.A_p = (uint32_t)j.sp.Ap; o.A_r = (uint32_t)j.sp.Ar; o.A_s = (uint32_t)j.sp.As;
         }
     }
+    return FS_OK;
+}
+
+int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* counts)
+{
+    if (!b || !counts) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    const Job& j = b->jobs[job];
+    std::memset(counts, 0, 3 * FS_N_OPCODES * sizeof(uint32_t));
+    for (size_t e = 0; e < j.prog.ops.size(); ++e) {
+        const int r = (int)e < j.sp.c1 ? 0 : ((int)e < j.sp.c2 ? 1 : 2);
+        const uint32_t code = j.prog.ops[e].code;
+        if (code < FS_N_OPCODES) counts[r * FS_N_OPCODES + code]++;
+    }
+    return FS_OK;
+}
+
+int fs_batch_job_words(const fs_batch* b, uint32_t job, uint32_t* words)
+{
+    if (!b || !words) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    *words = (uint32_t)b->jobs[job].W;
+    return FS_OK;
+}
+
+int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms)
+{
+    if (!dfma_per_s || !int_ops_per_s || !sms) return fail(FS_ERR_INVALID, "NULL argument");
+    int n = 0;
+    CUDA_TRY(fs::probe_peaks(dfma_per_s, int_ops_per_s, &n));
+    *sms = n;
     return FS_OK;
 }
 

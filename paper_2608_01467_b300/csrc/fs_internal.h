@@ -61,7 +61,7 @@ struct JobDev {
     const double2* coef;       // S
     Entry* table;              // pairs x 2^Ap
     double2* partials;         // pairs x spp
-    unsigned long long* stats; // [completed, valid, visits, entries]
+    unsigned long long* stats; // [completed, valid, history visits, entries, prefix visits, -, -, -]
     int32_t G, c1, c2;
     int32_t Ap, Ar, As;
     int32_t W, S, M;
@@ -78,6 +78,7 @@ struct JobDev {
 constexpr int TILE_LOG2 = 8;             // items per tile = threads per CTA
 constexpr int TILE = 1 << TILE_LOG2;
 constexpr int REDUCE_THREADS = 128;
+constexpr int STATS_PER_JOB = 8;
 
 // Device error word values.
 constexpr uint32_t DEV_ERR_BAD_OPCODE = 1;
@@ -90,5 +91,6 @@ cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t 
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, cudaStream_t s);
 int history_grid_size(int device);
+cudaError_t probe_peaks(double* dfma_per_s, double* int_ops_per_s, int* sms);
 
 }  // namespace fs

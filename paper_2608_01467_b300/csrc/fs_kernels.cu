@@ -282,11 +282,11 @@ __global__ void __launch_bounds__(256) prefix_kernel(const JobDev* __restrict__ 
         if (act == 0xffffffffu && same_job == 0xffffffffu) {
             const unsigned long long v = warp_sum_u64(visits), en = warp_sum_u64(entries);
             if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&jobs[j].stats[2], v);
+                atomicAdd(&jobs[j].stats[4], v);
                 atomicAdd(&jobs[j].stats[3], en);
             }
         } else if (idx < total) {
-            if (visits) atomicAdd(&jobs[j].stats[2], visits);
+            if (visits) atomicAdd(&jobs[j].stats[4], visits);
             if (entries) atomicAdd(&jobs[j].stats[3], entries);
         }
     }
@@ -451,7 +451,78 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
     }
 }
 
+
+// ---------------------------------------------------------------- peak probes
+
+// FP64 FMA throughput: 8 independent dependency chains per thread.
+__global__ void __launch_bounds__(256) probe_dfma_kernel(double* out, int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-9 + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __fma_rn(x[k], a, b);
+    }
+    double s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 12345.678) out[0] = s;   // keeps the chains live
+}
+
+// 32-bit integer logic throughput: 8 independent xor-rotate chains per thread.
+__global__ void __launch_bounds__(256) probe_int_kernel(unsigned* out, int iters, unsigned a)
+{
+    unsigned x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 2654435761u + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = (x[k] ^ a) + (unsigned)k;
+    }
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s ^= x[k];
+    if (s == 0x12345678u) out[0] = s;
+}
+
 }  // namespace
+
+cudaError_t probe_peaks(double* dfma_per_s, double* int_ops_per_s, int* sms)
+{
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    *sms = n_sm;
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 256);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    const int blocks = n_sm * 8, threads = 256;
+    float ms = 0;
+    const int di = 4096, ii = 65536;
+    probe_dfma_kernel<<<blocks, threads>>>((double*)buf, 16, 1.0000001, 1e-7);
+    cudaEventRecord(t0);
+    probe_dfma_kernel<<<blocks, threads>>>((double*)buf, di, 1.0000001, 1e-7);
+    cudaEventRecord(t1);
+    cudaEventSynchronize(t1);
+    cudaEventElapsedTime(&ms, t0, t1);
+    *dfma_per_s = (double)blocks * threads * di * 8 / (ms * 1e-3);
+    probe_int_kernel<<<blocks, threads>>>((unsigned*)buf, 16, 0x9e3779b9u);
+    cudaEventRecord(t0);
+    probe_int_kernel<<<blocks, threads>>>((unsigned*)buf, ii, 0x9e3779b9u);
+    cudaEventRecord(t1);
+    cudaEventSynchronize(t1);
+    cudaEventElapsedTime(&ms, t0, t1);
+    *int_ops_per_s = (double)blocks * threads * ii * 8 * 2 / (ms * 1e-3);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    e = cudaGetLastError();
+    cudaFree(buf);
+    return e;
+}
 
 cudaError_t launch_prefix(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
                           uint64_t total, uint32_t* d_err, cudaStream_t s)

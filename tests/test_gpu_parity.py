@@ -159,7 +159,7 @@ def test_qaoa8_exact_vs_dense_and_oracle_counts():
     (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
     close(a, dense.amplitudes(w.circuit, w.inputs, w.outputs))
     assert st[0]["completed"] == 64 * (1 << 16) == st[0]["valid"]
-    cost = feynman.region_counts(w.circuit, st["c1"], st["c2"])[1]
+    cost = feynman.region_counts(w.circuit, st[0]["c1"], st[0]["c2"])[1]
     assert st[0]["gate_visits"] == 64 * cost
 
 
