@@ -628,7 +628,11 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
             if (c1 < 0 || c2 < c1 || c2 > G) return fail(FS_ERR_INVALID, "job %zu: fixed cuts (%d, %d) outside [0, %d]", ji, c1, c2, G);
             j.sp = split_at(C, pre, c1, c2);
         } else if (b->opt.split == 2) {
-            j.sp = split_at(C, pre, 0, 0);
+            // Algorithm 1: no checkpoints.  The whole circuit is one region
+            // enumerated over h (one item per assignment) when the index
+            // range allows, else one item per pair looping over h.
+            const int lp = ilog2_ceil(std::max<uint64_t>(j.pairs, 1));
+            j.sp = (C.A + lp <= 40) ? split_at(C, pre, 0, G) : split_at(C, pre, 0, 0);
         } else {
             const uint64_t share = all_pairs ? (uint64_t)((long double)budget * j.pairs / all_pairs) : budget;
             const uint64_t per_pair = j.pairs ? share / (j.pairs * sizeof(fs::Entry)) : share;

@@ -405,7 +405,8 @@ def qw_workload(steps: int = 16, n_out: int = 4096, pos_bits: int = QW_POS_BITS,
             outs.append(y)
             seen.add(y)
     reach = len(outs)
-    wide = max(4 * n_out, 64)
+    wide = min(max(4 * n_out, 64), p0, (1 << pos_bits) - 1 - p0)
+    assert n_out <= 2 * wide + 2, "register too small for that many outputs"
     while len(outs) < n_out:
         k = rng.below(2 * wide + 1) - wide
         coin = rng.below(2)
