@@ -36,12 +36,13 @@ def op_cost(name, W):
     return int_ops, fp
 
 
-def workload_jobs(name, rank=0):
+def workload_jobs(name, rank=0, outputs=None):
     from workloads import qaoa_workload, qw_workload
     if name == "qw100":
-        w = qw_workload(seed=0x5EED0005 + rank)
-        return [w], {"workload": "qw100_t16_4096out_exact", "qubits": 100, "steps": 16,
-                     "outputs": 4096, "input_support": 2, "eps": 0.0}
+        n_out = outputs or 4096
+        w = qw_workload(n_out=n_out, seed=0x5EED0005 + rank)
+        return [w], {"workload": f"qw100_t16_{n_out}out_exact", "qubits": 100, "steps": 16,
+                     "outputs": n_out, "input_support": 2, "eps": 0.0}
     if name == "qw100+qaoa":
         ws = [qw_workload(seed=0x5EED0005 + rank)]
         for n in (16, 20, 24):
@@ -173,7 +174,7 @@ def run_reference(args):
     rank, world, local = dist_setup(args)
     if rank != 0:
         return
-    jobs, cfg = workload_jobs(args.workload)
+    jobs, cfg = workload_jobs(args.workload, 0, args.outputs)
     for _ in range(args.warmup):
         oracle_sample(jobs, budget_s=2.0, max_outputs=1)
     rates = []
@@ -201,7 +202,7 @@ def run_ours(args):
     rank, world, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    jobs, cfg = workload_jobs(args.workload, rank)
+    jobs, cfg = workload_jobs(args.workload, rank, args.outputs)
     b = fs.Batch()
     circs = []
     for w in jobs:
@@ -342,6 +343,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qw100")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--outputs", type=int, default=None, help="requested outputs (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

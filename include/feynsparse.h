@@ -111,6 +111,7 @@ typedef struct fs_analysis {
     uint32_t A_p, A_r, A_s;
     uint64_t gateops_lo, gateops_hi;  /* Eq. 8 at (c1, c2), 128-bit */
     uint32_t max_ap, min_apr;  /* the autotuner's memory / parallelism constraints */
+    uint32_t max_apr;          /* and its ceiling on A_p + A_r (items per pair) */
 } fs_analysis;
 
 /* Options of a batch.  split: 0 = autotuned, 1 = fixed cuts (c1, c2 applied
@@ -120,6 +121,8 @@ typedef struct fs_options {
     int32_t c1, c2;
     uint64_t table_budget_bytes;   /* checkpoint-table memory bound (0: 4 GiB) */
     uint64_t min_items;            /* parallelism floor for (prefix, root) items (0: 2^19) */
+    uint64_t max_items;            /* ceiling on (prefix, root) items per job; bounds the
+                                      per-tile partial sums (0: 2^28) */
 } fs_options;
 
 /* Counters of one job after a run. */

@@ -53,8 +53,8 @@ def lib():
             L.orc_region_counts.argtypes = [P(OrcGate), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_uint64)]
             L.orc_autotune.argtypes = [P(OrcGate), ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
-                                       P(ctypes.c_uint64)]
+                                       ctypes.c_int, ctypes.c_int, P(ctypes.c_int32),
+                                       P(ctypes.c_int32), P(ctypes.c_uint64)]
             L.orc_run.argtypes = [P(OrcGate), ctypes.c_int, ctypes.c_int,
                                   P(ctypes.c_uint64), P(ctypes.c_double), ctypes.c_int,
                                   P(ctypes.c_uint64), ctypes.c_int, ctypes.c_double,
@@ -127,12 +127,12 @@ def region_counts(circuit, c1, c2):
     return tuple(int(x) for x in out), int(cost[0]) | (int(cost[1]) << 64)
 
 
-def autotune(circuit, max_ap=64, min_apr=0):
+def autotune(circuit, max_ap=64, min_apr=0, max_apr=1 << 30):
     c1 = ctypes.c_int32(0)
     c2 = ctypes.c_int32(0)
     cost = np.zeros(2, np.uint64)
     rc = lib().orc_autotune(_gates(circuit), len(circuit.gates), circuit.n_qubits, max_ap,
-                            min_apr, ctypes.byref(c1), ctypes.byref(c2),
+                            min_apr, max_apr, ctypes.byref(c1), ctypes.byref(c2),
                             _p(cost, ctypes.c_uint64))
     if rc:
         raise ValueError(f"orc_autotune failed: {rc}")

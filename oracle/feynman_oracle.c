@@ -360,8 +360,8 @@ int orc_region_counts(const orc_gate_in* gates, int G, int n, int c1, int c2, in
 
 /* Autotuned partition (Sec. IV-C): the cut pair minimising Eq. 8
  * over every 0 <= c1 <= c2 <= G, subject to Ap <= max_ap and
- * Ap + Ar >= min(min_apr, A).  Ties go to the smallest c1, then c2. */
-int orc_autotune(const orc_gate_in* gates, int G, int n, int max_ap, int min_apr,
+ * min(min_apr, A) <= Ap + Ar <= max_apr.  Ties go to the smallest c1, then c2. */
+int orc_autotune(const orc_gate_in* gates, int G, int n, int max_ap, int min_apr, int max_apr,
                  int32_t* c1_out, int32_t* c2_out, uint64_t* cost2)
 {
     ocirc C;
@@ -378,6 +378,7 @@ int orc_autotune(const orc_gate_in* gates, int G, int n, int max_ap, int min_apr
         for (int c2 = c1; c2 <= G; c2++) {
             int Ar = pre[c2] - Ap, As = C.A - pre[c2];
             if (Ap + Ar < need) continue;
+            if (Ap + Ar > max_apr) break;
             unsigned __int128 v = gateops(c1, c2 - c1, G - c2, Ap, Ar, As);
             if (!found || v < best) { best = v; *c1_out = c1; *c2_out = c2; found = 1; }
         }

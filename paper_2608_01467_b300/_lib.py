@@ -37,12 +37,14 @@ class fs_analysis(ctypes.Structure):
                 ("G_p", ctypes.c_uint32), ("G_r", ctypes.c_uint32), ("G_s", ctypes.c_uint32),
                 ("A_p", ctypes.c_uint32), ("A_r", ctypes.c_uint32), ("A_s", ctypes.c_uint32),
                 ("gateops_lo", ctypes.c_uint64), ("gateops_hi", ctypes.c_uint64),
-                ("max_ap", ctypes.c_uint32), ("min_apr", ctypes.c_uint32)]
+                ("max_ap", ctypes.c_uint32), ("min_apr", ctypes.c_uint32),
+                ("max_apr", ctypes.c_uint32)]
 
 
 class fs_options(ctypes.Structure):
     _fields_ = [("split", ctypes.c_uint32), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
-                ("table_budget_bytes", ctypes.c_uint64), ("min_items", ctypes.c_uint64)]
+                ("table_budget_bytes", ctypes.c_uint64), ("min_items", ctypes.c_uint64),
+                ("max_items", ctypes.c_uint64)]
 
 
 class fs_stats(ctypes.Structure):

@@ -139,7 +139,7 @@ class Batch:
     kernels (graph-capturable); finish() synchronises and reads counters."""
 
     def __init__(self, split: str = "auto", c1: int = 0, c2: int = 0,
-                 table_budget_bytes: int = 0, min_items: int = 0):
+                 table_budget_bytes: int = 0, min_items: int = 0, max_items: int = 0):
         L = _lib.load()
         h = ctypes.c_void_p()
         check(L.fs_batch_create(ctypes.byref(h)))
@@ -149,6 +149,7 @@ class Batch:
         opt.c1, opt.c2 = c1, c2
         opt.table_budget_bytes = table_budget_bytes
         opt.min_items = min_items
+        opt.max_items = max_items
         check(L.fs_batch_set_options(self._h, ctypes.byref(opt)))
         self.jobs = []
         self.ws = None

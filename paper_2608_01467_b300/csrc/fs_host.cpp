@@ -480,8 +480,9 @@ int fs_analyze(fs_circuit* c, const uint64_t* input_bits, fs_analysis* out)
     // one output, default budget
     const int max_ap = ilog2_floor((4ull << 30) / 32);
     const int min_apr = ilog2_ceil(1ull << 19);
+    const int max_apr = ilog2_floor(1ull << 28);
     Split s;
-    if (!autotune(*c, max_ap, min_apr, 40, s)) return fail(FS_ERR_TOO_LARGE, "no admissible partition");
+    if (!autotune(*c, max_ap, min_apr, max_apr, s)) return fail(FS_ERR_TOO_LARGE, "no admissible partition");
     out->c1 = s.c1; out->c2 = s.c2;
     const int G = (int)c->g.size();
     out->G_p = (uint32_t)s.c1; out->G_r = (uint32_t)(s.c2 - s.c1); out->G_s = (uint32_t)(G - s.c2);
@@ -490,6 +491,7 @@ int fs_analyze(fs_circuit* c, const uint64_t* input_bits, fs_analysis* out)
     out->gateops_hi = (uint64_t)(s.cost >> 64);
     out->max_ap = (uint32_t)max_ap;
     out->min_apr = (uint32_t)min_apr;
+    out->max_apr = (uint32_t)max_apr;
     return FS_OK;
 }
 
@@ -607,6 +609,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     if (!b || !workspace_bytes) return fail(FS_ERR_INVALID, "NULL argument");
     const uint64_t budget = b->opt.table_budget_bytes ? b->opt.table_budget_bytes : (4ull << 30);
     const uint64_t min_items = b->opt.min_items ? b->opt.min_items : (1ull << 19);
+    const uint64_t max_items = b->opt.max_items ? b->opt.max_items : (1ull << 28);
     // table budget shared by the jobs in proportion to their pair counts
     uint64_t all_pairs = 0;
     for (Job& j : b->jobs) all_pairs += (uint64_t)j.outs.size() * j.ins.size();
@@ -638,7 +641,8 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
             const uint64_t per_pair = j.pairs ? share / (j.pairs * sizeof(fs::Entry)) : share;
             const int max_ap = per_pair ? std::min(ilog2_floor(per_pair), 40) : 0;
             const int min_apr = j.pairs ? ilog2_ceil((min_items + j.pairs - 1) / j.pairs) : 0;
-            const int max_apr = std::max(0, 40 - ilog2_ceil(std::max<uint64_t>(j.pairs, 1)));
+            const int max_apr = std::max(0, std::min(40, ilog2_floor(max_items)) -
+                                            ilog2_ceil(std::max<uint64_t>(j.pairs, 1)));
             if (!autotune(C, max_ap, min_apr, max_apr, j.sp))
                 return fail(FS_ERR_TOO_LARGE, "job %zu: no partition fits the table budget", ji);
         }

@@ -91,7 +91,7 @@ def test_analysis_bit_exact_vs_oracle(idx):
 def test_autotune_matches_oracle_argmin(idx):
     c = CIRCUITS[idx]
     a = fs.Circuit(c).analyze(0)
-    c1, c2, cost = feynman.autotune(c, max_ap=a["max_ap"], min_apr=a["min_apr"])
+    c1, c2, cost = feynman.autotune(c, max_ap=a["max_ap"], min_apr=a["min_apr"], max_apr=a["max_apr"])
     assert (a["c1"], a["c2"]) == (c1, c2)
     assert a["gateops"] == cost
     (Gp, Gr, Gs, Ap, Ar, As), cost2 = feynman.region_counts(c, c1, c2)
