@@ -248,6 +248,34 @@ FS_API int fs_batch_job_words(const fs_batch* b, uint32_t job, uint32_t* words);
  * reports the SM count.  Allocates and frees 256 bytes of device memory. */
 FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms);
 
+/* ---- allocation-free variant ---------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory at call time (code that must draw every
+ * device allocation from a pool it does not own, or that must not grow the
+ * process's device footprint while it runs).
+ *
+ * fs_amplitudes_noalloc computes the same amplitudes as fs_amplitudes
+ * (outputs: n_out x 2 words, host; amp_out: 2 * n_out doubles re/im, host,
+ * caller-owned; eps: 0 = exact) but calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its whole device workspace -- programs, bit strings,
+ * checkpoint table, partial sums, counters and the staged amplitudes -- lives
+ * in one static device array of FS_NOALLOC_SCRATCH_BYTES bytes, which every
+ * GPU that loads this part of the library holds until the process exits.
+ * A request whose workspace would exceed it fails with FS_ERR_TOO_LARGE and a
+ * message giving both sizes.
+ *   - The first call on a device looks up that array's device address (once
+ *     per device, with the device current); make that first call before any
+ *     stream capture.
+ *   - Every call uses the same array and leaves its contents behind; the
+ *     counters that must start at zero are cleared by each call.  Calls whose
+ *     GPU work overlaps (other host threads, or several streams) race on the
+ *     array: serialise them.
+ *   - stream: a cudaStream_t (NULL = legacy default stream); the call
+ *     synchronises it before returning. */
+#define FS_NOALLOC_SCRATCH_BYTES (16u << 20)
+FS_API int fs_amplitudes_noalloc(fs_circuit* c, const uint64_t* outputs, size_t n_out, double eps,
+                                 double* amp_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,7 +86,10 @@ SIGNATURES = {
     "fs_batch_op_histogram": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
     "fs_batch_job_words": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
     "fs_probe_peaks": (ctypes.c_int, [P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32)]),
+    "fs_amplitudes_noalloc": (ctypes.c_int, [vp, P(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_double,
+                                             P(ctypes.c_double), vp]),
 }
+NOALLOC_SCRATCH_BYTES = 16 << 20
 N_OPCODES = 16
 OPCODES = {1: "X", 2: "MCX", 3: "SWAP", 4: "PERM1", 5: "PERM2", 6: "DIAG1", 7: "PH1", 8: "NEG1",
            9: "MCPH", 10: "MCNEG", 11: "DIAG2", 12: "H", 13: "BR1", 14: "BR2"}

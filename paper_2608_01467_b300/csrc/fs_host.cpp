@@ -394,6 +394,12 @@ struct fs_batch {
     }
 };
 
+int fs::set_error(int code, const char* msg)
+{
+    g_err = msg;
+    return code;
+}
+
 extern "C" {
 
 const char* fs_last_error(void) { return g_err.c_str(); }

@@ -91,6 +91,9 @@ cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t 
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, cudaStream_t s);
 int history_grid_size(int device);
+
+// Sets the thread-local message read by fs_last_error and returns code.
+int set_error(int code, const char* msg);
 cudaError_t probe_peaks(double* dfma_per_s, double* int_ops_per_s, int* sms);
 
 }  // namespace fs
