@@ -203,7 +203,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     jobs, cfg = workload_jobs(args.workload, rank, args.outputs)
-    b = fs.Batch()
+    b = fs.Batch(engine=args.engine)
     circs = []
     for w in jobs:
         C = fs.Circuit(w.circuit)
@@ -214,6 +214,7 @@ def run_ours(args):
     b.allocate(dev)
     stream = torch.cuda.current_stream(dev)
     b.upload(stream)
+    engine, compile_ms = b.engine()
     b.time_kernels(True)
     n_out = b.total_outputs
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -316,7 +317,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded circuits and requests)",
             "config": dict(cfg, l2="flushed between steps (512 MiB write)",
                            parallelism=f"outputs sharded, {world} replica(s)",
-                           workspace_bytes=ws_bytes),
+                           workspace_bytes=ws_bytes, engine=engine,
+                           engine_compile_ms=round(compile_ms, 1)),
             "histories_per_s": hist_rate, "clocks": clocks,
             "e2e": {"value": e2e, "unit": "amplitudes/s",
                     "h2d_bytes_per_step": int(b.static_bytes()),
@@ -344,6 +346,7 @@ def main():
     ap.add_argument("--workload", default="qw100")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--outputs", type=int, default=None, help="requested outputs (small profiling cases)")
+    ap.add_argument("--engine", default="straight", choices=["straight", "interp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

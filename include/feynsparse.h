@@ -123,6 +123,8 @@ typedef struct fs_options {
     uint64_t min_items;            /* parallelism floor for (prefix, root) items (0: 2^19) */
     uint64_t max_items;            /* ceiling on (prefix, root) items per job; bounds the
                                       per-tile partial sums (0: 2^28) */
+    uint32_t engine;               /* history kernel: 0 = straight-line code generated per
+                                      batch at upload (NVRTC, sm_103a), 1 = interpreter */
 } fs_options;
 
 /* Counters of one job after a run. */
@@ -219,6 +221,11 @@ FS_API int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stat
 /* Bytes fs_batch_upload copies host-to-device (programs, bit strings,
  * descriptors, tile list) for the planned batch. */
 FS_API int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes);
+
+/* Engine actually used by the last fs_batch_upload (0 straight-line, 1
+ * interpreter) and the milliseconds spent generating and compiling the
+ * straight-line kernel. */
+FS_API int fs_batch_engine(const fs_batch* b, uint32_t* engine, double* compile_ms);
 
 /* Total outputs over the jobs added so far. */
 FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);

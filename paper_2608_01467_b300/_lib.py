@@ -44,7 +44,7 @@ class fs_analysis(ctypes.Structure):
 class fs_options(ctypes.Structure):
     _fields_ = [("split", ctypes.c_uint32), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
                 ("table_budget_bytes", ctypes.c_uint64), ("min_items", ctypes.c_uint64),
-                ("max_items", ctypes.c_uint64)]
+                ("max_items", ctypes.c_uint64), ("engine", ctypes.c_uint32)]
 
 
 class fs_stats(ctypes.Structure):
@@ -79,6 +79,7 @@ SIGNATURES = {
     "fs_batch_finish": (ctypes.c_int, [vp, vp, vp, P(fs_stats), ctypes.c_size_t]),
     "fs_batch_total_outputs": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
     "fs_batch_upload_bytes": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
+    "fs_batch_engine": (ctypes.c_int, [vp, P(ctypes.c_uint32), P(ctypes.c_double)]),
     "fs_batch_launch_count": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
     "fs_batch_time_kernels": (ctypes.c_int, [vp, ctypes.c_int]),
     "fs_batch_kernel_ms": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float),

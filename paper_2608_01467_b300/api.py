@@ -139,7 +139,8 @@ class Batch:
     kernels (graph-capturable); finish() synchronises and reads counters."""
 
     def __init__(self, split: str = "auto", c1: int = 0, c2: int = 0,
-                 table_budget_bytes: int = 0, min_items: int = 0, max_items: int = 0):
+                 table_budget_bytes: int = 0, min_items: int = 0, max_items: int = 0,
+                 engine: str = "straight"):
         L = _lib.load()
         h = ctypes.c_void_p()
         check(L.fs_batch_create(ctypes.byref(h)))
@@ -150,6 +151,7 @@ class Batch:
         opt.table_budget_bytes = table_budget_bytes
         opt.min_items = min_items
         opt.max_items = max_items
+        opt.engine = {"straight": 0, "interp": 1}[engine]
         check(L.fs_batch_set_options(self._h, ctypes.byref(opt)))
         self.jobs = []
         self.ws = None
@@ -188,6 +190,12 @@ class Batch:
         n = ctypes.c_size_t(0)
         check(_lib.load().fs_batch_total_outputs(self._h, ctypes.byref(n)))
         return n.value
+
+    def engine(self):
+        """(engine name, compile milliseconds) after upload."""
+        e, ms = ctypes.c_uint32(), ctypes.c_double()
+        check(_lib.load().fs_batch_engine(self._h, ctypes.byref(e), ctypes.byref(ms)))
+        return ("straight" if e.value == 0 else "interp"), ms.value
 
     def static_bytes(self) -> int:
         n = ctypes.c_size_t(0)

@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -388,9 +389,17 @@ struct fs_batch {
     bool timing = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
+    void* jit = nullptr;          // generated straight-line module (engine 0)
+    double jit_ms = 0;
+    void drop_jit()
+    {
+        if (jit) fs::jit_release(jit);
+        jit = nullptr;
+    }
     ~fs_batch()
     {
         for (auto& e : ev) if (e) cudaEventDestroy(e);
+        drop_jit();
     }
 };
 
@@ -561,11 +570,13 @@ int fs_batch_set_options(fs_batch* b, const fs_options* opt)
     if (!b) return fail(FS_ERR_INVALID, "NULL batch");
     if (opt) {
         if (opt->split > 2) return fail(FS_ERR_INVALID, "split must be 0, 1 or 2");
+        if (opt->engine > 1) return fail(FS_ERR_INVALID, "engine must be 0 or 1");
         b->opt = *opt;
     } else {
         std::memset(&b->opt, 0, sizeof b->opt);
     }
     b->planned = b->uploaded = false;
+    b->drop_jit();
     return FS_OK;
 }
 
@@ -598,6 +609,15 @@ int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes)
     if (!b || !bytes) return fail(FS_ERR_INVALID, "NULL argument");
     if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
     *bytes = b->static_bytes;
+    return FS_OK;
+}
+
+int fs_batch_engine(const fs_batch* b, uint32_t* engine, double* compile_ms)
+{
+    if (!b || !engine) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->uploaded) return fail(FS_ERR_STATE, "fs_batch_upload must come first");
+    *engine = b->jit ? 0u : 1u;
+    if (compile_ms) *compile_ms = b->jit ? b->jit_ms : 0.0;
     return FS_OK;
 }
 
@@ -708,6 +728,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     *workspace_bytes = off;
     b->planned = true;
     b->uploaded = false;
+    b->drop_jit();
     int dev = 0;
     cudaGetDevice(&dev);
     b->grid = fs::history_grid_size(dev);
@@ -773,6 +794,23 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         std::memcpy(&H[b->o_obegin], obegin.data(), nj * sizeof(uint64_t));
     }
     if (!b->tiles.empty()) std::memcpy(&H[b->o_tiles], b->tiles.data(), b->tiles.size() * sizeof(uint2));
+    if (b->opt.engine == 0 && !b->jit && nj) {
+        std::vector<fs::JitJobSpec> specs(nj);
+        for (size_t ji = 0; ji < nj; ++ji) {
+            const Job& j = b->jobs[ji];
+            specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
+                                       j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
+                                       j.sp.As, j.eps * j.eps};
+        }
+        std::string err, src;
+        const char* dump = getenv("FS_JIT_DUMP");   // optional: write the generated source here
+        const int jrc = fs::jit_build(specs, &b->jit, &err, &b->jit_ms, dump ? &src : nullptr);
+        if (dump) {
+            FILE* f = fopen(dump, "w");
+            if (f) { fwrite(src.data(), 1, src.size(), f); fclose(f); }
+        }
+        if (jrc) return fail(FS_ERR_CUDA, "straight-line engine: %s", err.c_str());
+    }
     if (b->static_bytes)
         CUDA_TRY(cudaMemcpyAsync(d_ws, H.data(), b->static_bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
     // the host staging copy must outlive the asynchronous copy
@@ -827,8 +865,12 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
                                (uint32_t*)(base + b->o_err), s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));
-    CUDA_TRY(fs::launch_history(jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
-                                (unsigned int*)(base + b->o_counter), (uint32_t*)(base + b->o_err), b->grid, s));
+    if (b->jit)
+        CUDA_TRY(fs::jit_launch_history(b->jit, jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
+                                        (unsigned int*)(base + b->o_counter), s));
+    else
+        CUDA_TRY(fs::launch_history(jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
+                                    (unsigned int*)(base + b->o_counter), (uint32_t*)(base + b->o_err), b->grid, s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[2], s));
     CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
                                (double2*)d_amp_out, s));

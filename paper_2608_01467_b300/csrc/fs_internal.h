@@ -4,6 +4,9 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+#include <string>
+#include <vector>
+
 namespace fs {
 
 // Opcodes of the evaluation-order program.  Every op moves the state from
@@ -51,28 +54,39 @@ struct Entry {
 };
 static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
 
-// Per-job descriptor in device memory.
+// Per-job descriptor in device memory.  The field list is a macro so that
+// the generated straight-line kernels (fs_jit.cpp) declare the identical
+// layout.  One declaration per field, no top-level commas.
+#define FS_JOBDEV_FIELDS                                                      \
+    const Op* ops;                                                            \
+    const uint32_t* masks;                                                    \
+    const double2* fac;                                                       \
+    const uint32_t* outs;      /* M x 4 words */                              \
+    const uint32_t* ins;       /* S x 4 words */                              \
+    const double2* coef;       /* S */                                        \
+    Entry* table;              /* pairs x 2^Ap */                             \
+    double2* partials;         /* pairs x spp */                              \
+    unsigned long long* stats; /* completed, valid, history visits, entries, prefix visits */ \
+    int32_t G;                                                                \
+    int32_t c1;                                                               \
+    int32_t c2;                                                               \
+    int32_t Ap;                                                               \
+    int32_t Ar;                                                               \
+    int32_t As;                                                               \
+    int32_t W;                                                                \
+    int32_t S;                                                                \
+    int32_t M;                                                                \
+    int32_t log2_ipp;          /* Ap + Ar */                                  \
+    int32_t log2_spp;          /* max(0, log2_ipp - TILE_LOG2) */             \
+    int32_t pad0;                                                             \
+    uint64_t n_pairs;          /* S * M */                                    \
+    uint64_t prefix_begin;     /* offset of this job in the flat prefix index space */ \
+    uint64_t out_begin;        /* offset of this job's outputs in amp_out */ \
+    uint64_t n_tiles;                                                         \
+    double eps2;               /* eps^2 (0: exact) */
+
 struct JobDev {
-    const Op* ops;
-    const uint32_t* masks;
-    const double2* fac;
-    const uint32_t* outs;      // M x 4 words
-    const uint32_t* ins;       // S x 4 words
-    const double2* coef;       // S
-    Entry* table;              // pairs x 2^Ap
-    double2* partials;         // pairs x spp
-    unsigned long long* stats; // [completed, valid, history visits, entries, prefix visits, -, -, -]
-    int32_t G, c1, c2;
-    int32_t Ap, Ar, As;
-    int32_t W, S, M;
-    int32_t log2_ipp;          // Ap + Ar
-    int32_t log2_spp;          // max(0, log2_ipp - TILE_LOG2)
-    int32_t pad0;
-    uint64_t n_pairs;          // S * M
-    uint64_t prefix_begin;     // offset of this job in the flat prefix index space
-    uint64_t out_begin;        // offset of this job's outputs in amp_out
-    uint64_t n_tiles;
-    double eps2;               // eps^2 (0: exact)
+    FS_JOBDEV_FIELDS
 };
 
 constexpr int TILE_LOG2 = 8;             // items per tile = threads per CTA
@@ -91,6 +105,22 @@ cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t 
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, cudaStream_t s);
 int history_grid_size(int device);
+
+// Straight-line engine (fs_jit.cpp): one generated persistent kernel for the
+// root and suffix regions of every job of a batch.
+struct JitJobSpec {
+    const Op* ops;
+    int G;
+    const uint32_t* masks;
+    const double2* fac;
+    int W, c1, c2, Ap, Ar, As;
+    double eps2;
+};
+int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
+              std::string* source_out);
+cudaError_t jit_launch_history(void* handle, const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
+                               unsigned int* d_counter, cudaStream_t s);
+void jit_release(void* handle);
 
 // Sets the thread-local message read by fs_last_error and returns code.
 int set_error(int code, const char* msg);

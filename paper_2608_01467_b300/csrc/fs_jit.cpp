@@ -1,0 +1,454 @@
+// Straight-line engine for the history kernel.
+//
+// At plan time every job's root and suffix regions (Algorithm 2) are
+// compiled into straight-line sm_103a code: each op of the evaluation-order
+// program becomes a few register instructions with its masks, bit positions
+// and matrix elements as immediates, so the device spends no instructions
+// fetching or decoding ops.  The generated source is this library's own CUDA
+// C++, compiled by NVRTC to a cubin and loaded with cudaLibraryLoadData; one
+// persistent kernel serves every job of the batch (a switch on the tile's
+// job), with the same atomic tile queue, fixed-order reduction and counters
+// as the interpreting kernel in fs_kernels.cu.
+//
+// Factors are applied with the same complex-product formula as the
+// interpreter, specialised only where the specialisation is exact (unit
+// factors skipped, -1 as a sign flip, purely real or imaginary factors as two
+// products), so both engines give bit-identical history amplitudes.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+namespace {
+
+#define FS_XSTR(...) #__VA_ARGS__
+#define FS_STR(...) FS_XSTR(__VA_ARGS__)
+
+const char* kPrelude = R"PRE(
+typedef unsigned int u32;
+typedef int i32;
+typedef unsigned long long u64;
+typedef u32 uint32_t;
+typedef i32 int32_t;
+typedef u64 uint64_t;
+struct Op;
+struct Entry { u32 st[4]; double2 amp; };
+)PRE"
+"struct JobDev { " FS_STR(FS_JOBDEV_FIELDS) " };\n"
+R"PRE(
+#define TILE_LOG2 8
+#define TILE 256
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)),
+                        __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ double dneg(double x)
+{
+    return __hiloint2double(__double2hiint(x) ^ 0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double2 cneg(double2 a) { return make_double2(dneg(a.x), dneg(a.y)); }
+__device__ __forceinline__ double2 cre(double2 a, double r) { return make_double2(__dmul_rn(a.x, r), __dmul_rn(a.y, r)); }
+__device__ __forceinline__ double2 cim(double2 a, double s) { return make_double2(dneg(__dmul_rn(a.y, s)), __dmul_rn(a.x, s)); }
+__device__ __forceinline__ bool cut(double2 a, double eps2) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)) < eps2; }
+__device__ __forceinline__ double2 sel2(bool c, double2 a, double2 b) { return c ? a : b; }
+
+__device__ __forceinline__ u64 warp_sum_u64(u64 v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <class T>
+__device__ void tile_body(const JobDev& J, u64 tile, double2* s_warp)
+{
+    constexpr int W = T::W;
+    const u64 item = tile * TILE + threadIdx.x;
+    const u64 n_items = J.n_pairs << J.log2_ipp;
+    const bool active = item < n_items;
+    double2 acc = make_double2(0.0, 0.0);
+    u64 completed = 0, valid = 0, visits = 0;
+    u64 pair = 0;
+    if (active) {
+        pair = item >> J.log2_ipp;
+        const u64 local = item & ((1ull << J.log2_ipp) - 1ull);
+        const u64 hp = local >> T::Ar;
+        const u64 hr = local & ((1ull << T::Ar) - 1ull);
+        const u64 o = pair / (u64)J.S;
+        const u64 s = pair - o * (u64)J.S;
+        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
+        const uint4 sv = __ldg(ent);
+        const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+        if (!isnan(a0.x)) {
+            u32 st[W], bin[W];
+            const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+            const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * s));
+            const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
+            double2 amp = a0;
+            if (T::root(st, amp, hr, bin, visits) < 0) {
+                const u64 ns = 1ull << T::As;
+                u64 hs = 0;
+                while (hs < ns) {
+                    u32 st2[W];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) st2[j] = st[j];
+                    double2 amp2 = amp;
+                    const int r2 = T::suffix(st2, amp2, hs, bin, visits);
+                    if (r2 < 0) {
+                        ++completed;
+                        u32 d = 0;
+#pragma unroll
+                        for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
+                        if (d == 0) {
+                            ++valid;
+                            acc.x += amp2.x;
+                            acc.y += amp2.y;
+                        }
+                        ++hs;
+                    } else {
+                        hs = ((hs >> r2) + 1ull) << r2;
+                    }
+                }
+            }
+        }
+    }
+    completed = warp_sum_u64(completed);
+    valid = warp_sum_u64(valid);
+    visits = warp_sum_u64(visits);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0 && (completed | valid | visits)) {
+        atomicAdd(&J.stats[0], completed);
+        atomicAdd(&J.stats[1], valid);
+        atomicAdd(&J.stats[2], visits);
+    }
+    const int seg_log2 = J.log2_ipp < TILE_LOG2 ? J.log2_ipp : TILE_LOG2;
+    if (seg_log2 < 5) {
+        const int seg = 1 << seg_log2;
+        for (int off = seg >> 1; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (active && (lane & (seg - 1)) == 0) J.partials[pair] = acc;
+    } else {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) s_warp[warp] = acc;
+        __syncthreads();
+        const int wps = 1 << (seg_log2 - 5);
+        const int nseg = TILE >> seg_log2;
+        if ((int)threadIdx.x < nseg) {
+            const u64 first = tile * TILE + (u64)threadIdx.x * (1ull << seg_log2);
+            if (first < n_items) {
+                double2 t = s_warp[threadIdx.x * wps];
+                for (int k = 1; k < wps; ++k) {
+                    t.x += s_warp[threadIdx.x * wps + k].x;
+                    t.y += s_warp[threadIdx.x * wps + k].y;
+                }
+                const u64 p = first >> J.log2_ipp;
+                const u64 l = first & ((1ull << J.log2_ipp) - 1ull);
+                J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = t;
+            }
+        }
+    }
+}
+)PRE";
+
+std::string hexd(double v)
+{
+    char buf[64];
+    snprintf(buf, sizeof buf, "%a", v);
+    return buf;
+}
+
+std::string d2lit(double2 f) { return "make_double2(" + hexd(f.x) + ", " + hexd(f.y) + ")"; }
+
+bool is_one(double2 f) { return f.x == 1.0 && f.y == 0.0; }
+bool is_mone(double2 f) { return f.x == -1.0 && f.y == 0.0; }
+bool is_real(double2 f) { return f.y == 0.0; }
+bool is_imag(double2 f) { return f.x == 0.0; }
+bool is_zero(double2 f) { return f.x == 0.0 && f.y == 0.0; }
+
+// "a = a * f" for a compile-time factor, exact specialisations only.
+std::string mul_const(double2 f)
+{
+    if (is_one(f)) return "";
+    if (is_mone(f)) return "a = cneg(a);";
+    if (is_real(f)) return "a = cre(a, " + hexd(f.x) + ");";
+    if (is_imag(f)) return "a = cim(a, " + hexd(f.y) + ");";
+    return "a = cmul(a, " + d2lit(f) + ");";
+}
+
+std::string bitexpr(int q) { return "((s[" + std::to_string(q >> 5) + "] >> " + std::to_string(q & 31) + ") & 1u)"; }
+
+std::string flip(int q, const std::string& v)
+{
+    return "s[" + std::to_string(q >> 5) + "] ^= (" + v + ") << " + std::to_string(q & 31) + ";";
+}
+
+std::string match_expr(const uint32_t* m, int W)
+{
+    std::string e;
+    for (int j = 0; j < W; ++j) {
+        if (m[j] == 0 && m[W + j] == 0) continue;
+        char buf[96];
+        snprintf(buf, sizeof buf, "((s[%d] & 0x%08xu) ^ 0x%08xu)", j, m[j], m[W + j]);
+        if (!e.empty()) e += " | ";
+        e += buf;
+    }
+    if (e.empty()) return "true";
+    return "((" + e + ") == 0u)";
+}
+
+// Selects among k factor constants by an index expression.
+std::string select_factor(const double2* f, int k, const std::string& idx)
+{
+    // balanced select tree; equal constants collapse
+    if (k == 1) return d2lit(f[0]);
+    bool all_same = true;
+    for (int i = 1; i < k; ++i) all_same &= (f[i].x == f[0].x && f[i].y == f[0].y);
+    if (all_same) return d2lit(f[0]);
+    if (k == 2) return "sel2((" + idx + ") != 0u, " + d2lit(f[1]) + ", " + d2lit(f[0]) + ")";
+    const int h = k / 2;
+    const std::string hi = select_factor(f + h, h, "(" + idx + ") - " + std::to_string(h) + "u");
+    const std::string lo = select_factor(f, h, idx);
+    return "sel2((" + idx + ") >= " + std::to_string(h) + "u, " + hi + ", " + lo + ")";
+}
+
+// Body of one region: ops [e0, e1).  nbits = the region's h width.
+void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbits)
+{
+    const int W = J.W;
+    out += "    int low = " + std::to_string(nbits) + ";\n";
+    for (int e = e0; e < e1; ++e) {
+        const Op& op = J.ops[e];
+        const int q0 = op.q0, q1 = op.q1;
+        const double2* F = J.fac + op.aux;
+        const std::string visits_cut = "{ visits += " + std::to_string(e - e0 + 1) + "ull; return low; }";
+        std::string c;
+        switch (op.code) {
+        case OP_X: c = flip(q0, "1u"); break;
+        case OP_MCX: c = "if (" + match_expr(J.masks + op.aux2, W) + ") " + flip(q0, "1u"); break;
+        case OP_SWAP:
+            c = "{ const u32 d = " + bitexpr(q0) + " ^ " + bitexpr(q1) + "; " + flip(q0, "d") + " " + flip(q1, "d") + " }";
+            break;
+        case OP_PERM1:
+            c = "{ const u32 o = " + bitexpr(q0) + "; a = cmul(a, " + select_factor(F, 2, "o") + "); " + flip(q0, "1u") + " }";
+            break;
+        case OP_PERM2: {
+            c = "{ const u32 o = " + bitexpr(q0) + " | (" + bitexpr(q1) + " << 1); ";
+            char buf[64];
+            snprintf(buf, sizeof buf, "const u32 i = (0x%xu >> (2u * o)) & 3u; ", op.aux2);
+            c += buf;
+            c += "a = cmul(a, " + select_factor(F, 4, "o") + "); " + flip(q0, "(o ^ i) & 1u") + " " +
+                 flip(q1, "((o ^ i) >> 1) & 1u") + " }";
+            break;
+        }
+        case OP_DIAG1:
+            c = "a = cmul(a, " + select_factor(F, 2, bitexpr(q0)) + ");";
+            break;
+        case OP_PH1: {
+            const std::string m = mul_const(F[0]);
+            if (!m.empty()) c = "if (" + bitexpr(q0) + ") { " + m + " }";
+            break;
+        }
+        case OP_NEG1: c = "if (" + bitexpr(q0) + ") a = cneg(a);"; break;
+        case OP_MCPH: {
+            const std::string m = mul_const(F[0]);
+            if (!m.empty()) c = "if (" + match_expr(J.masks + op.aux2, W) + ") { " + m + " }";
+            break;
+        }
+        case OP_MCNEG: c = "if (" + match_expr(J.masks + op.aux2, W) + ") a = cneg(a);"; break;
+        case OP_DIAG2: {
+            // RZZ-like symmetric diagonals only depend on the parity
+            const bool parity = F[0].x == F[3].x && F[0].y == F[3].y && F[1].x == F[2].x && F[1].y == F[2].y;
+            if (parity)
+                c = "a = cmul(a, " + select_factor(F, 2, bitexpr(q0) + " ^ " + bitexpr(q1)) + ");";
+            else
+                c = "a = cmul(a, " + select_factor(F, 4, bitexpr(q0) + " | (" + bitexpr(q1) + " << 1)") + ");";
+            break;
+        }
+        case OP_H: {
+            std::string ie = op.s0 >= 0 ? "((u32)(h >> " + std::to_string(op.s0) + ") & 1u)" : "((bin[" + std::to_string(q0 >> 5) + "] >> " + std::to_string(q0 & 31) + ") & 1u)";
+            c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + ie + "; "
+                "a = cre(a, (o & i) ? -0x1.6a09e667f3bcdp-1 : 0x1.6a09e667f3bcdp-1); " + flip(q0, "o ^ i") + " }";
+            if (op.s0 >= 0) {
+                c += " low = " + std::to_string(op.s0) + ";";
+                if (J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
+            }
+            break;
+        }
+        case OP_BR1: {
+            std::string ie = op.s0 >= 0 ? "((u32)(h >> " + std::to_string(op.s0) + ") & 1u)" : "((bin[" + std::to_string(q0 >> 5) + "] >> " + std::to_string(q0 & 31) + ") & 1u)";
+            bool any_zero = false;
+            for (int i = 0; i < 4; ++i) any_zero |= is_zero(F[i]);
+            c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + ie + "; a = cmul(a, " +
+                select_factor(F, 4, "(o << 1) | i") + "); " + flip(q0, "o ^ i");
+            if (op.s0 >= 0) c += " low = " + std::to_string(op.s0) + ";";
+            if (any_zero) {
+                std::string zc;
+                for (int k = 0; k < 4; ++k)
+                    if (is_zero(F[k])) zc += std::string(zc.empty() ? "" : " || ") + "((o << 1) | i) == " + std::to_string(k) + "u";
+                c += " if (" + zc + ") " + visits_cut;
+            }
+            if (op.s0 >= 0 && J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
+            c += " }";
+            break;
+        }
+        case OP_BR2: {
+            auto ie = [&](int s, int q) {
+                return s >= 0 ? "((u32)(h >> " + std::to_string(s) + ") & 1u)" : "((bin[" + std::to_string(q >> 5) + "] >> " + std::to_string(q & 31) + ") & 1u)";
+            };
+            c = "{ const u32 o = " + bitexpr(q0) + " | (" + bitexpr(q1) + " << 1); const u32 i = " + ie(op.s0, q0) +
+                " | (" + ie(op.s1, q1) + " << 1); a = cmul(a, " + select_factor(F, 16, "(o << 2) | i") + "); " +
+                flip(q0, "(o ^ i) & 1u") + " " + flip(q1, "((o ^ i) >> 1) & 1u");
+            int lo = 99;
+            if (op.s0 >= 0) lo = op.s0;
+            if (op.s1 >= 0 && op.s1 < lo) lo = op.s1;
+            if (lo != 99) c += " low = " + std::to_string(lo) + ";";
+            bool any_zero = false;
+            for (int i = 0; i < 16; ++i) any_zero |= is_zero(F[i]);
+            if (any_zero) {
+                std::string zc;
+                for (int k = 0; k < 16; ++k)
+                    if (is_zero(F[k])) zc += std::string(zc.empty() ? "" : " || ") + "((o << 2) | i) == " + std::to_string(k) + "u";
+                c += " if (" + zc + ") " + visits_cut;
+            }
+            if (lo != 99 && J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
+            c += " }";
+            break;
+        }
+        default:
+            c = "/* unknown op */";
+            break;
+        }
+        if (!c.empty()) out += "    " + c + "\n";
+    }
+    out += "    visits += " + std::to_string(e1 - e0) + "ull;\n    (void)low;\n    return -1;\n";
+}
+
+std::string generate(const std::vector<JitJobSpec>& jobs)
+{
+    std::string src = kPrelude;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const JitJobSpec& J = jobs[j];
+        const std::string W = std::to_string(J.W);
+        src += "struct J" + std::to_string(j) + " {\n";
+        src += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
+               std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
+        const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
+        src += "  static __device__ __forceinline__ int root" + sig + " {\n    (void)h; (void)bin;\n";
+        emit_region(src, J, J.c1, J.c2, J.Ar);
+        src += "  }\n";
+        src += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
+        emit_region(src, J, J.c2, J.G, J.As);
+        src += "  }\n};\n";
+    }
+    src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_history(const JobDev* __restrict__ jobs, "
+           "const uint2* __restrict__ tiles, u64 n_tiles, unsigned int* counter)\n{\n"
+           "    __shared__ unsigned int s_tile;\n    __shared__ double2 s_warp[8];\n"
+           "    for (;;) {\n"
+           "        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);\n"
+           "        __syncthreads();\n        const unsigned int t = s_tile;\n        __syncthreads();\n"
+           "        if ((u64)t >= n_tiles) break;\n        const uint2 td = tiles[t];\n"
+           "        switch (td.x) {\n";
+    for (size_t j = 0; j < jobs.size(); ++j)
+        src += "        case " + std::to_string(j) + "u: tile_body<J" + std::to_string(j) + ">(jobs[" +
+               std::to_string(j) + "], td.y, s_warp); break;\n";
+    src += "        default: break;\n        }\n    }\n}\n";
+    return src;
+}
+
+struct JitModule {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kernel = nullptr;
+    int grid = 0;
+};
+
+}  // namespace
+
+int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
+              std::string* source_out)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const std::string src = generate(jobs);
+    if (source_out) *source_out = src;
+    if (compile_ms) *compile_ms = 0;
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "fs_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        *err = "nvrtcCreateProgram failed";
+        return -1;
+    }
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+    const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        *err = std::string("NVRTC: ") + nvrtcGetErrorString(rc) + "\n" + log.substr(0, 2000);
+        nvrtcDestroyProgram(&prog);
+        return -1;
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    std::vector<char> cubin(n);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    if (compile_ms)
+        *compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    JitModule* m = new JitModule;
+    cudaError_t e = cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->kernel, m->lib, "fs_jit_history");
+    if (e != cudaSuccess) {
+        *err = std::string("loading the generated kernel (compiled in ") +
+               std::to_string(compile_ms ? *compile_ms : 0.0) + " ms): " + cudaGetErrorString(e);
+        if (m->lib) cudaLibraryUnload(m->lib);
+        delete m;
+        return -2;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)m->kernel, TILE, 0);
+    m->grid = (sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
+    *handle = m;
+    return 0;
+}
+
+cudaError_t jit_launch_history(void* handle, const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
+                               unsigned int* d_counter, cudaStream_t s)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    JitModule* m = (JitModule*)handle;
+    int grid = m->grid;
+    if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
+    void* args[] = {(void*)&d_jobs, (void*)&d_tiles, (void*)&n_tiles, (void*)&d_counter};
+    return cudaLaunchKernel((const void*)m->kernel, dim3(grid), dim3(TILE), args, 0, s);
+}
+
+void jit_release(void* handle)
+{
+    JitModule* m = (JitModule*)handle;
+    if (!m) return;
+    if (m->lib) cudaLibraryUnload(m->lib);
+    delete m;
+}
+
+}  // namespace fs

@@ -276,3 +276,34 @@ def test_edge_cases_ragged_and_empty():
     # host convenience call with zero outputs
     C = fs.Circuit(c)
     assert len(C.amplitudes([])) == 0
+
+
+@pytest.mark.parametrize("case", ["qaoa_exact", "qaoa_eps", "qw", "rand7", "rand70", "aa"])
+def test_engines_bitwise_equal(case):
+    """The generated straight-line kernel and the interpreter multiply the same
+    factors in the same order: amplitudes and counters agree to the bit."""
+    if case.startswith("qaoa"):
+        w = qaoa_workload(8, 2, n_out=40, seed=77)
+        jobs = [(w.circuit, w.inputs, w.outputs, 0.05 if case == "qaoa_eps" else 0.0)]
+    elif case == "qw":
+        w = qw_workload(steps=6, n_out=40, pos_bits=8)
+        jobs = [(w.circuit, w.inputs, w.outputs, 0.0)]
+    elif case == "aa":
+        w = aa_workload(n=4, iters=2, seed=3, all_outputs=True)
+        jobs = [(w.circuit, w.inputs, w.outputs[:6], 0.0)]
+    else:
+        n = 7 if case == "rand7" else 70
+        c = random_small_circuit(n, 40 if n == 7 else 90, 4242 + n)
+        rng = SplitMix64(n)
+        outs = list(range(1 << n)) if n == 7 else [rng.bits(n) for _ in range(30)]
+        jobs = [(c, [(rng.bits(n), 0.6), (rng.bits(n), 0.8j)], outs, 0.0)]
+    a1, s1, b1 = run_batch(jobs, engine="straight")
+    a2, s2, b2 = run_batch(jobs, engine="interp")
+    assert b1.engine()[0] == "straight" and b2.engine()[0] == "interp"
+    for x, y in zip(a1, a2):
+        assert np.array_equal(x, y)
+    for x, y in zip(s1, s2):
+        for k in ("completed", "valid", "gate_visits", "table_entries"):
+            assert x[k] == y[k], k
+    o, _ = oracle_counts(*jobs[0][:3], eps=jobs[0][3])
+    close(a1[0], o)
