@@ -25,17 +25,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "amplitudes/s and histories/s on 1 B300, batched+learned vs plain, fidelity≥0.999"
 
-# Algorithmic work per executed op for the roofline: integer
-# logic ops on a W-word register state and FP64 instructions on the FP64 pipe.
-def op_cost(name, W):
-    int_ops = {"X": 1, "MCX": 3 * W + 1, "SWAP": 5, "PERM1": 2, "PERM2": 6, "DIAG1": 2, "PH1": 2,
-               "NEG1": 3, "MCPH": 3 * W + 1, "MCNEG": 3 * W + 3, "DIAG2": 4, "H": 4, "BR1": 4,
-               "BR2": 8}[name]
-    fp = {"X": 0, "MCX": 0, "SWAP": 0, "PERM1": 4, "PERM2": 4, "DIAG1": 4, "PH1": 2, "NEG1": 0,
-          "MCPH": 2, "MCNEG": 0, "DIAG2": 4, "H": 2, "BR1": 4, "BR2": 4}[name]
-    return int_ops, fp
-
-
 def workload_jobs(name, rank=0, outputs=None):
     from workloads import qaoa_workload, qw_workload
     if name == "qw100":
@@ -272,25 +261,19 @@ def run_ours(args):
     e2e = sum_over_ranks(n_out * args.steps, world, dev) / t_e2e
 
     # roofline of the history kernel (the dominant kernel): algorithmic
-    # integer ops and FP64 instructions of the root + suffix per launch
+    # integer ops and FP64 instructions of the root + suffix per launch, from
+    # the library's per-region work of each job times the region executions
     peaks = fs.api.probe_peaks()
-    int_ops = 0
-    fp_ops = 0
-    exact = all(w.eps == 0 for w in jobs)
+    int_ops = 0.0
+    fp_ops = 0.0
     for ji, w in enumerate(jobs):
-        hist = b.op_histogram(ji)
-        W = b.job_words(ji)
+        iw, fw = b.region_work(ji)
         s0 = stats0[ji]
         pairs = len(w.outputs) * len(w.inputs)
-        root_runs = pairs << (s0["A_p"] + s0["A_r"])
-        suffix_runs = s0["completed"] if not exact else pairs << (s0["A_p"] + s0["A_r"] + s0["A_s"])
-        for region, runs in (("root", root_runs), ("suffix", suffix_runs)):
-            for name, cnt in hist[region].items():
-                i_o, f_o = op_cost(name, W)
-                int_ops += cnt * runs * i_o
-                fp_ops += cnt * runs * f_o
-        int_ops += s0["completed"] * 2 * W          # chi test per leaf
-        fp_ops += s0["valid"] * 2                    # accumulation per valid leaf
+        root_runs = s0["table_entries"] << s0["A_r"]          # live checkpoints x 2^A_r
+        suffix_runs = s0["completed"] if w.eps > 0 else pairs << (s0["A_p"] + s0["A_r"] + s0["A_s"])
+        int_ops += iw[1] * root_runs + iw[2] * suffix_runs + iw[3] * s0["completed"]
+        fp_ops += fw[1] * root_runs + fw[2] * suffix_runs + fw[3] * s0["valid"]
     h_s = statistics.mean(hist_ms) / 1000.0
     sm_max = clocks["sm_max_mhz"] or 2032.0
     int_peak = peaks["sms"] * 128 * sm_max * 1e6

@@ -86,6 +86,7 @@ SIGNATURES = {
                                           P(ctypes.c_float)]),
     "fs_batch_op_histogram": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
     "fs_batch_job_words": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
+    "fs_batch_region_work": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_double), P(ctypes.c_double)]),
     "fs_probe_peaks": (ctypes.c_int, [P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32)]),
     "fs_amplitudes_noalloc": (ctypes.c_int, [vp, P(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_double,
                                              P(ctypes.c_double), vp]),

@@ -248,6 +248,14 @@ class Batch:
                          for k in _lib.OPCODES if arr[r * _lib.N_OPCODES + k]}
         return out
 
+    def region_work(self, job: int):
+        """Per single execution: ([prefix, root, suffix, per-leaf] integer ops,
+        [prefix, root, suffix, per-valid-leaf] FP64 instructions)."""
+        i = (ctypes.c_double * 4)()
+        f = (ctypes.c_double * 4)()
+        check(_lib.load().fs_batch_region_work(self._h, job, i, f))
+        return list(i), list(f)
+
     def job_words(self, job: int) -> int:
         w = ctypes.c_uint32(0)
         check(_lib.load().fs_batch_job_words(self._h, job, ctypes.byref(w)))

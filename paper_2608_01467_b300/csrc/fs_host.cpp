@@ -862,8 +862,11 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
     CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[0], s));
-    CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
-                               (uint32_t*)(base + b->o_err), s));
+    if (b->jit)
+        CUDA_TRY(fs::jit_launch_prefix(b->jit, jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix, s));
+    else
+        CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
+                                   (uint32_t*)(base + b->o_err), s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));
     if (b->jit)
         CUDA_TRY(fs::jit_launch_history(b->jit, jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
@@ -928,6 +931,75 @@ int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* counts)
         const uint32_t code = j.prog.ops[e].code;
         if (code < FS_N_OPCODES) counts[r * FS_N_OPCODES + code]++;
     }
+    return FS_OK;
+}
+
+// Algorithmic work of one execution of each region of a job: integer
+// logic/compare instructions on the register state and FP64 instructions.
+// Per op, with nz = control-mask words that are not all zero:
+//   X 1 | MCX, MCPH, MCNEG: nz masked compares + ceil((nz-1)/2) 3-input ORs
+//   + 1 test, then 1 flip (MCX), or the phase (MCPH: its factor, MCNEG: 2
+//   sign flips) on half the histories | SWAP 5 | PERM1 3 + 4 FP64 |
+//   PERM2 8 + 4 FP64 | DIAG1 2 + 4 FP64 | PH1 1 + half the factor's cost |
+//   NEG1 1 + 1 | DIAG2 3 + 4 FP64 | H 4 + 2 FP64 | BR1 5 + 4 FP64 |
+//   BR2 10 + 4 FP64; a factor costs 0 (1), 2 integer (-1), 2 FP64 (real or
+//   imaginary) or 4 FP64 (general).
+static void factor_cost(double2 f, double& iops, double& fops)
+{
+    if (f.x == 1.0 && f.y == 0.0) return;
+    if (f.x == -1.0 && f.y == 0.0) { iops += 2; return; }
+    if (f.y == 0.0 || f.x == 0.0) { fops += 2; return; }
+    fops += 4;
+}
+
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops)
+{
+    const int W = j.W;
+    for (int e = e0; e < e1; ++e) {
+        const fs::Op& op = j.prog.ops[e];
+        int nz = 0;
+        if (op.code == fs::OP_MCX || op.code == fs::OP_MCPH || op.code == fs::OP_MCNEG)
+            for (int w = 0; w < W; ++w) nz += (j.prog.masks[op.aux2 + w] | j.prog.masks[op.aux2 + W + w]) != 0;
+        const double test = nz + (nz > 1 ? (nz - 1 + 1) / 2 : 0) + 1;
+        const double2* F = j.prog.fac.data() + op.aux;
+        double fi = 0, ff = 0;
+        switch (op.code) {
+        case fs::OP_X: iops += 1; break;
+        case fs::OP_MCX: iops += test + 1; break;
+        case fs::OP_SWAP: iops += 5; break;
+        case fs::OP_PERM1: iops += 3; fops += 4; break;
+        case fs::OP_PERM2: iops += 8; fops += 4; break;
+        case fs::OP_DIAG1: iops += 2; fops += 4; break;
+        case fs::OP_PH1: factor_cost(F[0], fi, ff); iops += 1 + fi / 2; fops += ff / 2; break;
+        case fs::OP_NEG1: iops += 1 + 1; break;
+        case fs::OP_MCPH: factor_cost(F[0], fi, ff); iops += test + fi / 2; fops += ff / 2; break;
+        case fs::OP_MCNEG: iops += test + 1; break;
+        case fs::OP_DIAG2: iops += 3; fops += 4; break;
+        case fs::OP_H: iops += 4; fops += 2; break;
+        case fs::OP_BR1: iops += 5; fops += 4; break;
+        case fs::OP_BR2: iops += 10; fops += 4; break;
+        default: break;
+        }
+    }
+}
+
+int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, double* fp64_ops)
+{
+    if (!b || !int_ops || !fp64_ops) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    const Job& j = b->jobs[job];
+    const int G = (int)j.prog.ops.size();
+    const int cuts[4] = {0, j.sp.c1, j.sp.c2, G};
+    for (int r = 0; r < 3; ++r) {
+        double i = 0, f = 0;
+        region_work(j, cuts[r], cuts[r + 1], i, f);
+        int_ops[r] = i;
+        fp64_ops[r] = f;
+    }
+    // per completed leaf: the chi test (2W); per valid leaf: two FP64 adds
+    int_ops[3] = 2.0 * j.W;
+    fp64_ops[3] = 2.0;
     return FS_OK;
 }
 

@@ -120,6 +120,8 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
               std::string* source_out);
 cudaError_t jit_launch_history(void* handle, const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
                                unsigned int* d_counter, cudaStream_t s);
+cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
+                              uint64_t total, cudaStream_t s);
 void jit_release(void* handle);
 
 // Sets the thread-local message read by fs_last_error and returns code.

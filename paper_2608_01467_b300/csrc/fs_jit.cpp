@@ -168,6 +168,43 @@ __device__ void tile_body(const JobDev& J, u64 tile, double2* s_warp)
         }
     }
 }
+
+__device__ __forceinline__ int find_job(const u64* __restrict__ begin, int n_jobs, u64 idx)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(begin + mid) <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class T>
+__device__ __forceinline__ void prefix_body(const JobDev& J, u64 local, u64& visits, u64& entries)
+{
+    constexpr int W = T::W;
+    const u64 pair = local >> T::Ap;
+    const u64 hp = local & ((1ull << T::Ap) - 1ull);
+    const u64 o = pair / (u64)J.S;
+    const u64 sidx = pair - o * (u64)J.S;
+    const uint4 ov = __ldg(reinterpret_cast<const uint4*>(J.outs + 4 * o));
+    const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
+    const u32 otmp[4] = {ov.x, ov.y, ov.z, ov.w};
+    const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+    u32 st[W], bin[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) { st[j] = otmp[j]; bin[j] = btmp[j]; }
+    double2 amp = make_double2(1.0, 0.0);
+    const int r = T::prefix(st, amp, hp, bin, visits);
+    u32 w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < W; ++j) w[j] = st[j];
+    if (r >= 0) amp.x = __longlong_as_double(0x7ff8000000000000ll);
+    else entries += 1;
+    uint4* dst = reinterpret_cast<uint4*>(J.table + local);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<double2*>(dst + 1)[0] = amp;
+}
 )PRE";
 
 std::string hexd(double v)
@@ -353,6 +390,9 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
         src += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
                std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
         const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
+        src += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
+        emit_region(src, J, 0, J.c1, J.Ap);
+        src += "  }\n";
         src += "  static __device__ __forceinline__ int root" + sig + " {\n    (void)h; (void)bin;\n";
         emit_region(src, J, J.c1, J.c2, J.Ar);
         src += "  }\n";
@@ -372,13 +412,35 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
         src += "        case " + std::to_string(j) + "u: tile_body<J" + std::to_string(j) + ">(jobs[" +
                std::to_string(j) + "], td.y, s_warp); break;\n";
     src += "        default: break;\n        }\n    }\n}\n";
+    src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_prefix(const JobDev* __restrict__ jobs, "
+           "const u64* __restrict__ begin, int n_jobs, u64 total)\n{\n"
+           "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (u64)gridDim.x * blockDim.x) {\n"
+           "        if (!__any_sync(0xffffffffu, idx < total)) break;\n"
+           "        u64 visits = 0, entries = 0;\n        int j = 0;\n"
+           "        if (idx < total) {\n            j = find_job(begin, n_jobs, idx);\n"
+           "            const u64 local = idx - jobs[j].prefix_begin;\n            switch (j) {\n";
+    for (size_t j = 0; j < jobs.size(); ++j)
+        src += "            case " + std::to_string(j) + ": prefix_body<J" + std::to_string(j) + ">(jobs[" +
+               std::to_string(j) + "], local, visits, entries); break;\n";
+    src += "            default: break;\n            }\n        }\n"
+           "        const unsigned act = __ballot_sync(0xffffffffu, idx < total);\n"
+           "        const unsigned same = __match_any_sync(0xffffffffu, idx < total ? j : -1);\n"
+           "        if (act == 0xffffffffu && same == 0xffffffffu) {\n"
+           "            const u64 v = warp_sum_u64(visits), en = warp_sum_u64(entries);\n"
+           "            if ((threadIdx.x & 31) == 0) { atomicAdd(&jobs[j].stats[4], v); atomicAdd(&jobs[j].stats[3], en); }\n"
+           "        } else if (idx < total) {\n"
+           "            if (visits) atomicAdd(&jobs[j].stats[4], visits);\n"
+           "            if (entries) atomicAdd(&jobs[j].stats[3], entries);\n"
+           "        }\n    }\n}\n";
     return src;
 }
 
 struct JitModule {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
+    cudaKernel_t prefix = nullptr;
     int grid = 0;
+    int sms = 148;
 };
 
 }  // namespace
@@ -416,6 +478,7 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
     JitModule* m = new JitModule;
     cudaError_t e = cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->kernel, m->lib, "fs_jit_history");
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->prefix, m->lib, "fs_jit_prefix");
     if (e != cudaSuccess) {
         *err = std::string("loading the generated kernel (compiled in ") +
                std::to_string(compile_ms ? *compile_ms : 0.0) + " ms): " + cudaGetErrorString(e);
@@ -428,6 +491,7 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)m->kernel, TILE, 0);
     m->grid = (sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
+    m->sms = sms > 0 ? sms : 148;
     *handle = m;
     return 0;
 }
@@ -441,6 +505,17 @@ cudaError_t jit_launch_history(void* handle, const JobDev* d_jobs, const uint2* 
     if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
     void* args[] = {(void*)&d_jobs, (void*)&d_tiles, (void*)&n_tiles, (void*)&d_counter};
     return cudaLaunchKernel((const void*)m->kernel, dim3(grid), dim3(TILE), args, 0, s);
+}
+
+cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
+                              uint64_t total, cudaStream_t s)
+{
+    if (total == 0) return cudaSuccess;
+    JitModule* m = (JitModule*)handle;
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > (uint64_t)m->sms * 64) blocks = (uint64_t)m->sms * 64;
+    void* args[] = {(void*)&d_jobs, (void*)&d_begin, (void*)&n_jobs, (void*)&total};
+    return cudaLaunchKernel((const void*)m->prefix, dim3((unsigned)blocks), dim3(256), args, 0, s);
 }
 
 void jit_release(void* handle)
