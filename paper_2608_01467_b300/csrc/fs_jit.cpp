@@ -16,6 +16,7 @@
 // products), so both engines give bit-identical history amplitudes.
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -268,16 +269,69 @@ std::string select_factor(const double2* f, int k, const std::string& idx)
     return "sel2((" + idx + ") >= " + std::to_string(h) + "u, " + hi + ", " + lo + ")";
 }
 
+// Two-valued factor classes for exact mode: an op whose factor is A when a
+// bit expression is 0 and B when it is 1 only adds that bit to the class
+// counter k; at the end of the region the product prod A^(n-k) B^k is one
+// lookup in a table built here in extended precision.  The result is the
+// same product reassociated (within rounding), so it is used only when no
+// pruning threshold reads the running amplitude.
+struct FactorClass {
+    double2 A, B;
+    int n = 0;
+};
+
+bool same_d2(double2 a, double2 b) { return a.x == b.x && a.y == b.y; }
+
+int class_of(std::vector<FactorClass>& cls, double2 A, double2 B)
+{
+    for (size_t c = 0; c < cls.size(); ++c)
+        if (same_d2(cls[c].A, A) && same_d2(cls[c].B, B)) { cls[c].n++; return (int)c; }
+    FactorClass f;
+    f.A = A; f.B = B; f.n = 1;
+    cls.push_back(f);
+    return (int)cls.size() - 1;
+}
+
+void emit_class_table(std::string& globals, const std::string& name, const FactorClass& f)
+{
+    using cl = std::complex<long double>;
+    const cl A((long double)f.A.x, (long double)f.A.y), B((long double)f.B.x, (long double)f.B.y);
+    std::vector<cl> pa(f.n + 1), pb(f.n + 1);
+    pa[0] = pb[0] = cl(1.0L, 0.0L);
+    for (int j = 1; j <= f.n; ++j) { pa[j] = pa[j - 1] * A; pb[j] = pb[j - 1] * B; }
+    globals += "__device__ const double2 " + name + "[" + std::to_string(f.n + 1) + "] = {";
+    for (int k = 0; k <= f.n; ++k) {
+        const cl v = pa[f.n - k] * pb[k];
+        double2 d;
+        d.x = (double)v.real();
+        d.y = (double)v.imag();
+        globals += (k ? ", " : "") + std::string("{") + hexd(d.x) + ", " + hexd(d.y) + "}";
+    }
+    globals += "};\n";
+}
+
 // Body of one region: ops [e0, e1).  nbits = the region's h width.
-void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbits)
+void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
+                 int e0, int e1, int nbits)
 {
     const int W = J.W;
-    out += "    int low = " + std::to_string(nbits) + ";\n";
+    const bool defer = J.eps2 == 0.0;
+    std::vector<FactorClass> cls;
+    std::string body;
+    auto count = [&](double2 A, double2 B, const std::string& bexpr) {
+        const int c = class_of(cls, A, B);
+        return "k" + std::to_string(c) + " += (" + bexpr + ");";
+    };
+    const double2 R = make_double2(0x1.6a09e667f3bcdp-1, 0.0), mR = make_double2(-0x1.6a09e667f3bcdp-1, 0.0);
     for (int e = e0; e < e1; ++e) {
         const Op& op = J.ops[e];
         const int q0 = op.q0, q1 = op.q1;
         const double2* F = J.fac + op.aux;
         const std::string visits_cut = "{ visits += " + std::to_string(e - e0 + 1) + "ull; return low; }";
+        auto srcbit = [&](int sidx, int q) {
+            return sidx >= 0 ? "((u32)(h >> " + std::to_string(sidx) + ") & 1u)"
+                             : "((bin[" + std::to_string(q >> 5) + "] >> " + std::to_string(q & 31) + ") & 1u)";
+        };
         std::string c;
         switch (op.code) {
         case OP_X: c = flip(q0, "1u"); break;
@@ -286,7 +340,10 @@ void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbit
             c = "{ const u32 d = " + bitexpr(q0) + " ^ " + bitexpr(q1) + "; " + flip(q0, "d") + " " + flip(q1, "d") + " }";
             break;
         case OP_PERM1:
-            c = "{ const u32 o = " + bitexpr(q0) + "; a = cmul(a, " + select_factor(F, 2, "o") + "); " + flip(q0, "1u") + " }";
+            if (defer)
+                c = "{ const u32 o = " + bitexpr(q0) + "; " + count(F[0], F[1], "o") + " " + flip(q0, "1u") + " }";
+            else
+                c = "{ const u32 o = " + bitexpr(q0) + "; a = cmul(a, " + select_factor(F, 2, "o") + "); " + flip(q0, "1u") + " }";
             break;
         case OP_PERM2: {
             c = "{ const u32 o = " + bitexpr(q0) + " | (" + bitexpr(q1) + " << 1); ";
@@ -298,33 +355,44 @@ void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbit
             break;
         }
         case OP_DIAG1:
-            c = "a = cmul(a, " + select_factor(F, 2, bitexpr(q0)) + ");";
+            if (defer) c = count(F[0], F[1], bitexpr(q0));
+            else c = "a = cmul(a, " + select_factor(F, 2, bitexpr(q0)) + ");";
             break;
         case OP_PH1: {
-            const std::string m = mul_const(F[0]);
-            if (!m.empty()) c = "if (" + bitexpr(q0) + ") { " + m + " }";
+            if (defer) {
+                if (!is_one(F[0])) c = count(make_double2(1.0, 0.0), F[0], bitexpr(q0));
+            } else {
+                const std::string m = mul_const(F[0]);
+                if (!m.empty()) c = "if (" + bitexpr(q0) + ") { " + m + " }";
+            }
             break;
         }
         case OP_NEG1: c = "if (" + bitexpr(q0) + ") a = cneg(a);"; break;
         case OP_MCPH: {
-            const std::string m = mul_const(F[0]);
-            if (!m.empty()) c = "if (" + match_expr(J.masks + op.aux2, W) + ") { " + m + " }";
+            if (defer) {
+                if (!is_one(F[0])) c = count(make_double2(1.0, 0.0), F[0], "(" + match_expr(J.masks + op.aux2, W) + ") ? 1u : 0u");
+            } else {
+                const std::string m = mul_const(F[0]);
+                if (!m.empty()) c = "if (" + match_expr(J.masks + op.aux2, W) + ") { " + m + " }";
+            }
             break;
         }
         case OP_MCNEG: c = "if (" + match_expr(J.masks + op.aux2, W) + ") a = cneg(a);"; break;
         case OP_DIAG2: {
-            // RZZ-like symmetric diagonals only depend on the parity
-            const bool parity = F[0].x == F[3].x && F[0].y == F[3].y && F[1].x == F[2].x && F[1].y == F[2].y;
-            if (parity)
+            const bool parity = same_d2(F[0], F[3]) && same_d2(F[1], F[2]);
+            if (parity && defer)
+                c = count(F[0], F[1], bitexpr(q0) + " ^ " + bitexpr(q1));
+            else if (parity)
                 c = "a = cmul(a, " + select_factor(F, 2, bitexpr(q0) + " ^ " + bitexpr(q1)) + ");";
             else
                 c = "a = cmul(a, " + select_factor(F, 4, bitexpr(q0) + " | (" + bitexpr(q1) + " << 1)") + ");";
             break;
         }
         case OP_H: {
-            std::string ie = op.s0 >= 0 ? "((u32)(h >> " + std::to_string(op.s0) + ") & 1u)" : "((bin[" + std::to_string(q0 >> 5) + "] >> " + std::to_string(q0 & 31) + ") & 1u)";
-            c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + ie + "; "
-                "a = cre(a, (o & i) ? -0x1.6a09e667f3bcdp-1 : 0x1.6a09e667f3bcdp-1); " + flip(q0, "o ^ i") + " }";
+            c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + srcbit(op.s0, q0) + "; ";
+            if (defer) c += count(R, mR, "o & i") + " ";
+            else c += "a = cre(a, (o & i) ? -0x1.6a09e667f3bcdp-1 : 0x1.6a09e667f3bcdp-1); ";
+            c += flip(q0, "o ^ i") + " }";
             if (op.s0 >= 0) {
                 c += " low = " + std::to_string(op.s0) + ";";
                 if (J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
@@ -332,11 +400,13 @@ void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbit
             break;
         }
         case OP_BR1: {
-            std::string ie = op.s0 >= 0 ? "((u32)(h >> " + std::to_string(op.s0) + ") & 1u)" : "((bin[" + std::to_string(q0 >> 5) + "] >> " + std::to_string(q0 & 31) + ") & 1u)";
             bool any_zero = false;
             for (int i = 0; i < 4; ++i) any_zero |= is_zero(F[i]);
-            c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + ie + "; a = cmul(a, " +
-                select_factor(F, 4, "(o << 1) | i") + "); " + flip(q0, "o ^ i");
+            const bool sym = same_d2(F[0], F[3]) && same_d2(F[1], F[2]);
+            c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + srcbit(op.s0, q0) + "; ";
+            if (defer && sym && !any_zero) c += count(F[0], F[1], "o ^ i") + " ";
+            else c += "a = cmul(a, " + select_factor(F, 4, "(o << 1) | i") + "); ";
+            c += flip(q0, "o ^ i");
             if (op.s0 >= 0) c += " low = " + std::to_string(op.s0) + ";";
             if (any_zero) {
                 std::string zc;
@@ -349,11 +419,8 @@ void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbit
             break;
         }
         case OP_BR2: {
-            auto ie = [&](int s, int q) {
-                return s >= 0 ? "((u32)(h >> " + std::to_string(s) + ") & 1u)" : "((bin[" + std::to_string(q >> 5) + "] >> " + std::to_string(q & 31) + ") & 1u)";
-            };
-            c = "{ const u32 o = " + bitexpr(q0) + " | (" + bitexpr(q1) + " << 1); const u32 i = " + ie(op.s0, q0) +
-                " | (" + ie(op.s1, q1) + " << 1); a = cmul(a, " + select_factor(F, 16, "(o << 2) | i") + "); " +
+            c = "{ const u32 o = " + bitexpr(q0) + " | (" + bitexpr(q1) + " << 1); const u32 i = " + srcbit(op.s0, q0) +
+                " | (" + srcbit(op.s1, q1) + " << 1); a = cmul(a, " + select_factor(F, 16, "(o << 2) | i") + "); " +
                 flip(q0, "(o ^ i) & 1u") + " " + flip(q1, "((o ^ i) >> 1) & 1u");
             int lo = 99;
             if (op.s0 >= 0) lo = op.s0;
@@ -375,7 +442,15 @@ void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbit
             c = "/* unknown op */";
             break;
         }
-        if (!c.empty()) out += "    " + c + "\n";
+        if (!c.empty()) body += "    " + c + "\n";
+    }
+    out += "    int low = " + std::to_string(nbits) + ";\n";
+    for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
+    out += body;
+    for (size_t k = 0; k < cls.size(); ++k) {
+        const std::string name = "T_" + tag + "_" + std::to_string(k);
+        emit_class_table(globals, name, cls[k]);
+        out += "    a = cmul(a, __ldg(&" + name + "[k" + std::to_string(k) + "]));\n";
     }
     out += "    visits += " + std::to_string(e1 - e0) + "ull;\n    (void)low;\n    return -1;\n";
 }
@@ -383,23 +458,26 @@ void emit_region(std::string& out, const JitJobSpec& J, int e0, int e1, int nbit
 std::string generate(const std::vector<JitJobSpec>& jobs)
 {
     std::string src = kPrelude;
+    std::string globals, structs;
     for (size_t j = 0; j < jobs.size(); ++j) {
         const JitJobSpec& J = jobs[j];
-        const std::string W = std::to_string(J.W);
-        src += "struct J" + std::to_string(j) + " {\n";
-        src += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
-               std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
+        const std::string W = std::to_string(J.W), js = std::to_string(j);
+        structs += "struct J" + js + " {\n";
+        structs += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
+                   std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
         const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
-        src += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
-        emit_region(src, J, 0, J.c1, J.Ap);
-        src += "  }\n";
-        src += "  static __device__ __forceinline__ int root" + sig + " {\n    (void)h; (void)bin;\n";
-        emit_region(src, J, J.c1, J.c2, J.Ar);
-        src += "  }\n";
-        src += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
-        emit_region(src, J, J.c2, J.G, J.As);
-        src += "  }\n};\n";
+        structs += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
+        emit_region(structs, globals, js + "p", J, 0, J.c1, J.Ap);
+        structs += "  }\n";
+        structs += "  static __device__ __forceinline__ int root" + sig + " {\n    (void)h; (void)bin;\n";
+        emit_region(structs, globals, js + "r", J, J.c1, J.c2, J.Ar);
+        structs += "  }\n";
+        structs += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
+        emit_region(structs, globals, js + "s", J, J.c2, J.G, J.As);
+        structs += "  }\n};\n";
     }
+    src += globals;
+    src += structs;
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_history(const JobDev* __restrict__ jobs, "
            "const uint2* __restrict__ tiles, u64 n_tiles, unsigned int* counter)\n{\n"
            "    __shared__ unsigned int s_tile;\n    __shared__ double2 s_warp[8];\n"
