@@ -952,11 +952,51 @@ static void factor_cost(double2 f, double& iops, double& fops)
     fops += 4;
 }
 
-static void region_work(const Job& j, int e0, int e1, double& iops, double& fops)
+static bool same2(double2 a, double2 b) { return a.x == b.x && a.y == b.y; }
+
+// deferred: the straight-line engine in exact mode, where two-valued factors
+// are counted per class (1 integer add) and applied once per region (one
+// complex product per class).
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred)
 {
     const int W = j.W;
+    std::vector<std::pair<double2, double2>> classes;
+    auto defer = [&](double2 A, double2 B) {
+        iops += 1;
+        for (auto& c : classes)
+            if (same2(c.first, A) && same2(c.second, B)) return;
+        classes.push_back({A, B});
+    };
+    const double2 one = make_double2(1.0, 0.0);
+    const double2 R = make_double2(std::sqrt(0.5), 0.0), mR = make_double2(-std::sqrt(0.5), 0.0);
     for (int e = e0; e < e1; ++e) {
-        const fs::Op& op = j.prog.ops[e];
+        const fs::Op& op0 = j.prog.ops[e];
+        if (deferred) {
+            const double2* F = j.prog.fac.data() + op0.aux;
+            bool z = false;
+            switch (op0.code) {
+            case fs::OP_PERM1: iops += 2; defer(F[0], F[1]); continue;
+            case fs::OP_DIAG1: iops += 1; defer(F[0], F[1]); continue;
+            case fs::OP_PH1: iops += 1; if (!same2(F[0], one)) defer(one, F[0]); continue;
+            case fs::OP_MCPH: {
+                int nz = 0;
+                for (int w = 0; w < W; ++w) nz += (j.prog.masks[op0.aux2 + w] | j.prog.masks[op0.aux2 + W + w]) != 0;
+                iops += nz + (nz > 1 ? nz / 2 : 0) + 1;
+                if (!same2(F[0], one)) defer(one, F[0]);
+                continue;
+            }
+            case fs::OP_DIAG2:
+                if (same2(F[0], F[3]) && same2(F[1], F[2])) { iops += 2; defer(F[0], F[1]); continue; }
+                break;
+            case fs::OP_H: iops += 3; defer(R, mR); continue;
+            case fs::OP_BR1:
+                for (int k = 0; k < 4; ++k) z |= (F[k].x == 0.0 && F[k].y == 0.0);
+                if (!z && same2(F[0], F[3]) && same2(F[1], F[2])) { iops += 3; defer(F[0], F[1]); continue; }
+                break;
+            default: break;
+            }
+        }
+        const fs::Op& op = op0;
         int nz = 0;
         if (op.code == fs::OP_MCX || op.code == fs::OP_MCPH || op.code == fs::OP_MCNEG)
             for (int w = 0; w < W; ++w) nz += (j.prog.masks[op.aux2 + w] | j.prog.masks[op.aux2 + W + w]) != 0;
@@ -981,6 +1021,7 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
         default: break;
         }
     }
+    fops += 4.0 * classes.size();
 }
 
 int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, double* fp64_ops)
@@ -993,7 +1034,7 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
     const int cuts[4] = {0, j.sp.c1, j.sp.c2, G};
     for (int r = 0; r < 3; ++r) {
         double i = 0, f = 0;
-        region_work(j, cuts[r], cuts[r + 1], i, f);
+        region_work(j, cuts[r], cuts[r + 1], i, f, b->opt.engine == 0 && j.eps == 0.0);
         int_ops[r] = i;
         fp64_ops[r] = f;
     }
