@@ -137,6 +137,7 @@ typedef struct fs_stats {
     uint64_t table_entries;   /* checkpoint entries written */
     int32_t c1, c2;
     uint32_t A_p, A_r, A_s;
+    uint64_t learned_cuts;    /* checkpoint entries cut by the learned pruner */
 } fs_stats;
 
 /* Thread-local message of the last failing call on this thread. */
@@ -263,6 +264,53 @@ FS_API int fs_batch_job_words(const fs_batch* b, uint32_t job, uint32_t* words);
  * the 32-bit integer logic rate (ops/s) with short probe kernels, and
  * reports the SM count.  Allocates and frees 256 bytes of device memory. */
 FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms);
+
+/* ---- learned pruning at the checkpoint boundary ---------------------------
+ * Not in the paper: a proposal built on its checkpoint boundary (Sec. IV-C).
+ * A 16 -> 128 -> 128 -> 1 ReLU MLP scores each live checkpoint entry (the
+ * partial history after the prefix of Algorithm 2) by the predicted
+ * log10 |exact subtree sum| of its root and suffix completions; entries
+ * scoring below tau are cut and every other entry is enumerated exactly (with
+ * eps pruning as configured).  BF16 tensor-core operands, FP32 accumulation.
+ * Parameters: FS_MLP_PARAMS FP32 values in device memory, laid out W1[16][128],
+ * b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][n]: input k to output n).
+ * Features (16 FP32 per entry): |beta|, log10|beta|, Re beta/|beta|,
+ * Im beta/|beta|, log10(|beta|/eps_ref) (eps_ref = the job's eps, else 1e-6),
+ * c1/G, (A - A_p)/A, Hamming(sigma, b_in)/n, and (sigma xor b_in) on the
+ * qubits of the next 8 artificial sources after the prefix. */
+#define FS_MLP_PARAMS 18817
+
+/* y[i] = MLP(x[i]) for n rows of 16 FP32 features (device pointers). */
+FS_API int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream);
+
+/* Loss mean((y - target)^2) and its gradient: d_grad receives FS_MLP_PARAMS
+ * gradient values followed by the loss (device, FS_MLP_PARAMS + 1 floats;
+ * zeroed by the call).  Gradients are accumulated with atomics (summation
+ * order not fixed). */
+FS_API int fs_mlp_grad(const float* d_params, const float* d_x, const float* d_target, uint64_t n,
+                       float* d_grad, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 parameters with
+ * moment buffers d_m, d_v (device, FS_MLP_PARAMS floats each); step >= 1. */
+FS_API int fs_mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_grad, float lr, int32_t step,
+                       void* stream);
+
+/* Features of every checkpoint entry of a job after a run (entries = pairs x
+ * 2^A_p, 16 floats each, device; bottom entries get NaN in feature 0). */
+FS_API int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, void* stream);
+
+/* Logging runs: makes the history kernel write each (prefix, root) item's
+ * exact subtree sum (re, im doubles) into d_log (device, 2 x items doubles,
+ * items from fs_batch_log_items).  With a fixed split c1 = c2 the items are
+ * the checkpoint entries.  Call before fs_batch_upload; NULL turns it off. */
+FS_API int fs_batch_log_subtrees(fs_batch* b, uint32_t job, double* d_log);
+FS_API int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items);
+
+/* Attaches a trained pruner (device parameters, threshold tau on the
+ * predicted log10 |subtree sum|) to a job; fs_batch_run then scores and cuts
+ * checkpoint entries between the prefix and history kernels.  Call before
+ * fs_batch_upload; NULL detaches it. */
+FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau);
 
 /* ---- allocation-free variant ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

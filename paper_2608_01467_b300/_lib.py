@@ -52,7 +52,8 @@ class fs_stats(ctypes.Structure):
                 ("valid", ctypes.c_uint64), ("gate_visits", ctypes.c_uint64),
                 ("history_visits", ctypes.c_uint64),
                 ("table_entries", ctypes.c_uint64), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
-                ("A_p", ctypes.c_uint32), ("A_r", ctypes.c_uint32), ("A_s", ctypes.c_uint32)]
+                ("A_p", ctypes.c_uint32), ("A_r", ctypes.c_uint32), ("A_s", ctypes.c_uint32),
+                ("learned_cuts", ctypes.c_uint64)]
 
 
 P = ctypes.POINTER
@@ -88,10 +89,18 @@ SIGNATURES = {
     "fs_batch_job_words": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
     "fs_batch_region_work": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_double), P(ctypes.c_double)]),
     "fs_probe_peaks": (ctypes.c_int, [P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32)]),
+    "fs_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_uint64, vp, vp]),
+    "fs_mlp_grad": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, vp, vp]),
+    "fs_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int32, vp]),
+    "fs_batch_features": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp, vp]),
+    "fs_batch_log_subtrees": (ctypes.c_int, [vp, ctypes.c_uint32, vp]),
+    "fs_batch_log_items": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint64)]),
+    "fs_batch_set_pruner": (ctypes.c_int, [vp, ctypes.c_uint32, vp, ctypes.c_float]),
     "fs_amplitudes_noalloc": (ctypes.c_int, [vp, P(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_double,
                                              P(ctypes.c_double), vp]),
 }
 NOALLOC_SCRATCH_BYTES = 16 << 20
+MLP_PARAMS = 18817
 N_OPCODES = 16
 OPCODES = {1: "X", 2: "MCX", 3: "SWAP", 4: "PERM1", 5: "PERM2", 6: "DIAG1", 7: "PH1", 8: "NEG1",
            9: "MCPH", 10: "MCNEG", 11: "DIAG2", 12: "H", 13: "BR1", 14: "BR2"}

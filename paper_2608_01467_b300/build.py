@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfeynsparse.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("fs_host.cpp", "fs_jit.cpp", "fs_kernels.cu", "fs_noalloc.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("fs_host.cpp", "fs_jit.cpp", "fs_kernels.cu", "fs_mlp.cu", "fs_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "fs_internal.h"), os.path.join(ROOT, "include", "feynsparse.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

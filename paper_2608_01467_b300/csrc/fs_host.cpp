@@ -368,6 +368,11 @@ struct Job {
     int log2_ipp = 0, log2_spp = 0;
     // offsets in the workspace
     size_t o_ops = 0, o_masks = 0, o_fac = 0, o_outs = 0, o_ins = 0, o_coef = 0, o_table = 0, o_part = 0;
+    // optional: per-item subtree sums (caller device buffer) and learned pruner
+    double2* d_log = nullptr;
+    const float* d_pruner = nullptr;
+    float tau = 0;
+    fs::FeatureSpec fspec{};
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -604,6 +609,67 @@ int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, size_t n_o
     return FS_OK;
 }
 
+int fs_batch_log_subtrees(fs_batch* b, uint32_t job, double* d_log)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    b->jobs[job].d_log = (double2*)d_log;
+    b->uploaded = false;
+    return FS_OK;
+}
+
+int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items)
+{
+    if (!b || !items) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    *items = b->jobs[job].pairs << b->jobs[job].log2_ipp;
+    return FS_OK;
+}
+
+int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    b->jobs[job].d_pruner = d_params;
+    b->jobs[job].tau = tau;
+    return FS_OK;
+}
+
+int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, void* stream)
+{
+    if (!b || !d_ws || !d_features) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "no run on this workspace");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    const Job& j = b->jobs[job];
+    const fs::JobDev* jobs = (const fs::JobDev*)((unsigned char*)d_ws + b->o_jobs);
+    CUDA_TRY(fs::mlp_features(jobs, (int)job, j.fspec, d_features, j.table_entries, (cudaStream_t)stream));
+    return FS_OK;
+}
+
+int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream)
+{
+    if (!d_params || (n && (!d_x || !d_y))) return fail(FS_ERR_INVALID, "NULL argument");
+    CUDA_TRY(fs::mlp_forward(d_params, d_x, (long long)n, d_y, (cudaStream_t)stream));
+    return FS_OK;
+}
+
+int fs_mlp_grad(const float* d_params, const float* d_x, const float* d_target, uint64_t n, float* d_grad,
+                void* stream)
+{
+    if (!d_params || !d_grad || (n && (!d_x || !d_target))) return fail(FS_ERR_INVALID, "NULL argument");
+    CUDA_TRY(fs::mlp_grad(d_params, d_x, d_target, (long long)n, d_grad, (cudaStream_t)stream));
+    return FS_OK;
+}
+
+int fs_mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_grad, float lr, int32_t step, void* stream)
+{
+    if (!d_params || !d_m || !d_v || !d_grad) return fail(FS_ERR_INVALID, "NULL argument");
+    if (step < 1) return fail(FS_ERR_INVALID, "Adam step counts from 1");
+    CUDA_TRY(fs::mlp_adam(d_params, d_m, d_v, d_grad, lr, step, (cudaStream_t)stream));
+    return FS_OK;
+}
+
 int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes)
 {
     if (!b || !bytes) return fail(FS_ERR_INVALID, "NULL argument");
@@ -675,6 +741,21 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         if (j.sp.Ap + j.sp.Ar + ilog2_ceil(std::max<uint64_t>(j.pairs, 1)) > 40)
             return fail(FS_ERR_TOO_LARGE, "job %zu: too many (prefix, root) items", ji);
         compile(C, j.W, j.sp, j.prog);
+        {
+            fs::FeatureSpec& f = j.fspec;
+            f.log10_eps_ref = (float)std::log10(j.eps > 0 ? j.eps : 1e-6);
+            f.depth = G ? (float)j.sp.c1 / (float)G : 0.f;
+            f.remaining = C.A ? (float)(C.A - j.sp.Ap) / (float)C.A : 0.f;
+            f.n_qubits = (int)C.n;
+            for (int k = 0; k < 8; ++k) f.next_qubits[k] = -1;
+            int nk = 0;
+            for (int e = j.sp.c1; e < G && nk < 8; ++e) {
+                const GateInfo& gi = C.g[G - 1 - e];
+                if (gi.role != BR) continue;
+                for (int t = 0; t < gi.k && nk < 8; ++t)
+                    if (gi.src[t] >= 0) f.next_qubits[nk++] = gi.q[t];
+            }
+        }
         j.log2_ipp = j.sp.Ap + j.sp.Ar;
         j.log2_spp = std::max(0, j.log2_ipp - fs::TILE_LOG2);
         j.table_entries = j.pairs << j.sp.Ap;
@@ -774,6 +855,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.out_begin = oacc;
         d.n_tiles = j.n_tiles;
         d.eps2 = j.eps * j.eps;
+        d.log = j.d_log;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
         pacc += j.table_entries;
@@ -867,6 +949,11 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     else
         CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
                                    (uint32_t*)(base + b->o_err), s));
+    for (int ji = 0; ji < nj; ++ji) {
+        const Job& j = b->jobs[ji];
+        if (j.d_pruner)
+            CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries, s));
+    }
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));
     if (b->jit)
         CUDA_TRY(fs::jit_launch_history(b->jit, jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
@@ -912,6 +999,7 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
             o.gate_visits = q[2] + q[4];
             o.history_visits = q[2];
             o.table_entries = q[3];
+            o.learned_cuts = q[5];
             o.c1 = j.sp.c1; o.c2 = j.sp.c2;
             o.A_p = (uint32_t)j.sp.Ap; o.A_r = (uint32_t)j.sp.Ar; o.A_s = (uint32_t)j.sp.As;
         }

@@ -83,7 +83,8 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     uint64_t prefix_begin;     /* offset of this job in the flat prefix index space */ \
     uint64_t out_begin;        /* offset of this job's outputs in amp_out */ \
     uint64_t n_tiles;                                                         \
-    double eps2;               /* eps^2 (0: exact) */
+    double eps2;               /* eps^2 (0: exact) */                         \
+    double2* log;              /* optional: per-item subtree sums (logging runs) */
 
 struct JobDev {
     FS_JOBDEV_FIELDS
@@ -92,7 +93,27 @@ struct JobDev {
 constexpr int TILE_LOG2 = 8;             // items per tile = threads per CTA
 constexpr int TILE = 1 << TILE_LOG2;
 constexpr int REDUCE_THREADS = 128;
-constexpr int STATS_PER_JOB = 8;
+constexpr int STATS_PER_JOB = 8;   // completed, valid, hist visits, entries, prefix visits, learned cuts
+constexpr int MLP_PARAMS = 18817;
+
+// Per-job constants of the learned pruner's features.
+struct FeatureSpec {
+    float log10_eps_ref;
+    float depth;           // c1 / G
+    float remaining;       // (A - A_p) / A
+    int n_qubits;
+    int next_qubits[8];    // targets of the next 8 artificial sources after the prefix (-1: none)
+};
+
+cudaError_t mlp_forward(const float* d_params, const float* d_x, long long n, float* d_y, cudaStream_t s);
+cudaError_t mlp_grad(const float* d_params, const float* d_x, const float* d_t, long long n, float* d_grad,
+                     cudaStream_t s);
+cudaError_t mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_grad, float lr, int step,
+                     cudaStream_t s);
+cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, float* d_feat,
+                         unsigned long long n_entries, cudaStream_t s);
+cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
+                              float tau, unsigned long long n_entries, cudaStream_t s);
 
 // Device error word values.
 constexpr uint32_t DEV_ERR_BAD_OPCODE = 1;

@@ -127,6 +127,7 @@ __device__ void tile_body(const JobDev& J, u64 tile, double2* s_warp)
             }
         }
     }
+    if (J.log && active) J.log[item] = acc;
     completed = warp_sum_u64(completed);
     valid = warp_sum_u64(valid);
     visits = warp_sum_u64(visits);

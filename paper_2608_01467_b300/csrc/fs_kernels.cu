@@ -345,6 +345,7 @@ __device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err, doub
             }
         }
     }
+    if (J.log && active) J.log[item] = acc;
     // counters: one atomic per warp
     completed = warp_sum_u64(completed);
     valid = warp_sum_u64(valid);

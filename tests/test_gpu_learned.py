@@ -1,0 +1,114 @@
+"""Learned pruning: the MLP kernels against the CPU reference MLP, Adam, the
+logging run, and the pruner end to end (cuts nothing at tau = -inf; keeps
+the fidelity bar at a tuned tau)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import mlp_init_params, qaoa_workload
+from oracle import closed_forms, mlp as omlp
+import paper_2608_01467_b300 as fs
+from paper_2608_01467_b300 import learned
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def test_mlp_forward_matches_cpu_reference():
+    rng = np.random.default_rng(1)
+    p = mlp_init_params(11)
+    X = rng.normal(size=(1003, 16)).astype(np.float32)
+    y = learned.forward(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    want, _ = omlp.forward(p, X)
+    assert rel_err(y, want) < 1e-2
+    assert np.max(np.abs(y - want)) < 2e-2 * np.max(np.abs(want))
+
+
+def test_mlp_gradient_matches_cpu_reference():
+    rng = np.random.default_rng(2)
+    p = mlp_init_params(12)
+    p[2048:2176] = rng.normal(size=128) * 0.1
+    p[18560:18688] = rng.normal(size=128) * 0.1
+    X = rng.normal(size=(777, 16)).astype(np.float32)
+    T = rng.normal(size=777).astype(np.float32)
+    g, loss = learned.grad(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    g = g.cpu().numpy()
+    wl, wg = omlp.loss_and_grad(p, X, T)
+    assert abs(float(loss) - wl) < 1e-3 * abs(wl)
+    for name, (lo, hi) in {"W1": (0, 2048), "b1": (2048, 2176), "W2": (2176, 18560), "b2": (18560, 18688),
+                           "w3": (18688, 18816), "b3": (18816, 18817)}.items():
+        assert rel_err(g[lo:hi], wg[lo:hi]) < 2e-2, name
+
+
+def test_adam_step_matches_formula():
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=18817).astype(np.float32)
+    g = rng.normal(size=18817).astype(np.float32)
+    P, M, V = (torch.from_numpy(p).cuda(), torch.zeros(18817, device="cuda"), torch.zeros(18817, device="cuda"))
+    G = torch.from_numpy(g).cuda()
+    for step in (1, 2):
+        learned.adam_step(P, M, V, G, 1e-3, step)
+    m = 0.0
+    v = 0.0
+    q = p.astype(np.float64)
+    for step in (1, 2):
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        q = q - 1e-3 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
+    assert np.max(np.abs(P.cpu().numpy() - q)) < 1e-5
+
+
+def test_training_reduces_loss_on_a_known_target():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(8192, 16)).astype(np.float32)
+    T = (X[:, 0] * 0.7 - np.abs(X[:, 3]) + 0.3 * X[:, 8] * X[:, 9]).astype(np.float32)
+    x, t = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    _, l0 = learned.grad(torch.from_numpy(mlp_init_params(5)).cuda(), x, t)
+    p, losses = learned.train(x, t, mlp_init_params(5), steps=300, batch=2048, lr=3e-3)
+    _, l1 = learned.grad(p, x, t)
+    assert float(l1) < 0.1 * float(l0)
+
+
+def _run(w, outs, cut, eps=0.0, pruner=None, tau=0.0):
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    b = fs.Batch(split="fixed", c1=cut, c2=cut)
+    b.add(C, outs, eps)
+    b.plan()
+    if pruner is not None:
+        learned.attach(b, 0, pruner, tau)
+    b.allocate()
+    b.upload()
+    b.run()
+    st = b.finish()[0]
+    return b.amp.cpu().numpy()[:len(outs)], st
+
+
+def test_learned_pruner_end_to_end():
+    n = 12
+    w = qaoa_workload(n, 2, n_out=128, seed=21)
+    cut = n                                  # after the last RX layer (A_p = n)
+    x, t, st = learned.log_training_data(w.circuit, w.inputs, w.outputs[:64], cut)
+    assert x.shape[0] == 64 * (1 << n) and st["valid"] == 64 * (1 << 24)
+    params, losses = learned.train(x, t, mlp_init_params(0), steps=300, batch=4096, lr=2e-3)
+    assert losses[-1] < losses[0]
+    held = w.outputs[64:]
+    exact, st_ex = _run(w, held, cut)
+    # tau below every prediction: nothing is cut, the result is the exact one
+    a, st0 = _run(w, held, cut, pruner=params, tau=-1e30)
+    assert st0["learned_cuts"] == 0 and np.array_equal(a, exact)
+    # some tau keeps fidelity >= 0.999 while cutting checkpoint entries
+    best = None
+    for tau in (-9.0, -8.0, -7.0, -6.0, -5.5, -5.0):
+        a, s = _run(w, held, cut, pruner=params, tau=tau)
+        F = closed_forms.fidelity(exact, a)
+        if F >= 0.999:
+            best = (tau, F, s["learned_cuts"], s["completed"])
+    assert best is not None and best[2] > 0, best

@@ -5,6 +5,7 @@ strings from splitmix64 streams.  It holds none of the method's arithmetic:
 no gate matrices, no propagation and no amplitudes.  Both the oracle and the
 library convert these neutral records into their own representations.
 """
+from .mlp_init import mlp_init_params  # noqa: F401
 from .circuits import (  # noqa: F401
     Gate, Circuit, Workload, SplitMix64,
     qft, amplitude_amplification, qaoa_maxcut, quantum_walk,
