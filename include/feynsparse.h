@@ -138,6 +138,7 @@ typedef struct fs_stats {
     int32_t c1, c2;
     uint32_t A_p, A_r, A_s;
     uint64_t learned_cuts;    /* checkpoint entries cut by the learned pruner */
+    uint64_t live_entries;    /* checkpoint entries enumerated by the history kernel */
 } fs_stats;
 
 /* Thread-local message of the last failing call on this thread. */
@@ -231,7 +232,10 @@ FS_API int fs_batch_engine(const fs_batch* b, uint32_t* engine, double* compile_
 /* Total outputs over the jobs added so far. */
 FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
 
-/* Number of kernel launches fs_batch_run enqueues. */
+/* Number of kernel launches fs_batch_run enqueues (prefix, reduce, the tiled
+ * history kernel when any job is exact, and per pruned job a learned-prune
+ * launch if attached plus count/scan/write compaction and the history over
+ * live entries). */
 FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
 
 /* Average duration of the history kernel of the last fs_batch_run that
@@ -309,7 +313,9 @@ FS_API int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items);
 /* Attaches a trained pruner (device parameters, threshold tau on the
  * predicted log10 |subtree sum|) to a job; fs_batch_run then scores and cuts
  * checkpoint entries between the prefix and history kernels.  Call before
- * fs_batch_upload; NULL detaches it. */
+ * fs_batch_plan (it changes the job's layout); NULL detaches it.  Jobs with a
+ * pruner or eps > 0 run the history over the compacted list of live
+ * checkpoint entries, so cut entries cost nothing downstream. */
 FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau);
 
 /* ---- allocation-free variant ---------------------------------------------

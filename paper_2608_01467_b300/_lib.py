@@ -53,7 +53,7 @@ class fs_stats(ctypes.Structure):
                 ("history_visits", ctypes.c_uint64),
                 ("table_entries", ctypes.c_uint64), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
                 ("A_p", ctypes.c_uint32), ("A_r", ctypes.c_uint32), ("A_s", ctypes.c_uint32),
-                ("learned_cuts", ctypes.c_uint64)]
+                ("learned_cuts", ctypes.c_uint64), ("live_entries", ctypes.c_uint64)]
 
 
 P = ctypes.POINTER

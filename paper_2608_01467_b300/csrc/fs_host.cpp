@@ -373,6 +373,10 @@ struct Job {
     const float* d_pruner = nullptr;
     float tau = 0;
     fs::FeatureSpec fspec{};
+    // pruned jobs (eps > 0 or a learned pruner) run over compacted live entries
+    bool compact = false;
+    size_t o_live = 0, o_esum = 0, o_blk = 0;
+    uint64_t nblk = 0;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -389,7 +393,7 @@ struct fs_batch {
     std::vector<unsigned char> host_static;
     std::vector<uint2> tiles;
     uint64_t total_prefix = 0, total_out = 0;
-    int grid = 0;
+    int grid = 0, compact_grid = 0;
     void* uploaded_ws = nullptr;
     bool timing = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -633,6 +637,8 @@ int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float 
     if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
     b->jobs[job].d_pruner = d_params;
     b->jobs[job].tau = tau;
+    b->planned = b->uploaded = false;   // the job's layout changes: plan again
+    b->drop_jit();
     return FS_OK;
 }
 
@@ -756,12 +762,14 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
                     if (gi.src[t] >= 0) f.next_qubits[nk++] = gi.q[t];
             }
         }
+        j.compact = j.eps > 0.0 || j.d_pruner != nullptr;
         j.log2_ipp = j.sp.Ap + j.sp.Ar;
         j.log2_spp = std::max(0, j.log2_ipp - fs::TILE_LOG2);
         j.table_entries = j.pairs << j.sp.Ap;
-        j.n_partials = j.pairs << j.log2_spp;
+        j.n_partials = j.compact ? 0 : (j.pairs << j.log2_spp);
         const uint64_t items = j.pairs << j.log2_ipp;
-        j.n_tiles = (items + fs::TILE - 1) / fs::TILE;
+        j.n_tiles = j.compact ? 0 : (items + fs::TILE - 1) / fs::TILE;
+        j.nblk = j.compact ? (j.table_entries + fs::COMPACT_BLOCK - 1) / fs::COMPACT_BLOCK : 0;
         if (j.n_tiles >= (1ull << 32)) return fail(FS_ERR_TOO_LARGE, "job %zu: too many tiles", ji);
         b->total_prefix += j.table_entries;
         b->total_out += j.outs.size();
@@ -804,6 +812,11 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     for (Job& j : b->jobs) {
         j.o_table = take(j.table_entries * sizeof(fs::Entry));
         j.o_part = take(j.n_partials * sizeof(double2));
+        if (j.compact) {
+            j.o_live = take(j.table_entries * sizeof(uint64_t));
+            j.o_esum = take(j.table_entries * sizeof(double2));
+            j.o_blk = take(j.nblk * sizeof(uint32_t));
+        }
     }
     b->ws_bytes = off;
     *workspace_bytes = off;
@@ -813,6 +826,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     int dev = 0;
     cudaGetDevice(&dev);
     b->grid = fs::history_grid_size(dev);
+    b->compact_grid = fs::compact_grid_size(dev);
     return FS_OK;
 }
 
@@ -856,6 +870,11 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.n_tiles = j.n_tiles;
         d.eps2 = j.eps * j.eps;
         d.log = j.d_log;
+        d.compact = j.compact ? 1 : 0;
+        d.live = j.compact ? (uint64_t*)(base + j.o_live) : nullptr;
+        d.esum = j.compact ? (double2*)(base + j.o_esum) : nullptr;
+        d.blk = j.compact ? (uint32_t*)(base + j.o_blk) : nullptr;
+        d.n_entries = j.table_entries;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
         pacc += j.table_entries;
@@ -882,7 +901,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
             const Job& j = b->jobs[ji];
             specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
                                        j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
-                                       j.sp.As, j.eps * j.eps};
+                                       j.sp.As, j.eps * j.eps, j.compact};
         }
         std::string err, src;
         const char* dump = getenv("FS_JIT_DUMP");   // optional: write the generated source here
@@ -905,7 +924,14 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
 int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
 {
     if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
-    *n = 3;   // prefix, history, reduce
+    uint32_t k = 2;   // prefix, reduce
+    bool tiled = false;
+    for (const Job& j : b->jobs) {
+        tiled |= !j.compact;
+        if (j.d_pruner) k += 1;                 // learned prune
+        if (j.compact) k += 4;                  // count, scan, write, history over live entries
+    }
+    *n = k + (tiled ? 1 : 0);
     return FS_OK;
 }
 
@@ -954,13 +980,22 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
         if (j.d_pruner)
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries, s));
     }
+    for (int ji = 0; ji < nj; ++ji)
+        if (b->jobs[ji].compact) CUDA_TRY(fs::launch_compact(jobs + ji, b->jobs[ji].table_entries, s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));
-    if (b->jit)
+    if (b->tiles.empty()) {
+        // no tiled (exact) job: nothing to launch
+    } else if (b->jit)
         CUDA_TRY(fs::jit_launch_history(b->jit, jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
                                         (unsigned int*)(base + b->o_counter), s));
     else
         CUDA_TRY(fs::launch_history(jobs, (const uint2*)(base + b->o_tiles), b->tiles.size(),
                                     (unsigned int*)(base + b->o_counter), (uint32_t*)(base + b->o_err), b->grid, s));
+    for (int ji = 0; ji < nj; ++ji) {
+        if (!b->jobs[ji].compact) continue;
+        if (b->jit) CUDA_TRY(fs::jit_launch_compact(b->jit, jobs, ji, s));
+        else CUDA_TRY(fs::launch_history_compact(jobs + ji, (uint32_t*)(base + b->o_err), b->compact_grid, s));
+    }
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[2], s));
     CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
                                (double2*)d_amp_out, s));
@@ -1000,6 +1035,7 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
             o.history_visits = q[2];
             o.table_entries = q[3];
             o.learned_cuts = q[5];
+            o.live_entries = j.compact ? q[6] : q[3];
             o.c1 = j.sp.c1; o.c2 = j.sp.c2;
             o.A_p = (uint32_t)j.sp.Ap; o.A_r = (uint32_t)j.sp.Ar; o.A_s = (uint32_t)j.sp.As;
         }

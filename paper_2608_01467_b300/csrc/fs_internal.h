@@ -84,7 +84,13 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     uint64_t out_begin;        /* offset of this job's outputs in amp_out */ \
     uint64_t n_tiles;                                                         \
     double eps2;               /* eps^2 (0: exact) */                         \
-    double2* log;              /* optional: per-item subtree sums (logging runs) */
+    double2* log;              /* optional: per-item subtree sums (logging runs) */     \
+    int32_t compact;           /* 1: history over the compacted live entries */         \
+    int32_t pad1;                                                             \
+    uint64_t* live;            /* compacted live entry indices, table order */            \
+    double2* esum;             /* subtree sum per live entry */                          \
+    uint32_t* blk;             /* per compaction block: live count, then offset */       \
+    uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */
 
 struct JobDev {
     FS_JOBDEV_FIELDS
@@ -93,7 +99,9 @@ struct JobDev {
 constexpr int TILE_LOG2 = 8;             // items per tile = threads per CTA
 constexpr int TILE = 1 << TILE_LOG2;
 constexpr int REDUCE_THREADS = 128;
-constexpr int STATS_PER_JOB = 8;   // completed, valid, hist visits, entries, prefix visits, learned cuts
+constexpr int STATS_PER_JOB = 8;   // completed, valid, hist visits, entries, prefix visits, learned cuts,
+                                   // live entries after compaction, compact work counter
+constexpr int COMPACT_BLOCK = 1024;   // entries per compaction block (256 threads x 4)
 constexpr int MLP_PARAMS = 18817;
 
 // Per-job constants of the learned pruner's features.
@@ -123,6 +131,10 @@ cudaError_t launch_prefix(const JobDev* d_jobs, const uint64_t* d_job_prefix_beg
                           uint64_t total_prefix, uint32_t* d_err, cudaStream_t s);
 cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
                            unsigned int* d_counter, uint32_t* d_err, int grid, cudaStream_t s);
+cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t s);
+cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s);
+int compact_grid_size(int device);
+cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s);
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, cudaStream_t s);
 int history_grid_size(int device);
@@ -136,6 +148,7 @@ struct JitJobSpec {
     const double2* fac;
     int W, c1, c2, Ap, Ar, As;
     double eps2;
+    bool compact;
 };
 int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
               std::string* source_out);

@@ -171,6 +171,62 @@ __device__ void tile_body(const JobDev& J, u64 tile, double2* s_warp)
     }
 }
 
+template <class T>
+__device__ void compact_body(const JobDev& J, u64 i, u64& completed, u64& valid, u64& visits)
+{
+    constexpr int W = T::W;
+    const u64 e = J.live[i];
+    const u64 pair = e >> T::Ap;
+    const u64 o = pair / (u64)J.S;
+    const u64 sidx = pair - o * (u64)J.S;
+    const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
+    const uint4 sv = __ldg(ent);
+    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
+    const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+    const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+    u32 st0[W], bin[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) { st0[j] = tmp[j]; bin[j] = btmp[j]; }
+    double2 acc = make_double2(0.0, 0.0);
+    for (u64 hr = 0; hr < (1ull << T::Ar); ++hr) {
+        u32 st[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) st[j] = st0[j];
+        double2 amp = a0;
+        const int r = T::root(st, amp, hr, bin, visits);
+        if (r >= 0) {
+            hr = ((hr >> r) + 1ull) << r;
+            --hr;
+            continue;
+        }
+        const u64 ns = 1ull << T::As;
+        u64 hs = 0;
+        while (hs < ns) {
+            u32 st2[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) st2[j] = st[j];
+            double2 amp2 = amp;
+            const int r2 = T::suffix(st2, amp2, hs, bin, visits);
+            if (r2 < 0) {
+                ++completed;
+                u32 d = 0;
+#pragma unroll
+                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
+                if (d == 0) {
+                    ++valid;
+                    acc.x += amp2.x;
+                    acc.y += amp2.y;
+                }
+                ++hs;
+            } else {
+                hs = ((hs >> r2) + 1ull) << r2;
+            }
+        }
+    }
+    J.esum[i] = acc;
+}
+
 __device__ __forceinline__ int find_job(const u64* __restrict__ begin, int n_jobs, u64 idx)
 {
     int lo = 0, hi = n_jobs - 1;
@@ -491,6 +547,20 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
         src += "        case " + std::to_string(j) + "u: tile_body<J" + std::to_string(j) + ">(jobs[" +
                std::to_string(j) + "], td.y, s_warp); break;\n";
     src += "        default: break;\n        }\n    }\n}\n";
+    src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job)\n{\n"
+           "    const JobDev& J = jobs[job];\n    const u64 nlive = J.stats[6];\n    const int lane = threadIdx.x & 31;\n"
+           "    u64 completed = 0, valid = 0, visits = 0;\n    for (;;) {\n"
+           "        u64 base = 0;\n        if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);\n"
+           "        base = __shfl_sync(0xffffffffu, base, 0);\n        if (base >= nlive) break;\n"
+           "        const u64 i = base + lane;\n        if (i < nlive) {\n            switch (job) {\n";
+    for (size_t j = 0; j < jobs.size(); ++j)
+        if (jobs[j].compact)
+            src += "            case " + std::to_string(j) + ": compact_body<J" + std::to_string(j) +
+                   ">(J, i, completed, valid, visits); break;\n";
+    src += "            default: break;\n            }\n        }\n    }\n"
+           "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
+           "    if (lane == 0 && (completed | valid | visits)) {\n"
+           "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_prefix(const JobDev* __restrict__ jobs, "
            "const u64* __restrict__ begin, int n_jobs, u64 total)\n{\n"
            "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (u64)gridDim.x * blockDim.x) {\n"
@@ -518,6 +588,8 @@ struct JitModule {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
     cudaKernel_t prefix = nullptr;
+    cudaKernel_t compact = nullptr;
+    int compact_grid = 0;
     int grid = 0;
     int sms = 148;
 };
@@ -558,6 +630,7 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
     cudaError_t e = cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->kernel, m->lib, "fs_jit_history");
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->prefix, m->lib, "fs_jit_prefix");
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->compact, m->lib, "fs_jit_compact");
     if (e != cudaSuccess) {
         *err = std::string("loading the generated kernel (compiled in ") +
                std::to_string(compile_ms ? *compile_ms : 0.0) + " ms): " + cudaGetErrorString(e);
@@ -571,6 +644,9 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)m->kernel, TILE, 0);
     m->grid = (sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
     m->sms = sms > 0 ? sms : 148;
+    per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)m->compact, TILE, 0);
+    m->compact_grid = m->sms * (per_sm > 0 ? per_sm : 1);
     *handle = m;
     return 0;
 }
@@ -595,6 +671,13 @@ cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t
     if (blocks > (uint64_t)m->sms * 64) blocks = (uint64_t)m->sms * 64;
     void* args[] = {(void*)&d_jobs, (void*)&d_begin, (void*)&n_jobs, (void*)&total};
     return cudaLaunchKernel((const void*)m->prefix, dim3((unsigned)blocks), dim3(256), args, 0, s);
+}
+
+cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s)
+{
+    JitModule* m = (JitModule*)handle;
+    void* args[] = {(void*)&d_jobs, (void*)&job};
+    return cudaLaunchKernel((const void*)m->compact, dim3(m->compact_grid), dim3(TILE), args, 0, s);
 }
 
 void jit_release(void* handle)

@@ -411,6 +411,194 @@ __global__ void __launch_bounds__(TILE) history_kernel(const JobDev* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- compaction
+
+// Live (non-bottom) checkpoint entries are compacted into a list in table
+// order: count per block, exclusive scan of the block counts, write.
+__device__ __forceinline__ bool entry_live(const JobDev& J, uint64_t e)
+{
+    return !isnan(reinterpret_cast<const double2*>(reinterpret_cast<const uint4*>(J.table + e) + 1)->x);
+}
+
+__global__ void __launch_bounds__(256) compact_count_kernel(const JobDev* __restrict__ jobp)
+{
+    const JobDev& J = *jobp;
+    const uint64_t base = (uint64_t)blockIdx.x * COMPACT_BLOCK;
+    unsigned c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
+        c += (e < J.n_entries && entry_live(J, e)) ? 1u : 0u;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ unsigned s_w[8];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < 8; ++w) t += s_w[w];
+        J.blk[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) compact_scan_kernel(const JobDev* __restrict__ jobp, uint32_t nblk)
+{
+    const JobDev& J = *jobp;
+    __shared__ unsigned long long s_carry;
+    __shared__ unsigned s_w[32];
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < nblk; b0 += 1024) {
+        const uint32_t b = b0 + threadIdx.x;
+        const unsigned v = b < nblk ? J.blk[b] : 0u;
+        unsigned x = v;   // inclusive warp scan
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+            if ((threadIdx.x & 31) >= (unsigned)off) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            unsigned w = s_w[threadIdx.x];
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, w, off);
+                if (threadIdx.x >= (unsigned)off) w += y;
+            }
+            s_w[threadIdx.x] = w;   // inclusive scan of warp totals
+        }
+        __syncthreads();
+        const unsigned warp_off = (threadIdx.x >> 5) ? s_w[(threadIdx.x >> 5) - 1] : 0u;
+        const unsigned long long excl = s_carry + warp_off + x - v;
+        if (b < nblk) J.blk[b] = (uint32_t)excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) J.stats[6] = s_carry;
+}
+
+__global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __restrict__ jobp)
+{
+    const JobDev& J = *jobp;
+    const uint64_t base = (uint64_t)blockIdx.x * COMPACT_BLOCK;
+    bool lv[4];
+    unsigned c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
+        lv[k] = e < J.n_entries && entry_live(J, e);
+        c += lv[k];
+    }
+    unsigned x = c;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+        if ((threadIdx.x & 31) >= (unsigned)off) x += y;
+    }
+    __shared__ unsigned s_w[8];
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned woff = 0;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) woff += s_w[w];
+    uint64_t pos = (uint64_t)J.blk[blockIdx.x] + woff + x - c;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (lv[k]) J.live[pos++] = base + (uint64_t)threadIdx.x * 4 + k;
+}
+
+// History over the compacted live entries: a warp takes 32 consecutive
+// live entries off the job's work counter; each thread runs all 2^A_r root
+// assignments of its entry and the suffix of each, and writes the entry's
+// subtree sum (one slot per live entry: fixed reduction order downstream).
+template <int W>
+__device__ void compact_entry(const JobDev& J, uint64_t i, uint32_t* err, unsigned long long& completed,
+                              unsigned long long& valid, unsigned long long& visits)
+{
+    const uint64_t e = J.live[i];
+    const uint64_t pair = e >> J.Ap;
+    const uint64_t o = pair / (uint64_t)J.S;
+    const uint64_t s = pair - o * (uint64_t)J.S;
+    const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
+    const uint4 sv = __ldg(ent);
+    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    uint32_t st0[W], bin[W];
+    const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+    for (int j = 0; j < W; ++j) st0[j] = tmp[j];
+    load_bits<W>(J.ins + 4 * s, bin);
+    double2 acc = make_double2(0.0, 0.0);
+    for (uint64_t hr = 0; hr < (1ull << J.Ar); ++hr) {
+        uint32_t st[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) st[j] = st0[j];
+        double2 amp = a0;
+        const int r = run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err);
+        if (r >= 0) {
+            hr = ((hr >> r) + 1ull) << r;
+            --hr;
+            continue;
+        }
+        const uint64_t ns = 1ull << J.As;
+        uint64_t hs = 0;
+        while (hs < ns) {
+            uint32_t st2[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) st2[j] = st[j];
+            double2 amp2 = amp;
+            const int r2 = run_ops<W>(J, J.c2, J.G, st2, amp2, hs, J.As, bin, visits, err);
+            if (r2 < 0) {
+                ++completed;
+                if (same<W>(st2, bin)) {
+                    ++valid;
+                    acc.x += amp2.x;
+                    acc.y += amp2.y;
+                }
+                ++hs;
+            } else {
+                hs = ((hs >> r2) + 1ull) << r2;
+            }
+        }
+    }
+    J.esum[i] = acc;
+}
+
+__global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __restrict__ jobp, uint32_t* err)
+{
+    const JobDev& J = *jobp;
+    const uint64_t nlive = J.stats[6];
+    const int lane = threadIdx.x & 31;
+    unsigned long long completed = 0, valid = 0, visits = 0;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= nlive) break;
+        const uint64_t i = base + lane;
+        if (i < nlive) {
+            if (J.W == 1) compact_entry<1>(J, i, err, completed, valid, visits);
+            else if (J.W == 2) compact_entry<2>(J, i, err, completed, valid, visits);
+            else compact_entry<4>(J, i, err, completed, valid, visits);
+        }
+    }
+    completed = warp_sum_u64(completed);
+    valid = warp_sum_u64(valid);
+    visits = warp_sum_u64(visits);
+    if (lane == 0 && (completed | valid | visits)) {
+        atomicAdd(&J.stats[0], completed);
+        atomicAdd(&J.stats[1], valid);
+        atomicAdd(&J.stats[2], visits);
+    }
+}
+
+__device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t* __restrict__ a, uint64_t n, uint64_t key)
+{
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------- reduce
 
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
@@ -425,12 +613,24 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
         double2 amp = make_double2(0.0, 0.0);
         const uint64_t nslots = 1ull << J.log2_spp;
         for (int s = 0; s < J.S; ++s) {
-            const uint64_t base = ((o * (uint64_t)J.S + (uint64_t)s) << J.log2_spp);
+            const uint64_t pair = o * (uint64_t)J.S + (uint64_t)s;
             double2 t = make_double2(0.0, 0.0);
-            for (uint64_t k = threadIdx.x; k < nslots; k += REDUCE_THREADS) {
-                const double2 v = J.partials[base + k];
-                t.x += v.x;
-                t.y += v.y;
+            if (J.compact) {
+                const uint64_t nlive = J.stats[6];
+                const uint64_t lo = lower_bound_u64(J.live, nlive, pair << J.Ap);
+                const uint64_t hi = lower_bound_u64(J.live, nlive, (pair + 1) << J.Ap);
+                for (uint64_t k = lo + threadIdx.x; k < hi; k += REDUCE_THREADS) {
+                    const double2 v = J.esum[k];
+                    t.x += v.x;
+                    t.y += v.y;
+                }
+            } else {
+                const uint64_t base = pair << J.log2_spp;
+                for (uint64_t k = threadIdx.x; k < nslots; k += REDUCE_THREADS) {
+                    const double2 v = J.partials[base + k];
+                    t.x += v.x;
+                    t.y += v.y;
+                }
             }
             s_red[threadIdx.x] = t;
             __syncthreads();
@@ -551,6 +751,30 @@ cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t 
     if (n_tiles == 0) return cudaSuccess;
     if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
     history_kernel<<<grid, TILE, 0, s>>>(d_jobs, d_tiles, n_tiles, d_counter, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t s)
+{
+    const uint64_t nblk = (n_entries + COMPACT_BLOCK - 1) / COMPACT_BLOCK;
+    if (nblk == 0) return cudaSuccess;
+    compact_count_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
+    compact_scan_kernel<<<1, 1024, 0, s>>>(d_job, (uint32_t)nblk);
+    compact_write_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
+    return cudaGetLastError();
+}
+
+int compact_grid_size(int device)
+{
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, history_compact_kernel, 256, 0);
+    return (sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
+}
+
+cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s)
+{
+    history_compact_kernel<<<grid, 256, 0, s>>>(d_job, d_err);
     return cudaGetLastError();
 }
 

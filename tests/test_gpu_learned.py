@@ -81,9 +81,9 @@ def _run(w, outs, cut, eps=0.0, pruner=None, tau=0.0):
     C.set_input(w.inputs)
     b = fs.Batch(split="fixed", c1=cut, c2=cut)
     b.add(C, outs, eps)
-    b.plan()
     if pruner is not None:
         learned.attach(b, 0, pruner, tau)
+    b.plan()
     b.allocate()
     b.upload()
     b.run()
