@@ -349,11 +349,41 @@ __global__ void adam_kernel(float* __restrict__ P, float* __restrict__ M, float*
 
 // ---------------------------------------------------------------- features
 
+// 1 + log2 |x - y| (0 when x = y) of two 128-bit registers read as unsigned
+// integers (qubit q = bit q); the fraction comes from the 32 bits below the
+// leading one.
+__device__ __forceinline__ float log2_distance(const uint32_t* x, const uint32_t* y)
+{
+    uint32_t d[4];
+    bool ge = true;   // x >= y ?
+    for (int w = 3; w >= 0; --w) {
+        if (x[w] != y[w]) { ge = x[w] > y[w]; break; }
+    }
+    const uint32_t* a = ge ? x : y;
+    const uint32_t* b = ge ? y : x;
+    unsigned long long borrow = 0;
+    for (int w = 0; w < 4; ++w) {
+        const unsigned long long t = (unsigned long long)a[w] - b[w] - borrow;
+        d[w] = (uint32_t)t;
+        borrow = (t >> 63) & 1ull;
+    }
+    for (int w = 3; w >= 0; --w) {
+        if (d[w]) {
+            const int msb = 31 - __clz(d[w]);
+            const unsigned long long top = ((unsigned long long)d[w] << 32) | (w ? d[w - 1] : 0u);
+            const double mant = (double)top / (double)(1ull << (msb + 32 - 32)) / 4294967296.0;
+            return (float)(32 * w + msb + log2(mant) + 1.0);
+        }
+    }
+    return 0.f;
+}
+
 // 16 features of one live checkpoint entry (partial history after the
 // prefix): |beta|, log10|beta|, Re beta/|beta|, Im beta/|beta|,
-// log10(|beta|/eps_ref), prefix depth c1/G, remaining artificial sources
-// (A - A_p)/A, Hamming distance(sigma, b_in)/n, and (sigma xor b_in) on the
-// qubits of the next 8 artificial sources.  Bottom entries give NaN in 0.
+// (1 + log2 |int(sigma) - int(b_in)|)/64 (0 if equal), prefix depth c1/G, remaining
+// artificial sources (A - A_p)/A, Hamming distance(sigma, b_in)/n, and
+// (sigma xor b_in) on the qubits of the next 8 artificial sources.  Bottom
+// entries give NaN in feature 0.
 __device__ void entry_features(const JobDev& J, unsigned long long local, const FeatureSpec& sp, float* out)
 {
     const unsigned long long pair = local >> J.Ap;
@@ -373,7 +403,7 @@ __device__ void entry_features(const JobDev& J, unsigned long long local, const 
     out[1] = (float)fmax(lg, -30.0);
     out[2] = mag > 0 ? (float)(re / mag) : 0.f;
     out[3] = mag > 0 ? (float)(im / mag) : 0.f;
-    out[4] = (float)fmax(lg - sp.log10_eps_ref, -30.0);
+    out[4] = log2_distance(e.st, bin) / 64.f;
     out[5] = sp.depth;
     out[6] = sp.remaining;
     int ham = 0;
