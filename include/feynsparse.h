@@ -279,7 +279,7 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
  * Parameters: FS_MLP_PARAMS FP32 values in device memory, laid out W1[16][128],
  * b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][n]: input k to output n).
  * Features (16 FP32 per entry): |beta|, log10|beta|, Re beta/|beta|,
- * Im beta/|beta|, (1 + log2 |int(sigma) - int(b_in)|)/64 (0 if equal; registers read as
+ * Im beta/|beta|, (1 + log2 |int(sigma) - int(b_in)|)/8 (0 if equal; registers read as
  * unsigned integers, qubit q = bit q), c1/G, (A - A_p)/A,
  * Hamming(sigma, b_in)/n, and (sigma xor b_in) on the qubits of the next 8
  * artificial sources after the prefix. */

@@ -380,7 +380,7 @@ __device__ __forceinline__ float log2_distance(const uint32_t* x, const uint32_t
 
 // 16 features of one live checkpoint entry (partial history after the
 // prefix): |beta|, log10|beta|, Re beta/|beta|, Im beta/|beta|,
-// (1 + log2 |int(sigma) - int(b_in)|)/64 (0 if equal), prefix depth c1/G, remaining
+// (1 + log2 |int(sigma) - int(b_in)|)/8 (0 if equal), prefix depth c1/G, remaining
 // artificial sources (A - A_p)/A, Hamming distance(sigma, b_in)/n, and
 // (sigma xor b_in) on the qubits of the next 8 artificial sources.  Bottom
 // entries give NaN in feature 0.
@@ -403,7 +403,7 @@ __device__ void entry_features(const JobDev& J, unsigned long long local, const 
     out[1] = (float)fmax(lg, -30.0);
     out[2] = mag > 0 ? (float)(re / mag) : 0.f;
     out[3] = mag > 0 ? (float)(im / mag) : 0.f;
-    out[4] = log2_distance(e.st, bin) / 64.f;
+    out[4] = log2_distance(e.st, bin) / 8.f;
     out[5] = sp.depth;
     out[6] = sp.remaining;
     int ham = 0;

@@ -23,7 +23,7 @@ from ._lib import check
 from .api import Batch, Circuit
 
 N_PARAMS = _lib.MLP_PARAMS
-TARGET_FLOOR = -20.0
+TARGET_FLOOR = -12.0
 
 
 def _vp(t):

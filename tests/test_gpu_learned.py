@@ -101,9 +101,11 @@ def test_learned_pruner_end_to_end():
     assert losses[-1] < losses[0]
     held = w.outputs[64:]
     exact, st_ex = _run(w, held, cut)
-    # tau below every prediction: nothing is cut, the result is the exact one
+    # tau below every prediction: nothing is cut and the result is the exact
+    # one (summed over the compacted entries: equal to rounding)
     a, st0 = _run(w, held, cut, pruner=params, tau=-1e30)
-    assert st0["learned_cuts"] == 0 and np.array_equal(a, exact)
+    assert st0["learned_cuts"] == 0 and st0["valid"] == st_ex["valid"]
+    assert np.max(np.abs(a - exact) - (1e-12 + 1e-10 * np.abs(exact))) <= 0
     # some tau keeps fidelity >= 0.999 while cutting checkpoint entries
     best = None
     for tau in (-9.0, -8.0, -7.0, -6.0, -5.5, -5.0):
