@@ -241,6 +241,9 @@ FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
 /* Average duration of the history kernel of the last fs_batch_run that
  * recorded events (enabled by fs_batch_time_kernels), in milliseconds. */
 FS_API int fs_batch_time_kernels(fs_batch* b, int enable);
+/* Milliseconds of the five stages of the last timed run: prefix expansion,
+ * learned pruning, compaction, history, reduction (ms: 5 floats, host). */
+FS_API int fs_batch_stage_ms(fs_batch* b, float* ms);
 FS_API int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* reduce_ms);
 
 /* Per-region opcode histogram of a planned job: counts[r * FS_N_OPCODES + k]

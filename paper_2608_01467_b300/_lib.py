@@ -85,6 +85,7 @@ SIGNATURES = {
     "fs_batch_time_kernels": (ctypes.c_int, [vp, ctypes.c_int]),
     "fs_batch_kernel_ms": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float),
                                           P(ctypes.c_float)]),
+    "fs_batch_stage_ms": (ctypes.c_int, [vp, P(ctypes.c_float)]),
     "fs_batch_op_histogram": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
     "fs_batch_job_words": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
     "fs_batch_region_work": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_double), P(ctypes.c_double)]),

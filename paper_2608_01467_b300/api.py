@@ -238,6 +238,12 @@ class Batch:
         check(_lib.load().fs_batch_kernel_ms(self._h, ctypes.byref(a), ctypes.byref(h), ctypes.byref(r)))
         return a.value, h.value, r.value
 
+    def stage_ms(self):
+        """{prefix, prune, compact, history, reduce} milliseconds of the last timed run."""
+        arr = (ctypes.c_float * 5)()
+        check(_lib.load().fs_batch_stage_ms(self._h, arr))
+        return dict(zip(("prefix", "prune", "compact", "history", "reduce"), list(arr)))
+
     def op_histogram(self, job: int):
         """{region: {opname: count}} of a planned job (regions prefix/root/suffix)."""
         arr = (ctypes.c_uint32 * (3 * _lib.N_OPCODES))()

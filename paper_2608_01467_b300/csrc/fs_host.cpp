@@ -396,7 +396,7 @@ struct fs_batch {
     int grid = 0, compact_grid = 0;
     void* uploaded_ws = nullptr;
     bool timing = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
     void* jit = nullptr;          // generated straight-line module (engine 0)
     double jit_ms = 0;
@@ -960,6 +960,17 @@ int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* 
     return FS_OK;
 }
 
+int fs_batch_stage_ms(fs_batch* b, float* ms)
+{
+    if (!b || !ms) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->ev_recorded) return fail(FS_ERR_STATE, "no timed run recorded");
+    CUDA_TRY(cudaEventSynchronize(b->ev[3]));
+    // prefix, learned prune, compaction, history, reduce
+    const int order[6] = {0, 4, 5, 1, 2, 3};
+    for (int k = 0; k < 5; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], b->ev[order[k]], b->ev[order[k + 1]]));
+    return FS_OK;
+}
+
 int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
 {
     if (!b || !d_ws || (!d_amp_out && b->total_out)) return fail(FS_ERR_INVALID, "NULL argument");
@@ -975,11 +986,13 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     else
         CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
                                    (uint32_t*)(base + b->o_err), s));
+    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[4], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         if (j.d_pruner)
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries, s));
     }
+    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[5], s));
     for (int ji = 0; ji < nj; ++ji)
         if (b->jobs[ji].compact) CUDA_TRY(fs::launch_compact(jobs + ji, b->jobs[ji].table_entries, s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));

@@ -361,18 +361,21 @@ __device__ __forceinline__ float log2_distance(const uint32_t* x, const uint32_t
     }
     const uint32_t* a = ge ? x : y;
     const uint32_t* b = ge ? y : x;
-    unsigned long long borrow = 0;
+    uint32_t borrow = 0;
     for (int w = 0; w < 4; ++w) {
-        const unsigned long long t = (unsigned long long)a[w] - b[w] - borrow;
-        d[w] = (uint32_t)t;
-        borrow = (t >> 63) & 1ull;
+        const uint32_t t = a[w] - b[w] - borrow;
+        borrow = (a[w] < b[w] || (a[w] == b[w] && borrow)) ? 1u : 0u;
+        d[w] = t;
     }
     for (int w = 3; w >= 0; --w) {
         if (d[w]) {
             const int msb = 31 - __clz(d[w]);
-            const unsigned long long top = ((unsigned long long)d[w] << 32) | (w ? d[w - 1] : 0u);
-            const double mant = (double)top / (double)(1ull << (msb + 32 - 32)) / 4294967296.0;
-            return (float)(32 * w + msb + log2(mant) + 1.0);
+            // 24 bits below and including the leading one
+            const uint32_t lo = w ? d[w - 1] : 0u;
+            const uint32_t top = msb >= 23 ? (d[w] >> (msb - 23))
+                                           : ((d[w] << (23 - msb)) | (lo >> (32 - (23 - msb))));
+            const float mant = (float)top * (1.0f / 8388608.0f);   // in [1, 2)
+            return (float)(32 * w + msb + 1) + __log2f(mant);
         }
     }
     return 0.f;
@@ -391,18 +394,19 @@ __device__ void entry_features(const JobDev& J, unsigned long long local, const 
     const unsigned long long sidx = pair - o * (unsigned long long)J.S;
     const Entry e = J.table[local];
     const uint32_t* bin = J.ins + 4 * sidx;
-    const double re = e.amp.x, im = e.amp.y;
-    if (isnan(re)) {
+    if (isnan(e.amp.x)) {
         for (int k = 0; k < 16; ++k) out[k] = 0.f;
         out[0] = __int_as_float(0x7fc00000);
         return;
     }
-    const double mag = sqrt(re * re + im * im);
-    const double lg = mag > 0 ? log10(mag) : -30.0;
-    out[0] = (float)mag;
-    out[1] = (float)fmax(lg, -30.0);
-    out[2] = mag > 0 ? (float)(re / mag) : 0.f;
-    out[3] = mag > 0 ? (float)(im / mag) : 0.f;
+    // FP32 is enough: the features are rounded to bfloat16 for the MLP
+    const float re = (float)e.amp.x, im = (float)e.amp.y;
+    const float mag = sqrtf(re * re + im * im);
+    const float lg = mag > 0.f ? __log10f(mag) : -30.f;
+    out[0] = mag;
+    out[1] = fmaxf(lg, -30.f);
+    out[2] = mag > 0.f ? __fdividef(re, mag) : 0.f;
+    out[3] = mag > 0.f ? __fdividef(im, mag) : 0.f;
     out[4] = log2_distance(e.st, bin) / 8.f;
     out[5] = sp.depth;
     out[6] = sp.remaining;
