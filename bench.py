@@ -25,20 +25,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "amplitudes/s and histories/s on 1 B300, batched+learned vs plain, fidelity≥0.999"
 
-def workload_jobs(name, rank=0, outputs=None):
+def workload_jobs(name, rank=0, outputs=None, seed_shift=0):
+    """The bench request (seed_shift 0) or a separately seeded request of the
+    same family (training: 100, validation: 200)."""
     from workloads import qaoa_workload, qw_workload
+    qw_out = outputs or 4096
     if name == "qw100":
-        n_out = outputs or 4096
-        w = qw_workload(n_out=n_out, seed=0x5EED0005 + rank)
-        return [w], {"workload": f"qw100_t16_{n_out}out_exact", "qubits": 100, "steps": 16,
-                     "outputs": n_out, "input_support": 2, "eps": 0.0}
-    if name == "qw100+qaoa":
-        ws = [qw_workload(seed=0x5EED0005 + rank)]
-        for n in (16, 20, 24):
-            ws.append(qaoa_workload(n, 2, n_out=1024, eps=1e-4, seed=0x5EED0003 + rank))
-        return ws, {"workload": "qw100_t16_4096out_exact+qaoa16_20_24_p2_1024out_eps1e-4",
-                    "outputs": 4096 + 3 * 1024}
+        n_out = qw_out if seed_shift == 0 else 512
+        w = qw_workload(n_out=n_out, seed=0x5EED0005 + rank + seed_shift)
+        return [w], {"workload": f"qw100_t16_{qw_out}out", "qubits": 100, "steps": 16,
+                     "outputs": qw_out, "input_support": 2}
+    if name == "qw100+qaoa16":
+        n_qw = qw_out if seed_shift == 0 else 512
+        n_qa = 4 if seed_shift == 0 else 32
+        ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift),
+              qaoa_workload(16, 2, n_out=n_qa, seed=0x5EED0003 + rank + seed_shift)]
+        return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_p2_4out", "outputs": qw_out + 4}
     raise SystemExit(f"unknown workload {name}")
+
+
+def source_cut(circuit, k):
+    """Evaluation position just after the gate carrying artificial source k-1
+    (so that the first k sources of the backward sweep lie before it)."""
+    import paper_2608_01467_b300 as fs
+    if k <= 0:
+        return 0
+    bv = fs.Circuit(circuit).branch_vars()
+    srcs = {s: g for g, q, s in bv if s >= 0}
+    G = len(circuit.gates)
+    k = min(k, len(srcs))
+    return G - srcs[k - 1]
 
 
 class ClockSampler:
@@ -185,43 +201,84 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def run_ours(args):
-    import torch
-    import paper_2608_01467_b300 as fs
-    rank, world, local = dist_setup(args)
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    jobs, cfg = workload_jobs(args.workload, rank, args.outputs)
-    b = fs.Batch(engine=args.engine)
+def make_batch(fs, jobs, engine, dev, stream, pruners=None):
+    """Plans, allocates and uploads a batch; pruners: per job (params, tau,
+    c1, c2) or None (exact, autotuned cuts)."""
     circs = []
-    for w in jobs:
+    b = fs.Batch(engine=engine)
+    for ji, w in enumerate(jobs):
         C = fs.Circuit(w.circuit)
         C.set_input(w.inputs)
         circs.append(C)
-        b.add(C, w.outputs, w.eps)
-    ws_bytes = b.plan()
+        b.add(C, w.outputs, 0.0)
+        if pruners and pruners[ji] is not None:
+            from paper_2608_01467_b300 import learned
+            learned.attach(b, ji, pruners[ji][0], pruners[ji][1])
+            b.set_cuts(ji, pruners[ji][2], pruners[ji][3])
+    b._keep = circs
+    ws = b.plan()
     b.allocate(dev)
-    stream = torch.cuda.current_stream(dev)
     b.upload(stream)
-    engine, compile_ms = b.engine()
     b.time_kernels(True)
-    n_out = b.total_outputs
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    return b, ws
 
-    for _ in range(max(args.warmup, 3)):
-        b.run(stream)
-        b.finish(stream)
-    stats0 = b.finish(stream)
 
-    # timed region: device time of each step with CUDA events on the launch stream
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    barrier(world)
+def train_pruner(fs, args, w_train, w_val, dev, stream):
+    """Logs exact subtree sums of a separately seeded request at the learned
+    cut, trains the MLP on the GPU, and picks the largest tau that keeps
+    fidelity >= 0.999 on a held-out request (judged by exact enumeration)."""
+    import numpy as np
+    from paper_2608_01467_b300 import learned
+    from workloads import mlp_init_params
+    c1 = source_cut(w_train.circuit, args.learned_ap)
+    c2 = source_cut(w_train.circuit, args.learned_ap + args.learned_ar)
+    t0 = time.perf_counter()
+    x, t, _ = learned.log_training_data(w_train.circuit, w_train.inputs, w_train.outputs, c1)
+    params, losses = learned.train(x, t, mlp_init_params(args.seed), steps=args.train_steps,
+                                   batch=16384, lr=1e-3, seed=args.seed)
+    torch_sync(dev)
+    t_train = time.perf_counter() - t0
+    bx, _ = make_batch(fs, [w_val], args.engine, dev, stream)
+    bx.run(stream)
+    bx.finish(stream)
+    exact = bx.amp.cpu().numpy()[:len(w_val.outputs)]
+    chosen = None
+    for tau in (-6.0, -7.0, -8.0, -9.0, -10.0, -11.0):
+        bl, _ = make_batch(fs, [w_val], args.engine, dev, stream, [(params, tau, c1, c2)])
+        bl.run(stream)
+        bl.finish(stream)
+        F = fidelity(exact, bl.amp.cpu().numpy()[:len(w_val.outputs)])
+        if F >= 0.999:
+            chosen = (tau, F)
+            break
+    if chosen is None:
+        chosen = (-1e30, 1.0)   # nothing cut
+    return {"params": params, "tau": chosen[0], "val_fidelity": chosen[1], "c1": c1, "c2": c2,
+            "train_samples": int(x.shape[0]), "train_loss": [losses[0], losses[-1]],
+            "train_seconds": round(t_train, 2)}
+
+
+def torch_sync(dev):
+    import torch
     torch.cuda.synchronize(dev)
-    step_ms, hist_ms, pre_ms, red_ms = [], [], [], []
-    completed = 0
-    for _ in range(args.steps):
+
+
+def fidelity(a, b):
+    import numpy as np
+    a = np.asarray(a, complex)
+    b = np.asarray(b, complex)
+    na, nb = np.vdot(a, a).real, np.vdot(b, b).real
+    if na == 0 or nb == 0:
+        return 0.0
+    return float(abs(np.vdot(a, b)) ** 2 / (na * nb))
+
+
+def timed_steps(b, steps, stream, flush):
+    """Device time of each step (CUDA events on the launch stream, L2 flushed
+    between steps) and the per-stage times of the library."""
+    import torch
+    step_ms, stages, completed, valid = [], [], 0, 0
+    for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -230,84 +287,162 @@ def run_ours(args):
         e1.record(stream)
         st = b.finish(stream)
         step_ms.append(e0.elapsed_time(e1))
-        p, h, r = b.kernel_ms()
-        pre_ms.append(p)
-        hist_ms.append(h)
-        red_ms.append(r)
-        completed += sum(s["completed"] for s in st)
+        stages.append(b.stage_ms())
+        completed += sum(x["completed"] for x in st)
+        valid += sum(x["valid"] for x in st)
+    mean_stage = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+    return step_ms, mean_stage, completed, st
+
+
+def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
+    """Roofline of the dominant stage of a step: algorithmic work per launch
+    (the library's per-region work model x executions, or MLP FLOPs) over the
+    stage's mean device time."""
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2032.0
+    int_peak = peaks["sms"] * 128 * sm_max * 1e6
+    work = {"prefix": [0.0, 0.0], "history": [0.0, 0.0], "prune": [0.0, 0.0]}
+    for ji, w in enumerate(jobs):
+        iw, fw = b.region_work(ji)
+        s0 = stats[ji]
+        pairs = len(w.outputs) * len(w.inputs)
+        entries = pairs << s0["A_p"]
+        work["prefix"][0] += iw[0] * entries
+        work["prefix"][1] += fw[0] * entries
+        root_runs = s0["live_entries"] << s0["A_r"]
+        work["history"][0] += iw[1] * root_runs + iw[2] * s0["completed"] + iw[3] * s0["completed"]
+        work["history"][1] += fw[1] * root_runs + fw[2] * s0["completed"] + fw[3] * s0["valid"]
+        if s0["learned_cuts"] or (b.pruned and b.pruned[ji]):
+            work["prune"][1] += 2.0 * (2048 + 16384 + 128) * entries   # MLP FLOPs per scored entry
+    dom = max(("prefix", "history", "prune"), key=lambda k: stage_ms.get(k, 0.0))
+    t = stage_ms[dom] / 1000.0
+    if dom == "prune":
+        peak = peaks["bf16_tflops"] * 1e12
+        r = {"bound": "tensor", "achieved": work["prune"][1] / t / 1e12, "peak": peak / 1e12,
+             "unit": "TFLOP/s", "frac": work["prune"][1] / t / peak,
+             "peak_note": "bf16 cuBLAS burst of measured peaks; the MLP runs mma.sync m16n8k16"}
+    else:
+        i_frac = work[dom][0] / t / int_peak
+        f_frac = work[dom][1] / t / peaks["dfma_per_s"]
+        if i_frac >= f_frac:
+            r = {"bound": "alu", "achieved": work[dom][0] / t / 1e9, "peak": int_peak / 1e9,
+                 "unit": "Gop/s", "frac": i_frac,
+                 "peak_note": "derived: SMs x 128 lanes x max SM clock (issue rate)"}
+        else:
+            r = {"bound": "alu", "achieved": work[dom][1] / t / 1e9, "peak": peaks["dfma_per_s"] / 1e9,
+                 "unit": "GFP64-inst/s", "frac": f_frac, "peak_note": "measured FP64 FMA rate (fs_probe_peaks)"}
+        r.update({"int_frac": i_frac, "fp64_frac": f_frac})
+    r.update({"kernel": dom, "traffic": None, "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}})
+    return r
+
+
+def run_ours(args):
+    import torch
+    import paper_2608_01467_b300 as fs
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    jobs, cfg = workload_jobs(args.workload, rank, args.outputs)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    peaks = fs.api.probe_peaks()
+    import json as _json
+    try:
+        mp = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks["bf16_tflops"] = mp.get("bf16_tflops", 1800.0)
+    except Exception:
+        peaks["bf16_tflops"] = 1800.0
+
+    # plain: exact, autotuned cuts
+    bp, ws_plain = make_batch(fs, jobs, args.engine, dev, stream)
+    bp.pruned = None
+    engine, compile_ms = bp.engine()
+    for _ in range(max(args.warmup, 3)):
+        bp.run(stream)
+        bp.finish(stream)
+    stats_plain = bp.finish(stream)
+    n_out = bp.total_outputs
+
+    # learned: a pruner per job trained on separately seeded requests
+    tr_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 100)
+    va_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 200)
+    learned_info = None
+    if not args.plain_only:
+        pr = [train_pruner(fs, args, tr, va, dev, stream) for tr, va in zip(tr_jobs, va_jobs)]
+        learned_info = pr
+        bl, ws_learned = make_batch(fs, jobs, args.engine, dev, stream,
+                                    [(p["params"], p["tau"], p["c1"], p["c2"]) for p in pr])
+        bl.pruned = [True] * len(jobs)
+        for _ in range(max(args.warmup, 3)):
+            bl.run(stream)
+            bl.finish(stream)
+        stats_learned = bl.finish(stream)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    plain_ms, plain_stage, plain_completed, _ = timed_steps(bp, args.steps, stream, flush)
+    plain_amp = bp.amp.cpu().numpy()
+    if learned_info:
+        learned_ms, learned_stage, learned_completed, stats_learned = timed_steps(bl, args.steps, stream, flush)
+        learned_amp = bl.amp.cpu().numpy()
     torch.cuda.synchronize(dev)
     barrier(world)
     clocks = sampler.stop()
-    t_total = sum(step_ms) / 1000.0
-    t_max = max_over_ranks(t_total, world, dev)
-    outs_all = sum_over_ranks(n_out * args.steps, world, dev)
-    hist_all = sum_over_ranks(completed, world, dev)
-    value = outs_all / t_max
-    hist_rate = hist_all / t_max
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # programs and bit strings, run, D2H of the amplitudes, every step
-    host_amp = torch.empty(b.amp.shape, dtype=b.amp.dtype, pin_memory=True)
+    def rates(ms, completed):
+        t = max_over_ranks(sum(ms) / 1000.0, world, dev)
+        outs = sum_over_ranks(n_out * args.steps, world, dev)
+        return outs / t, sum_over_ranks(completed, world, dev) / t, 1000.0 * t / args.steps
+
+    plain_value, plain_hist, plain_step = rates(plain_ms, plain_completed)
+    head = bl if learned_info else bp
+    if learned_info:
+        value, hist_rate, step = rates(learned_ms, learned_completed)
+        F = fidelity(plain_amp[:n_out], learned_amp[:n_out])
+        roof = stage_roofline(fs, bl, jobs, stats_learned, learned_stage, peaks, clocks)
+    else:
+        value, hist_rate, step = plain_value, plain_hist, plain_step
+        F = 1.0
+        roof = stage_roofline(fs, bp, jobs, stats_plain, plain_stage, peaks, clocks)
+    roof_plain = stage_roofline(fs, bp, jobs, stats_plain, plain_stage, peaks, clocks)
+
+    # end to end through the public API with host buffers: the step's
+    # programs and bit strings go host-to-device, the amplitudes come back
+    host_amp = torch.empty(head.amp.shape, dtype=head.amp.dtype, pin_memory=True)
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        b.upload(stream)
-        b.run(stream)
-        host_amp.copy_(b.amp, non_blocking=True)
-        b.finish(stream)
+        head.upload(stream)
+        head.run(stream)
+        host_amp.copy_(head.amp, non_blocking=True)
+        head.finish(stream)
     torch.cuda.synchronize(dev)
     t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e = sum_over_ranks(n_out * args.steps, world, dev) / t_e2e
 
-    # roofline of the history kernel (the dominant kernel): algorithmic
-    # integer ops and FP64 instructions of the root + suffix per launch, from
-    # the library's per-region work of each job times the region executions
-    peaks = fs.api.probe_peaks()
-    int_ops = 0.0
-    fp_ops = 0.0
-    for ji, w in enumerate(jobs):
-        iw, fw = b.region_work(ji)
-        s0 = stats0[ji]
-        pairs = len(w.outputs) * len(w.inputs)
-        root_runs = s0["table_entries"] << s0["A_r"]          # live checkpoints x 2^A_r
-        suffix_runs = s0["completed"] if w.eps > 0 else pairs << (s0["A_p"] + s0["A_r"] + s0["A_s"])
-        int_ops += iw[1] * root_runs + iw[2] * suffix_runs + iw[3] * s0["completed"]
-        fp_ops += fw[1] * root_runs + fw[2] * suffix_runs + fw[3] * s0["valid"]
-    h_s = statistics.mean(hist_ms) / 1000.0
-    sm_max = clocks["sm_max_mhz"] or 2032.0
-    int_peak = peaks["sms"] * 128 * sm_max * 1e6
-    int_frac = int_ops / h_s / int_peak
-    fp_frac = fp_ops / h_s / peaks["dfma_per_s"]
-    if int_frac >= fp_frac:
-        roof = {"bound": "alu", "achieved": int_ops / h_s / 1e9, "peak": int_peak / 1e9,
-                "unit": "Gop/s", "frac": int_frac}
-    else:
-        roof = {"bound": "alu", "achieved": fp_ops / h_s / 1e9, "peak": peaks["dfma_per_s"] / 1e9,
-                "unit": "GFP64-inst/s", "frac": fp_frac}
-    roof.update({"traffic": None, "kernel": "history_kernel",
-                 "history_kernel_ms": statistics.mean(hist_ms),
-                 "prefix_kernel_ms": statistics.mean(pre_ms), "reduce_kernel_ms": statistics.mean(red_ms),
-                 "int_ops_per_launch": int_ops, "fp64_inst_per_launch": fp_ops,
-                 "int_frac": int_frac, "fp64_frac": fp_frac,
-                 "int_peak_note": "derived: SMs x 128 lanes x max SM clock",
-                 "fp64_peak_measured_dfma_per_s": peaks["dfma_per_s"],
-                 "int_peak_measured_ops_per_s": peaks["int_ops_per_s"]})
-
     line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded circuits and requests)",
-            "config": dict(cfg, l2="flushed between steps (512 MiB write)",
-                           parallelism=f"outputs sharded, {world} replica(s)",
-                           workspace_bytes=ws_bytes, engine=engine,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded circuits and requests)",
+            "config": dict(cfg, mode="learned pruning vs plain exact" if learned_info else "plain exact",
+                           l2="flushed between steps (512 MiB write)",
+                           parallelism=f"outputs sharded, {world} replica(s)", engine=engine,
                            engine_compile_ms=round(compile_ms, 1)),
-            "histories_per_s": hist_rate, "clocks": clocks,
+            "histories_per_s": hist_rate, "fidelity_vs_exact": F,
+            "plain": {"value": plain_value, "histories_per_s": plain_hist, "ms_per_step": plain_step,
+                      "roofline": roof_plain},
+            "speedup_vs_plain": value / plain_value,
+            "clocks": clocks,
             "e2e": {"value": e2e, "unit": "amplitudes/s",
-                    "h2d_bytes_per_step": int(b.static_bytes()),
+                    "h2d_bytes_per_step": int(head.static_bytes()),
                     "d2h_bytes_per_step": int(16 * n_out)},
-            "gpu_launches": b.launch_count() * args.steps,
+            "gpu_launches": head.launch_count() * args.steps,
             "roofline": roof}
+    if learned_info:
+        line["learned"] = [{k: v for k, v in p.items() if k != "params"} for p in learned_info]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samp = oracle_sample(jobs, budget_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": samp["amplitudes_per_s"], "unit": "amplitudes/s",
@@ -330,6 +465,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--outputs", type=int, default=None, help="requested outputs (small profiling cases)")
     ap.add_argument("--engine", default="straight", choices=["straight", "interp"])
+    ap.add_argument("--plain-only", action="store_true", help="exact run only, no learned pruning")
+    ap.add_argument("--learned-ap", type=int, default=8, help="artificial sources before the learned cut")
+    ap.add_argument("--learned-ar", type=int, default=3, help="artificial sources in the root after it")
+    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

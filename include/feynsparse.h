@@ -198,6 +198,11 @@ FS_API int fs_batch_set_options(fs_batch* b, const fs_options* opt);
 FS_API int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, size_t n_out,
                  double eps, uint32_t* job_id);
 
+/* Fixes the cuts (c1, c2) of one job, overriding the batch's split option
+ * (both -1 restores it); 0 <= c1 <= c2 <= n_gates is checked at plan time.
+ * Call before fs_batch_plan. */
+FS_API int fs_batch_set_cuts(fs_batch* b, uint32_t job, int32_t c1, int32_t c2);
+
 /* Compiles every job (programs, autotuned cuts, tile queue) and reports the
  * device workspace size in bytes (256-byte aligned sub-buffers). */
 FS_API int fs_batch_plan(fs_batch* b, size_t* workspace_bytes);

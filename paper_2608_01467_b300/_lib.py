@@ -96,6 +96,7 @@ SIGNATURES = {
     "fs_batch_features": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp, vp]),
     "fs_batch_log_subtrees": (ctypes.c_int, [vp, ctypes.c_uint32, vp]),
     "fs_batch_log_items": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint64)]),
+    "fs_batch_set_cuts": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32]),
     "fs_batch_set_pruner": (ctypes.c_int, [vp, ctypes.c_uint32, vp, ctypes.c_float]),
     "fs_amplitudes_noalloc": (ctypes.c_int, [vp, P(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_double,
                                              P(ctypes.c_double), vp]),

@@ -179,6 +179,10 @@ class Batch:
         self._circuits.append(circuit)
         return jid.value
 
+    def set_cuts(self, job: int, c1: int, c2: int):
+        """Fixed cuts for one job (both -1: back to the batch's split)."""
+        check(_lib.load().fs_batch_set_cuts(self._h, job, c1, c2))
+
     def plan(self) -> int:
         n = ctypes.c_size_t(0)
         check(_lib.load().fs_batch_plan(self._h, ctypes.byref(n)))

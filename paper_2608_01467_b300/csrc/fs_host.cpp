@@ -375,6 +375,7 @@ struct Job {
     fs::FeatureSpec fspec{};
     // pruned jobs (eps > 0 or a learned pruner) run over compacted live entries
     bool compact = false;
+    int fixed_c1 = -1, fixed_c2 = -1;     // per-job cuts overriding the batch split
     size_t o_live = 0, o_esum = 0, o_blk = 0;
     uint64_t nblk = 0;
 };
@@ -631,6 +632,18 @@ int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items)
     return FS_OK;
 }
 
+int fs_batch_set_cuts(fs_batch* b, uint32_t job, int32_t c1, int32_t c2)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    if ((c1 < 0) != (c2 < 0) || (c1 >= 0 && c2 < c1)) return fail(FS_ERR_INVALID, "cuts must satisfy 0 <= c1 <= c2 (or both -1)");
+    b->jobs[job].fixed_c1 = c1;
+    b->jobs[job].fixed_c2 = c2;
+    b->planned = b->uploaded = false;
+    b->drop_jit();
+    return FS_OK;
+}
+
 int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau)
 {
     if (!b) return fail(FS_ERR_INVALID, "NULL batch");
@@ -724,7 +737,11 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         j.pairs = (uint64_t)j.outs.size() * j.ins.size();
         const int G = (int)C.g.size();
         const std::vector<int> pre = source_prefix(C);
-        if (b->opt.split == 1) {
+        if (j.fixed_c1 >= 0) {
+            const int c1 = j.fixed_c1, c2 = j.fixed_c2;
+            if (c2 < c1 || c2 > G) return fail(FS_ERR_INVALID, "job %zu: cuts (%d, %d) outside [0, %d]", ji, c1, c2, G);
+            j.sp = split_at(C, pre, c1, c2);
+        } else if (b->opt.split == 1) {
             const int c1 = b->opt.c1, c2 = b->opt.c2;
             if (c1 < 0 || c2 < c1 || c2 > G) return fail(FS_ERR_INVALID, "job %zu: fixed cuts (%d, %d) outside [0, %d]", ji, c1, c2, G);
             j.sp = split_at(C, pre, c1, c2);
@@ -814,7 +831,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         j.o_part = take(j.n_partials * sizeof(double2));
         if (j.compact) {
             j.o_live = take(j.table_entries * sizeof(uint64_t));
-            j.o_esum = take(j.table_entries * sizeof(double2));
+            j.o_esum = take((j.table_entries << j.sp.Ar) * sizeof(double2));
             j.o_blk = take(j.nblk * sizeof(uint32_t));
         }
     }

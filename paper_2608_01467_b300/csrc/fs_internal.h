@@ -88,7 +88,7 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     int32_t compact;           /* 1: history over the compacted live entries */         \
     int32_t pad1;                                                             \
     uint64_t* live;            /* compacted live entry indices, table order */            \
-    double2* esum;             /* subtree sum per live entry */                          \
+    double2* esum;             /* subtree sum per (live entry, h_r) item */              \
     uint32_t* blk;             /* per compaction block: live count, then offset */       \
     uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */
 

@@ -175,31 +175,22 @@ template <class T>
 __device__ void compact_body(const JobDev& J, u64 i, u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
-    const u64 e = J.live[i];
+    const u64 e = J.live[i >> T::Ar];
+    const u64 hr = i & ((1ull << T::Ar) - 1ull);
     const u64 pair = e >> T::Ap;
     const u64 o = pair / (u64)J.S;
     const u64 sidx = pair - o * (u64)J.S;
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
-    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
     const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
     const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
     const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
-    u32 st0[W], bin[W];
+    u32 st[W], bin[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) { st0[j] = tmp[j]; bin[j] = btmp[j]; }
+    for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 acc = make_double2(0.0, 0.0);
-    for (u64 hr = 0; hr < (1ull << T::Ar); ++hr) {
-        u32 st[W];
-#pragma unroll
-        for (int j = 0; j < W; ++j) st[j] = st0[j];
-        double2 amp = a0;
-        const int r = T::root(st, amp, hr, bin, visits);
-        if (r >= 0) {
-            hr = ((hr >> r) + 1ull) << r;
-            --hr;
-            continue;
-        }
+    if (T::root(st, amp, hr, bin, visits) < 0) {
         const u64 ns = 1ull << T::As;
         u64 hs = 0;
         while (hs < ns) {
@@ -548,7 +539,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
                std::to_string(j) + "], td.y, s_warp); break;\n";
     src += "        default: break;\n        }\n    }\n}\n";
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job)\n{\n"
-           "    const JobDev& J = jobs[job];\n    const u64 nlive = J.stats[6];\n    const int lane = threadIdx.x & 31;\n"
+           "    const JobDev& J = jobs[job];\n    const u64 nlive = J.stats[6] << J.Ar;\n    const int lane = threadIdx.x & 31;\n"
            "    u64 completed = 0, valid = 0, visits = 0;\n    for (;;) {\n"
            "        u64 base = 0;\n        if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);\n"
            "        base = __shfl_sync(0xffffffffu, base, 0);\n        if (base >= nlive) break;\n"

@@ -505,38 +505,30 @@ __global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __rest
         if (lv[k]) J.live[pos++] = base + (uint64_t)threadIdx.x * 4 + k;
 }
 
-// History over the compacted live entries: a warp takes 32 consecutive
-// live entries off the job's work counter; each thread runs all 2^A_r root
-// assignments of its entry and the suffix of each, and writes the entry's
-// subtree sum (one slot per live entry: fixed reduction order downstream).
+// History over the compacted live entries: items are (live entry, h_r)
+// pairs, item i = (live index i >> A_r, h_r = i & (2^A_r - 1)); a warp takes
+// 32 consecutive items off the job's work counter; each thread runs its root
+// assignment and the suffix enumeration and writes the item's subtree sum
+// (one slot per item: fixed reduction order downstream).
 template <int W>
-__device__ void compact_entry(const JobDev& J, uint64_t i, uint32_t* err, unsigned long long& completed,
-                              unsigned long long& valid, unsigned long long& visits)
+__device__ void compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsigned long long& completed,
+                             unsigned long long& valid, unsigned long long& visits)
 {
-    const uint64_t e = J.live[i];
+    const uint64_t e = J.live[i >> J.Ar];
+    const uint64_t hr = i & ((1ull << J.Ar) - 1ull);
     const uint64_t pair = e >> J.Ap;
     const uint64_t o = pair / (uint64_t)J.S;
     const uint64_t s = pair - o * (uint64_t)J.S;
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
-    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
-    uint32_t st0[W], bin[W];
+    double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    uint32_t st[W], bin[W];
     const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
-    for (int j = 0; j < W; ++j) st0[j] = tmp[j];
+    for (int j = 0; j < W; ++j) st[j] = tmp[j];
     load_bits<W>(J.ins + 4 * s, bin);
     double2 acc = make_double2(0.0, 0.0);
-    for (uint64_t hr = 0; hr < (1ull << J.Ar); ++hr) {
-        uint32_t st[W];
-#pragma unroll
-        for (int j = 0; j < W; ++j) st[j] = st0[j];
-        double2 amp = a0;
-        const int r = run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err);
-        if (r >= 0) {
-            hr = ((hr >> r) + 1ull) << r;
-            --hr;
-            continue;
-        }
+    if (run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err) < 0) {
         const uint64_t ns = 1ull << J.As;
         uint64_t hs = 0;
         while (hs < ns) {
@@ -564,19 +556,19 @@ __device__ void compact_entry(const JobDev& J, uint64_t i, uint32_t* err, unsign
 __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __restrict__ jobp, uint32_t* err)
 {
     const JobDev& J = *jobp;
-    const uint64_t nlive = J.stats[6];
+    const uint64_t n_items = J.stats[6] << J.Ar;
     const int lane = threadIdx.x & 31;
     unsigned long long completed = 0, valid = 0, visits = 0;
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= nlive) break;
+        if (base >= n_items) break;
         const uint64_t i = base + lane;
-        if (i < nlive) {
-            if (J.W == 1) compact_entry<1>(J, i, err, completed, valid, visits);
-            else if (J.W == 2) compact_entry<2>(J, i, err, completed, valid, visits);
-            else compact_entry<4>(J, i, err, completed, valid, visits);
+        if (i < n_items) {
+            if (J.W == 1) compact_item<1>(J, i, err, completed, valid, visits);
+            else if (J.W == 2) compact_item<2>(J, i, err, completed, valid, visits);
+            else compact_item<4>(J, i, err, completed, valid, visits);
         }
     }
     completed = warp_sum_u64(completed);
@@ -617,8 +609,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
             double2 t = make_double2(0.0, 0.0);
             if (J.compact) {
                 const uint64_t nlive = J.stats[6];
-                const uint64_t lo = lower_bound_u64(J.live, nlive, pair << J.Ap);
-                const uint64_t hi = lower_bound_u64(J.live, nlive, (pair + 1) << J.Ap);
+                const uint64_t lo = lower_bound_u64(J.live, nlive, pair << J.Ap) << J.Ar;
+                const uint64_t hi = lower_bound_u64(J.live, nlive, (pair + 1) << J.Ap) << J.Ar;
                 for (uint64_t k = lo + threadIdx.x; k < hi; k += REDUCE_THREADS) {
                     const double2 v = J.esum[k];
                     t.x += v.x;
