@@ -30,16 +30,21 @@ def workload_jobs(name, rank=0, outputs=None, seed_shift=0):
     same family (training: 100, validation: 200)."""
     from workloads import qaoa_workload, qw_workload
     qw_out = outputs or 4096
+    # learned cut per job: (artificial sources before the cut, in the root) or
+    # None for the exact plan's autotuned cuts
     if name == "qw100":
         n_out = qw_out if seed_shift == 0 else 512
         w = qw_workload(n_out=n_out, seed=0x5EED0005 + rank + seed_shift)
+        w.meta["learned_cut"] = (8, 3)
         return [w], {"workload": f"qw100_t16_{qw_out}out", "qubits": 100, "steps": 16,
-                     "outputs": qw_out, "input_support": 2}
+                     "outputs": qw_out, "input_support": 2, "learned_cut_sources": [8, 3]}
     if name == "qw100+qaoa16":
         n_qw = qw_out if seed_shift == 0 else 512
         n_qa = 4 if seed_shift == 0 else 32
         ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift),
               qaoa_workload(16, 2, n_out=n_qa, seed=0x5EED0003 + rank + seed_shift)]
+        ws[0].meta["learned_cut"] = (8, 3)
+        ws[1].meta["learned_cut"] = None
         return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_p2_4out", "outputs": qw_out + 4}
     raise SystemExit(f"unknown workload {name}")
 
@@ -223,15 +228,19 @@ def make_batch(fs, jobs, engine, dev, stream, pruners=None):
     return b, ws
 
 
-def train_pruner(fs, args, w_train, w_val, dev, stream):
+def train_pruner(fs, args, w_train, w_val, dev, stream, plain_stats):
     """Logs exact subtree sums of a separately seeded request at the learned
     cut, trains the MLP on the GPU, and picks the largest tau that keeps
     fidelity >= 0.999 on a held-out request (judged by exact enumeration)."""
     import numpy as np
     from paper_2608_01467_b300 import learned
     from workloads import mlp_init_params
-    c1 = source_cut(w_train.circuit, args.learned_ap)
-    c2 = source_cut(w_train.circuit, args.learned_ap + args.learned_ar)
+    cut = w_train.meta.get("learned_cut")
+    if cut is None:
+        c1, c2 = plain_stats["c1"], plain_stats["c2"]
+    else:
+        c1 = source_cut(w_train.circuit, cut[0])
+        c2 = source_cut(w_train.circuit, cut[0] + cut[1])
     t0 = time.perf_counter()
     x, t, _ = learned.log_training_data(w_train.circuit, w_train.inputs, w_train.outputs, c1)
     params, losses = learned.train(x, t, mlp_init_params(args.seed), steps=args.train_steps,
@@ -273,18 +282,21 @@ def fidelity(a, b):
     return float(abs(np.vdot(a, b)) ** 2 / (na * nb))
 
 
-def timed_steps(b, steps, stream, flush):
+def timed_steps(b, steps, stream, flush, name):
     """Device time of each step (CUDA events on the launch stream, L2 flushed
-    between steps) and the per-stage times of the library."""
+    between steps) and the per-stage times of the library.  Each step is an
+    NVTX range `name` (for profiler filtering)."""
     import torch
     step_ms, stages, completed, valid = [], [], 0, 0
     for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(name)
         e0.record(stream)
         b.run(stream)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         st = b.finish(stream)
         step_ms.append(e0.elapsed_time(e1))
         stages.append(b.stage_ms())
@@ -367,7 +379,7 @@ def run_ours(args):
     va_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 200)
     learned_info = None
     if not args.plain_only:
-        pr = [train_pruner(fs, args, tr, va, dev, stream) for tr, va in zip(tr_jobs, va_jobs)]
+        pr = [train_pruner(fs, args, tr, va, dev, stream, sp) for tr, va, sp in zip(tr_jobs, va_jobs, stats_plain)]
         learned_info = pr
         bl, ws_learned = make_batch(fs, jobs, args.engine, dev, stream,
                                     [(p["params"], p["tau"], p["c1"], p["c2"]) for p in pr])
@@ -382,10 +394,10 @@ def run_ours(args):
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize(dev)
-    plain_ms, plain_stage, plain_completed, _ = timed_steps(bp, args.steps, stream, flush)
+    plain_ms, plain_stage, plain_completed, _ = timed_steps(bp, args.steps, stream, flush, "plain_step")
     plain_amp = bp.amp.cpu().numpy()
     if learned_info:
-        learned_ms, learned_stage, learned_completed, stats_learned = timed_steps(bl, args.steps, stream, flush)
+        learned_ms, learned_stage, learned_completed, stats_learned = timed_steps(bl, args.steps, stream, flush, "learned_step")
         learned_amp = bl.amp.cpu().numpy()
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -466,8 +478,6 @@ def main():
     ap.add_argument("--outputs", type=int, default=None, help="requested outputs (small profiling cases)")
     ap.add_argument("--engine", default="straight", choices=["straight", "interp"])
     ap.add_argument("--plain-only", action="store_true", help="exact run only, no learned pruning")
-    ap.add_argument("--learned-ap", type=int, default=8, help="artificial sources before the learned cut")
-    ap.add_argument("--learned-ar", type=int, default=3, help="artificial sources in the root after it")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -753,7 +753,9 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
             j.sp = (C.A + lp <= 40) ? split_at(C, pre, 0, G) : split_at(C, pre, 0, 0);
         } else {
             const uint64_t share = all_pairs ? (uint64_t)((long double)budget * j.pairs / all_pairs) : budget;
-            const uint64_t per_pair = j.pairs ? share / (j.pairs * sizeof(fs::Entry)) : share;
+            // pruned jobs also keep a compacted live list (8 B per entry)
+            const uint64_t entry_bytes = sizeof(fs::Entry) + ((j.eps > 0.0 || j.d_pruner) ? 8 : 0);
+            const uint64_t per_pair = j.pairs ? share / (j.pairs * entry_bytes) : share;
             const int max_ap = per_pair ? std::min(ilog2_floor(per_pair), 40) : 0;
             const int min_apr = j.pairs ? ilog2_ceil((min_items + j.pairs - 1) / j.pairs) : 0;
             const int max_apr = std::max(0, std::min(40, ilog2_floor(max_items)) -

@@ -60,9 +60,12 @@ extern "C" FS_API int fs_amplitudes_noalloc(fs_circuit* c, const uint64_t* outpu
     rc = fs_batch_create(&b);
     if (rc) return rc;
     size_t ws = 0;
-    // keep the autotuned checkpoint table inside half of the scratch
+    // keep the autotuned checkpoint table (and the live list of pruned
+    // requests) inside a quarter of the scratch, and the per-item partial or
+    // subtree sums (16 B each) inside another quarter
     fs_options opt = {};
-    opt.table_budget_bytes = FS_NOALLOC_SCRATCH_BYTES / 2;
+    opt.table_budget_bytes = FS_NOALLOC_SCRATCH_BYTES / 4;
+    opt.max_items = FS_NOALLOC_SCRATCH_BYTES / 4 / 16;
     rc = fs_batch_set_options(b, &opt);
     if (!rc) rc = fs_batch_add(b, c, outputs, n_out, eps, nullptr);
     if (!rc) rc = fs_batch_plan(b, &ws);
