@@ -721,7 +721,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     const uint64_t budget = b->opt.table_budget_bytes ? b->opt.table_budget_bytes : (4ull << 30);
     const uint64_t max_items = b->opt.max_items ? b->opt.max_items : (1ull << 28);
     // the parallelism floor never exceeds the ceiling
-    const uint64_t min_items = std::min(b->opt.min_items ? b->opt.min_items : (1ull << 19), max_items);
+    const uint64_t min_items = std::min<uint64_t>(b->opt.min_items ? b->opt.min_items : (1ull << 19), max_items);
     // table budget shared by the jobs in proportion to their pair counts
     uint64_t all_pairs = 0;
     for (Job& j : b->jobs) all_pairs += (uint64_t)j.outs.size() * j.ins.size();
