@@ -114,3 +114,48 @@ def test_learned_pruner_end_to_end():
         if F >= 0.999:
             best = (tau, F, s["learned_cuts"], s["completed"])
     assert best is not None and best[2] > 0, best
+
+
+def _qw_run(w, split="auto", c1=0, c2=0, eps=0.0, pruner=None, tau=0.0):
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    b = fs.Batch(split=split, c1=c1, c2=c2)
+    b.add(C, w.outputs, eps)
+    if pruner is not None:
+        learned.attach(b, 0, pruner, tau)
+    b.plan()
+    b.allocate()
+    b.upload()
+    b.run()
+    st = b.finish()[0]
+    return b.amp.cpu().numpy()[:len(w.outputs)], st
+
+
+def test_learned_pruner_gain_over_threshold_on_the_walk():
+    """What the trained network adds: on the 100-qubit walk most checkpoint
+    entries can no longer reach the input (their subtree sums are exactly
+    zero).  The pruner learns to cut them and keeps the fidelity; threshold
+    pruning cannot, because every branch at a given depth has the same
+    magnitude (1/sqrt2)^k, so any eps either cuts nothing or cuts whole
+    depths."""
+    from workloads import qw_workload
+    tr = qw_workload(n_out=256, seed=0x5EED0005 + 300)
+    ev = qw_workload(n_out=512, seed=0x5EED0005 + 400)
+    bv = fs.Circuit(ev.circuit).branch_vars()
+    src_gate = {s: g for g, q, s in bv if s >= 0}
+    G = len(ev.circuit.gates)
+    c1, c2 = G - src_gate[7], G - src_gate[10]          # 8 sources before, 3 in the root
+    x, t, _ = learned.log_training_data(tr.circuit, tr.inputs, tr.outputs, c1)
+    params, _ = learned.train(x, t, mlp_init_params(1), steps=1200, batch=16384, lr=1e-3)
+    exact, st_ex = _qw_run(ev)
+    a, st = _qw_run(ev, "fixed", c1, c2, pruner=params, tau=-9.0)
+    F = closed_forms.fidelity(exact, a)
+    assert F >= 0.999
+    assert st["completed"] < 0.1 * st_ex["completed"]
+    gains = []
+    for eps in (1e-4, 1e-3, 3e-3, 6e-3, 1e-2):
+        a2, s2 = _qw_run(ev, "fixed", c1, c2, eps=eps)
+        F2 = closed_forms.fidelity(exact, a2)
+        gains.append((eps, F2, s2["completed"]))
+        assert F2 < 0.999 or s2["completed"] == st_ex["completed"], (eps, F2, s2["completed"])
+    print("learned:", F, st["completed"], "of", st_ex["completed"], "threshold:", gains)
