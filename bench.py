@@ -355,6 +355,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     jobs, cfg = workload_jobs(args.workload, rank, args.outputs)
+    if args.learned_cut:
+        ap_, ar_ = (int(v) for v in args.learned_cut.split(","))
+        for w in jobs:
+            if w.meta.get("learned_cut") is not None:
+                w.meta["learned_cut"] = (ap_, ar_)
+        cfg["learned_cut_sources"] = [ap_, ar_]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     peaks = fs.api.probe_peaks()
     import json as _json
@@ -377,6 +383,9 @@ def run_ours(args):
     # learned: a pruner per job trained on separately seeded requests
     tr_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 100)
     va_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 200)
+    for wl in (tr_jobs, va_jobs):
+        for w, w0 in zip(wl, jobs):
+            w.meta["learned_cut"] = w0.meta.get("learned_cut")
     learned_info = None
     if not args.plain_only:
         pr = [train_pruner(fs, args, tr, va, dev, stream, sp) for tr, va, sp in zip(tr_jobs, va_jobs, stats_plain)]
@@ -479,6 +488,8 @@ def main():
     ap.add_argument("--engine", default="straight", choices=["straight", "interp"])
     ap.add_argument("--plain-only", action="store_true", help="exact run only, no learned pruning")
     ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--learned-cut", default=None,
+                    help="A_p,A_r: artificial sources before the learned cut and in the root after it")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
