@@ -35,15 +35,15 @@ def workload_jobs(name, rank=0, outputs=None, seed_shift=0):
     if name == "qw100":
         n_out = qw_out if seed_shift == 0 else 512
         w = qw_workload(n_out=n_out, seed=0x5EED0005 + rank + seed_shift)
-        w.meta["learned_cut"] = (8, 3)
+        w.meta["learned_cut"] = (7, 6)
         return [w], {"workload": f"qw100_t16_{qw_out}out", "qubits": 100, "steps": 16,
-                     "outputs": qw_out, "input_support": 2, "learned_cut_sources": [8, 3]}
+                     "outputs": qw_out, "input_support": 2, "learned_cut_sources": [7, 6]}
     if name == "qw100+qaoa16":
         n_qw = qw_out if seed_shift == 0 else 512
         n_qa = 4 if seed_shift == 0 else 32
         ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift),
               qaoa_workload(16, 2, n_out=n_qa, seed=0x5EED0003 + rank + seed_shift)]
-        ws[0].meta["learned_cut"] = (8, 3)
+        ws[0].meta["learned_cut"] = (7, 6)
         ws[1].meta["learned_cut"] = None
         return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_p2_4out", "outputs": qw_out + 4}
     raise SystemExit(f"unknown workload {name}")

@@ -125,6 +125,10 @@ typedef struct fs_options {
                                       per-tile partial sums (0: 2^28) */
     uint32_t engine;               /* history kernel: 0 = straight-line code generated per
                                       batch at upload (NVRTC, sm_103a), 1 = interpreter */
+    uint32_t prefix_mode;          /* 0 = prefix expanded level by level, one level per
+                                      branching op carrying a source (each level's gates run
+                                      once per partial assignment); 1 = one region per
+                                      prefix assignment, as in Algorithm 2 */
 } fs_options;
 
 /* Counters of one job after a run. */

@@ -44,7 +44,8 @@ class fs_analysis(ctypes.Structure):
 class fs_options(ctypes.Structure):
     _fields_ = [("split", ctypes.c_uint32), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
                 ("table_budget_bytes", ctypes.c_uint64), ("min_items", ctypes.c_uint64),
-                ("max_items", ctypes.c_uint64), ("engine", ctypes.c_uint32)]
+                ("max_items", ctypes.c_uint64), ("engine", ctypes.c_uint32),
+                ("prefix_mode", ctypes.c_uint32)]
 
 
 class fs_stats(ctypes.Structure):

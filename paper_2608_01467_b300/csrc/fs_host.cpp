@@ -376,6 +376,8 @@ struct Job {
     // pruned jobs (eps > 0 or a learned pruner) run over compacted live entries
     bool compact = false;
     int fixed_c1 = -1, fixed_c2 = -1;     // per-job cuts overriding the batch split
+    std::vector<fs::PrefixLevel> levels;  // per-source prefix expansion (empty: single region)
+    size_t o_lvscratch = 0;
     size_t o_live = 0, o_esum = 0, o_blk = 0;
     uint64_t nblk = 0;
 };
@@ -581,6 +583,7 @@ int fs_batch_set_options(fs_batch* b, const fs_options* opt)
     if (opt) {
         if (opt->split > 2) return fail(FS_ERR_INVALID, "split must be 0, 1 or 2");
         if (opt->engine > 1) return fail(FS_ERR_INVALID, "engine must be 0 or 1");
+        if (opt->prefix_mode > 1) return fail(FS_ERR_INVALID, "prefix_mode must be 0 or 1");
         b->opt = *opt;
     } else {
         std::memset(&b->opt, 0, sizeof b->opt);
@@ -767,6 +770,36 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         if (j.sp.Ap + j.sp.Ar + ilog2_ceil(std::max<uint64_t>(j.pairs, 1)) > 40)
             return fail(FS_ERR_TOO_LARGE, "job %zu: too many (prefix, root) items", ji);
         compile(C, j.W, j.sp, j.prog);
+        j.levels.clear();
+        if (b->opt.prefix_mode == 0 && j.sp.Ap > 0 && j.pairs > 0) {
+            // boundaries after every op carrying a prefix source; the tail
+            // without sources joins the last level
+            std::vector<int> ends;
+            int a = 0;
+            std::vector<int> bits;
+            for (int e = 0; e < j.sp.c1; ++e) {
+                const fs::Op& op = j.prog.ops[e];
+                const int na = (op.s0 >= 0) + (op.s1 >= 0);
+                if (na && (op.code == fs::OP_H || op.code == fs::OP_BR1 || op.code == fs::OP_BR2)) {
+                    a += na;
+                    ends.push_back(e + 1);
+                    bits.push_back(a);
+                }
+            }
+            if (ends.size() >= 2) {
+                int prev_e = 0, prev_a = 0;
+                for (size_t k = 0; k < ends.size(); ++k) {
+                    fs::PrefixLevel L;
+                    L.e0 = prev_e;
+                    L.e1 = (k + 1 == ends.size()) ? j.sp.c1 : ends[k];
+                    L.a_prev = prev_a;
+                    L.a_next = bits[k];
+                    j.levels.push_back(L);
+                    prev_e = L.e1;
+                    prev_a = L.a_next;
+                }
+            }
+        }
         {
             fs::FeatureSpec& f = j.fspec;
             f.log10_eps_ref = (float)std::log10(j.eps > 0 ? j.eps : 1e-6);
@@ -791,7 +824,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         j.n_tiles = j.compact ? 0 : (items + fs::TILE - 1) / fs::TILE;
         j.nblk = j.compact ? (j.table_entries + fs::COMPACT_BLOCK - 1) / fs::COMPACT_BLOCK : 0;
         if (j.n_tiles >= (1ull << 32)) return fail(FS_ERR_TOO_LARGE, "job %zu: too many tiles", ji);
-        b->total_prefix += j.table_entries;
+        if (j.levels.empty()) b->total_prefix += j.table_entries;
         b->total_out += j.outs.size();
         // predicted cost of one tile (Eq. 8 per item): G_r + 2^As G_s
         const double tile_cost = (double)(j.sp.c2 - j.sp.c1) + std::ldexp((double)(G - j.sp.c2), j.sp.As);
@@ -832,6 +865,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     for (Job& j : b->jobs) {
         j.o_table = take(j.table_entries * sizeof(fs::Entry));
         j.o_part = take(j.n_partials * sizeof(double2));
+        if (!j.levels.empty()) j.o_lvscratch = take((j.table_entries / 2) * sizeof(fs::Entry));
         if (j.compact) {
             j.o_live = take(j.table_entries * sizeof(uint64_t));
             j.o_esum = take((j.table_entries << j.sp.Ar) * sizeof(double2));
@@ -897,7 +931,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.n_entries = j.table_entries;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
-        pacc += j.table_entries;
+        if (j.levels.empty()) pacc += j.table_entries;
         oacc += j.outs.size();
         std::memcpy(&H[j.o_ops], j.prog.ops.data(), j.prog.ops.size() * sizeof(fs::Op));
         std::memcpy(&H[j.o_masks], j.prog.masks.data(), j.prog.masks.size() * sizeof(uint32_t));
@@ -921,7 +955,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
             const Job& j = b->jobs[ji];
             specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
                                        j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
-                                       j.sp.As, j.eps * j.eps, j.compact};
+                                       j.sp.As, j.eps * j.eps, j.compact, j.levels};
         }
         std::string err, src;
         const char* dump = getenv("FS_JIT_DUMP");   // optional: write the generated source here
@@ -944,14 +978,16 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
 int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
 {
     if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
-    uint32_t k = 2;   // prefix, reduce
-    bool tiled = false;
+    uint32_t k = 1;   // reduce
+    bool tiled = false, flat_prefix = false;
     for (const Job& j : b->jobs) {
         tiled |= !j.compact;
+        flat_prefix |= j.levels.empty();
+        k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
         if (j.compact) k += 4;                  // count, scan, write, history over live entries
     }
-    *n = k + (tiled ? 1 : 0);
+    *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
 }
 
@@ -1001,7 +1037,26 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
     CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
     if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[0], s));
-    if (b->jit)
+    for (int ji = 0; ji < nj; ++ji) {
+        const Job& j = b->jobs[ji];
+        const int m = (int)j.levels.size();
+        for (int k = 0; k < m; ++k) {
+            // the last level writes the table; earlier ones alternate with the scratch
+            fs::Entry* table = (fs::Entry*)(base + j.o_table);
+            fs::Entry* scratch = (fs::Entry*)(base + j.o_lvscratch);
+            fs::Entry* dst = ((m - 1 - k) % 2 == 0) ? table : scratch;
+            const fs::Entry* src = k == 0 ? nullptr : (((m - k) % 2 == 0) ? table : scratch);
+            const uint64_t n = j.pairs << j.levels[k].a_next;
+            if (b->jit)
+                CUDA_TRY(fs::jit_launch_prefix_level(b->jit, jobs, ji, k, j.levels[k], src, dst, n, k + 1 == m, s));
+            else
+                CUDA_TRY(fs::launch_prefix_level(jobs + ji, j.levels[k], src, dst, n, k + 1 == m,
+                                                 (uint32_t*)(base + b->o_err), s));
+        }
+    }
+    if (b->total_prefix == 0) {
+        // every job expanded its prefix level by level
+    } else if (b->jit)
         CUDA_TRY(fs::jit_launch_prefix(b->jit, jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix, s));
     else
         CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
@@ -1189,11 +1244,25 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
     const Job& j = b->jobs[job];
     const int G = (int)j.prog.ops.size();
     const int cuts[4] = {0, j.sp.c1, j.sp.c2, G};
+    const bool deferred = b->opt.engine == 0 && j.eps == 0.0;
     for (int r = 0; r < 3; ++r) {
         double i = 0, f = 0;
-        region_work(j, cuts[r], cuts[r + 1], i, f, b->opt.engine == 0 && j.eps == 0.0);
+        region_work(j, cuts[r], cuts[r + 1], i, f, deferred);
         int_ops[r] = i;
         fp64_ops[r] = f;
+    }
+    if (!j.levels.empty()) {
+        // level-by-level prefix: each level's ops run once per entry of that
+        // level; reported per final table entry
+        double i = 0, f = 0;
+        for (const fs::PrefixLevel& L : j.levels) {
+            double li = 0, lf = 0;
+            region_work(j, L.e0, L.e1, li, lf, deferred);
+            i += li * std::ldexp(1.0, L.a_next - j.sp.Ap);
+            f += lf * std::ldexp(1.0, L.a_next - j.sp.Ap);
+        }
+        int_ops[0] = i;
+        fp64_ops[0] = f;
     }
     // per completed leaf: the chi test (2W); per valid leaf: two FP64 adds
     int_ops[3] = 2.0 * j.W;

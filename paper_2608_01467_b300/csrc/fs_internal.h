@@ -126,11 +126,24 @@ cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int j
 // Device error word values.
 constexpr uint32_t DEV_ERR_BAD_OPCODE = 1;
 
+// One level of the per-source prefix expansion: ops [e0, e1) extend every
+// entry of the previous level (a_prev source bits, in src; NULL for the
+// first level, which starts at b_out) to a_next bits, into dst.
+struct PrefixLevel {
+    int e0, e1;
+    int a_prev, a_next;
+};
+
+
 // Launch entry points (fs_kernels.cu).
 cudaError_t launch_prefix(const JobDev* d_jobs, const uint64_t* d_job_prefix_begin, int n_jobs,
                           uint64_t total_prefix, uint32_t* d_err, cudaStream_t s);
 cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
                            unsigned int* d_counter, uint32_t* d_err, int grid, cudaStream_t s);
+cudaError_t launch_prefix_level(const JobDev* d_job, const PrefixLevel& L, const Entry* src, Entry* dst,
+                                uint64_t n_dst, bool last, uint32_t* d_err, cudaStream_t s);
+cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job, int level, const PrefixLevel& L,
+                                    const Entry* src, Entry* dst, uint64_t n_dst, bool last, cudaStream_t s);
 cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t s);
 cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s);
 int compact_grid_size(int device);
@@ -149,6 +162,7 @@ struct JitJobSpec {
     int W, c1, c2, Ap, Ar, As;
     double eps2;
     bool compact;
+    std::vector<PrefixLevel> levels;   // empty: single-region prefix
 };
 int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
               std::string* source_out);

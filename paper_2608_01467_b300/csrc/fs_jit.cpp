@@ -218,6 +218,45 @@ __device__ void compact_body(const JobDev& J, u64 i, u64& completed, u64& valid,
     J.esum[i] = acc;
 }
 
+// Level expansion prologue / epilogue (per-source prefix levels).
+template <class T>
+__device__ __forceinline__ bool lv_load(const JobDev& J, int a_prev, int a_next, const Entry* __restrict__ src,
+                                        u64 idx, u32 (&st)[T::W], u32 (&bin)[T::W], double2& amp)
+{
+    constexpr int W = T::W;
+    const u64 pair = idx >> a_next;
+    const u64 child = idx & ((1ull << a_next) - 1ull);
+    const u64 o = pair / (u64)J.S;
+    const u64 sidx = pair - o * (u64)J.S;
+    const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
+    const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+    uint4 sv;
+    if (!src) {
+        sv = __ldg(reinterpret_cast<const uint4*>(J.outs + 4 * o));
+        amp = make_double2(1.0, 0.0);
+    } else {
+        const uint4* ent = reinterpret_cast<const uint4*>(src + (pair << a_prev) + (child >> (a_next - a_prev)));
+        sv = ent[0];
+        amp = reinterpret_cast<const double2*>(ent + 1)[0];
+    }
+    const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+    for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
+    return !isnan(amp.x);
+}
+
+template <class T>
+__device__ __forceinline__ void lv_store(Entry* __restrict__ dst, u64 idx, const u32 (&st)[T::W], double2 amp, bool live)
+{
+    u32 w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < T::W; ++j) w[j] = st[j];
+    if (!live) amp.x = __longlong_as_double(0x7ff8000000000000ll);
+    uint4* d = reinterpret_cast<uint4*>(dst + idx);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<double2*>(d + 1)[0] = amp;
+}
+
 __device__ __forceinline__ int find_job(const u64* __restrict__ begin, int n_jobs, u64 idx)
 {
     int lo = 0, hi = n_jobs - 1;
@@ -515,8 +554,14 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
                    std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
         const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
         structs += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
-        emit_region(structs, globals, js + "p", J, 0, J.c1, J.Ap);
+        if (J.levels.empty()) emit_region(structs, globals, js + "p", J, 0, J.c1, J.Ap);
+        else structs += "    (void)s; (void)a; (void)visits;\n    return -1;   // expanded level by level\n";
         structs += "  }\n";
+        for (size_t k = 0; k < J.levels.size(); ++k) {
+            structs += "  static __device__ __forceinline__ int lv" + std::to_string(k) + sig + " {\n    (void)h; (void)bin;\n";
+            emit_region(structs, globals, js + "l" + std::to_string(k), J, J.levels[k].e0, J.levels[k].e1, J.Ap);
+            structs += "  }\n";
+        }
         structs += "  static __device__ __forceinline__ int root" + sig + " {\n    (void)h; (void)bin;\n";
         emit_region(structs, globals, js + "r", J, J.c1, J.c2, J.Ar);
         structs += "  }\n";
@@ -552,6 +597,27 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
            "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
            "    if (lane == 0 && (completed | valid | visits)) {\n"
            "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        if (jobs[j].levels.empty()) continue;
+        const std::string js = std::to_string(j), T = "J" + js;
+        src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_lv_" + js +
+               "(const JobDev* __restrict__ jobs, int level, int a_prev, int a_next, const Entry* __restrict__ src, "
+               "Entry* __restrict__ dst, u64 n, int last)\n{\n"
+               "    const JobDev& J = jobs[" + js + "];\n    u64 visits = 0, entries = 0;\n"
+               "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (u64)gridDim.x * blockDim.x) {\n"
+               "        u32 st[" + T + "::W], bin[" + T + "::W];\n        double2 a;\n"
+               "        bool live = lv_load<" + T + ">(J, a_prev, a_next, src, idx, st, bin, a);\n"
+               "        if (live) {\n            const u64 h = (idx & ((1ull << a_next) - 1ull)) << (" + T + "::Ap - a_next);\n"
+               "            int r = -1;\n            switch (level) {\n";
+        for (size_t k = 0; k < jobs[j].levels.size(); ++k)
+            src += "            case " + std::to_string(k) + ": r = " + T + "::lv" + std::to_string(k) + "(st, a, h, bin, visits); break;\n";
+        src += "            default: break;\n            }\n            live = r < 0;\n        }\n"
+               "        if (live && last) ++entries;\n"
+               "        lv_store<" + T + ">(dst, idx, st, a, live);\n    }\n"
+               "    visits = warp_sum_u64(visits);\n    entries = warp_sum_u64(entries);\n"
+               "    if ((threadIdx.x & 31) == 0) {\n        if (visits) atomicAdd(&J.stats[4], visits);\n"
+               "        if (entries) atomicAdd(&J.stats[3], entries);\n    }\n}\n";
+    }
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_prefix(const JobDev* __restrict__ jobs, "
            "const u64* __restrict__ begin, int n_jobs, u64 total)\n{\n"
            "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (u64)gridDim.x * blockDim.x) {\n"
@@ -576,6 +642,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
 }
 
 struct JitModule {
+    std::vector<cudaKernel_t> lv;     // per job: level kernel (nullptr when the job has no levels)
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
     cudaKernel_t prefix = nullptr;
@@ -622,6 +689,10 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->kernel, m->lib, "fs_jit_history");
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->prefix, m->lib, "fs_jit_prefix");
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->compact, m->lib, "fs_jit_compact");
+    m->lv.assign(jobs.size(), nullptr);
+    for (size_t j = 0; j < jobs.size() && e == cudaSuccess; ++j)
+        if (!jobs[j].levels.empty())
+            e = cudaLibraryGetKernel(&m->lv[j], m->lib, ("fs_jit_lv_" + std::to_string(j)).c_str());
     if (e != cudaSuccess) {
         *err = std::string("loading the generated kernel (compiled in ") +
                std::to_string(compile_ms ? *compile_ms : 0.0) + " ms): " + cudaGetErrorString(e);
@@ -662,6 +733,20 @@ cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t
     if (blocks > (uint64_t)m->sms * 64) blocks = (uint64_t)m->sms * 64;
     void* args[] = {(void*)&d_jobs, (void*)&d_begin, (void*)&n_jobs, (void*)&total};
     return cudaLaunchKernel((const void*)m->prefix, dim3((unsigned)blocks), dim3(256), args, 0, s);
+}
+
+cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job, int level, const PrefixLevel& L,
+                                    const Entry* src, Entry* dst, uint64_t n_dst, bool last, cudaStream_t s)
+{
+    if (n_dst == 0) return cudaSuccess;
+    JitModule* m = (JitModule*)handle;
+    if (job < 0 || job >= (int)m->lv.size() || !m->lv[job]) return cudaErrorInvalidValue;
+    uint64_t blocks = (n_dst + 255) / 256;
+    if (blocks > (uint64_t)m->sms * 64) blocks = (uint64_t)m->sms * 64;
+    int a_prev = L.a_prev, a_next = L.a_next, lst = last ? 1 : 0;
+    void* args[] = {(void*)&d_jobs, (void*)&level, (void*)&a_prev, (void*)&a_next, (void*)&src, (void*)&dst,
+                    (void*)&n_dst, (void*)&lst};
+    return cudaLaunchKernel((const void*)m->lv[job], dim3((unsigned)blocks), dim3(TILE), args, 0, s);
 }
 
 cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s)

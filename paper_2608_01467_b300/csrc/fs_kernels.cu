@@ -292,6 +292,67 @@ __global__ void __launch_bounds__(256) prefix_kernel(const JobDev* __restrict__ 
     }
 }
 
+// One level of the per-source prefix expansion: thread per entry of the
+// next level; the entry's parent is the previous level's entry with the same
+// leading source bits (or b_out at the first level).
+template <int W>
+__device__ void prefix_level_one(const JobDev& J, const PrefixLevel& L, const Entry* __restrict__ src,
+                                 Entry* __restrict__ dst, uint64_t idx, bool last, uint32_t* err,
+                                 unsigned long long& visits, unsigned long long& entries)
+{
+    const uint64_t pair = idx >> L.a_next;
+    const uint64_t child = idx & ((1ull << L.a_next) - 1ull);
+    const uint64_t o = pair / (uint64_t)J.S;
+    const uint64_t s = pair - o * (uint64_t)J.S;
+    uint32_t st[W], bin[W];
+    load_bits<W>(J.ins + 4 * s, bin);
+    double2 amp = make_double2(1.0, 0.0);
+    bool live = true;
+    if (!src) {
+        load_bits<W>(J.outs + 4 * o, st);
+    } else {
+        const uint64_t parent = (pair << L.a_prev) + (child >> (L.a_next - L.a_prev));
+        const uint4* ent = reinterpret_cast<const uint4*>(src + parent);
+        const uint4 sv = ent[0];
+        amp = reinterpret_cast<const double2*>(ent + 1)[0];
+        const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+        for (int j = 0; j < W; ++j) st[j] = tmp[j];
+        live = !isnan(amp.x);
+    }
+    if (live) {
+        const uint64_t h = child << (J.Ap - L.a_next);
+        live = run_ops<W>(J, L.e0, L.e1, st, amp, h, J.Ap, bin, visits, err) < 0;
+    }
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < W; ++j) w[j] = st[j];
+    if (!live) amp.x = __longlong_as_double(0x7ff8000000000000ll);
+    else if (last) entries += 1;
+    uint4* d = reinterpret_cast<uint4*>(dst + idx);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<double2*>(d + 1)[0] = amp;
+}
+
+__global__ void __launch_bounds__(256) prefix_level_kernel(const JobDev* __restrict__ jobp, PrefixLevel L,
+                                                           const Entry* __restrict__ src, Entry* __restrict__ dst,
+                                                           uint64_t n, int last, uint32_t* err)
+{
+    const JobDev& J = *jobp;
+    unsigned long long visits = 0, entries = 0;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (uint64_t)gridDim.x * blockDim.x) {
+        if (J.W == 1) prefix_level_one<1>(J, L, src, dst, idx, last != 0, err, visits, entries);
+        else if (J.W == 2) prefix_level_one<2>(J, L, src, dst, idx, last != 0, err, visits, entries);
+        else prefix_level_one<4>(J, L, src, dst, idx, last != 0, err, visits, entries);
+    }
+    visits = warp_sum_u64(visits);
+    entries = warp_sum_u64(entries);
+    if ((threadIdx.x & 31) == 0) {
+        if (visits) atomicAdd(&J.stats[4], visits);
+        if (entries) atomicAdd(&J.stats[3], entries);
+    }
+}
+
 // ---------------------------------------------------------------- history
 
 template <int W>
@@ -743,6 +804,16 @@ cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t 
     if (n_tiles == 0) return cudaSuccess;
     if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
     history_kernel<<<grid, TILE, 0, s>>>(d_jobs, d_tiles, n_tiles, d_counter, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prefix_level(const JobDev* d_job, const PrefixLevel& L, const Entry* src, Entry* dst,
+                                uint64_t n_dst, bool last, uint32_t* d_err, cudaStream_t s)
+{
+    if (n_dst == 0) return cudaSuccess;
+    uint64_t blocks = (n_dst + 255) / 256;
+    if (blocks > 148ull * 64) blocks = 148ull * 64;
+    prefix_level_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_job, L, src, dst, n_dst, last ? 1 : 0, d_err);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ constexpr int T_STRIDE = 136;     // bf16 per row of per-warp 16 x 128 tiles
 constexpr int X_STRIDE = 24;      // bf16 per row of per-warp 16 x 16 input tiles
 constexpr int FWD_WARPS = 8;
 constexpr int BWD_WARPS = 4;
+constexpr int PRUNE_WARPS = 4;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -44,6 +45,13 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_cuts(unsigned long long v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
 }
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
@@ -131,6 +139,59 @@ __device__ __forceinline__ void forward_tile(const float* __restrict__ P, const 
     f.y1 = s1 + P[OFF_B3];
 }
 
+// Inference-only forward of 16 rows: layer-2 tiles are reduced into the
+// layer-3 dot as they are produced, so neither h1 nor h2 stays live
+// (low register use).  Same operands, roundings and sums as forward_tile.
+__device__ __forceinline__ void score_tile(const float* __restrict__ P, const __nv_bfloat16* xs,
+                                           const __nv_bfloat16* w1t, const __nv_bfloat16* w2t,
+                                           float& y0, float& y1)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t a[4];
+    a[0] = ld32(xs + g * X_STRIDE + 2 * t);
+    a[1] = ld32(xs + (g + 8) * X_STRIDE + 2 * t);
+    a[2] = ld32(xs + g * X_STRIDE + 2 * t + 8);
+    a[3] = ld32(xs + (g + 8) * X_STRIDE + 2 * t + 8);
+    uint32_t a2[8][4];
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+        float c[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * kt + h;
+            const float b0 = P[OFF_B1 + 8 * j + 2 * t], b1v = P[OFF_B1 + 8 * j + 2 * t + 1];
+            c[h][0] = b0; c[h][1] = b1v; c[h][2] = b0; c[h][3] = b1v;
+            const __nv_bfloat16* wb = w1t + (8 * j + g) * W1T_STRIDE + 2 * t;
+            mma_bf16(c[h], a, ld32(wb), ld32(wb + 8));
+        }
+        a2[kt][0] = pack_bf16(fmaxf(c[0][0], 0.f), fmaxf(c[0][1], 0.f));
+        a2[kt][1] = pack_bf16(fmaxf(c[0][2], 0.f), fmaxf(c[0][3], 0.f));
+        a2[kt][2] = pack_bf16(fmaxf(c[1][0], 0.f), fmaxf(c[1][1], 0.f));
+        a2[kt][3] = pack_bf16(fmaxf(c[1][2], 0.f), fmaxf(c[1][3], 0.f));
+    }
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+        float d[4];
+        const float b0 = P[OFF_B2 + 8 * j + 2 * t], b1v = P[OFF_B2 + 8 * j + 2 * t + 1];
+        d[0] = b0; d[1] = b1v; d[2] = b0; d[3] = b1v;
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+            const __nv_bfloat16* wb = w2t + (8 * j + g) * W2_STRIDE + 16 * kt + 2 * t;
+            mma_bf16(d, a2[kt], ld32(wb), ld32(wb + 8));
+        }
+        const float w0 = bf16r(P[OFF_W3 + 8 * j + 2 * t]), w1 = bf16r(P[OFF_W3 + 8 * j + 2 * t + 1]);
+        s0 += fmaxf(d[0], 0.f) * w0 + fmaxf(d[1], 0.f) * w1;
+        s1 += fmaxf(d[2], 0.f) * w0 + fmaxf(d[3], 0.f) * w1;
+    }
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+    y0 = s0 + P[OFF_B3];
+    y1 = s1 + P[OFF_B3];
+}
+
 // Loads 16 rows of 16 FP32 features (rows >= n are zero) as bf16 into xs.
 __device__ __forceinline__ void load_x(const float* __restrict__ X, long long row0, long long n, __nv_bfloat16* xs)
 {
@@ -157,12 +218,12 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) mlp_forward_kernel(const float
     const long long tiles = (n + 15) / 16;
     for (long long tile = (long long)blockIdx.x * FWD_WARPS + warp; tile < tiles; tile += (long long)gridDim.x * FWD_WARPS) {
         load_x(X, tile * 16, n, xs);
-        Fwd f;
-        forward_tile(P, xs, w1t, w2t, f);
+        float y0, y1;
+        score_tile(P, xs, w1t, w2t, y0, y1);
         if (t == 0) {
             const long long r0 = tile * 16 + g, r1 = r0 + 8;
-            if (r0 < n) Y[r0] = f.y0;
-            if (r1 < n) Y[r1] = f.y1;
+            if (r0 < n) Y[r0] = y0;
+            if (r1 < n) Y[r1] = y1;
         }
         __syncwarp();
     }
@@ -430,51 +491,54 @@ __global__ void features_kernel(const JobDev* __restrict__ jobs, int job, Featur
 
 // Scores every live entry of a job's checkpoint table with the MLP and cuts
 // (marks bottom) those predicted below tau; counts cuts into stats[5].
-__global__ void __launch_bounds__(FWD_WARPS * 32) learned_prune_kernel(const float* __restrict__ P,
-                                                                       const JobDev* __restrict__ jobs, int job,
-                                                                       FeatureSpec sp, float tau)
+__global__ void __launch_bounds__(PRUNE_WARPS * 32) learned_prune_kernel(const float* __restrict__ P,
+                                                                         const JobDev* __restrict__ jobs, int job,
+                                                                         FeatureSpec sp, float tau)
 {
     __shared__ __align__(16) __nv_bfloat16 w1t[H * W1T_STRIDE];
     __shared__ __align__(16) __nv_bfloat16 w2t[H * W2_STRIDE];
-    __shared__ __align__(16) __nv_bfloat16 xs_all[FWD_WARPS][16 * X_STRIDE];
-    __shared__ unsigned char live[FWD_WARPS][16];
+    __shared__ __align__(16) __nv_bfloat16 xs_all[PRUNE_WARPS][32 * X_STRIDE];
     stage_weights(P, w1t, w2t, nullptr);
     __syncthreads();
     const JobDev& J = jobs[job];
     const unsigned long long n = J.n_pairs << J.Ap;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     __nv_bfloat16* xs = xs_all[warp];
-    const long long tiles = (long long)((n + 15) / 16);
+    const long long tiles = (long long)((n + 31) / 32);
     unsigned long long cuts = 0;
-    for (long long tile = (long long)blockIdx.x * FWD_WARPS + warp; tile < tiles; tile += (long long)gridDim.x * FWD_WARPS) {
-        if (lane < 16) {
-            const unsigned long long row = (unsigned long long)tile * 16 + lane;
-            float fv[16];
-            bool ok = false;
-            if (row < n) {
-                entry_features(J, row, sp, fv);
-                ok = !isnan(fv[0]);
-            }
-            for (int k = 0; k < 16; ++k) xs[lane * X_STRIDE + k] = __float2bfloat16_rn(ok ? fv[k] : 0.f);
-            live[warp][lane] = ok ? 1 : 0;
+    for (long long tile = (long long)blockIdx.x * PRUNE_WARPS + warp; tile < tiles; tile += (long long)gridDim.x * PRUNE_WARPS) {
+        // every lane computes the features of one entry
+        const unsigned long long row = (unsigned long long)tile * 32 + lane;
+        float fv[16];
+        bool ok = false;
+        if (row < n) {
+            entry_features(J, row, sp, fv);
+            ok = !isnan(fv[0]);
         }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) xs[lane * X_STRIDE + k] = __float2bfloat16_rn(ok ? fv[k] : 0.f);
+        const unsigned live = __ballot_sync(0xffffffffu, ok);
         __syncwarp();
-        Fwd f;
-        forward_tile(P, xs, w1t, w2t, f);
-        if (t == 0) {
-            const int rows[2] = {g, g + 8};
-            const float ys[2] = {f.y0, f.y1};
-            for (int k = 0; k < 2; ++k) {
-                const unsigned long long row = (unsigned long long)tile * 16 + rows[k];
-                if (live[warp][rows[k]] && ys[k] < tau) {
-                    J.table[row].amp.x = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float y0, y1;
+            score_tile(P, xs + 16 * half * X_STRIDE, w1t, w2t, y0, y1);
+            if (t == 0) {
+                const int r0 = 16 * half + g, r1 = r0 + 8;
+                if (((live >> r0) & 1u) && y0 < tau) {
+                    J.table[(unsigned long long)tile * 32 + r0].amp.x = __longlong_as_double(0x7ff8000000000000ll);
+                    ++cuts;
+                }
+                if (((live >> r1) & 1u) && y1 < tau) {
+                    J.table[(unsigned long long)tile * 32 + r1].amp.x = __longlong_as_double(0x7ff8000000000000ll);
                     ++cuts;
                 }
             }
         }
         __syncwarp();
     }
-    if (cuts) atomicAdd(&J.stats[5], cuts);
+    cuts = warp_sum_cuts(cuts);
+    if (lane == 0 && cuts) atomicAdd(&J.stats[5], cuts);
 }
 
 size_t grad_smem_bytes()
@@ -525,10 +589,10 @@ cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int j
                               float tau, unsigned long long n_entries, cudaStream_t s)
 {
     if (n_entries == 0) return cudaSuccess;
-    const unsigned long long tiles = (n_entries + 15) / 16;
-    unsigned long long blocks = (tiles + FWD_WARPS - 1) / FWD_WARPS;
-    if (blocks > 148 * 4) blocks = 148 * 4;
-    learned_prune_kernel<<<(unsigned)blocks, FWD_WARPS * 32, 0, s>>>(d_params, d_jobs, job, sp, tau);
+    const unsigned long long tiles = (n_entries + 31) / 32;
+    unsigned long long blocks = (tiles + PRUNE_WARPS - 1) / PRUNE_WARPS;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    learned_prune_kernel<<<(unsigned)blocks, PRUNE_WARPS * 32, 0, s>>>(d_params, d_jobs, job, sp, tau);
     return cudaGetLastError();
 }
 

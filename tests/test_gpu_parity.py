@@ -141,9 +141,9 @@ def test_aa_fig8_ablation_rows_agree():
     want = dense.amplitudes(w.circuit, w.inputs, outs)
     G = len(w.circuit.gates)
     res = {}
-    for name, kw in (("none", dict(split="none")),
-                     ("thirds", dict(split="fixed", c1=G // 3, c2=2 * G // 3)),
-                     ("auto", dict(split="auto"))):
+    for name, kw in (("none", dict(split="none", prefix="single")),
+                     ("thirds", dict(split="fixed", c1=G // 3, c2=2 * G // 3, prefix="single")),
+                     ("auto", dict(split="auto", prefix="single"))):
         (a,), st, _ = run_batch([(w.circuit, w.inputs, outs, 0.0)], **kw)
         close(a, want)
         assert st[0]["valid"] == 10 * (1 << 24)
@@ -156,7 +156,7 @@ def test_aa_fig8_ablation_rows_agree():
 
 def test_qaoa8_exact_vs_dense_and_oracle_counts():
     w = qaoa_workload(8, 2, n_out=64, seed=31)
-    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)], prefix="single")
     close(a, dense.amplitudes(w.circuit, w.inputs, w.outputs))
     assert st[0]["completed"] == 64 * (1 << 16) == st[0]["valid"]
     cost = feynman.region_counts(w.circuit, st[0]["c1"], st[0]["c2"])[1]
@@ -312,3 +312,20 @@ def test_engines_bitwise_equal(case):
             assert x[k] == y[k], k
     o, _ = oracle_counts(*jobs[0][:3], eps=jobs[0][3])
     close(a1[0], o)
+
+
+@pytest.mark.parametrize("engine", ["straight", "interp"])
+def test_level_prefix_equals_single_region_prefix(engine):
+    """The prefix expanded one source level at a time gives the same
+    checkpoint table as Algorithm 2's one region per prefix assignment:
+    same amplitudes and history counts, fewer prefix gate visits."""
+    for w, eps in ((qaoa_workload(8, 2, n_out=48, seed=51), 0.0), (qaoa_workload(8, 2, n_out=48, seed=52), 0.02),
+                   (qw_workload(steps=6, n_out=40, pos_bits=8), 0.0)):
+        G = len(w.circuit.gates)
+        jobs = [(w.circuit, w.inputs, w.outputs, eps)]
+        a1, s1, _ = run_batch(jobs, split="fixed", c1=2 * G // 3, c2=5 * G // 6, prefix="single", engine=engine)
+        a2, s2, _ = run_batch(jobs, split="fixed", c1=2 * G // 3, c2=5 * G // 6, prefix="levels", engine=engine)
+        close(a2[0], a1[0])
+        for k in ("completed", "valid", "table_entries", "history_visits"):
+            assert s1[0][k] == s2[0][k], k
+        assert s2[0]["gate_visits"] - s2[0]["history_visits"] < s1[0]["gate_visits"] - s1[0]["history_visits"]

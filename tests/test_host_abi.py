@@ -163,13 +163,18 @@ def test_plan_layout_and_fixed_split_errors():
     b.add(C, w.outputs)
     with pytest.raises(_lib.FsError):
         b.plan()
-    b2 = fs.Batch()
+    b2 = fs.Batch(prefix="single")
     b2.add(C, w.outputs)
     b2.add(C, [])                      # empty job is allowed
     n = b2.plan()
     assert n > 0 and n % 256 == 0
     assert b2.total_outputs == 16
-    assert b2.launch_count() == 3
+    assert b2.launch_count() == 3      # prefix, history, reduce
+    b3 = fs.Batch()                    # prefix expanded level by level
+    b3.add(C, w.outputs)
+    b3.plan()
+    st_levels = b3.launch_count() - 2  # levels + history + reduce
+    assert st_levels >= 2
 
 
 def test_run_before_upload_is_a_state_error():
