@@ -282,10 +282,21 @@ def fidelity(a, b):
     return float(abs(np.vdot(a, b)) ** 2 / (na * nb))
 
 
-def timed_steps(b, steps, stream, flush, name):
+def capture(b, stream):
+    """The step's launches (counter reset, prefix levels, pruner, compaction,
+    history, reduction) captured once into a CUDA graph."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        b.run(stream)
+    torch.cuda.synchronize()
+    return g
+
+
+def timed_steps(b, steps, stream, flush, name, graph=None):
     """Device time of each step (CUDA events on the launch stream, L2 flushed
-    between steps) and the per-stage times of the library.  Each step is an
-    NVTX range `name` (for profiler filtering)."""
+    between steps) and the per-stage times of the library (its events are
+    nodes of the captured graph).  Each step is an NVTX range `name`."""
     import torch
     step_ms, stages, completed, valid = [], [], 0, 0
     for _ in range(steps):
@@ -294,7 +305,10 @@ def timed_steps(b, steps, stream, flush, name):
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push(name)
         e0.record(stream)
-        b.run(stream)
+        if graph is not None:
+            graph.replay()
+        else:
+            b.run(stream)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         st = b.finish(stream)
@@ -398,15 +412,18 @@ def run_ours(args):
             bl.finish(stream)
         stats_learned = bl.finish(stream)
 
+    graph_p = None if args.no_graph else capture(bp, stream)
+    graph_l = None if (args.no_graph or not learned_info) else capture(bl, stream)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize(dev)
-    plain_ms, plain_stage, plain_completed, _ = timed_steps(bp, args.steps, stream, flush, "plain_step")
+    plain_ms, plain_stage, plain_completed, _ = timed_steps(bp, args.steps, stream, flush, "plain_step", graph_p)
     plain_amp = bp.amp.cpu().numpy()
     if learned_info:
-        learned_ms, learned_stage, learned_completed, stats_learned = timed_steps(bl, args.steps, stream, flush, "learned_step")
+        learned_ms, learned_stage, learned_completed, stats_learned = timed_steps(bl, args.steps, stream, flush,
+                                                                                  "learned_step", graph_l)
         learned_amp = bl.amp.cpu().numpy()
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -449,6 +466,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded circuits and requests)",
             "config": dict(cfg, mode="learned pruning vs plain exact" if learned_info else "plain exact",
+                           launch="one CUDA graph per step" if not args.no_graph else "stream launches",
                            l2="flushed between steps (512 MiB write)",
                            parallelism=f"outputs sharded, {world} replica(s)", engine=engine,
                            engine_compile_ms=round(compile_ms, 1)),
@@ -487,6 +505,7 @@ def main():
     ap.add_argument("--outputs", type=int, default=None, help="requested outputs (small profiling cases)")
     ap.add_argument("--engine", default="straight", choices=["straight", "interp"])
     ap.add_argument("--plain-only", action="store_true", help="exact run only, no learned pruning")
+    ap.add_argument("--no-graph", action="store_true", help="launch on the stream instead of replaying a graph")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--learned-cut", default=None,
                     help="A_p,A_r: artificial sources before the learned cut and in the root after it")

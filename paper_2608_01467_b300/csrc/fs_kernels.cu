@@ -654,57 +654,54 @@ __device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t* __restrict__
 
 // ---------------------------------------------------------------- reduce
 
+// One warp per output: lanes stride over the pair's partials (or live
+// subtree sums) in a fixed order, a fixed xor butterfly combines them, and
+// lane 0 adds c_in * alpha over the input support in order.
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
                                                                 const uint64_t* __restrict__ begin,
                                                                 int n_jobs, uint64_t total, double2* amp_out)
 {
-    __shared__ double2 s_red[REDUCE_THREADS];
-    for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (REDUCE_THREADS / 32);
+    for (uint64_t g = (uint64_t)blockIdx.x * (REDUCE_THREADS / 32) + (threadIdx.x >> 5); g < total; g += warps) {
         const int j = find_job(begin, n_jobs, g);
         const JobDev& J = jobs[j];
         const uint64_t o = g - J.out_begin;
         double2 amp = make_double2(0.0, 0.0);
-        const uint64_t nslots = 1ull << J.log2_spp;
         for (int s = 0; s < J.S; ++s) {
             const uint64_t pair = o * (uint64_t)J.S + (uint64_t)s;
-            double2 t = make_double2(0.0, 0.0);
+            uint64_t lo, hi;
+            const double2* src;
             if (J.compact) {
                 const uint64_t nlive = J.stats[6];
-                const uint64_t lo = lower_bound_u64(J.live, nlive, pair << J.Ap) << J.Ar;
-                const uint64_t hi = lower_bound_u64(J.live, nlive, (pair + 1) << J.Ap) << J.Ar;
-                for (uint64_t k = lo + threadIdx.x; k < hi; k += REDUCE_THREADS) {
-                    const double2 v = J.esum[k];
-                    t.x += v.x;
-                    t.y += v.y;
-                }
+                lo = lower_bound_u64(J.live, nlive, pair << J.Ap) << J.Ar;
+                hi = lower_bound_u64(J.live, nlive, (pair + 1) << J.Ap) << J.Ar;
+                src = J.esum;
             } else {
-                const uint64_t base = pair << J.log2_spp;
-                for (uint64_t k = threadIdx.x; k < nslots; k += REDUCE_THREADS) {
-                    const double2 v = J.partials[base + k];
-                    t.x += v.x;
-                    t.y += v.y;
-                }
+                lo = pair << J.log2_spp;
+                hi = lo + (1ull << J.log2_spp);
+                src = J.partials;
             }
-            s_red[threadIdx.x] = t;
-            __syncthreads();
-            for (int w = REDUCE_THREADS / 2; w >= 1; w >>= 1) {
-                if ((int)threadIdx.x < w) {
-                    s_red[threadIdx.x].x += s_red[threadIdx.x + w].x;
-                    s_red[threadIdx.x].y += s_red[threadIdx.x + w].y;
-                }
-                __syncthreads();
+            double2 t = make_double2(0.0, 0.0);
+            for (uint64_t k = lo + lane; k < hi; k += 32) {
+                const double2 v = src[k];
+                t.x += v.x;
+                t.y += v.y;
             }
-            if (threadIdx.x == 0) {
-                const double2 w2 = cmul(__ldg(J.coef + s), s_red[0]);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+            }
+            if (lane == 0) {
+                const double2 w2 = cmul(__ldg(J.coef + s), t);
                 amp.x += w2.x;
                 amp.y += w2.y;
             }
-            __syncthreads();
         }
-        if (threadIdx.x == 0) amp_out[g] = amp;
+        if (lane == 0) amp_out[g] = amp;
     }
 }
-
 
 // ---------------------------------------------------------------- peak probes
 
@@ -845,7 +842,9 @@ cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_j
                           uint64_t total_out, double2* d_amp, cudaStream_t s)
 {
     if (total_out == 0) return cudaSuccess;
-    uint64_t blocks = total_out < 148ull * 16 ? total_out : 148ull * 16;
+    const uint64_t per_block = REDUCE_THREADS / 32;
+    uint64_t blocks = (total_out + per_block - 1) / per_block;
+    if (blocks > 148ull * 16) blocks = 148ull * 16;
     reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp);
     return cudaGetLastError();
 }
