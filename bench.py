@@ -367,7 +367,10 @@ def run_ours(args):
     rank, world, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream (graph capture needs a non-default one), made current
+    # so that torch's own work (L2 flush, events, copies) is ordered with ours
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     jobs, cfg = workload_jobs(args.workload, rank, args.outputs)
     if args.learned_cut:
         ap_, ar_ = (int(v) for v in args.learned_cut.split(","))
