@@ -1016,6 +1016,14 @@ int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* 
     return FS_OK;
 }
 
+// Stage events are recorded as external event nodes when the stream is being
+// captured into a graph (plain records otherwise), so a replayed graph still
+// times its stages.
+static cudaError_t record(cudaEvent_t e, cudaStream_t s)
+{
+    return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+}
+
 int fs_batch_stage_ms(fs_batch* b, float* ms)
 {
     if (!b || !ms) return fail(FS_ERR_INVALID, "NULL argument");
@@ -1036,7 +1044,7 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     const int nj = (int)b->jobs.size();
     const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
     CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
-    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[0], s));
+    if (b->timing) CUDA_TRY(record(b->ev[0], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         const int m = (int)j.levels.size();
@@ -1061,16 +1069,16 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     else
         CUDA_TRY(fs::launch_prefix(jobs, (const uint64_t*)(base + b->o_pbegin), nj, b->total_prefix,
                                    (uint32_t*)(base + b->o_err), s));
-    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[4], s));
+    if (b->timing) CUDA_TRY(record(b->ev[4], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         if (j.d_pruner)
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries, s));
     }
-    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[5], s));
+    if (b->timing) CUDA_TRY(record(b->ev[5], s));
     for (int ji = 0; ji < nj; ++ji)
         if (b->jobs[ji].compact) CUDA_TRY(fs::launch_compact(jobs + ji, b->jobs[ji].table_entries, s));
-    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[1], s));
+    if (b->timing) CUDA_TRY(record(b->ev[1], s));
     if (b->tiles.empty()) {
         // no tiled (exact) job: nothing to launch
     } else if (b->jit)
@@ -1084,11 +1092,11 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
         if (b->jit) CUDA_TRY(fs::jit_launch_compact(b->jit, jobs, ji, s));
         else CUDA_TRY(fs::launch_history_compact(jobs + ji, (uint32_t*)(base + b->o_err), b->compact_grid, s));
     }
-    if (b->timing) CUDA_TRY(cudaEventRecord(b->ev[2], s));
+    if (b->timing) CUDA_TRY(record(b->ev[2], s));
     CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
                                (double2*)d_amp_out, s));
     if (b->timing) {
-        CUDA_TRY(cudaEventRecord(b->ev[3], s));
+        CUDA_TRY(record(b->ev[3], s));
         b->ev_recorded = true;
     }
     return FS_OK;
