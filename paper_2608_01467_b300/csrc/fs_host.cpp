@@ -1021,7 +1021,11 @@ int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* 
 // times its stages.
 static cudaError_t record(cudaEvent_t e, cudaStream_t s)
 {
-    return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    const cudaError_t q = cudaStreamIsCapturing(s, &st);
+    if (q != cudaSuccess) return q;
+    if (st == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    return cudaEventRecord(e, s);
 }
 
 int fs_batch_stage_ms(fs_batch* b, float* ms)
