@@ -378,7 +378,7 @@ struct Job {
     int fixed_c1 = -1, fixed_c2 = -1;     // per-job cuts overriding the batch split
     std::vector<fs::PrefixLevel> levels;  // per-source prefix expansion (empty: single region)
     size_t o_lvscratch = 0;
-    size_t o_live = 0, o_esum = 0, o_blk = 0;
+    size_t o_live = 0, o_esum = 0, o_blk = 0, o_prange = 0;
     uint64_t nblk = 0;
 };
 
@@ -870,6 +870,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
             j.o_live = take(j.table_entries * sizeof(uint64_t));
             j.o_esum = take((j.table_entries << j.sp.Ar) * sizeof(double2));
             j.o_blk = take(j.nblk * sizeof(uint32_t));
+            j.o_prange = take(2 * j.pairs * sizeof(uint64_t));
         }
     }
     b->ws_bytes = off;
@@ -928,6 +929,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.live = j.compact ? (uint64_t*)(base + j.o_live) : nullptr;
         d.esum = j.compact ? (double2*)(base + j.o_esum) : nullptr;
         d.blk = j.compact ? (uint32_t*)(base + j.o_blk) : nullptr;
+        d.prange = j.compact ? (uint64_t*)(base + j.o_prange) : nullptr;
         d.n_entries = j.table_entries;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
@@ -985,7 +987,7 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         flat_prefix |= j.levels.empty();
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
-        if (j.compact) k += 4;                  // count, scan, write, history over live entries
+        if (j.compact) k += 5;                  // count, scan, write, pair ranges, history over live entries
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
@@ -1080,8 +1082,12 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries, s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[5], s));
-    for (int ji = 0; ji < nj; ++ji)
-        if (b->jobs[ji].compact) CUDA_TRY(fs::launch_compact(jobs + ji, b->jobs[ji].table_entries, s));
+    for (int ji = 0; ji < nj; ++ji) {
+        const Job& j = b->jobs[ji];
+        if (!j.compact) continue;
+        CUDA_TRY(cudaMemsetAsync(base + j.o_prange, 0, 2 * j.pairs * sizeof(uint64_t), s));
+        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, s));
+    }
     if (b->timing) CUDA_TRY(record(b->ev[1], s));
     if (b->tiles.empty()) {
         // no tiled (exact) job: nothing to launch

@@ -90,6 +90,7 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     uint64_t* live;            /* compacted live entry indices, table order */            \
     double2* esum;             /* subtree sum per (live entry, h_r) item */              \
     uint32_t* blk;             /* per compaction block: live count, then offset */       \
+    uint64_t* prange;          /* per pair: [lo, hi) of its live entries */              \
     uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */
 
 struct JobDev {

@@ -566,6 +566,19 @@ __global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __rest
         if (lv[k]) J.live[pos++] = base + (uint64_t)threadIdx.x * 4 + k;
 }
 
+// Each pair's range [lo, hi) in the live list (zeroed beforehand: pairs
+// without live entries keep an empty range).
+__global__ void __launch_bounds__(256) pair_range_kernel(const JobDev* __restrict__ jobp)
+{
+    const JobDev& J = *jobp;
+    const uint64_t nlive = J.stats[6];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlive; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p = J.live[i] >> J.Ap;
+        if (i == 0 || (J.live[i - 1] >> J.Ap) != p) J.prange[2 * p] = i;
+        if (i + 1 == nlive || (J.live[i + 1] >> J.Ap) != p) J.prange[2 * p + 1] = i + 1;
+    }
+}
+
 // History over the compacted live entries: items are (live entry, h_r)
 // pairs, item i = (live index i >> A_r, h_r = i & (2^A_r - 1)); a warp takes
 // 32 consecutive items off the job's work counter; each thread runs its root
@@ -642,15 +655,6 @@ __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __re
     }
 }
 
-__device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t* __restrict__ a, uint64_t n, uint64_t key)
-{
-    uint64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (a[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
 // ---------------------------------------------------------------- reduce
 
@@ -673,9 +677,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
             uint64_t lo, hi;
             const double2* src;
             if (J.compact) {
-                const uint64_t nlive = J.stats[6];
-                lo = lower_bound_u64(J.live, nlive, pair << J.Ap) << J.Ar;
-                hi = lower_bound_u64(J.live, nlive, (pair + 1) << J.Ap) << J.Ar;
+                lo = J.prange[2 * pair] << J.Ar;
+                hi = J.prange[2 * pair + 1] << J.Ar;
                 src = J.esum;
             } else {
                 lo = pair << J.log2_spp;
@@ -821,6 +824,9 @@ cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t
     compact_count_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
     compact_scan_kernel<<<1, 1024, 0, s>>>(d_job, (uint32_t)nblk);
     compact_write_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
+    uint64_t rblocks = (n_entries + 255) / 256;
+    if (rblocks > 148ull * 8) rblocks = 148ull * 8;
+    pair_range_kernel<<<(unsigned)rblocks, 256, 0, s>>>(d_job);
     return cudaGetLastError();
 }
 
