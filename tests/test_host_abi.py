@@ -185,3 +185,39 @@ def test_run_before_upload_is_a_state_error():
     L = _lib.load()
     rc = L.fs_batch_run(b._h, ctypes.c_void_p(256), ctypes.c_void_p(512), None)
     assert rc == -10
+
+
+def test_upload_rejects_truncated_or_misaligned_workspace():
+    """Truncated and misaligned device buffers are refused on the host,
+    before any device work is enqueued."""
+    w = qaoa_workload(6, 2, n_out=8, seed=4)
+    C = fs.Circuit(w.circuit)
+    b = fs.Batch()
+    b.add(C, w.outputs)
+    n = b.plan()
+    L = _lib.load()
+    assert L.fs_batch_upload(b._h, ctypes.c_void_p(1 << 20), n - 256, None) == -1
+    assert b"needed" in L.fs_last_error()
+    assert L.fs_batch_upload(b._h, ctypes.c_void_p((1 << 20) + 16), n, None) == -1
+    assert b"aligned" in L.fs_last_error()
+    assert L.fs_batch_upload(b._h, None, n, None) == -1
+
+
+def test_options_and_cut_validation():
+    L = _lib.load()
+    b = fs.Batch()
+    bad = _lib.fs_options()
+    bad.split = 7
+    assert L.fs_batch_set_options(b._h, ctypes.byref(bad)) == -1
+    bad = _lib.fs_options()
+    bad.engine = 3
+    assert L.fs_batch_set_options(b._h, ctypes.byref(bad)) == -1
+    C = fs.Circuit(qft(4))
+    b.add(C, [1, 2])
+    assert L.fs_batch_set_cuts(b._h, 0, 5, 2) == -1
+    assert L.fs_batch_set_cuts(b._h, 3, 0, 0) == -1
+    assert L.fs_batch_set_cuts(b._h, 0, 2, 99) == 0
+    with pytest.raises(_lib.FsError):
+        b.plan()                       # c2 beyond the gate count
+    assert L.fs_batch_set_cuts(b._h, 0, -1, -1) == 0
+    assert b.plan() > 0
