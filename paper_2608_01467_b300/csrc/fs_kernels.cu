@@ -658,16 +658,18 @@ __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __re
 
 // ---------------------------------------------------------------- reduce
 
-// One warp per output: lanes stride over the pair's partials (or live
-// subtree sums) in a fixed order, a fixed xor butterfly combines them, and
-// lane 0 adds c_in * alpha over the input support in order.
+// One block per output: threads stride over the pair's partials (or live
+// subtree sums) with 4 independent accumulators each (loads in flight), then
+// a fixed butterfly per warp and the warps in order; thread 0 adds
+// c_in * alpha over the input support in order.  The order is fixed by the
+// layout alone, so the result is run-to-run identical.
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
                                                                 const uint64_t* __restrict__ begin,
                                                                 int n_jobs, uint64_t total, double2* amp_out)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (REDUCE_THREADS / 32);
-    for (uint64_t g = (uint64_t)blockIdx.x * (REDUCE_THREADS / 32) + (threadIdx.x >> 5); g < total; g += warps) {
+    __shared__ double2 s_w[REDUCE_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
         const int j = find_job(begin, n_jobs, g);
         const JobDev& J = jobs[j];
         const uint64_t o = g - J.out_begin;
@@ -675,7 +677,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
         for (int s = 0; s < J.S; ++s) {
             const uint64_t pair = o * (uint64_t)J.S + (uint64_t)s;
             uint64_t lo, hi;
-            const double2* src;
+            const double2* __restrict__ src;
             if (J.compact) {
                 lo = J.prange[2 * pair] << J.Ar;
                 hi = J.prange[2 * pair + 1] << J.Ar;
@@ -685,24 +687,45 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
                 hi = lo + (1ull << J.log2_spp);
                 src = J.partials;
             }
-            double2 t = make_double2(0.0, 0.0);
-            for (uint64_t k = lo + lane; k < hi; k += 32) {
-                const double2 v = src[k];
-                t.x += v.x;
-                t.y += v.y;
+            double2 acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+            uint64_t k = lo + threadIdx.x;
+            for (; k + 3 * REDUCE_THREADS < hi; k += 4 * REDUCE_THREADS) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double2 v = src[k + (uint64_t)u * REDUCE_THREADS];
+                    acc[u].x += v.x;
+                    acc[u].y += v.y;
+                }
             }
+            for (int u = 0; k < hi; k += REDUCE_THREADS, ++u) {
+                const double2 v = src[k];
+                acc[u & 3].x += v.x;
+                acc[u & 3].y += v.y;
+            }
+            double2 t = make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                                     (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) {
                 t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
                 t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
             }
-            if (lane == 0) {
-                const double2 w2 = cmul(__ldg(J.coef + s), t);
+            if (lane == 0) s_w[warp] = t;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double2 a = s_w[0];
+                for (int w = 1; w < REDUCE_THREADS / 32; ++w) {
+                    a.x += s_w[w].x;
+                    a.y += s_w[w].y;
+                }
+                const double2 w2 = cmul(__ldg(J.coef + s), a);
                 amp.x += w2.x;
                 amp.y += w2.y;
             }
+            __syncthreads();
         }
-        if (lane == 0) amp_out[g] = amp;
+        if (threadIdx.x == 0) amp_out[g] = amp;
     }
 }
 
@@ -848,9 +871,7 @@ cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_j
                           uint64_t total_out, double2* d_amp, cudaStream_t s)
 {
     if (total_out == 0) return cudaSuccess;
-    const uint64_t per_block = REDUCE_THREADS / 32;
-    uint64_t blocks = (total_out + per_block - 1) / per_block;
-    if (blocks > 148ull * 16) blocks = 148ull * 16;
+    uint64_t blocks = total_out < 148ull * 16 ? total_out : 148ull * 16;
     reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp);
     return cudaGetLastError();
 }
