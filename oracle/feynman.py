@@ -60,6 +60,10 @@ def lib():
                                   P(ctypes.c_uint64), ctypes.c_int, ctypes.c_double,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   P(ctypes.c_double), P(ctypes.c_uint64), P(ctypes.c_int32)]
+            L.orc_checkpoints.argtypes = [P(OrcGate), ctypes.c_int, ctypes.c_int, P(ctypes.c_uint64),
+                                          P(ctypes.c_uint64), ctypes.c_int, P(ctypes.c_uint64),
+                                          P(ctypes.c_double), P(ctypes.c_uint8), P(ctypes.c_double),
+                                          P(ctypes.c_int32)]
             _lib = L
     return _lib
 
@@ -161,3 +165,30 @@ def run(circuit, inputs, outputs, eps=0.0, c1=0, c2=0, threads=1):
     c = counts[:3 * M].reshape(M, 3)
     return a, {"completed": c[:, 0].copy(), "valid": c[:, 1].copy(),
                "visits": c[:, 2].copy(), "A": int(A.value)}
+
+
+def checkpoints(circuit, b_in: int, b_out: int, c1: int):
+    """Checkpoint table of one (input, output) pair after the prefix [0, c1)
+    of Algorithm 2 (exact mode): per prefix assignment h_p (source j = bit j)
+    the state (int), beta_p (complex), live (False = an exactly zero factor)
+    and the exact subtree sum over the remaining sources; and A_p."""
+    G = len(circuit.gates)
+    size = 1 << region_counts(circuit, c1, c1)[0][3]
+    bi, bo = _words([b_in]), _words([b_out])
+    st = np.zeros(2 * size, np.uint64)
+    amp = np.zeros(2 * size, np.float64)
+    ok = np.zeros(size, np.uint8)
+    sub = np.zeros(2 * size, np.float64)
+    Ap = ctypes.c_int32(0)
+    rc = lib().orc_checkpoints(_gates(circuit), G, circuit.n_qubits, _p(bi, ctypes.c_uint64),
+                               _p(bo, ctypes.c_uint64), int(c1), _p(st, ctypes.c_uint64),
+                               _p(amp, ctypes.c_double), _p(ok, ctypes.c_uint8), _p(sub, ctypes.c_double),
+                               ctypes.byref(Ap))
+    if rc:
+        raise ValueError(f"orc_checkpoints failed: {rc}")
+    m = 1 << Ap.value
+    states = [int(st[2 * i]) | (int(st[2 * i + 1]) << 64) for i in range(m)]
+    return {"Ap": int(Ap.value), "state": states,
+            "beta": amp[0:2 * m:2] + 1j * amp[1:2 * m:2],
+            "live": ok[:m].astype(bool),
+            "subtree": sub[0:2 * m:2] + 1j * sub[1:2 * m:2]}

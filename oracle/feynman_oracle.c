@@ -427,6 +427,55 @@ static void* worker(void* arg)
     return NULL;
 }
 
+/* The checkpoint table of one (input, output) pair after the prefix region
+ * [0, c1) of Algorithm 2, exact mode: for every prefix assignment h_p
+ * (artificial source j <-> bit j of h_p) the state sigma_p (2 words), the
+ * partial amplitude beta_p, ok = 0 where an exactly zero factor was met
+ * (bottom), and the exact subtree sum: the sum of the amplitudes of every
+ * valid completion of h_p over the remaining sources (one region [c1, G)).
+ * Arrays hold 2^Ap entries; Ap is returned in *Ap_out. */
+int orc_checkpoints(const orc_gate_in* gates, int G, int n, const uint64_t* b_in, const uint64_t* b_out, int c1,
+                    uint64_t* st, double* amp, uint8_t* ok, double* sub, int32_t* Ap_out)
+{
+    ocirc C;
+    int rc = make_circ(gates, G, n, &C);
+    if (rc) return rc;
+    if (c1 < 0 || c1 > G || C.A > 40) { free(C.g); return -1; }
+    const int Ap = sources_in(&C, 0, c1), Ar = sources_in(&C, c1, G);
+    *Ap_out = Ap;
+    uint8_t* h = (uint8_t*)calloc((size_t)C.A + 1, 1);
+    uint64_t visits = 0;
+    for (uint64_t hp = 0; hp < ((uint64_t)1 << Ap); hp++) {
+        for (int j = 0; j < Ap; j++) h[j] = (uint8_t)((hp >> j) & 1);
+        uint64_t sp[2] = {b_out[0], b_out[1]};
+        cplx bp = cx(1, 0);
+        const int live = advance(&C, 0, c1, sp, &bp, h, b_in, 0.0, &visits);
+        st[2 * hp] = sp[0];
+        st[2 * hp + 1] = sp[1];
+        amp[2 * hp] = bp.re;
+        amp[2 * hp + 1] = bp.im;
+        ok[hp] = (uint8_t)live;
+        neum sr = {0, 0}, si = {0, 0};
+        if (live) {
+            for (uint64_t hr = 0; hr < ((uint64_t)1 << Ar); hr++) {
+                for (int j = 0; j < Ar; j++) h[Ap + j] = (uint8_t)((hr >> j) & 1);
+                uint64_t ss[2] = {sp[0], sp[1]};
+                cplx bs = bp;
+                if (!advance(&C, c1, G, ss, &bs, h, b_in, 0.0, &visits)) continue;
+                if (ss[0] == b_in[0] && ss[1] == b_in[1]) {
+                    neum_add(&sr, bs.re);
+                    neum_add(&si, bs.im);
+                }
+            }
+        }
+        sub[2 * hp] = sr.s + sr.c;
+        sub[2 * hp + 1] = si.s + si.c;
+    }
+    free(h);
+    free(C.g);
+    return 0;
+}
+
 /* Amplitudes of M requested outputs for a sparse input of S basis states
  * (Eq. 2), with checkpoints (c1, c2) (c1 = c2 = 0: Algorithm 1), threshold
  * eps (0 = exact) on n_threads host threads.  counts: per output

@@ -392,6 +392,7 @@ struct fs_batch {
     bool planned = false, uploaded = false;
     size_t ws_bytes = 0;
     size_t o_jobs = 0, o_pbegin = 0, o_obegin = 0, o_tiles = 0, o_stats = 0, o_counter = 0, o_err = 0;
+    size_t o_bigcount = 0, o_biglist = 0;   // outputs left to the block-per-output reduction
     size_t static_bytes = 0, dyn_begin = 0;
     std::vector<unsigned char> host_static;
     std::vector<uint2> tiles;
@@ -672,6 +673,7 @@ int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, 
 int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream)
 {
     if (!d_params || (n && (!d_x || !d_y))) return fail(FS_ERR_INVALID, "NULL argument");
+    CUDA_TRY(fs::mlp_prepare());
     CUDA_TRY(fs::mlp_forward(d_params, d_x, (long long)n, d_y, (cudaStream_t)stream));
     return FS_OK;
 }
@@ -859,7 +861,9 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     b->dyn_begin = off;
     b->o_stats = take(nj * fs::STATS_PER_JOB * sizeof(unsigned long long));
     b->o_counter = take(sizeof(unsigned int));
-    b->o_err = take(sizeof(uint32_t));
+    b->o_bigcount = take(sizeof(unsigned int));
+    b->o_err = take(sizeof(uint32_t));   // last of the words zeroed at the start of every run
+    b->o_biglist = take(b->total_out * sizeof(uint64_t));
     const size_t zero_end = off;
     (void)zero_end;
     for (Job& j : b->jobs) {
@@ -891,6 +895,11 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
     if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
     if (ws_bytes < b->ws_bytes) return fail(FS_ERR_INVALID, "workspace of %zu bytes < %zu needed", ws_bytes, b->ws_bytes);
     if (((uintptr_t)d_ws) & 255) return fail(FS_ERR_INVALID, "workspace must be 256-byte aligned");
+    for (const Job& j : b->jobs)
+        if (j.d_pruner) {
+            CUDA_TRY(fs::mlp_prepare());
+            break;
+        }
     unsigned char* base = (unsigned char*)d_ws;
     std::vector<unsigned char>& H = b->host_static;
     H.assign(b->static_bytes, 0);
@@ -980,7 +989,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
 int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
 {
     if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
-    uint32_t k = 1;   // reduce
+    uint32_t k = b->total_out ? 2 : 0;   // reduce: outputs by lane groups, then the listed large ones
     bool tiled = false, flat_prefix = false;
     for (const Job& j : b->jobs) {
         tiled |= !j.compact;
@@ -1079,7 +1088,8 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         if (j.d_pruner)
-            CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries, s));
+            CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries,
+                                           (uint32_t*)(base + b->o_err), s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[5], s));
     for (int ji = 0; ji < nj; ++ji) {
@@ -1104,7 +1114,8 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     }
     if (b->timing) CUDA_TRY(record(b->ev[2], s));
     CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
-                               (double2*)d_amp_out, s));
+                               (double2*)d_amp_out, (unsigned int*)(base + b->o_bigcount),
+                               (uint64_t*)(base + b->o_biglist), s));
     if (b->timing) {
         CUDA_TRY(record(b->ev[3], s));
         b->ev_recorded = true;
@@ -1126,6 +1137,7 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
     if (err & fs::DEV_ERR_BAD_OPCODE) return fail(FS_ERR_BAD_PROGRAM, "device found an unknown opcode");
+    if (err & fs::DEV_ERR_TIMEOUT) return fail(FS_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core scoring)");
     if (stats) {
         for (size_t ji = 0; ji < nj && ji < cap; ++ji) {
             const Job& j = b->jobs[ji];

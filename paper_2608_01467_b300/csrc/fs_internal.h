@@ -122,10 +122,14 @@ cudaError_t mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_gra
 cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, float* d_feat,
                          unsigned long long n_entries, cudaStream_t s);
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
-                              float tau, unsigned long long n_entries, cudaStream_t s);
+                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s);
+// Raises the dynamic shared-memory limit of the tensor-core scoring kernels
+// (outside any stream capture, before their first launch).
+cudaError_t mlp_prepare();
 
 // Device error word values.
 constexpr uint32_t DEV_ERR_BAD_OPCODE = 1;
+constexpr uint32_t DEV_ERR_TIMEOUT = 2;   // a bounded wait on an mbarrier gave up
 
 // One level of the per-source prefix expansion: ops [e0, e1) extend every
 // entry of the previous level (a_prev source bits, in src; NULL for the
@@ -149,8 +153,12 @@ cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t
 cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s);
 int compact_grid_size(int device);
 cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s);
+// Two launches: lane groups sum most outputs and list the large ones in
+// d_big_list (count in d_big_count, zeroed by the caller); one block per
+// listed output sums the rest.
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
-                          uint64_t total_out, double2* d_amp, cudaStream_t s);
+                          uint64_t total_out, double2* d_amp, unsigned int* d_big_count, uint64_t* d_big_list,
+                          cudaStream_t s);
 int history_grid_size(int device);
 
 // Straight-line engine (fs_jit.cpp): one generated persistent kernel for the

@@ -658,54 +658,134 @@ __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __re
 
 // ---------------------------------------------------------------- reduce
 
-// One block per output: threads stride over the pair's partials (or live
-// subtree sums) with 4 independent accumulators each (loads in flight), then
-// a fixed butterfly per warp and the warps in order; thread 0 adds
-// c_in * alpha over the input support in order.  The order is fixed by the
-// layout alone, so the result is run-to-run identical.
+// Items of one (output, input) pair: the per-tile partials of an exact job,
+// or the per-(live entry, h_r) subtree sums of a pruned job.
+__device__ __forceinline__ const double2* pair_items(const JobDev& J, uint64_t pair, uint64_t& lo, uint64_t& hi)
+{
+    if (J.compact) {
+        lo = J.prange[2 * pair] << J.Ar;
+        hi = J.prange[2 * pair + 1] << J.Ar;
+        return J.esum;
+    }
+    lo = pair << J.log2_spp;
+    hi = lo + (1ull << J.log2_spp);
+    return J.partials;
+}
+
+// src[k], src[k + stride], ... below hi: the i-th item goes to accumulator
+// i mod 4, combined as (a0 + a1) + (a2 + a3); eight loads in flight.
+__device__ __forceinline__ double2 strided_sum(const double2* __restrict__ src, uint64_t k, uint64_t hi,
+                                               uint32_t stride)
+{
+    double2 a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = make_double2(0.0, 0.0);
+    for (; k + 7 * (uint64_t)stride < hi; k += 8 * (uint64_t)stride) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = src[k + (uint64_t)u * stride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            a[u & 3].x += v[u].x;
+            a[u & 3].y += v[u].y;
+        }
+    }
+    // at most 7 items remain
+#pragma unroll
+    for (int u = 0; u < 7; ++u) {
+        if (k < hi) {
+            const double2 v = src[k];
+            a[u & 3].x += v.x;
+            a[u & 3].y += v.y;
+        }
+        k += stride;
+    }
+    return make_double2((a[0].x + a[1].x) + (a[2].x + a[3].x), (a[0].y + a[1].y) + (a[2].y + a[3].y));
+}
+
+constexpr int RED_LPO = 4;            // lanes per output in the common path
+constexpr uint64_t RED_SMALL = 1024;  // outputs with more items go to reduce_big_kernel
+constexpr int RED_BIG_THREADS = 256;
+
+// FP64 is scarce on this part (about 2 FMA per clock per SM), so the
+// reduction keeps FP64 instructions per output low: each warp takes 8
+// outputs, 4 lanes each (lane-strided sums, a 2-level butterfly), then adds
+// c_in * alpha over the input support in order (Eq. 2).  An output with more
+// than RED_SMALL items is listed for reduce_big_kernel instead.  The order
+// of every sum depends only on the item counts, so results are run-to-run
+// identical.
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
                                                                 const uint64_t* __restrict__ begin,
-                                                                int n_jobs, uint64_t total, double2* amp_out)
+                                                                int n_jobs, uint64_t total, double2* amp_out,
+                                                                unsigned int* big_count, uint64_t* big_list)
 {
-    __shared__ double2 s_w[REDUCE_THREADS / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
-        const int j = find_job(begin, n_jobs, g);
+    constexpr int OPW = 32 / RED_LPO;
+    const int lane = threadIdx.x & 31, sub = lane & (RED_LPO - 1), slot = lane / RED_LPO;
+    const uint64_t warp = ((uint64_t)blockIdx.x * REDUCE_THREADS + threadIdx.x) >> 5;
+    const uint64_t nwarp = ((uint64_t)gridDim.x * REDUCE_THREADS) >> 5;
+    for (uint64_t g0 = warp * OPW; g0 < total; g0 += nwarp * OPW) {
+        const uint64_t g = g0 + (uint64_t)slot;
+        const bool have = g < total;
+        const int j = have ? find_job(begin, n_jobs, g) : 0;
         const JobDev& J = jobs[j];
+        const int S = have ? J.S : 0;
+        const uint64_t o = have ? g - J.out_begin : 0;
+        uint64_t n = 0;
+        for (int s = 0; s < S; ++s) {
+            uint64_t lo, hi;
+            pair_items(J, o * (uint64_t)S + (uint64_t)s, lo, hi);
+            n += hi - lo;
+        }
+        const bool small = n <= RED_SMALL;
+        const int s_max = (int)__reduce_max_sync(0xffffffffu, small ? (unsigned)S : 0u);
+        double2 amp = make_double2(0.0, 0.0);
+        for (int s = 0; s < s_max; ++s) {
+            const bool act = small && s < S;
+            double2 t = make_double2(0.0, 0.0);
+            if (act) {
+                uint64_t lo, hi;
+                const double2* src = pair_items(J, o * (uint64_t)S + (uint64_t)s, lo, hi);
+                t = strided_sum(src, lo + (uint64_t)sub, hi, RED_LPO);
+            }
+#pragma unroll
+            for (int off = RED_LPO / 2; off >= 1; off >>= 1) {
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+            }
+            if (act) {
+                const double2 w = cmul(__ldg(J.coef + s), t);
+                amp.x += w.x;
+                amp.y += w.y;
+            }
+        }
+        if (have && sub == 0) {
+            if (small) amp_out[g] = amp;
+            else big_list[atomicAdd(big_count, 1u)] = g;
+        }
+    }
+}
+
+// One block per listed output: block-strided sums (eight loads in flight per
+// thread), a butterfly per warp, the warps added in order, then c_in * alpha
+// over the input support in order.
+__global__ void __launch_bounds__(RED_BIG_THREADS) reduce_big_kernel(const JobDev* __restrict__ jobs,
+                                                                     const uint64_t* __restrict__ begin, int n_jobs,
+                                                                     const unsigned int* big_count,
+                                                                     const uint64_t* __restrict__ big_list,
+                                                                     double2* amp_out)
+{
+    __shared__ double2 s_w[RED_BIG_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int count = *big_count;
+    for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint64_t g = big_list[i];
+        const JobDev& J = jobs[find_job(begin, n_jobs, g)];
         const uint64_t o = g - J.out_begin;
         double2 amp = make_double2(0.0, 0.0);
         for (int s = 0; s < J.S; ++s) {
-            const uint64_t pair = o * (uint64_t)J.S + (uint64_t)s;
             uint64_t lo, hi;
-            const double2* __restrict__ src;
-            if (J.compact) {
-                lo = J.prange[2 * pair] << J.Ar;
-                hi = J.prange[2 * pair + 1] << J.Ar;
-                src = J.esum;
-            } else {
-                lo = pair << J.log2_spp;
-                hi = lo + (1ull << J.log2_spp);
-                src = J.partials;
-            }
-            double2 acc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
-            uint64_t k = lo + threadIdx.x;
-            for (; k + 3 * REDUCE_THREADS < hi; k += 4 * REDUCE_THREADS) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const double2 v = src[k + (uint64_t)u * REDUCE_THREADS];
-                    acc[u].x += v.x;
-                    acc[u].y += v.y;
-                }
-            }
-            for (int u = 0; k < hi; k += REDUCE_THREADS, ++u) {
-                const double2 v = src[k];
-                acc[u & 3].x += v.x;
-                acc[u & 3].y += v.y;
-            }
-            double2 t = make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
-                                     (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
+            const double2* src = pair_items(J, o * (uint64_t)J.S + (uint64_t)s, lo, hi);
+            double2 t = strided_sum(src, lo + threadIdx.x, hi, RED_BIG_THREADS);
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) {
                 t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
@@ -715,7 +795,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
             __syncthreads();
             if (threadIdx.x == 0) {
                 double2 a = s_w[0];
-                for (int w = 1; w < REDUCE_THREADS / 32; ++w) {
+                for (int w = 1; w < RED_BIG_THREADS / 32; ++w) {
                     a.x += s_w[w].x;
                     a.y += s_w[w].y;
                 }
@@ -868,11 +948,20 @@ cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int gri
 }
 
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
-                          uint64_t total_out, double2* d_amp, cudaStream_t s)
+                          uint64_t total_out, double2* d_amp, unsigned int* d_big_count, uint64_t* d_big_list,
+                          cudaStream_t s)
 {
     if (total_out == 0) return cudaSuccess;
-    uint64_t blocks = total_out < 148ull * 16 ? total_out : 148ull * 16;
-    reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp);
+    const uint64_t per_block = (REDUCE_THREADS / 32) * (32 / RED_LPO);   // outputs per block pass
+    uint64_t blocks = (total_out + per_block - 1) / per_block;
+    if (blocks > 148ull * 16) blocks = 148ull * 16;
+    reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp,
+                                                              d_big_count, d_big_list);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t big_blocks = total_out < 148ull * 4 ? total_out : 148ull * 4;
+    reduce_big_kernel<<<(unsigned)big_blocks, RED_BIG_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, d_big_count,
+                                                                       d_big_list, d_amp);
     return cudaGetLastError();
 }
 

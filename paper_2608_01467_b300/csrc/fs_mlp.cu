@@ -3,10 +3,13 @@
 // prefix of Algorithm 2) by the predicted log10 |exact subtree sum|; entries
 // scoring below a threshold tau are cut, the rest are enumerated exactly.
 //
-// Numerics: BF16 operands on the tensor cores (mma.sync m16n8k16, FP32
-// accumulate); FP32 master weights and Adam state.  Rounded to BF16: the
-// inputs X, W1, W2, w3, the hidden activation h1 (layer-2 operand) and, in the
-// backward pass, the GEMM operands dh2 and dh1.  Everything else is FP32.
+// Numerics: BF16 operands on the tensor cores with FP32 accumulation;
+// FP32 master weights and Adam state.  Scoring (forward, learned pruning)
+// runs on tcgen05.mma with the accumulators in tensor memory; training
+// (forward + backward on minibatches, off the amplitude path) uses
+// mma.sync m16n8k16.  Rounded to BF16: the inputs X, W1, W2, w3, the hidden
+// activation h1 (layer-2 operand) and, in the backward pass, the GEMM
+// operands dh2 and dh1.  Everything else is FP32.
 //
 // Parameter layout (FP32, 18817 values): W1[16][128] at 0, b1[128] at 2048,
 // W2[128][128] at 2176, b2[128] at 18560, w3[128] at 18688, b3 at 18816;
@@ -26,9 +29,7 @@ constexpr int W1T_STRIDE = 24;    // bf16 per row of W1t[n][k] (padded: no bank 
 constexpr int W2_STRIDE = 136;    // bf16 per row of W2t / W2s (padded)
 constexpr int T_STRIDE = 136;     // bf16 per row of per-warp 16 x 128 tiles
 constexpr int X_STRIDE = 24;      // bf16 per row of per-warp 16 x 16 input tiles
-constexpr int FWD_WARPS = 8;
 constexpr int BWD_WARPS = 4;
-constexpr int PRUNE_WARPS = 4;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -139,59 +140,6 @@ __device__ __forceinline__ void forward_tile(const float* __restrict__ P, const 
     f.y1 = s1 + P[OFF_B3];
 }
 
-// Inference-only forward of 16 rows: layer-2 tiles are reduced into the
-// layer-3 dot as they are produced, so neither h1 nor h2 stays live
-// (low register use).  Same operands, roundings and sums as forward_tile.
-__device__ __forceinline__ void score_tile(const float* __restrict__ P, const __nv_bfloat16* xs,
-                                           const __nv_bfloat16* w1t, const __nv_bfloat16* w2t,
-                                           float& y0, float& y1)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    uint32_t a[4];
-    a[0] = ld32(xs + g * X_STRIDE + 2 * t);
-    a[1] = ld32(xs + (g + 8) * X_STRIDE + 2 * t);
-    a[2] = ld32(xs + g * X_STRIDE + 2 * t + 8);
-    a[3] = ld32(xs + (g + 8) * X_STRIDE + 2 * t + 8);
-    uint32_t a2[8][4];
-#pragma unroll
-    for (int kt = 0; kt < 8; ++kt) {
-        float c[2][4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = 2 * kt + h;
-            const float b0 = P[OFF_B1 + 8 * j + 2 * t], b1v = P[OFF_B1 + 8 * j + 2 * t + 1];
-            c[h][0] = b0; c[h][1] = b1v; c[h][2] = b0; c[h][3] = b1v;
-            const __nv_bfloat16* wb = w1t + (8 * j + g) * W1T_STRIDE + 2 * t;
-            mma_bf16(c[h], a, ld32(wb), ld32(wb + 8));
-        }
-        a2[kt][0] = pack_bf16(fmaxf(c[0][0], 0.f), fmaxf(c[0][1], 0.f));
-        a2[kt][1] = pack_bf16(fmaxf(c[0][2], 0.f), fmaxf(c[0][3], 0.f));
-        a2[kt][2] = pack_bf16(fmaxf(c[1][0], 0.f), fmaxf(c[1][1], 0.f));
-        a2[kt][3] = pack_bf16(fmaxf(c[1][2], 0.f), fmaxf(c[1][3], 0.f));
-    }
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-        float d[4];
-        const float b0 = P[OFF_B2 + 8 * j + 2 * t], b1v = P[OFF_B2 + 8 * j + 2 * t + 1];
-        d[0] = b0; d[1] = b1v; d[2] = b0; d[3] = b1v;
-#pragma unroll
-        for (int kt = 0; kt < 8; ++kt) {
-            const __nv_bfloat16* wb = w2t + (8 * j + g) * W2_STRIDE + 16 * kt + 2 * t;
-            mma_bf16(d, a2[kt], ld32(wb), ld32(wb + 8));
-        }
-        const float w0 = bf16r(P[OFF_W3 + 8 * j + 2 * t]), w1 = bf16r(P[OFF_W3 + 8 * j + 2 * t + 1]);
-        s0 += fmaxf(d[0], 0.f) * w0 + fmaxf(d[1], 0.f) * w1;
-        s1 += fmaxf(d[2], 0.f) * w0 + fmaxf(d[3], 0.f) * w1;
-    }
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-    y0 = s0 + P[OFF_B3];
-    y1 = s1 + P[OFF_B3];
-}
-
 // Loads 16 rows of 16 FP32 features (rows >= n are zero) as bf16 into xs.
 __device__ __forceinline__ void load_x(const float* __restrict__ X, long long row0, long long n, __nv_bfloat16* xs)
 {
@@ -202,31 +150,6 @@ __device__ __forceinline__ void load_x(const float* __restrict__ X, long long ro
         xs[r * X_STRIDE + k] = __float2bfloat16_rn(row < n ? X[row * F + k] : 0.f);
     }
     __syncwarp();
-}
-
-__global__ void __launch_bounds__(FWD_WARPS * 32) mlp_forward_kernel(const float* __restrict__ P,
-                                                                     const float* __restrict__ X, long long n,
-                                                                     float* __restrict__ Y)
-{
-    __shared__ __align__(16) __nv_bfloat16 w1t[H * W1T_STRIDE];
-    __shared__ __align__(16) __nv_bfloat16 w2t[H * W2_STRIDE];
-    __shared__ __align__(16) __nv_bfloat16 xs_all[FWD_WARPS][16 * X_STRIDE];
-    stage_weights(P, w1t, w2t, nullptr);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* xs = xs_all[warp];
-    const long long tiles = (n + 15) / 16;
-    for (long long tile = (long long)blockIdx.x * FWD_WARPS + warp; tile < tiles; tile += (long long)gridDim.x * FWD_WARPS) {
-        load_x(X, tile * 16, n, xs);
-        float y0, y1;
-        score_tile(P, xs, w1t, w2t, y0, y1);
-        if (t == 0) {
-            const long long r0 = tile * 16 + g, r1 = r0 + 8;
-            if (r0 < n) Y[r0] = y0;
-            if (r1 < n) Y[r1] = y1;
-        }
-        __syncwarp();
-    }
 }
 
 // Loss and gradients (accumulated into G, 18817 FP32 + 1 loss, zeroed by the
@@ -415,31 +338,44 @@ __global__ void adam_kernel(float* __restrict__ P, float* __restrict__ M, float*
 // leading one.
 __device__ __forceinline__ float log2_distance(const uint32_t* x, const uint32_t* y)
 {
-    uint32_t d[4];
-    bool ge = true;   // x >= y ?
-    for (int w = 3; w >= 0; --w) {
-        if (x[w] != y[w]) { ge = x[w] > y[w]; break; }
-    }
-    const uint32_t* a = ge ? x : y;
-    const uint32_t* b = ge ? y : x;
-    uint32_t borrow = 0;
+    uint32_t xv[4], yv[4];
+#pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const uint32_t t = a[w] - b[w] - borrow;
-        borrow = (a[w] < b[w] || (a[w] == b[w] && borrow)) ? 1u : 0u;
-        d[w] = t;
+        xv[w] = x[w];
+        yv[w] = y[w];
     }
+    bool ge = true, decided = false;   // x >= y ?
+#pragma unroll
     for (int w = 3; w >= 0; --w) {
-        if (d[w]) {
+        if (!decided && xv[w] != yv[w]) {
+            ge = xv[w] > yv[w];
+            decided = true;
+        }
+    }
+    uint32_t d[4];
+    uint32_t borrow = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t a = ge ? xv[w] : yv[w], b = ge ? yv[w] : xv[w];
+        d[w] = a - b - borrow;
+        borrow = (a < b || (a == b && borrow)) ? 1u : 0u;
+    }
+    float res = 0.f;
+    bool found = false;
+#pragma unroll
+    for (int w = 3; w >= 0; --w) {
+        if (!found && d[w]) {
+            found = true;
             const int msb = 31 - __clz(d[w]);
             // 24 bits below and including the leading one
-            const uint32_t lo = w ? d[w - 1] : 0u;
+            const uint32_t lo = w ? d[w > 0 ? w - 1 : 0] : 0u;
             const uint32_t top = msb >= 23 ? (d[w] >> (msb - 23))
                                            : ((d[w] << (23 - msb)) | (lo >> (32 - (23 - msb))));
             const float mant = (float)top * (1.0f / 8388608.0f);   // in [1, 2)
-            return (float)(32 * w + msb + 1) + __log2f(mant);
+            res = (float)(32 * w + msb + 1) + __log2f(mant);
         }
     }
-    return 0.f;
+    return res;
 }
 
 // 16 features of one live checkpoint entry (partial history after the
@@ -448,12 +384,12 @@ __device__ __forceinline__ float log2_distance(const uint32_t* x, const uint32_t
 // artificial sources (A - A_p)/A, Hamming distance(sigma, b_in)/n, and
 // (sigma xor b_in) on the qubits of the next 8 artificial sources.  Bottom
 // entries give NaN in feature 0.
-__device__ void entry_features(const JobDev& J, unsigned long long local, const FeatureSpec& sp, float* out)
+__device__ __forceinline__ void entry_features_of(const JobDev& J, const Entry& e, unsigned long long local,
+                                                  const FeatureSpec& sp, float* out)
 {
     const unsigned long long pair = local >> J.Ap;
     const unsigned long long o = pair / (unsigned long long)J.S;
     const unsigned long long sidx = pair - o * (unsigned long long)J.S;
-    const Entry e = J.table[local];
     const uint32_t* bin = J.ins + 4 * sidx;
     if (isnan(e.amp.x)) {
         for (int k = 0; k < 16; ++k) out[k] = 0.f;
@@ -476,8 +412,15 @@ __device__ void entry_features(const JobDev& J, unsigned long long local, const 
     out[7] = (float)ham / (float)sp.n_qubits;
     for (int k = 0; k < 8; ++k) {
         const int q = sp.next_qubits[k];
-        out[8 + k] = q < 0 ? 0.f : (float)(((e.st[q >> 5] ^ bin[q >> 5]) >> (q & 31)) & 1u);
+        const int w = q >> 5;   // register word, selected without a local-memory index
+        const uint32_t sw = w == 0 ? e.st[0] : w == 1 ? e.st[1] : w == 2 ? e.st[2] : e.st[3];
+        out[8 + k] = q < 0 ? 0.f : (float)(((sw ^ bin[w & 3]) >> (q & 31)) & 1u);
     }
+}
+
+__device__ void entry_features(const JobDev& J, unsigned long long local, const FeatureSpec& sp, float* out)
+{
+    entry_features_of(J, J.table[local], local, sp, out);
 }
 
 __global__ void features_kernel(const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float* __restrict__ feat,
@@ -489,57 +432,358 @@ __global__ void features_kernel(const JobDev* __restrict__ jobs, int job, Featur
         entry_features(J, i, sp, feat + 16 * i);
 }
 
-// Scores every live entry of a job's checkpoint table with the MLP and cuts
-// (marks bottom) those predicted below tau; counts cuts into stats[5].
-__global__ void __launch_bounds__(PRUNE_WARPS * 32) learned_prune_kernel(const float* __restrict__ P,
-                                                                         const JobDev* __restrict__ jobs, int job,
-                                                                         FeatureSpec sp, float tau)
+// ------------------------------------------------------- tcgen05 scoring
+//
+// Inference on the 5th-generation tensor cores (tcgen05.mma, accumulators in
+// tensor memory).  A CTA of 256 threads runs two independent pipelines, one
+// per warpgroup; each scores tiles of 128 rows, one row per thread:
+//   X (128 x 16 bf16, shared)  --1 MMA (M 128, N 128, K 16)-->  D (FP32, TMEM)
+//   epilogue 1: D + b1, ReLU, round to bf16 -> H1 (128 x 128 bf16, shared)
+//   H1 --8 MMAs (K 16 each)--> D (the same 128 TMEM columns)
+//   epilogue 2: D + b2, ReLU, dot with bf16(w3), + b3 -> y.
+// The operands, roundings and FP32 accumulation are those of the training
+// kernels (only the summation order inside the tensor core differs).
+// Shared operands use the K-major layout without swizzle: core matrices of
+// 8 rows x 16 bytes (8 bf16 of one row), LBO = byte distance between core
+// matrices along K (128 here), SBO = between 8-row groups along M or N.
+
+constexpr int TC_THREADS = 256;
+constexpr uint32_t TC_COLS = 256;             // TMEM columns per CTA, 128 per warpgroup
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;  // mbarrier polls before a wait gives up
+constexpr int SM_W1 = 0;                      // B of layer 1: 128 n x 16 k
+constexpr int SM_W2 = SM_W1 + 4096;           // B of layer 2: 128 n x 128 k
+constexpr int SM_X = SM_W2 + 32768;           // per warpgroup: 128 rows x 16 k
+constexpr int SM_H1 = SM_X + 2 * 4096;        // per warpgroup: 128 rows x 128 k
+constexpr int SM_VEC = SM_H1 + 2 * 32768;     // b1, b2, bf16(w3) (FP32), b3
+constexpr int SM_BAR = SM_VEC + (3 * H + 4) * 4;   // 2 mbarriers, TMEM address, 2 abort flags
+constexpr int TC_SMEM = SM_BAR + 64;
+static_assert(SM_BAR % 8 == 0, "mbarrier alignment");
+static_assert(2 * (TC_SMEM + 1024) <= 233472, "two CTAs per SM");
+
+// instruction descriptor of kind::f16: FP32 D (bits 4-5 = 1), bf16 A and B
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, k) in a K-major no-swizzle operand whose
+// 8-row groups are sbo bytes apart
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k, uint32_t sbo)
 {
-    __shared__ __align__(16) __nv_bfloat16 w1t[H * W1T_STRIDE];
-    __shared__ __align__(16) __nv_bfloat16 w2t[H * W2_STRIDE];
-    __shared__ __align__(16) __nv_bfloat16 xs_all[PRUNE_WARPS][32 * X_STRIDE];
-    stage_weights(P, w1t, w2t, nullptr);
-    __syncthreads();
-    const JobDev& J = jobs[job];
-    const unsigned long long n = J.n_pairs << J.Ap;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* xs = xs_all[warp];
-    const long long tiles = (long long)((n + 31) / 32);
-    unsigned long long cuts = 0;
-    for (long long tile = (long long)blockIdx.x * PRUNE_WARPS + warp; tile < tiles; tile += (long long)gridDim.x * PRUNE_WARPS) {
-        // every lane computes the features of one entry
-        const unsigned long long row = (unsigned long long)tile * 32 + lane;
-        float fv[16];
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4
+// (16-29), SBO >> 4 (32-45), descriptor version 1 (46-48), base offset 0,
+// no swizzle (61-63 = 0)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d_tmem), "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+
+// arrives on the mbarrier once every MMA issued so far by this thread is done
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// named barrier of one warpgroup (ids 1 and 2; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int grp)
+{
+    if (grp == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
+    else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane; the wait is in the
+// same statement so no use of v can be scheduled before the data arrive
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Packed FP32 pairs (low word = even column) for the epilogues.
+__device__ __forceinline__ uint64_t pack_f32x2(uint32_t lo, uint32_t hi)
+{
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t relu_f32x2(uint64_t a)
+{
+    const float lo = fmaxf(__uint_as_float((uint32_t)a), 0.f);
+    const float hi = fmaxf(__uint_as_float((uint32_t)(a >> 32)), 0.f);
+    return pack_f32x2(__float_as_uint(lo), __float_as_uint(hi));
+}
+
+// ReLU of both halves, rounded to bf16 (nearest even), low half first
+__device__ __forceinline__ uint32_t relu_bf16x2(uint64_t a)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;"
+        : "=r"(d)
+        : "f"(__uint_as_float((uint32_t)(a >> 32))), "f"(__uint_as_float((uint32_t)a)));
+    return d;
+}
+
+// Thread 0 of the warpgroup polls the MMA-completion barrier (bounded); the
+// group then learns the outcome together.  False: the wait gave up, the
+// error word has DEV_ERR_TIMEOUT and the group stops.
+__device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag, int r,
+                                           int grp, uint32_t* err)
+{
+    if (r == 0) {
         bool ok = false;
-        if (row < n) {
-            entry_features(J, row, sp, fv);
-            ok = !isnan(fv[0]);
+        for (uint32_t i = 0; i < TC_WAIT_LIMIT && !ok; ++i) ok = mbar_try_wait(bar, parity);
+        if (!ok) {
+            *abort_flag = 1u;
+            if (err) atomicOr(err, DEV_ERR_TIMEOUT);
         }
+    }
+    group_sync(grp);
+    tc_fence_after();
+    return *abort_flag == 0u;
+}
+
+// PRUNE: rows are the entries of a job's checkpoint table, features computed
+// here, entries scoring below tau cut (amplitude set to NaN, counted in
+// stats[5]).  Otherwise rows are X [n][16] and y goes to Y.
+template <bool PRUNE>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    mlp_tc_kernel(const float* __restrict__ P, const float* __restrict__ X, long long n_rows, float* __restrict__ Y,
+                  const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int tid = threadIdx.x, grp = tid >> 7, r = tid & 127, warp = tid >> 5;
+    float* vb1 = (float*)(sm + SM_VEC);
+    float* vb2 = vb1 + H;
+    float* vw3 = vb2 + H;
+    uint64_t* bars = (uint64_t*)(sm + SM_BAR);
+    uint32_t* tmem_slot = (uint32_t*)(sm + SM_BAR + 16);
+    volatile uint32_t* abort_flag = (volatile uint32_t*)(sm + SM_BAR + 20) + grp;
+
+    // weights as the B operands (B[n][k] = W[k][n]), biases, bf16-rounded w3
+    for (int i = tid; i < F * H; i += TC_THREADS) {
+        const int k = i / H, n = i % H;
+        *(__nv_bfloat16*)(sm + SM_W1 + kmajor_off(n, k, 256)) = __float2bfloat16_rn(P[OFF_W1 + i]);
+    }
+    for (int i = tid; i < H * H; i += TC_THREADS) {
+        const int k = i / H, n = i % H;
+        *(__nv_bfloat16*)(sm + SM_W2 + kmajor_off(n, k, 2048)) = __float2bfloat16_rn(P[OFF_W2 + i]);
+    }
+    for (int i = tid; i < H; i += TC_THREADS) {
+        vb1[i] = P[OFF_B1 + i];
+        vb2[i] = P[OFF_B2 + i];
+        vw3[i] = bf16r(P[OFF_W3 + i]);
+    }
+    if (tid == 0) {
+        vw3[H] = P[OFF_B3];
+        for (int g = 0; g < 2; ++g)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[g])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 2) ((volatile uint32_t*)(sm + SM_BAR + 20))[tid] = 0u;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const uint32_t tmem = *tmem_slot + (uint32_t)grp * 128u;          // this group's columns
+    const uint32_t t_row = tmem + ((uint32_t)(warp & 3) * 32u << 16);  // lane quarter of this warp
+    unsigned char* xs = sm + SM_X + grp * 4096;
+    unsigned char* h1 = sm + SM_H1 + grp * 32768;
+    const uint32_t sx = smem_u32(xs), sh = smem_u32(h1);
+    const uint32_t sw1 = smem_u32(sm + SM_W1), sw2 = smem_u32(sm + SM_W2);
+    const uint32_t bar = smem_u32(&bars[grp]);
+    const float b3 = vw3[H];
+    uint32_t phase = 0;
+    unsigned long long cuts = 0;
+    const JobDev* J = PRUNE ? &jobs[job] : nullptr;
+    const long long n = PRUNE ? (long long)(J->n_pairs << J->Ap) : n_rows;
+    const long long tiles = (n + 127) / 128;
+    const long long tstride = (long long)gridDim.x * 2;
+    // PRUNE: the entry of the next tile is loaded while this tile's MMAs run
+    Entry cur;
+    {
+        const long long row0 = ((long long)blockIdx.x * 2 + grp) * 128 + r;
+        if (PRUNE && row0 < n) cur = J->table[row0];
+    }
+    for (long long tile = (long long)blockIdx.x * 2 + grp; tile < tiles; tile += tstride) {
+        const long long row = tile * 128 + r;
+        float fv[16];
+        bool live = false;
+        if (row < n) {
+            if (PRUNE) {
+                entry_features_of(*J, cur, (unsigned long long)row, sp, fv);
+                live = !isnan(fv[0]);
+            } else {
+                const float4* x4 = reinterpret_cast<const float4*>(X + row * F);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) xs[lane * X_STRIDE + k] = __float2bfloat16_rn(ok ? fv[k] : 0.f);
-        const unsigned live = __ballot_sync(0xffffffffu, ok);
-        __syncwarp();
-#pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            float y0, y1;
-            score_tile(P, xs + 16 * half * X_STRIDE, w1t, w2t, y0, y1);
-            if (t == 0) {
-                const int r0 = 16 * half + g, r1 = r0 + 8;
-                if (((live >> r0) & 1u) && y0 < tau) {
-                    J.table[(unsigned long long)tile * 32 + r0].amp.x = __longlong_as_double(0x7ff8000000000000ll);
-                    ++cuts;
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = x4[q];
+                    fv[4 * q] = v.x; fv[4 * q + 1] = v.y; fv[4 * q + 2] = v.z; fv[4 * q + 3] = v.w;
                 }
-                if (((live >> r1) & 1u) && y1 < tau) {
-                    J.table[(unsigned long long)tile * 32 + r1].amp.x = __longlong_as_double(0x7ff8000000000000ll);
-                    ++cuts;
-                }
+                live = true;
             }
         }
-        __syncwarp();
+        if (!live) {
+#pragma unroll
+            for (int k = 0; k < F; ++k) fv[k] = 0.f;
+        }
+        *(uint4*)(xs + kmajor_off(r, 0, 256)) = make_uint4(pack_bf16(fv[0], fv[1]), pack_bf16(fv[2], fv[3]),
+                                                           pack_bf16(fv[4], fv[5]), pack_bf16(fv[6], fv[7]));
+        *(uint4*)(xs + kmajor_off(r, 8, 256)) = make_uint4(pack_bf16(fv[8], fv[9]), pack_bf16(fv[10], fv[11]),
+                                                           pack_bf16(fv[12], fv[13]), pack_bf16(fv[14], fv[15]));
+        fence_async_smem();
+        group_sync(grp);
+        if (r == 0) {
+            tc_fence_after();
+            tc_mma(tmem, sdesc(sx, 256), sdesc(sw1, 256), 0u);
+            tc_commit(bar);
+        }
+        if (PRUNE) {
+            const long long nrow = row + tstride * 128;
+            if (nrow < n) cur = J->table[nrow];
+        }
+        if (!group_wait(bar, phase, abort_flag, r, grp, err)) break;
+        phase ^= 1u;
+        // epilogue 1: h1 = bf16(relu(x W1 + b1)) into the layer-2 A operand
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t v[32];
+            tmem_ld32(t_row + 32u * c, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int n0 = 32 * c + 8 * q + 2 * e;
+                    const uint64_t x = add_f32x2(pack_f32x2(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]),
+                                                 *(const uint64_t*)(vb1 + n0));
+                    w[e] = relu_bf16x2(x);
+                }
+                *(uint4*)(h1 + kmajor_off(r, 32 * c + 8 * q, 2048)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        group_sync(grp);
+        if (r == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kt = 0; kt < 8; ++kt)
+                tc_mma(tmem, sdesc(sh + 256u * kt, 2048), sdesc(sw2 + 256u * kt, 2048), kt ? 1u : 0u);
+            tc_commit(bar);
+        }
+        if (!group_wait(bar, phase, abort_flag, r, grp, err)) break;
+        phase ^= 1u;
+        // epilogue 2: y = relu(h1 W2 + b2) . bf16(w3) + b3
+        uint64_t acc2 = 0;   // two FP32 partial sums (even, odd columns)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t v[32];
+            tmem_ld32(t_row + 32u * c, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int n0 = 32 * c + 2 * e;
+                const uint64_t x = add_f32x2(pack_f32x2(v[2 * e], v[2 * e + 1]), *(const uint64_t*)(vb2 + n0));
+                acc2 = fma_f32x2(relu_f32x2(x), *(const uint64_t*)(vw3 + n0), acc2);
+            }
+        }
+        tc_fence_before();   // TMEM reads complete before the next tile's MMA
+        const float y = (__uint_as_float((uint32_t)acc2) + __uint_as_float((uint32_t)(acc2 >> 32))) + b3;
+        if (PRUNE) {
+            if (live && y < tau) {
+                J->table[row].amp.x = __longlong_as_double(0x7ff8000000000000ll);
+                ++cuts;
+            }
+        } else if (row < n) {
+            Y[row] = y;
+        }
     }
-    cuts = warp_sum_cuts(cuts);
-    if (lane == 0 && cuts) atomicAdd(&J.stats[5], cuts);
+    if (PRUNE) {
+        cuts = warp_sum_cuts(cuts);
+        if ((tid & 31) == 0 && cuts) atomicAdd(&J->stats[5], cuts);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(TC_COLS)
+                     : "memory");
+    }
 }
+
+template <bool PRUNE>
+cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y, const JobDev* jobs, int job,
+                      const FeatureSpec& sp, float tau, uint32_t* err, unsigned long long rows, cudaStream_t s)
+{
+    const unsigned long long tiles = (rows + 127) / 128;
+    unsigned long long blocks = (tiles + 1) / 2;
+    if (blocks > 148 * 2) blocks = 148 * 2;
+    mlp_tc_kernel<PRUNE><<<(unsigned)blocks, TC_THREADS, TC_SMEM, s>>>(P, X, n_rows, Y, jobs, job, sp, tau, err);
+    return cudaGetLastError();
+}
+
 
 size_t grad_smem_bytes()
 {
@@ -553,11 +797,8 @@ size_t grad_smem_bytes()
 cudaError_t mlp_forward(const float* d_params, const float* d_x, long long n, float* d_y, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    const long long tiles = (n + 15) / 16;
-    long long blocks = (tiles + FWD_WARPS - 1) / FWD_WARPS;
-    if (blocks > 148 * 4) blocks = 148 * 4;
-    mlp_forward_kernel<<<(unsigned)blocks, FWD_WARPS * 32, 0, s>>>(d_params, d_x, n, d_y);
-    return cudaGetLastError();
+    return launch_tc<false>(d_params, d_x, n, d_y, nullptr, 0, FeatureSpec{}, 0.f, nullptr,
+                            (unsigned long long)n, s);
 }
 
 cudaError_t mlp_grad(const float* d_params, const float* d_x, const float* d_t, long long n, float* d_grad,
@@ -586,14 +827,17 @@ cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, f
 }
 
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
-                              float tau, unsigned long long n_entries, cudaStream_t s)
+                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s)
 {
     if (n_entries == 0) return cudaSuccess;
-    const unsigned long long tiles = (n_entries + 31) / 32;
-    unsigned long long blocks = (tiles + PRUNE_WARPS - 1) / PRUNE_WARPS;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    learned_prune_kernel<<<(unsigned)blocks, PRUNE_WARPS * 32, 0, s>>>(d_params, d_jobs, job, sp, tau);
-    return cudaGetLastError();
+    return launch_tc<true>(d_params, nullptr, 0, nullptr, d_jobs, job, sp, tau, d_err, n_entries, s);
+}
+
+cudaError_t mlp_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(mlp_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
 }
 
 cudaError_t mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_grad, float lr, int step,

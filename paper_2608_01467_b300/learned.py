@@ -57,9 +57,11 @@ def subtree_targets(log_sums: torch.Tensor) -> torch.Tensor:
     return torch.clamp(torch.log10(mag + 1e-300), min=TARGET_FLOOR).float()
 
 
-def log_training_data(circuit, inputs, outputs, cut: int, device="cuda"):
-    """Features and exact log10 |subtree sum| of every live checkpoint entry
-    after the first `cut` gates in evaluation order (output-to-input)."""
+def table_data(circuit, inputs, outputs, cut: int, device="cuda"):
+    """Features [entries, 16] (NaN in column 0 for bottom entries) and exact
+    subtree sums [entries, 2] (re, im) of the whole checkpoint table after
+    the first `cut` gates in evaluation order, in table order
+    (entry = ((output * S + input) << A_p) | h_p), and the run's stats."""
     C = Circuit(circuit)
     C.set_input(inputs)
     b = Batch(split="fixed", c1=cut, c2=cut)
@@ -76,8 +78,15 @@ def log_training_data(circuit, inputs, outputs, cut: int, device="cuda"):
     feat = torch.empty((items.value, 16), dtype=torch.float32, device=device)
     check(_lib.load().fs_batch_features(b._h, 0, ctypes.c_void_p(b.ws_ptr), _vp(feat), _stream()))
     torch.cuda.synchronize()
+    return feat, log, st[0]
+
+
+def log_training_data(circuit, inputs, outputs, cut: int, device="cuda"):
+    """Features and exact log10 |subtree sum| of every live checkpoint entry
+    after the first `cut` gates in evaluation order (output-to-input)."""
+    feat, log, st = table_data(circuit, inputs, outputs, cut, device)
     live = ~torch.isnan(feat[:, 0])
-    return feat[live].contiguous(), subtree_targets(log[live]).contiguous(), st[0]
+    return feat[live].contiguous(), subtree_targets(log[live]).contiguous(), st
 
 
 def train(x: torch.Tensor, t: torch.Tensor, init: np.ndarray, steps: int = 400, batch: int = 4096,

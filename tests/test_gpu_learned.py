@@ -91,6 +91,75 @@ def _run(w, outs, cut, eps=0.0, pruner=None, tau=0.0):
     return b.amp.cpu().numpy()[:len(outs)], st
 
 
+def _bitrev(x, bits):
+    return int(format(x, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+@pytest.mark.parametrize("case", ["qaoa", "walk", "random"])
+def test_table_features_and_logged_subtree_sums_match_oracle(case):
+    """Every checkpoint entry's 16 features (FP32 on the GPU) and exact
+    subtree sum (the training target) against the oracle's checkpoint table
+    and its FP64 feature definition.  The library numbers prefix sources
+    from the most significant bit of h_p, the oracle from the least."""
+    from oracle import features as ofeat
+    if case == "qaoa":
+        w = qaoa_workload(8, 2, n_out=5, seed=17)
+        circ, inputs, outs = w.circuit, w.inputs, w.outputs
+        cut = 24
+    elif case == "walk":
+        from workloads import qw_workload
+        w = qw_workload(steps=7, n_out=6, pos_bits=8)
+        circ, inputs, outs = w.circuit, w.inputs, w.outputs
+        cut = len(circ.gates) // 2
+    else:
+        from workloads import SplitMix64, random_small_circuit
+        circ = random_small_circuit(7, 40, 4321)
+        rng = SplitMix64(4321)
+        inputs = [(rng.bits(7), 0.6), (rng.bits(7), 0.8j)]
+        outs = [rng.bits(7) for _ in range(5)]
+        cut = 20
+    feat, log, st = learned.table_data(circ, inputs, outs, cut)
+    feat = feat.cpu().numpy()
+    sub = log.cpu().numpy()
+    sub = sub[:, 0] + 1j * sub[:, 1]
+    S = len(inputs)
+    Ap = st["A_p"]
+    assert feat.shape[0] == len(outs) * S << Ap
+    for o, b_out in enumerate(outs):
+        for s, (b_in, _) in enumerate(inputs):
+            F, T, ap = ofeat.table_features(circ, b_in, b_out, cut)
+            assert ap == Ap
+            base = (o * S + s) << Ap
+            idx = [base + _bitrev(h, Ap) for h in range(1 << Ap)]
+            g, gs = feat[idx], sub[idx]
+            live = ~np.isnan(F[:, 0])
+            assert np.array_equal(np.isnan(g[:, 0]), ~live)
+            err = np.abs(gs - T)
+            assert np.all(err <= 1e-12 + 1e-10 * np.abs(T)), err.max()
+            d = np.abs(g[live].astype(np.float64) - F[live])
+            assert np.all(d[:, :8] <= 2e-5 + 2e-5 * np.abs(F[live][:, :8])), d.max(axis=0)
+            assert np.array_equal(g[live][:, 8:], F[live][:, 8:])
+
+
+def test_prune_decisions_match_cpu_mlp_on_logged_features():
+    """The tensor-core scoring inside the prune step against the CPU
+    reference MLP on the same checkpoint entries: every entry whose CPU score
+    is clearly below tau is cut, every entry clearly above is kept."""
+    n = 10
+    w = qaoa_workload(n, 2, n_out=24, seed=23)
+    cut = n
+    x, t, _ = learned.log_training_data(w.circuit, w.inputs, w.outputs, cut)
+    p = mlp_init_params(31)
+    score, _ = omlp.forward(p, x.cpu().numpy())
+    tau = float(np.median(score))
+    margin = 2e-2 * float(np.max(np.abs(score)))
+    below = int(np.sum(score < tau - margin))
+    near = int(np.sum(np.abs(score - tau) <= margin))
+    _, st = _run(w, w.outputs, cut, pruner=torch.from_numpy(p).cuda(), tau=tau)
+    assert below > 0 and below <= st["learned_cuts"] <= below + near, (below, near, st["learned_cuts"])
+    assert st["live_entries"] == x.shape[0] - st["learned_cuts"]
+
+
 def test_learned_pruner_end_to_end():
     n = 12
     w = qaoa_workload(n, 2, n_out=128, seed=21)

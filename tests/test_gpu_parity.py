@@ -233,6 +233,38 @@ def test_mixed_batch_one_launch():
         close(a, o)
 
 
+def test_reduction_large_and_small_outputs_in_one_warp():
+    """Outputs with thousands of per-tile partials (the whole-warp path of
+    the reduction) next to outputs with a handful, with input supports of
+    1 and 2 terms, in one batch; every amplitude against the oracle."""
+    big = qaoa_workload(10, 2, n_out=3, seed=5)            # A = 20
+    small = qft_workload(8)
+    c = random_small_circuit(6, 30, 606)
+    rng = SplitMix64(606)
+    two = (c, [(rng.bits(6), 0.6), (rng.bits(6), 0.8j)], list(range(64)), 0.0)
+    jobs = [(small.circuit, small.inputs, small.outputs[:5], 0.0),
+            (big.circuit, big.inputs, big.outputs, 0.0), two,
+            (small.circuit, small.inputs, small.outputs[5:40], 0.0)]
+    b = fs.Batch()
+    circs = []
+    for circ, ins, outs, eps in jobs:
+        C = fs.Circuit(circ)
+        C.set_input(ins)
+        circs.append(C)
+        b.add(C, outs, eps)
+    b.set_cuts(1, 0, len(big.circuit.gates))   # one region: 2^20 items, 4096 partials per output
+    b.plan()
+    b.allocate()
+    b.upload()
+    b.run()
+    st = b.finish()
+    assert st[1]["A_r"] == 20
+    amp = b.amp.cpu().numpy()
+    for (circ, ins, outs, eps), sl in zip(jobs, b.job_slices()):
+        o, _ = oracle_counts(circ, ins, outs)
+        close(amp[sl], o)
+
+
 def test_deterministic_and_host_path_bitwise():
     w = qaoa_workload(8, 2, n_out=40, seed=9)
     (a1,), _, b = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
