@@ -125,10 +125,13 @@ typedef struct fs_options {
                                       per-tile partial sums (0: 2^28) */
     uint32_t engine;               /* history kernel: 0 = straight-line code generated per
                                       batch at upload (NVRTC, sm_103a), 1 = interpreter */
-    uint32_t prefix_mode;          /* 0 = prefix expanded level by level, one level per
-                                      branching op carrying a source (each level's gates run
-                                      once per partial assignment); 1 = one region per
-                                      prefix assignment, as in Algorithm 2 */
+    uint32_t prefix_mode;          /* 0 = automatic: the prefix is split into levels at ops
+                                      carrying sources where a cost model (ops per entry,
+                                      32 B per entry read and written, one launch per
+                                      level) says it pays; each level's gates run once per
+                                      partial assignment; 1 = one region per prefix
+                                      assignment, as in Algorithm 2; 2 = one level per
+                                      branching op carrying a source */
 } fs_options;
 
 /* Counters of one job after a run. */
@@ -213,8 +216,13 @@ FS_API int fs_batch_plan(fs_batch* b, size_t* workspace_bytes);
 
 /* Copies the planned static data (programs, bit strings, tile list) into the
  * caller's device workspace d_ws (at least workspace_bytes, 256-byte
- * aligned) on stream (a cudaStream_t, NULL = legacy default stream).
- * Asynchronous; the host arrays stay owned by the batch. */
+ * aligned) on stream (a cudaStream_t, NULL = legacy default stream).  The
+ * first upload of a plan builds the straight-line kernel (engine 0), stages
+ * through pageable memory and returns after the copy; later uploads stage
+ * through a pinned buffer owned by the batch and return at once (the copy is
+ * ordered on stream; the next upload waits for it before reusing the
+ * buffer).  A graph captured from fs_batch_run stays valid across uploads of
+ * the same plan. */
 FS_API int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Enqueues one evaluation of every job on stream: counter reset, prefix

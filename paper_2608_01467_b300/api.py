@@ -140,7 +140,7 @@ class Batch:
 
     def __init__(self, split: str = "auto", c1: int = 0, c2: int = 0,
                  table_budget_bytes: int = 0, min_items: int = 0, max_items: int = 0,
-                 engine: str = "straight", prefix: str = "levels"):
+                 engine: str = "straight", prefix: str = "auto"):
         L = _lib.load()
         h = ctypes.c_void_p()
         check(L.fs_batch_create(ctypes.byref(h)))
@@ -152,7 +152,7 @@ class Batch:
         opt.min_items = min_items
         opt.max_items = max_items
         opt.engine = {"straight": 0, "interp": 1}[engine]
-        opt.prefix_mode = {"levels": 0, "single": 1}[prefix]
+        opt.prefix_mode = {"auto": 0, "single": 1, "levels": 2}[prefix]
         check(L.fs_batch_set_options(self._h, ctypes.byref(opt)))
         self.jobs = []
         self.ws = None

@@ -22,6 +22,52 @@
 using cd = std::complex<double>;
 using u128 = unsigned __int128;
 
+namespace fs {
+
+bool find_cascade(const Op* ops, const uint32_t* masks, int W, int e, int e1, CascadeRun& r)
+{
+    const Op& o0 = ops[e];
+    if (o0.code != OP_X && o0.code != OP_MCX) return false;
+    std::memset(&r, 0, sizeof r);
+    if (o0.code == OP_MCX)
+        for (int j = 0; j < W; ++j) {
+            r.cm[j] = masks[o0.aux2 + j];
+            r.cv[j] = masks[o0.aux2 + W + j];
+        }
+    const int t0 = o0.q0;
+    uint32_t field[4] = {0, 0, 0, 0};   // targets of the ops so far
+    field[t0 >> 5] |= 1u << (t0 & 31);
+    int len = 1, v = -1;
+    while (e + len < e1) {
+        const Op& o = ops[e + len];
+        const int t = t0 + len;
+        if (o.code != OP_MCX || t >= 32 * W || o.q0 != t) break;
+        if ((r.cm[t >> 5] >> (t & 31)) & 1u) break;   // a common control on the new target
+        const uint32_t* m = masks + o.aux2;
+        bool ok = true;
+        int pol = -1;
+        for (int j = 0; j < W && ok; ++j) {
+            ok = m[j] == (r.cm[j] | field[j]) && (m[W + j] & r.cm[j]) == r.cv[j];
+            const uint32_t fv = m[W + j] & field[j];
+            if (!field[j]) continue;
+            const int pj = fv == field[j] ? 1 : fv == 0 ? 0 : -2;
+            if (pj == -2 || (pol >= 0 && pj != pol)) ok = false;
+            pol = pj;
+        }
+        if (!ok || (v >= 0 && pol != v)) break;
+        v = pol;
+        field[t >> 5] |= 1u << (t & 31);
+        ++len;
+    }
+    if (len < 3) return false;
+    r.len = len;
+    r.t0 = t0;
+    r.dec = v == 1;
+    return true;
+}
+
+}  // namespace fs
+
 namespace {
 
 thread_local std::string g_err;
@@ -395,6 +441,19 @@ struct fs_batch {
     size_t o_bigcount = 0, o_biglist = 0;   // outputs left to the block-per-output reduction
     size_t static_bytes = 0, dyn_begin = 0;
     std::vector<unsigned char> host_static;
+    // repeated uploads stage through pinned memory (asynchronous copy; the
+    // event guards the buffer until the previous copy has finished)
+    unsigned char* h_pinned = nullptr;
+    size_t h_pinned_bytes = 0;
+    cudaEvent_t up_ev = nullptr;
+    bool up_pending = false;
+    uint64_t n_uploads = 0;
+    bool image_valid = false;     // h_pinned holds this plan's image for image_ws
+    void* image_ws = nullptr;
+    unsigned char* h_words = nullptr;   // pinned copy of the counters and error word
+    size_t h_words_bytes = 0;
+    uint64_t n_finishes = 0;
+    bool no_host_alloc = false;         // set by the allocation-free entry point
     std::vector<uint2> tiles;
     uint64_t total_prefix = 0, total_out = 0;
     int grid = 0, compact_grid = 0;
@@ -412,9 +471,20 @@ struct fs_batch {
     ~fs_batch()
     {
         for (auto& e : ev) if (e) cudaEventDestroy(e);
+        if (up_ev) {
+            if (up_pending) cudaEventSynchronize(up_ev);
+            cudaEventDestroy(up_ev);
+        }
+        if (h_pinned) cudaFreeHost(h_pinned);
+        if (h_words) cudaFreeHost(h_words);
         drop_jit();
     }
 };
+
+void fs::batch_forbid_host_alloc(fs_batch* b)
+{
+    if (b) b->no_host_alloc = true;
+}
 
 int fs::set_error(int code, const char* msg)
 {
@@ -584,7 +654,7 @@ int fs_batch_set_options(fs_batch* b, const fs_options* opt)
     if (opt) {
         if (opt->split > 2) return fail(FS_ERR_INVALID, "split must be 0, 1 or 2");
         if (opt->engine > 1) return fail(FS_ERR_INVALID, "engine must be 0 or 1");
-        if (opt->prefix_mode > 1) return fail(FS_ERR_INVALID, "prefix_mode must be 0 or 1");
+        if (opt->prefix_mode > 2) return fail(FS_ERR_INVALID, "prefix_mode must be 0, 1 or 2");
         b->opt = *opt;
     } else {
         std::memset(&b->opt, 0, sizeof b->opt);
@@ -720,6 +790,13 @@ int fs_batch_total_outputs(const fs_batch* b, size_t* n)
     return FS_OK;
 }
 
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused);
+
+// Rates of the prefix cost model (work-model integer ops and FP64
+// instructions per second, HBM bytes per second, seconds per launch),
+// measured on B300 for the history and prefix kernels.
+constexpr double kModelIntOps = 2.5e13, kModelFp64Ops = 5.0e11, kModelBytes = 5.0e12, kModelLaunch = 4.0e-6;
+
 int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
 {
     if (!b || !workspace_bytes) return fail(FS_ERR_INVALID, "NULL argument");
@@ -773,32 +850,57 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
             return fail(FS_ERR_TOO_LARGE, "job %zu: too many (prefix, root) items", ji);
         compile(C, j.W, j.sp, j.prog);
         j.levels.clear();
-        if (b->opt.prefix_mode == 0 && j.sp.Ap > 0 && j.pairs > 0) {
-            // boundaries after every op carrying a prefix source; the tail
-            // without sources joins the last level
-            std::vector<int> ends;
+        if (b->opt.prefix_mode != 1 && j.sp.Ap > 0 && j.pairs > 0) {
+            // candidate boundaries: after every op carrying a prefix source
+            // (the tail without sources joins the last level)
+            std::vector<int> E{0}, Abits{0};
             int a = 0;
-            std::vector<int> bits;
             for (int e = 0; e < j.sp.c1; ++e) {
                 const fs::Op& op = j.prog.ops[e];
                 const int na = (op.s0 >= 0) + (op.s1 >= 0);
                 if (na && (op.code == fs::OP_H || op.code == fs::OP_BR1 || op.code == fs::OP_BR2)) {
                     a += na;
-                    ends.push_back(e + 1);
-                    bits.push_back(a);
+                    E.push_back(e + 1);
+                    Abits.push_back(a);
                 }
             }
-            if (ends.size() >= 2) {
-                int prev_e = 0, prev_a = 0;
-                for (size_t k = 0; k < ends.size(); ++k) {
+            const size_t m = E.size() - 1;
+            if (m >= 1) E[m] = j.sp.c1;
+            std::vector<size_t> from(m + 1, 0);
+            if (b->opt.prefix_mode == 2) {
+                for (size_t k = 1; k <= m; ++k) from[k] = k - 1;
+            } else {
+                // segmentation with the least modelled time: a level over
+                // boundaries (i, k] runs its ops once per entry of level k,
+                // reads level i and writes level k (32 B per entry) and costs
+                // one launch; a single segment is the flat prefix
+                const bool deferred = b->opt.engine == 0 && j.eps == 0.0, fused = b->opt.engine == 0;
+                std::vector<double> best(m + 1, 1e300);
+                best[0] = 0.0;
+                for (size_t k = 1; k <= m; ++k)
+                    for (size_t i = 0; i < k; ++i) {
+                        double io = 0, fo = 0;
+                        region_work(j, E[i], E[k], io, fo, deferred, fused);
+                        const double n_out = std::ldexp((double)j.pairs, Abits[k]);
+                        const double n_in = i ? std::ldexp((double)j.pairs, Abits[i]) : 0.0;
+                        const double t = n_out * (io / kModelIntOps + fo / kModelFp64Ops) +
+                                         32.0 * (n_out + n_in) / kModelBytes + kModelLaunch;
+                        if (best[i] + t < best[k]) { best[k] = best[i] + t; from[k] = i; }
+                    }
+            }
+            std::vector<size_t> cut_at;
+            for (size_t k = m; k > 0; k = from[k]) cut_at.push_back(k);
+            std::reverse(cut_at.begin(), cut_at.end());
+            if (cut_at.size() >= 2) {
+                size_t prev = 0;
+                for (size_t k : cut_at) {
                     fs::PrefixLevel L;
-                    L.e0 = prev_e;
-                    L.e1 = (k + 1 == ends.size()) ? j.sp.c1 : ends[k];
-                    L.a_prev = prev_a;
-                    L.a_next = bits[k];
+                    L.e0 = E[prev];
+                    L.e1 = E[k];
+                    L.a_prev = Abits[prev];
+                    L.a_next = Abits[k];
                     j.levels.push_back(L);
-                    prev_e = L.e1;
-                    prev_a = L.a_next;
+                    prev = k;
                 }
             }
         }
@@ -872,7 +974,8 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         if (!j.levels.empty()) j.o_lvscratch = take((j.table_entries / 2) * sizeof(fs::Entry));
         if (j.compact) {
             j.o_live = take(j.table_entries * sizeof(uint64_t));
-            j.o_esum = take((j.table_entries << j.sp.Ar) * sizeof(double2));
+            // subtree partials: one per warp of 32 items when A_r >= 5, else per item
+            j.o_esum = take((j.table_entries << (j.sp.Ar >= 5 ? j.sp.Ar - 5 : j.sp.Ar)) * sizeof(double2));
             j.o_blk = take(j.nblk * sizeof(uint32_t));
             j.o_prange = take(2 * j.pairs * sizeof(uint64_t));
         }
@@ -881,6 +984,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     *workspace_bytes = off;
     b->planned = true;
     b->uploaded = false;
+    b->image_valid = false;
     b->drop_jit();
     int dev = 0;
     cudaGetDevice(&dev);
@@ -901,8 +1005,42 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
             break;
         }
     unsigned char* base = (unsigned char*)d_ws;
-    std::vector<unsigned char>& H = b->host_static;
-    H.assign(b->static_bytes, 0);
+    // the first upload of a batch stages through pageable memory and waits;
+    // later ones (a request refreshed every step) through pinned memory
+    const bool pinned = b->n_uploads > 0 && !b->no_host_alloc;
+    unsigned char* H = nullptr;
+    const bool engine_ready = b->opt.engine != 0 || b->jit || b->jobs.empty();
+    if (pinned && b->image_valid && b->image_ws == d_ws && engine_ready) {
+        // the pinned image of this plan for this workspace is current: copy it
+        if (b->static_bytes)
+            CUDA_TRY(cudaMemcpyAsync(d_ws, b->h_pinned, b->static_bytes, cudaMemcpyHostToDevice,
+                                     (cudaStream_t)stream));
+        CUDA_TRY(cudaEventRecord(b->up_ev, (cudaStream_t)stream));
+        b->up_pending = true;
+        b->n_uploads++;
+        b->uploaded_ws = d_ws;
+        b->uploaded = true;
+        return FS_OK;
+    }
+    if (pinned) {
+        if (b->up_pending) {
+            CUDA_TRY(cudaEventSynchronize(b->up_ev));
+            b->up_pending = false;
+        }
+        if (b->h_pinned_bytes < b->static_bytes) {
+            if (b->h_pinned) CUDA_TRY(cudaFreeHost(b->h_pinned));
+            b->h_pinned = nullptr;
+            b->h_pinned_bytes = 0;
+            CUDA_TRY(cudaMallocHost((void**)&b->h_pinned, b->static_bytes ? b->static_bytes : 1));
+            b->h_pinned_bytes = b->static_bytes;
+        }
+        if (!b->up_ev) CUDA_TRY(cudaEventCreateWithFlags(&b->up_ev, cudaEventDisableTiming));
+        H = b->h_pinned;
+    } else {
+        b->host_static.assign(b->static_bytes, 0);
+        H = b->host_static.data();
+    }
+    if (b->static_bytes) std::memset(H, 0, b->static_bytes);
     const size_t nj = b->jobs.size();
     std::vector<fs::JobDev> jd(nj);
     std::vector<uint64_t> pbegin(nj), obegin(nj);
@@ -978,9 +1116,17 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         if (jrc) return fail(FS_ERR_CUDA, "straight-line engine: %s", err.c_str());
     }
     if (b->static_bytes)
-        CUDA_TRY(cudaMemcpyAsync(d_ws, H.data(), b->static_bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
-    // the host staging copy must outlive the asynchronous copy
-    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        CUDA_TRY(cudaMemcpyAsync(d_ws, H, b->static_bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    if (pinned) {
+        CUDA_TRY(cudaEventRecord(b->up_ev, (cudaStream_t)stream));
+        b->up_pending = true;
+        b->image_valid = true;
+        b->image_ws = d_ws;
+    } else {
+        // the pageable staging copy must outlive the copy
+        CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    }
+    b->n_uploads++;
     b->uploaded_ws = d_ws;
     b->uploaded = true;
     return FS_OK;
@@ -1132,10 +1278,30 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
     std::vector<unsigned long long> st(fs::STATS_PER_JOB * nj + 1, 0);
     uint32_t err = 0;
     unsigned char* base = (unsigned char*)d_ws;
-    if (nj) CUDA_TRY(cudaMemcpyAsync(st.data(), base + b->o_stats, fs::STATS_PER_JOB * nj * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(&err, base + b->o_err, sizeof err, cudaMemcpyDeviceToHost, s));
+    // counters ... error word are one contiguous range, copied at once; from
+    // the second finish on into pinned memory owned by the batch
+    const size_t words = b->o_err + sizeof(uint32_t) - b->o_stats;
+    std::vector<unsigned char> pageable;
+    unsigned char* hw = nullptr;
+    if (b->n_finishes > 0 && !b->no_host_alloc) {
+        if (b->h_words_bytes < words) {
+            if (b->h_words) CUDA_TRY(cudaFreeHost(b->h_words));
+            b->h_words = nullptr;
+            b->h_words_bytes = 0;
+            CUDA_TRY(cudaMallocHost((void**)&b->h_words, words));
+            b->h_words_bytes = words;
+        }
+        hw = b->h_words;
+    } else {
+        pageable.resize(words);
+        hw = pageable.data();
+    }
+    b->n_finishes++;
+    CUDA_TRY(cudaMemcpyAsync(hw, base + b->o_stats, words, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
+    if (nj) std::memcpy(st.data(), hw, fs::STATS_PER_JOB * nj * sizeof(unsigned long long));
+    std::memcpy(&err, hw + (b->o_err - b->o_stats), sizeof err);
     if (err & fs::DEV_ERR_BAD_OPCODE) return fail(FS_ERR_BAD_PROGRAM, "device found an unknown opcode");
     if (err & fs::DEV_ERR_TIMEOUT) return fail(FS_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core scoring)");
     if (stats) {
@@ -1199,7 +1365,7 @@ static bool same2(double2 a, double2 b) { return a.x == b.x && a.y == b.y; }
 // deferred: the straight-line engine in exact mode, where two-valued factors
 // are counted per class (1 integer add) and applied once per region (one
 // complex product per class).
-static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred)
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused)
 {
     const int W = j.W;
     std::vector<std::pair<double2, double2>> classes;
@@ -1213,6 +1379,16 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
     const double2 R = make_double2(std::sqrt(0.5), 0.0), mR = make_double2(-std::sqrt(0.5), 0.0);
     for (int e = e0; e < e1; ++e) {
         const fs::Op& op0 = j.prog.ops[e];
+        fs::CascadeRun run;
+        if (fused && fs::find_cascade(j.prog.ops.data(), j.prog.masks.data(), W, e, e1, run)) {
+            // common-control test, then per field word: mask, subtract, borrow, xor-and, flip
+            int nz = 0;
+            for (int w = 0; w < W; ++w) nz += (run.cm[w] | run.cv[w]) != 0;
+            iops += (nz ? nz + (nz > 1 ? nz / 2 : 0) + 1 : 0) +
+                    5.0 * (((run.t0 + run.len - 1) >> 5) - (run.t0 >> 5) + 1);
+            e += run.len - 1;
+            continue;
+        }
         if (deferred) {
             const double2* F = j.prog.fac.data() + op0.aux;
             bool z = false;
@@ -1275,9 +1451,10 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
     const int G = (int)j.prog.ops.size();
     const int cuts[4] = {0, j.sp.c1, j.sp.c2, G};
     const bool deferred = b->opt.engine == 0 && j.eps == 0.0;
+    const bool fused = b->opt.engine == 0;   // the straight-line engine fuses incrementer cascades
     for (int r = 0; r < 3; ++r) {
         double i = 0, f = 0;
-        region_work(j, cuts[r], cuts[r + 1], i, f, deferred);
+        region_work(j, cuts[r], cuts[r + 1], i, f, deferred, fused);
         int_ops[r] = i;
         fp64_ops[r] = f;
     }
@@ -1287,7 +1464,7 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
         double i = 0, f = 0;
         for (const fs::PrefixLevel& L : j.levels) {
             double li = 0, lf = 0;
-            region_work(j, L.e0, L.e1, li, lf, deferred);
+            region_work(j, L.e0, L.e1, li, lf, deferred, fused);
             i += li * std::ldexp(1.0, L.a_next - j.sp.Ap);
             f += lf * std::ldexp(1.0, L.a_next - j.sp.Ap);
         }

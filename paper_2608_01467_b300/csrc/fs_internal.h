@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+struct fs_batch;
+
 namespace fs {
 
 // Opcodes of the evaluation-order program.  Every op moves the state from
@@ -44,6 +46,25 @@ struct Op {
     uint32_t aux2;
 };
 static_assert(sizeof(Op) == 16, "Op must be 16 bytes");
+
+// Keeps a batch on pageable staging (no pinned host buffers) for callers
+// that must not allocate.
+void batch_forbid_host_alloc(::fs_batch* b);
+
+// A run of controlled-X ops [e, e + len) in evaluation order whose targets
+// are the contiguous qubits t0, t0 + 1, ... and where op k is also
+// controlled on the targets of ops 0..k-1, all with one polarity v, plus
+// common controls (cm, cv) that do not touch the targets.  Applied in order
+// the run maps the field x = bits [t0, t0 + len) of the register to x - 1
+// (v = 1) or x + 1 (v = 0) modulo 2^len when the common controls hold: the
+// ripple-carry incrementer / decrementer written as a cascade of
+// multi-controlled X gates.
+struct CascadeRun {
+    int len, t0;
+    bool dec;
+    uint32_t cm[4], cv[4];
+};
+bool find_cascade(const Op* ops, const uint32_t* masks, int W, int e, int e1, CascadeRun& r);
 
 // One checkpoint-table entry (Algorithm 2: propagated state sigma_p and
 // partial amplitude beta_p after the prefix).  An entry whose prefix was cut
@@ -88,7 +109,7 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     int32_t compact;           /* 1: history over the compacted live entries */         \
     int32_t pad1;                                                             \
     uint64_t* live;            /* compacted live entry indices, table order */            \
-    double2* esum;             /* subtree sum per (live entry, h_r) item */              \
+    double2* esum;             /* subtree sums of live items: per 32 (A_r >= 5) or per item */ \
     uint32_t* blk;             /* per compaction block: live count, then offset */       \
     uint64_t* prange;          /* per pair: [lo, hi) of its live entries */              \
     uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */

@@ -172,7 +172,7 @@ __device__ void tile_body(const JobDev& J, u64 tile, double2* s_warp)
 }
 
 template <class T>
-__device__ void compact_body(const JobDev& J, u64 i, u64& completed, u64& valid, u64& visits)
+__device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
     const u64 e = J.live[i >> T::Ar];
@@ -215,7 +215,24 @@ __device__ void compact_body(const JobDev& J, u64 i, u64& completed, u64& valid,
             }
         }
     }
-    J.esum[i] = acc;
+    return acc;
+}
+
+// Subtree sums of 32 consecutive items (one warp).  With A_r >= 5 they share
+// a live entry and are added by a fixed butterfly into one partial per warp
+// (esum[i / 32]); otherwise each item keeps its own (esum[i]).
+__device__ __forceinline__ void store_esum(const JobDev& J, u64 i, double2 acc, bool active)
+{
+    if (J.Ar >= 5) {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if ((threadIdx.x & 31) == 0 && active) J.esum[i >> 5] = acc;
+    } else if (active) {
+        J.esum[i] = acc;
+    }
 }
 
 // Level expansion prologue / epilogue (per-source prefix levels).
@@ -397,7 +414,37 @@ void emit_class_table(std::string& globals, const std::string& name, const Facto
     globals += "};\n";
 }
 
-// Body of one region: ops [e0, e1).  nbits = the region's h width.
+// A controlled incrementer / decrementer (find_cascade) as one borrow
+// chain over the field's words: with y the field's ones (x - 1) or zeros
+// (x + 1), the bits that flip are y ^ (y - 2^t0) restricted to the field.
+std::string emit_cascade(const CascadeRun& r, int W)
+{
+    const int p = r.t0, top = r.t0 + r.len - 1;
+    const int w0 = p >> 5, w1 = top >> 5;
+    std::string c = "{ u32 b = " + std::to_string(1u << (p & 31)) + "u; ";
+    for (int w = w0; w <= w1; ++w) {
+        const int lo = w == w0 ? (p & 31) : 0, hi = w == w1 ? (top & 31) : 31;
+        const uint32_t F = (hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+        char buf[64];
+        snprintf(buf, sizeof buf, "0x%08xu", F);
+        const std::string ws = std::to_string(w);
+        c += "{ const u32 y = " + std::string(r.dec ? "" : "~") + "s[" + ws + "] & " + buf + "; const u32 d = y - b; ";
+        if (w < w1) c += "b = (y < b) ? 1u : 0u; ";
+        c += "s[" + ws + "] ^= (y ^ d) & " + buf + "; } ";
+    }
+    c += "}";
+    bool any = false;
+    for (int j = 0; j < W; ++j) any |= r.cm[j] != 0;
+    if (!any) return c;
+    uint32_t m[8];
+    for (int j = 0; j < W; ++j) {
+        m[j] = r.cm[j];
+        m[W + j] = r.cv[j];
+    }
+    return "if (" + match_expr(m, W) + ") " + c;
+}
+
+// Body of one region: ops [e0, e1).  nbits = the region's h width.// Body of one region: ops [e0, e1).  nbits = the region's h width.
 void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
                  int e0, int e1, int nbits)
 {
@@ -411,6 +458,13 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
     };
     const double2 R = make_double2(0x1.6a09e667f3bcdp-1, 0.0), mR = make_double2(-0x1.6a09e667f3bcdp-1, 0.0);
     for (int e = e0; e < e1; ++e) {
+        CascadeRun run;
+        if (find_cascade(J.ops, J.masks, W, e, e1, run)) {
+            body += "    " + emit_cascade(run, W) + "   // ops " + std::to_string(e) + ".." +
+                    std::to_string(e + run.len - 1) + ": x " + (run.dec ? "- 1" : "+ 1") + "\n";
+            e += run.len - 1;
+            continue;
+        }
         const Op& op = J.ops[e];
         const int q0 = op.q0, q1 = op.q1;
         const double2* F = J.fac + op.aux;
@@ -588,12 +642,13 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
            "    u64 completed = 0, valid = 0, visits = 0;\n    for (;;) {\n"
            "        u64 base = 0;\n        if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);\n"
            "        base = __shfl_sync(0xffffffffu, base, 0);\n        if (base >= nlive) break;\n"
-           "        const u64 i = base + lane;\n        if (i < nlive) {\n            switch (job) {\n";
+           "        const u64 i = base + lane;\n        double2 acc = make_double2(0.0, 0.0);\n"
+           "        if (i < nlive) {\n            switch (job) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
         if (jobs[j].compact)
-            src += "            case " + std::to_string(j) + ": compact_body<J" + std::to_string(j) +
+            src += "            case " + std::to_string(j) + ": acc = compact_body<J" + std::to_string(j) +
                    ">(J, i, completed, valid, visits); break;\n";
-    src += "            default: break;\n            }\n        }\n    }\n"
+    src += "            default: break;\n            }\n        }\n        store_esum(J, i, acc, i < nlive);\n    }\n"
            "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
            "    if (lane == 0 && (completed | valid | visits)) {\n"
            "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";

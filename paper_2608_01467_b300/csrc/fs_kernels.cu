@@ -585,8 +585,8 @@ __global__ void __launch_bounds__(256) pair_range_kernel(const JobDev* __restric
 // assignment and the suffix enumeration and writes the item's subtree sum
 // (one slot per item: fixed reduction order downstream).
 template <int W>
-__device__ void compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsigned long long& completed,
-                             unsigned long long& valid, unsigned long long& visits)
+__device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsigned long long& completed,
+                                unsigned long long& valid, unsigned long long& visits)
 {
     const uint64_t e = J.live[i >> J.Ar];
     const uint64_t hr = i & ((1ull << J.Ar) - 1ull);
@@ -624,7 +624,24 @@ __device__ void compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsigne
             }
         }
     }
-    J.esum[i] = acc;
+    return acc;
+}
+
+// Subtree sums of one warp's 32 consecutive items: with A_r >= 5 they share a
+// live entry and one fixed butterfly leaves one partial per warp (esum[i /
+// 32]); otherwise each item keeps its own (esum[i]).
+__device__ __forceinline__ void store_esum(const JobDev& J, uint64_t i, double2 acc, bool active)
+{
+    if (J.Ar >= 5) {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if ((threadIdx.x & 31) == 0 && active) J.esum[i >> 5] = acc;
+    } else if (active) {
+        J.esum[i] = acc;
+    }
 }
 
 __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __restrict__ jobp, uint32_t* err)
@@ -639,11 +656,13 @@ __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __re
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n_items) break;
         const uint64_t i = base + lane;
+        double2 acc = make_double2(0.0, 0.0);
         if (i < n_items) {
-            if (J.W == 1) compact_item<1>(J, i, err, completed, valid, visits);
-            else if (J.W == 2) compact_item<2>(J, i, err, completed, valid, visits);
-            else compact_item<4>(J, i, err, completed, valid, visits);
+            if (J.W == 1) acc = compact_item<1>(J, i, err, completed, valid, visits);
+            else if (J.W == 2) acc = compact_item<2>(J, i, err, completed, valid, visits);
+            else acc = compact_item<4>(J, i, err, completed, valid, visits);
         }
+        store_esum(J, i, acc, i < n_items);
     }
     completed = warp_sum_u64(completed);
     valid = warp_sum_u64(valid);
@@ -663,8 +682,9 @@ __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __re
 __device__ __forceinline__ const double2* pair_items(const JobDev& J, uint64_t pair, uint64_t& lo, uint64_t& hi)
 {
     if (J.compact) {
-        lo = J.prange[2 * pair] << J.Ar;
-        hi = J.prange[2 * pair + 1] << J.Ar;
+        const int sh = J.Ar >= 5 ? J.Ar - 5 : J.Ar;   // partials per live entry: 2^(A_r - 5) or 2^A_r
+        lo = J.prange[2 * pair] << sh;
+        hi = J.prange[2 * pair + 1] << sh;
         return J.esum;
     }
     lo = pair << J.log2_spp;

@@ -59,6 +59,7 @@ extern "C" FS_API int fs_amplitudes_noalloc(fs_circuit* c, const uint64_t* outpu
     fs_batch* b = nullptr;
     rc = fs_batch_create(&b);
     if (rc) return rc;
+    fs::batch_forbid_host_alloc(b);
     size_t ws = 0;
     // keep the autotuned checkpoint table (and the live list of pruned
     // requests) inside a quarter of the scratch, and the per-item partial or

@@ -183,6 +183,24 @@ def test_threshold_pruning_matches_oracle(eps):
     assert st[0]["valid"] == int(cnt["valid"].sum())
 
 
+@pytest.mark.parametrize("ap,ar", [(4, 2), (4, 5), (3, 8), (2, 12)])
+def test_pruned_runs_any_root_width(ap, ar):
+    """Pruned jobs run over compacted live entries; with A_r >= 5 a warp's 32
+    items share an entry and leave one partial sum, below that one per item.
+    Amplitudes and leaf counts against the oracle at the same cuts."""
+    w = qaoa_workload(8, 2, n_out=24, seed=61)
+    G = len(w.circuit.gates)
+    src_gate = {sid: g for g, q, sid in fs.Circuit(w.circuit).branch_vars() if sid >= 0}
+    c1, c2 = G - src_gate[ap - 1], G - src_gate[ap + ar - 1]
+    eps = 2e-3
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, eps)], split="fixed", c1=c1, c2=c2)
+    assert (st[0]["A_p"], st[0]["A_r"]) == (ap, ar)
+    o, cnt = oracle_counts(w.circuit, w.inputs, w.outputs, eps=eps, c1=c1, c2=c2)
+    close(a, o)
+    assert st[0]["completed"] == int(cnt["completed"].sum())
+    assert st[0]["valid"] == int(cnt["valid"].sum())
+
+
 def test_qw_small_vs_offset_walk():
     w = qw_workload(steps=6, n_out=64, pos_bits=8)
     (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
@@ -265,6 +283,58 @@ def test_reduction_large_and_small_outputs_in_one_warp():
         close(amp[sl], o)
 
 
+def _cascade_circuit(n, field, common, inc, order_msb_first, hs):
+    """H on qubits hs, then a +1 (inc) or -1 on the qubits `field` (first =
+    least significant) controlled on `common`, written as multi-controlled X
+    gates most (or least) significant first, then H on hs again."""
+    from workloads import Circuit as WC
+    g = [Gate("H", (q,)) for q in hs]
+    v = 1 if inc else 0
+    ks = range(len(field) - 1, -1, -1) if order_msb_first else range(len(field))
+    for k in ks:
+        ctr = tuple(common) + tuple((field[j], v) for j in range(k))
+        g.append(Gate("X", (field[k],), ctr) if ctr else Gate("X", (field[k],)))
+    g += [Gate("H", (q,)) for q in hs]
+    return WC(n, g, "cascade")
+
+
+@pytest.mark.parametrize("n,f0,L,common,inc,msb", [
+    (12, 2, 8, (), True, True), (12, 2, 8, ((0, 1),), False, True), (45, 27, 12, ((1, 0),), True, True),
+    (70, 5, 60, ((0, 1), (68, 0)), False, True), (128, 1, 120, ((0, 1),), True, True),
+    (45, 27, 12, ((1, 1),), True, False)])
+def test_incrementer_cascades_match_oracle(n, f0, L, common, inc, msb):
+    """Controlled +-1 on a contiguous field (within a word and across word
+    boundaries, with and without common controls of either polarity): the
+    straight-line engine replaces such MCX cascades by one borrow chain,
+    which must agree with the oracle's gate-by-gate evaluation and with the
+    interpreter bit for bit."""
+    field = list(range(f0, f0 + L))
+    hs = [f0, f0 + 1, f0 + L - 1] + [q for q, _ in common]
+    c = _cascade_circuit(n, field, common, inc, msb, hs)
+    rng = SplitMix64(n + L)
+    ins = [(rng.bits(n), 1.0)]
+    outs = [rng.bits(n) for _ in range(6)]
+    # outputs reachable from the input: flip the H qubits and move the field by one
+    b = ins[0][0]
+    for k in range(16):
+        y = b
+        for j, q in enumerate(hs):
+            if (k >> j) & 1:
+                y ^= 1 << q
+        x = (y >> f0) & ((1 << L) - 1)
+        x = (x + (1 if inc else -1)) % (1 << L)
+        outs.append((y & ~(((1 << L) - 1) << f0)) | (x << f0))
+    a1, s1, _ = run_batch([(c, ins, outs, 0.0)], engine="straight")
+    a2, s2, _ = run_batch([(c, ins, outs, 0.0)], engine="interp")
+    o, cnt = oracle_counts(c, ins, outs)
+    close(a1[0], o)
+    close(a2[0], o)
+    assert np.abs(o).max() > 0.1
+    for k in ("completed", "valid", "gate_visits"):
+        assert s1[0][k] == s2[0][k], k
+    assert s1[0]["valid"] == int(cnt["valid"].sum())
+
+
 def test_deterministic_and_host_path_bitwise():
     w = qaoa_workload(8, 2, n_out=40, seed=9)
     (a1,), _, b = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
@@ -291,6 +361,15 @@ def test_cuda_graph_capture_of_run():
         g.replay()
     torch.cuda.synchronize()
     assert np.array_equal(b.amp.cpu().numpy(), a1)
+    # later uploads stage through pinned memory without waiting; the graph
+    # stays valid and sees the refreshed request
+    for _ in range(3):
+        b.upload(stream=s)
+        with torch.cuda.stream(s):
+            b.amp.zero_()
+            g.replay()
+        b.finish(stream=s)
+        assert np.array_equal(b.amp.cpu().numpy(), a1)
 
 
 def test_edge_cases_ragged_and_empty():
@@ -310,7 +389,7 @@ def test_edge_cases_ragged_and_empty():
     assert len(C.amplitudes([])) == 0
 
 
-@pytest.mark.parametrize("case", ["qaoa_exact", "qaoa_eps", "qw", "rand7", "rand70", "aa"])
+@pytest.mark.parametrize("case", ["qaoa_exact", "qaoa_eps", "qw", "qw96", "rand7", "rand70", "aa"])
 def test_engines_bitwise_equal(case):
     """The generated straight-line kernel and the interpreter agree: to the
     bit in threshold mode (same factors, same order), within the exact-mode
@@ -321,6 +400,9 @@ def test_engines_bitwise_equal(case):
         jobs = [(w.circuit, w.inputs, w.outputs, 0.05 if case == "qaoa_eps" else 0.0)]
     elif case == "qw":
         w = qw_workload(steps=6, n_out=40, pos_bits=8)
+        jobs = [(w.circuit, w.inputs, w.outputs, 0.0)]
+    elif case == "qw96":
+        w = qw_workload(steps=6, n_out=40)
         jobs = [(w.circuit, w.inputs, w.outputs, 0.0)]
     elif case == "aa":
         w = aa_workload(n=4, iters=2, seed=3, all_outputs=True)
@@ -357,7 +439,12 @@ def test_level_prefix_equals_single_region_prefix(engine):
         jobs = [(w.circuit, w.inputs, w.outputs, eps)]
         a1, s1, _ = run_batch(jobs, split="fixed", c1=2 * G // 3, c2=5 * G // 6, prefix="single", engine=engine)
         a2, s2, _ = run_batch(jobs, split="fixed", c1=2 * G // 3, c2=5 * G // 6, prefix="levels", engine=engine)
+        a3, s3, b3 = run_batch(jobs, split="fixed", c1=2 * G // 3, c2=5 * G // 6, prefix="auto", engine=engine)
         close(a2[0], a1[0])
+        close(a3[0], a1[0])
         for k in ("completed", "valid", "table_entries", "history_visits"):
-            assert s1[0][k] == s2[0][k], k
+            assert s1[0][k] == s2[0][k] == s3[0][k], k
         assert s2[0]["gate_visits"] - s2[0]["history_visits"] < s1[0]["gate_visits"] - s1[0]["history_visits"]
+        # the automatic split is one of the segmentations in between
+        pre = lambda st: st["gate_visits"] - st["history_visits"]
+        assert pre(s2[0]) <= pre(s3[0]) <= pre(s1[0])

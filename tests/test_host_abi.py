@@ -170,7 +170,7 @@ def test_plan_layout_and_fixed_split_errors():
     assert n > 0 and n % 256 == 0
     assert b2.total_outputs == 16
     assert b2.launch_count() == 4      # prefix, history, reduce (lane groups + large outputs)
-    b3 = fs.Batch()                    # prefix expanded level by level
+    b3 = fs.Batch(prefix="levels")     # prefix expanded one level per source op
     b3.add(C, w.outputs)
     b3.plan()
     st_levels = b3.launch_count() - 3  # levels + history + reduce (2)
