@@ -423,6 +423,7 @@ struct Job {
     bool compact = false;
     int fixed_c1 = -1, fixed_c2 = -1;     // per-job cuts overriding the batch split
     std::vector<fs::PrefixLevel> levels;  // per-source prefix expansion (empty: single region)
+    double2 scale = make_double2(1.0, 0.0);   // constant left out by the generated root and suffix
     size_t o_lvscratch = 0;
     size_t o_live = 0, o_esum = 0, o_blk = 0, o_prange = 0;
     uint64_t nblk = 0;
@@ -467,6 +468,7 @@ struct fs_batch {
     {
         if (jit) fs::jit_release(jit);
         jit = nullptr;
+        for (Job& j : jobs) j.scale = make_double2(1.0, 0.0);
     }
     ~fs_batch()
     {
@@ -790,7 +792,8 @@ int fs_batch_total_outputs(const fs_batch* b, size_t* n)
     return FS_OK;
 }
 
-static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused);
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused,
+                        bool hoisted = false);
 
 // Rates of the prefix cost model (work-model integer ops and FP64
 // instructions per second, HBM bytes per second, seconds per launch),
@@ -1042,6 +1045,27 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
     }
     if (b->static_bytes) std::memset(H, 0, b->static_bytes);
     const size_t nj = b->jobs.size();
+    // the straight-line kernel is built first: it reports the constant factor
+    // each job's generated root and suffix leave out (folded into c_in below)
+    if (b->opt.engine == 0 && !b->jit && nj) {
+        std::vector<fs::JitJobSpec> specs(nj);
+        for (size_t ji = 0; ji < nj; ++ji) {
+            const Job& j = b->jobs[ji];
+            specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
+                                       j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
+                                       j.sp.As, j.eps * j.eps, j.compact, j.levels};
+        }
+        std::string err, src;
+        const char* dump = getenv("FS_JIT_DUMP");   // optional: write the generated source here
+        std::vector<double2> scales;
+        const int jrc = fs::jit_build(specs, &b->jit, &err, &b->jit_ms, dump ? &src : nullptr, &scales);
+        for (size_t ji = 0; ji < nj && !jrc; ++ji) b->jobs[ji].scale = scales[ji];
+        if (dump) {
+            FILE* f = fopen(dump, "w");
+            if (f) { fwrite(src.data(), 1, src.size(), f); fclose(f); }
+        }
+        if (jrc) return fail(FS_ERR_CUDA, "straight-line engine: %s", err.c_str());
+    }
     std::vector<fs::JobDev> jd(nj);
     std::vector<uint64_t> pbegin(nj), obegin(nj);
     uint64_t pacc = 0, oacc = 0;
@@ -1078,6 +1102,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.blk = j.compact ? (uint32_t*)(base + j.o_blk) : nullptr;
         d.prange = j.compact ? (uint64_t*)(base + j.o_prange) : nullptr;
         d.n_entries = j.table_entries;
+        d.scale = j.scale;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
         if (j.levels.empty()) pacc += j.table_entries;
@@ -1087,8 +1112,12 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         std::memcpy(&H[j.o_fac], j.prog.fac.data(), j.prog.fac.size() * sizeof(double2));
         for (size_t i = 0; i < j.outs.size(); ++i) std::memcpy(&H[j.o_outs + 16 * i], j.outs[i].w, 16);
         for (size_t i = 0; i < j.ins.size(); ++i) std::memcpy(&H[j.o_ins + 16 * i], j.ins[i].w, 16);
+        // c_in times the hoisted constant, rounded once from extended precision
+        const std::complex<long double> sc((long double)j.scale.x, (long double)j.scale.y);
         for (size_t i = 0; i < j.coef.size(); ++i) {
-            const double2 v = make_double2(j.coef[i].real(), j.coef[i].imag());
+            const std::complex<long double> c =
+                std::complex<long double>((long double)j.coef[i].real(), (long double)j.coef[i].imag()) * sc;
+            const double2 v = make_double2((double)c.real(), (double)c.imag());
             std::memcpy(&H[j.o_coef + sizeof(double2) * i], &v, sizeof v);
         }
     }
@@ -1098,23 +1127,6 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         std::memcpy(&H[b->o_obegin], obegin.data(), nj * sizeof(uint64_t));
     }
     if (!b->tiles.empty()) std::memcpy(&H[b->o_tiles], b->tiles.data(), b->tiles.size() * sizeof(uint2));
-    if (b->opt.engine == 0 && !b->jit && nj) {
-        std::vector<fs::JitJobSpec> specs(nj);
-        for (size_t ji = 0; ji < nj; ++ji) {
-            const Job& j = b->jobs[ji];
-            specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
-                                       j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
-                                       j.sp.As, j.eps * j.eps, j.compact, j.levels};
-        }
-        std::string err, src;
-        const char* dump = getenv("FS_JIT_DUMP");   // optional: write the generated source here
-        const int jrc = fs::jit_build(specs, &b->jit, &err, &b->jit_ms, dump ? &src : nullptr);
-        if (dump) {
-            FILE* f = fopen(dump, "w");
-            if (f) { fwrite(src.data(), 1, src.size(), f); fclose(f); }
-        }
-        if (jrc) return fail(FS_ERR_CUDA, "straight-line engine: %s", err.c_str());
-    }
     if (b->static_bytes)
         CUDA_TRY(cudaMemcpyAsync(d_ws, H, b->static_bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
     if (pinned) {
@@ -1365,7 +1377,10 @@ static bool same2(double2 a, double2 b) { return a.x == b.x && a.y == b.y; }
 // deferred: the straight-line engine in exact mode, where two-valued factors
 // are counted per class (1 integer add) and applied once per region (one
 // complex product per class).
-static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused)
+// hoisted: the straight-line root and suffix, where a class whose factors
+// differ by a unit phase is applied as sign flips and swaps (integer pipe).
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused,
+                        bool hoisted)
 {
     const int W = j.W;
     std::vector<std::pair<double2, double2>> classes;
@@ -1439,7 +1454,13 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
         default: break;
         }
     }
-    fops += 4.0 * classes.size();
+    for (const auto& c : classes) {
+        const double2 A = c.first, B = c.second;
+        const bool unit = (B.x == A.x && B.y == A.y) || (B.x == -A.x && B.y == -A.y) ||
+                          (B.x == -A.y && B.y == A.x) || (B.x == A.y && B.y == -A.x);
+        if (hoisted && unit) iops += 3;   // select and sign flips
+        else fops += 4;                   // one complex product per region
+    }
 }
 
 int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, double* fp64_ops)
@@ -1454,7 +1475,7 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
     const bool fused = b->opt.engine == 0;   // the straight-line engine fuses incrementer cascades
     for (int r = 0; r < 3; ++r) {
         double i = 0, f = 0;
-        region_work(j, cuts[r], cuts[r + 1], i, f, deferred, fused);
+        region_work(j, cuts[r], cuts[r + 1], i, f, deferred, fused, r > 0 && deferred);
         int_ops[r] = i;
         fp64_ops[r] = f;
     }

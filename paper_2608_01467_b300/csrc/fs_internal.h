@@ -112,7 +112,8 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     double2* esum;             /* subtree sums of live items: per 32 (A_r >= 5) or per item */ \
     uint32_t* blk;             /* per compaction block: live count, then offset */       \
     uint64_t* prange;          /* per pair: [lo, hi) of its live entries */              \
-    uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */
+    uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */                   \
+    double2 scale;             /* constant factor hoisted out of the root and suffix */
 
 struct JobDev {
     FS_JOBDEV_FIELDS
@@ -194,8 +195,10 @@ struct JitJobSpec {
     bool compact;
     std::vector<PrefixLevel> levels;   // empty: single-region prefix
 };
+// scales (per job): the constant factor the generated root and suffix
+// leave out of every history (applied through the input coefficients).
 int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
-              std::string* source_out);
+              std::string* source_out, std::vector<double2>* scales);
 cudaError_t jit_launch_history(void* handle, const JobDev* d_jobs, const uint2* d_tiles, uint64_t n_tiles,
                                unsigned int* d_counter, cudaStream_t s);
 cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,

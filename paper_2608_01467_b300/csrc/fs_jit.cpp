@@ -60,6 +60,13 @@ __device__ __forceinline__ double dneg(double x)
     return __hiloint2double(__double2hiint(x) ^ 0x80000000, __double2loint(x));
 }
 __device__ __forceinline__ double2 cneg(double2 a) { return make_double2(dneg(a.x), dneg(a.y)); }
+// a * i^r (r in 0..3): swaps and sign flips on the integer pipe, exact
+__device__ __forceinline__ double2 qrot(double2 a, u32 r)
+{
+    const double x = (r & 1u) ? a.y : a.x, y = (r & 1u) ? a.x : a.y;
+    const bool nx = r == 1u || r == 2u, ny = r >= 2u;
+    return make_double2(nx ? dneg(x) : x, ny ? dneg(y) : y);
+}
 __device__ __forceinline__ double2 cre(double2 a, double r) { return make_double2(__dmul_rn(a.x, r), __dmul_rn(a.y, r)); }
 __device__ __forceinline__ double2 cim(double2 a, double s) { return make_double2(dneg(__dmul_rn(a.y, s)), __dmul_rn(a.x, s)); }
 __device__ __forceinline__ bool cut(double2 a, double eps2) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)) < eps2; }
@@ -72,102 +79,164 @@ __device__ __forceinline__ u64 warp_sum_u64(u64 v)
     return v;
 }
 
+// (output, input) of a pair index, pair = o * S + s, without the 64-bit
+// division routine (it runs through the scarce FP64 pipe): S = 1, or
+// 32-bit division for pair indices below 2^32.
+__device__ __forceinline__ u64 pair_split(u64 pair, u32 S, u64& s)
+{
+    if (S == 1u) { s = 0; return pair; }
+    if (pair < (1ull << 32)) {
+        const u32 p = (u32)pair, o = p / S;
+        s = p - o * S;
+        return o;
+    }
+    const u64 o = pair / S;
+    s = pair - o * S;
+    return o;
+}
+
+// Sum of acc over each aligned group of seg lanes (seg a power of two, at
+// most 32), valid in every lane of the group.  FP64 instructions cost the
+// same for every lane on this part, and most histories' sums are exactly
+// zero, so zero values (+-0, tested on the bits) are skipped: when no group
+// holds more than four nonzero values they are added one by one in lane
+// order, otherwise the xor butterfly runs.  The order depends only on which
+// values are zero, so results are run-to-run identical.
+__device__ __forceinline__ double2 group_sum(double2 acc, int seg)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool nz = ((((unsigned long long)__double_as_longlong(acc.x)) |
+                      ((unsigned long long)__double_as_longlong(acc.y))) << 1) != 0ull;
+    const unsigned m = __ballot_sync(full, nz);
+    if (m == 0u) return make_double2(0.0, 0.0);
+    const unsigned gmask = seg >= 32 ? full : (((1u << seg) - 1u) << (lane & ~(seg - 1)));
+    unsigned rem = m & gmask;
+    const int cnt = __popc(rem);
+    const int maxcnt = (int)__reduce_max_sync(full, (unsigned)cnt);
+    if (maxcnt <= 4) {
+        double2 r = make_double2(0.0, 0.0);
+        for (int it = 0; it < maxcnt; ++it) {
+            const int src = rem ? __ffs(rem) - 1 : lane;
+            rem &= rem - 1u;
+            const double vx = __shfl_sync(full, acc.x, src), vy = __shfl_sync(full, acc.y, src);
+            if (it == 0) {
+                r = make_double2(vx, vy);
+            } else if (it < cnt) {
+                r.x += vx;
+                r.y += vy;
+            }
+        }
+        return cnt ? r : make_double2(0.0, 0.0);
+    }
+    for (int off = seg >> 1; off >= 1; off >>= 1) {
+        acc.x += __shfl_xor_sync(full, acc.x, off);
+        acc.y += __shfl_xor_sync(full, acc.y, off);
+    }
+    return acc;
+}
+
+// bottom entries carry a NaN real part; tested on the bits (integer pipe)
+__device__ __forceinline__ bool is_bottom(double x)
+{
+    return ((u64)__double_as_longlong(x) << 1) > 0xffe0000000000000ull;
+}
+
+// Sum over the valid leaves of one (prefix, root) item: the root once, the
+// suffix for every h_s (skipping cut subtrees), the chi test at the input.
 template <class T>
-__device__ void tile_body(const JobDev& J, u64 tile, double2* s_warp)
+__device__ __forceinline__ double2 item_sum(const JobDev& J, u64 item, u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
-    const u64 item = tile * TILE + threadIdx.x;
-    const u64 n_items = J.n_pairs << J.log2_ipp;
-    const bool active = item < n_items;
     double2 acc = make_double2(0.0, 0.0);
-    u64 completed = 0, valid = 0, visits = 0;
-    u64 pair = 0;
-    if (active) {
-        pair = item >> J.log2_ipp;
-        const u64 local = item & ((1ull << J.log2_ipp) - 1ull);
-        const u64 hp = local >> T::Ar;
-        const u64 hr = local & ((1ull << T::Ar) - 1ull);
-        const u64 o = pair / (u64)J.S;
-        const u64 s = pair - o * (u64)J.S;
-        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
-        const uint4 sv = __ldg(ent);
-        const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
-        if (!isnan(a0.x)) {
-            u32 st[W], bin[W];
-            const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
-            const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * s));
-            const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+    const u64 pair = item >> J.log2_ipp;
+    const u64 local = item & ((1ull << J.log2_ipp) - 1ull);
+    const u64 hp = local >> T::Ar;
+    const u64 hr = local & ((1ull << T::Ar) - 1ull);
+    u64 s;
+    const u64 o = pair_split(pair, (u32)J.S, s);
+    (void)o;
+    const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
+    const uint4 sv = __ldg(ent);
+    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    if (is_bottom(a0.x)) return acc;
+    u32 st[W], bin[W];
+    const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+    const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * s));
+    const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-            for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
-            double2 amp = a0;
-            if (T::root(st, amp, hr, bin, visits) < 0) {
-                const u64 ns = 1ull << T::As;
-                u64 hs = 0;
-                while (hs < ns) {
-                    u32 st2[W];
+    for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
+    double2 amp = a0;
+    if (T::root(st, amp, hr, bin, visits) < 0) {
+        const u64 ns = 1ull << T::As;
+        u64 hs = 0;
+        while (hs < ns) {
+            u32 st2[W];
 #pragma unroll
-                    for (int j = 0; j < W; ++j) st2[j] = st[j];
-                    double2 amp2 = amp;
-                    const int r2 = T::suffix(st2, amp2, hs, bin, visits);
-                    if (r2 < 0) {
-                        ++completed;
-                        u32 d = 0;
+            for (int j = 0; j < W; ++j) st2[j] = st[j];
+            double2 amp2 = amp;
+            const int r2 = T::suffix(st2, amp2, hs, bin, visits);
+            if (r2 < 0) {
+                ++completed;
+                u32 d = 0;
 #pragma unroll
-                        for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
-                        if (d == 0) {
-                            ++valid;
-                            acc.x += amp2.x;
-                            acc.y += amp2.y;
-                        }
-                        ++hs;
-                    } else {
-                        hs = ((hs >> r2) + 1ull) << r2;
-                    }
+                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
+                if (d == 0) {
+                    ++valid;
+                    acc.x += amp2.x;
+                    acc.y += amp2.y;
                 }
+                ++hs;
+            } else {
+                hs = ((hs >> r2) + 1ull) << r2;
             }
         }
     }
-    if (J.log && active) J.log[item] = acc;
+    return acc;
+}
+
+// One 256-item tile on one warp: lane L takes items 8L .. 8L+7 in order and
+// sums them per pair segment; segments of at least 8 items are then added
+// across lanes (group_sum) into one partial per (pair, 256-item block).  No
+// block-wide barrier: warps run their tiles independently.
+template <class T>
+__device__ void tile_body(const JobDev& J, u64 tile)
+{
+    const int lane = threadIdx.x & 31;
+    const u64 n_items = J.n_pairs << J.log2_ipp;
+    const int lg = J.log2_ipp;
+    const u64 first = tile * TILE + (u64)lane * 8u;
+    u64 completed = 0, valid = 0, visits = 0;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const u64 item = first + (u64)k;
+        if (item >= n_items) break;
+        const double2 v = item_sum<T>(J, item, completed, valid, visits);
+        if (J.log) J.log[item] = cmul(J.scale, v);
+        acc.x += v.x;
+        acc.y += v.y;
+        if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
+            J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
+            acc = make_double2(0.0, 0.0);
+        }
+    }
+    if (lg >= 3) {
+        const int lps = lg >= 8 ? 32 : (1 << (lg - 3));   // lanes per pair segment
+        acc = group_sum(acc, lps);
+        if ((lane & (lps - 1)) == 0 && first < n_items) {
+            const u64 p = first >> lg;
+            const u64 l = first & ((1ull << lg) - 1ull);
+            J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = acc;
+        }
+    }
     completed = warp_sum_u64(completed);
     valid = warp_sum_u64(valid);
     visits = warp_sum_u64(visits);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0 && (completed | valid | visits)) {
         atomicAdd(&J.stats[0], completed);
         atomicAdd(&J.stats[1], valid);
         atomicAdd(&J.stats[2], visits);
-    }
-    const int seg_log2 = J.log2_ipp < TILE_LOG2 ? J.log2_ipp : TILE_LOG2;
-    if (seg_log2 < 5) {
-        const int seg = 1 << seg_log2;
-        for (int off = seg >> 1; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
-        if (active && (lane & (seg - 1)) == 0) J.partials[pair] = acc;
-    } else {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
-        if (lane == 0) s_warp[warp] = acc;
-        __syncthreads();
-        const int wps = 1 << (seg_log2 - 5);
-        const int nseg = TILE >> seg_log2;
-        if ((int)threadIdx.x < nseg) {
-            const u64 first = tile * TILE + (u64)threadIdx.x * (1ull << seg_log2);
-            if (first < n_items) {
-                double2 t = s_warp[threadIdx.x * wps];
-                for (int k = 1; k < wps; ++k) {
-                    t.x += s_warp[threadIdx.x * wps + k].x;
-                    t.y += s_warp[threadIdx.x * wps + k].y;
-                }
-                const u64 p = first >> J.log2_ipp;
-                const u64 l = first & ((1ull << J.log2_ipp) - 1ull);
-                J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = t;
-            }
-        }
     }
 }
 
@@ -178,8 +247,8 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
     const u64 e = J.live[i >> T::Ar];
     const u64 hr = i & ((1ull << T::Ar) - 1ull);
     const u64 pair = e >> T::Ap;
-    const u64 o = pair / (u64)J.S;
-    const u64 sidx = pair - o * (u64)J.S;
+    u64 sidx;
+    const u64 o = pair_split(pair, (u32)J.S, sidx);
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
     double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
@@ -219,16 +288,12 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
 }
 
 // Subtree sums of 32 consecutive items (one warp).  With A_r >= 5 they share
-// a live entry and are added by a fixed butterfly into one partial per warp
+// a live entry and are added (group_sum) into one partial per warp
 // (esum[i / 32]); otherwise each item keeps its own (esum[i]).
 __device__ __forceinline__ void store_esum(const JobDev& J, u64 i, double2 acc, bool active)
 {
     if (J.Ar >= 5) {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
+        acc = group_sum(acc, 32);
         if ((threadIdx.x & 31) == 0 && active) J.esum[i >> 5] = acc;
     } else if (active) {
         J.esum[i] = acc;
@@ -243,8 +308,8 @@ __device__ __forceinline__ bool lv_load(const JobDev& J, int a_prev, int a_next,
     constexpr int W = T::W;
     const u64 pair = idx >> a_next;
     const u64 child = idx & ((1ull << a_next) - 1ull);
-    const u64 o = pair / (u64)J.S;
-    const u64 sidx = pair - o * (u64)J.S;
+    u64 sidx;
+    const u64 o = pair_split(pair, (u32)J.S, sidx);
     const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
     const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
     uint4 sv;
@@ -259,7 +324,7 @@ __device__ __forceinline__ bool lv_load(const JobDev& J, int a_prev, int a_next,
     const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
-    return !isnan(amp.x);
+    return !is_bottom(amp.x);
 }
 
 template <class T>
@@ -290,8 +355,8 @@ __device__ __forceinline__ void prefix_body(const JobDev& J, u64 local, u64& vis
     constexpr int W = T::W;
     const u64 pair = local >> T::Ap;
     const u64 hp = local & ((1ull << T::Ap) - 1ull);
-    const u64 o = pair / (u64)J.S;
-    const u64 sidx = pair - o * (u64)J.S;
+    u64 sidx;
+    const u64 o = pair_split(pair, (u32)J.S, sidx);
     const uint4 ov = __ldg(reinterpret_cast<const uint4*>(J.outs + 4 * o));
     const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
     const u32 otmp[4] = {ov.x, ov.y, ov.z, ov.w};
@@ -444,9 +509,16 @@ std::string emit_cascade(const CascadeRun& r, int W)
     return "if (" + match_expr(m, W) + ") " + c;
 }
 
-// Body of one region: ops [e0, e1).  nbits = the region's h width.// Body of one region: ops [e0, e1).  nbits = the region's h width.
+// Body of one region: ops [e0, e1).  nbits = the region's h width.
+// chi_only: the region ends at the input boundary (the suffix); the deferred
+// class products are then applied only when the final state passes the chi
+// test, since only valid leaves are summed.
+// hoist (root and suffix regions): a class whose two factors differ by a
+// unit phase (B = A, -A, iA or -iA) is applied as that phase to the k-th
+// power (sign flips and swaps on the integer pipe) and its constant A^n is
+// multiplied into *hoist, to be applied once per (output, input) pair.
 void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
-                 int e0, int e1, int nbits)
+                 int e0, int e1, int nbits, bool chi_only = false, std::complex<long double>* hoist = nullptr)
 {
     const int W = J.W;
     const bool defer = J.eps2 == 0.0;
@@ -588,15 +660,42 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
     out += "    int low = " + std::to_string(nbits) + ";\n";
     for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
     out += body;
-    for (size_t k = 0; k < cls.size(); ++k) {
-        const std::string name = "T_" + tag + "_" + std::to_string(k);
-        emit_class_table(globals, name, cls[k]);
-        out += "    a = cmul(a, __ldg(&" + name + "[k" + std::to_string(k) + "]));\n";
+    if (chi_only && !cls.empty()) {
+        out += "    u32 dchi = 0u;\n";
+        for (int j = 0; j < W; ++j) out += "    dchi |= s[" + std::to_string(j) + "] ^ bin[" + std::to_string(j) + "];\n";
+        out += "    if (dchi == 0u) {\n";
     }
+    for (size_t k = 0; k < cls.size(); ++k) {
+        const FactorClass& f = cls[k];
+        const std::string kv = "k" + std::to_string(k);
+        if (hoist) {
+            using cl = std::complex<long double>;
+            const double2 A = f.A, B = f.B;
+            int kind = -1;   // 0: B = A, 1: B = -A, 2: B = iA, 3: B = -iA
+            if (B.x == A.x && B.y == A.y) kind = 0;
+            else if (B.x == -A.x && B.y == -A.y) kind = 1;
+            else if (B.x == -A.y && B.y == A.x) kind = 2;
+            else if (B.x == A.y && B.y == -A.x) kind = 3;
+            if (kind >= 0) {
+                cl An(1.0L, 0.0L);
+                const cl Al((long double)A.x, (long double)A.y);
+                for (int i = 0; i < f.n; ++i) An *= Al;
+                *hoist *= An;
+                if (kind == 1) out += "    if (" + kv + " & 1u) a = cneg(a);\n";
+                else if (kind == 2) out += "    a = qrot(a, " + kv + " & 3u);\n";
+                else if (kind == 3) out += "    a = qrot(a, (4u - (" + kv + " & 3u)) & 3u);\n";
+                continue;
+            }
+        }
+        const std::string name = "T_" + tag + "_" + std::to_string(k);
+        emit_class_table(globals, name, f);
+        out += "    a = cmul(a, __ldg(&" + name + "[" + kv + "]));\n";
+    }
+    if (chi_only && !cls.empty()) out += "    }\n";
     out += "    visits += " + std::to_string(e1 - e0) + "ull;\n    (void)low;\n    return -1;\n";
 }
 
-std::string generate(const std::vector<JitJobSpec>& jobs)
+std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* scales)
 {
     std::string src = kPrelude;
     std::string globals, structs;
@@ -617,26 +716,29 @@ std::string generate(const std::vector<JitJobSpec>& jobs)
             structs += "  }\n";
         }
         structs += "  static __device__ __forceinline__ int root" + sig + " {\n    (void)h; (void)bin;\n";
-        emit_region(structs, globals, js + "r", J, J.c1, J.c2, J.Ar);
+        std::complex<long double> hoisted(1.0L, 0.0L);
+        emit_region(structs, globals, js + "r", J, J.c1, J.c2, J.Ar, false, &hoisted);
         structs += "  }\n";
         structs += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
-        emit_region(structs, globals, js + "s", J, J.c2, J.G, J.As);
+        emit_region(structs, globals, js + "s", J, J.c2, J.G, J.As, true, &hoisted);
+        if (scales) (*scales)[j] = make_double2((double)hoisted.real(), (double)hoisted.imag());
         structs += "  }\n};\n";
     }
     src += globals;
     src += structs;
+    // persistent warps pull tiles off the queue; the next index is fetched
+    // while the current tile runs
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_history(const JobDev* __restrict__ jobs, "
            "const uint2* __restrict__ tiles, u64 n_tiles, unsigned int* counter)\n{\n"
-           "    __shared__ unsigned int s_tile;\n    __shared__ double2 s_warp[8];\n"
-           "    for (;;) {\n"
-           "        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);\n"
-           "        __syncthreads();\n        const unsigned int t = s_tile;\n        __syncthreads();\n"
-           "        if ((u64)t >= n_tiles) break;\n        const uint2 td = tiles[t];\n"
+           "    const int lane = threadIdx.x & 31;\n    unsigned int t = 0u, next = 0u;\n"
+           "    if (lane == 0) t = atomicAdd(counter, 1u);\n    t = __shfl_sync(0xffffffffu, t, 0);\n"
+           "    while ((u64)t < n_tiles) {\n"
+           "        if (lane == 0) next = atomicAdd(counter, 1u);\n        const uint2 td = tiles[t];\n"
            "        switch (td.x) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
         src += "        case " + std::to_string(j) + "u: tile_body<J" + std::to_string(j) + ">(jobs[" +
-               std::to_string(j) + "], td.y, s_warp); break;\n";
-    src += "        default: break;\n        }\n    }\n}\n";
+               std::to_string(j) + "], td.y); break;\n";
+    src += "        default: break;\n        }\n        t = __shfl_sync(0xffffffffu, next, 0);\n    }\n}\n";
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job)\n{\n"
            "    const JobDev& J = jobs[job];\n    const u64 nlive = J.stats[6] << J.Ar;\n    const int lane = threadIdx.x & 31;\n"
            "    u64 completed = 0, valid = 0, visits = 0;\n    for (;;) {\n"
@@ -710,10 +812,11 @@ struct JitModule {
 }  // namespace
 
 int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
-              std::string* source_out)
+              std::string* source_out, std::vector<double2>* scales)
 {
     const auto t0 = std::chrono::steady_clock::now();
-    const std::string src = generate(jobs);
+    if (scales) scales->assign(jobs.size(), make_double2(1.0, 0.0));
+    const std::string src = generate(jobs, scales);
     if (source_out) *source_out = src;
     if (compile_ms) *compile_ms = 0;
     nvrtcProgram prog;

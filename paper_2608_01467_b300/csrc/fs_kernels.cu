@@ -42,6 +42,71 @@ __device__ __forceinline__ double2 ldf(const double2* p)
     return __ldg(p);
 }
 
+// (output, input) of a pair index: pair = o * S + s.  64-bit integer
+// division runs through the FP64 pipe, which is scarce on this part, so the
+// common cases avoid it: S = 1, and pair indices below 2^32 (32-bit
+// division).
+__device__ __forceinline__ uint64_t pair_split(uint64_t pair, uint32_t S, uint64_t& s)
+{
+    if (S == 1u) { s = 0; return pair; }
+    if (pair < (1ull << 32)) {
+        const uint32_t p = (uint32_t)pair, o = p / S;
+        s = p - o * S;
+        return o;
+    }
+    const uint64_t o = pair / S;
+    s = pair - o * S;
+    return o;
+}
+
+// Sum of acc over each aligned group of seg lanes (seg a power of two, at
+// most 32), valid in every lane of the group.  FP64 instructions cost the
+// same for every lane on this part, and most histories' sums are exactly
+// zero, so zero values (+-0, tested on the bits) are skipped: when no group
+// holds more than four nonzero values they are added one by one in lane
+// order, otherwise the xor butterfly runs.  The order depends only on which
+// values are zero, so results are run-to-run identical.
+__device__ __forceinline__ double2 group_sum(double2 acc, int seg)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool nz = ((((unsigned long long)__double_as_longlong(acc.x)) |
+                      ((unsigned long long)__double_as_longlong(acc.y))) << 1) != 0ull;
+    const unsigned m = __ballot_sync(full, nz);
+    if (m == 0u) return make_double2(0.0, 0.0);
+    const unsigned gmask = seg >= 32 ? full : (((1u << seg) - 1u) << (lane & ~(seg - 1)));
+    unsigned rem = m & gmask;
+    const int cnt = __popc(rem);
+    const int maxcnt = (int)__reduce_max_sync(full, (unsigned)cnt);
+    if (maxcnt <= 4) {
+        double2 r = make_double2(0.0, 0.0);
+        for (int it = 0; it < maxcnt; ++it) {
+            const int src = rem ? __ffs(rem) - 1 : lane;
+            rem &= rem - 1u;
+            const double vx = __shfl_sync(full, acc.x, src), vy = __shfl_sync(full, acc.y, src);
+            if (it == 0) {
+                r = make_double2(vx, vy);
+            } else if (it < cnt) {
+                r.x += vx;
+                r.y += vy;
+            }
+        }
+        return cnt ? r : make_double2(0.0, 0.0);
+    }
+    for (int off = seg >> 1; off >= 1; off >>= 1) {
+        acc.x += __shfl_xor_sync(full, acc.x, off);
+        acc.y += __shfl_xor_sync(full, acc.y, off);
+    }
+    return acc;
+}
+
+// A bottom entry (its prefix met an exactly zero factor) carries a NaN real
+// part; tested on the bits (a double compare would use the FP64 pipe).
+__device__ __forceinline__ bool is_bottom(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) << 1) > 0xffe0000000000000ull;
+}
+
 template <int W>
 __device__ __forceinline__ uint32_t word_of(const uint32_t (&st)[W], uint32_t q)
 {
@@ -240,8 +305,8 @@ __device__ void prefix_one(const JobDev& J, uint64_t local, uint32_t* err,
 {
     const uint64_t pair = local >> J.Ap;
     const uint64_t hp = local & ((1ull << J.Ap) - 1ull);
-    const uint64_t o = pair / (uint64_t)J.S;
-    const uint64_t s = pair - o * (uint64_t)J.S;
+    uint64_t s;
+    const uint64_t o = pair_split(pair, (uint32_t)J.S, s);
     uint32_t st[W], bin[W];
     load_bits<W>(J.outs + 4 * o, st);
     load_bits<W>(J.ins + 4 * s, bin);
@@ -302,8 +367,8 @@ __device__ void prefix_level_one(const JobDev& J, const PrefixLevel& L, const En
 {
     const uint64_t pair = idx >> L.a_next;
     const uint64_t child = idx & ((1ull << L.a_next) - 1ull);
-    const uint64_t o = pair / (uint64_t)J.S;
-    const uint64_t s = pair - o * (uint64_t)J.S;
+    uint64_t s;
+    const uint64_t o = pair_split(pair, (uint32_t)J.S, s);
     uint32_t st[W], bin[W];
     load_bits<W>(J.ins + 4 * s, bin);
     double2 amp = make_double2(1.0, 0.0);
@@ -318,7 +383,7 @@ __device__ void prefix_level_one(const JobDev& J, const PrefixLevel& L, const En
         const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
         for (int j = 0; j < W; ++j) st[j] = tmp[j];
-        live = !isnan(amp.x);
+        live = !is_bottom(amp.x);
     }
     if (live) {
         const uint64_t h = child << (J.Ap - L.a_next);
@@ -355,120 +420,118 @@ __global__ void __launch_bounds__(256) prefix_level_kernel(const JobDev* __restr
 
 // ---------------------------------------------------------------- history
 
+// Sum over the valid leaves of one (prefix, root) item: the root once, the
+// suffix for every h_s (skipping cut subtrees), the chi test at the input.
 template <int W>
-__device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err, double2* s_warp)
+__device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, unsigned long long& completed,
+                                unsigned long long& valid, unsigned long long& visits)
 {
-    const uint64_t item = tile * TILE + threadIdx.x;
-    const uint64_t n_items = J.n_pairs << J.log2_ipp;
-    const bool active = item < n_items;
     double2 acc = make_double2(0.0, 0.0);
-    unsigned long long completed = 0, valid = 0, visits = 0;
-    uint64_t pair = 0, local = 0;
-    if (active) {
-        pair = item >> J.log2_ipp;
-        local = item & ((1ull << J.log2_ipp) - 1ull);
-        const uint64_t hp = local >> J.Ar;
-        const uint64_t hr = local & ((1ull << J.Ar) - 1ull);
-        const uint64_t o = pair / (uint64_t)J.S;
-        const uint64_t s = pair - o * (uint64_t)J.S;
-        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << J.Ap) + hp);
-        const uint4 sv = __ldg(ent);
-        const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
-        if (!isnan(a0.x)) {
-            uint32_t st[W], bin[W];
-            const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+    const uint64_t pair = item >> J.log2_ipp;
+    const uint64_t local = item & ((1ull << J.log2_ipp) - 1ull);
+    const uint64_t hp = local >> J.Ar;
+    const uint64_t hr = local & ((1ull << J.Ar) - 1ull);
+    uint64_t s;
+    pair_split(pair, (uint32_t)J.S, s);
+    const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << J.Ap) + hp);
+    const uint4 sv = __ldg(ent);
+    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    if (is_bottom(a0.x)) return acc;
+    uint32_t st[W], bin[W];
+    const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
-            for (int j = 0; j < W; ++j) st[j] = tmp[j];
-            load_bits<W>(J.ins + 4 * s, bin);
-            double2 amp = a0;
-            const int r = run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err);
-            if (r < 0) {
-                const uint64_t ns = 1ull << J.As;
-                uint64_t hs = 0;
-                while (hs < ns) {
-                    uint32_t st2[W];
+    for (int j = 0; j < W; ++j) st[j] = tmp[j];
+    load_bits<W>(J.ins + 4 * s, bin);
+    double2 amp = a0;
+    if (run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err) < 0) {
+        const uint64_t ns = 1ull << J.As;
+        uint64_t hs = 0;
+        while (hs < ns) {
+            uint32_t st2[W];
 #pragma unroll
-                    for (int j = 0; j < W; ++j) st2[j] = st[j];
-                    double2 amp2 = amp;
-                    const int r2 = run_ops<W>(J, J.c2, J.G, st2, amp2, hs, J.As, bin, visits, err);
-                    if (r2 < 0) {
-                        ++completed;
-                        if (same<W>(st2, bin)) {
-                            ++valid;
-                            acc.x += amp2.x;
-                            acc.y += amp2.y;
-                        }
-                        ++hs;
-                    } else {
-                        hs = ((hs >> r2) + 1ull) << r2;
-                    }
+            for (int j = 0; j < W; ++j) st2[j] = st[j];
+            double2 amp2 = amp;
+            const int r2 = run_ops<W>(J, J.c2, J.G, st2, amp2, hs, J.As, bin, visits, err);
+            if (r2 < 0) {
+                ++completed;
+                if (same<W>(st2, bin)) {
+                    ++valid;
+                    acc.x += amp2.x;
+                    acc.y += amp2.y;
                 }
+                ++hs;
+            } else {
+                hs = ((hs >> r2) + 1ull) << r2;
             }
         }
     }
-    if (J.log && active) J.log[item] = acc;
-    // counters: one atomic per warp
+    return acc;
+}
+
+// One 256-item tile on one warp: lane L takes items 8L .. 8L+7 in order and
+// sums them per pair segment; segments of at least 8 items are then added
+// across lanes (group_sum) into one partial per (pair, 256-item block).  The
+// same order as the generated engine, so the two agree bit for bit whenever
+// both multiply the same factors.
+template <int W>
+__device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t n_items = J.n_pairs << J.log2_ipp;
+    const int lg = J.log2_ipp;
+    const uint64_t first = tile * TILE + (uint64_t)lane * 8u;
+    unsigned long long completed = 0, valid = 0, visits = 0;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const uint64_t item = first + (uint64_t)k;
+        if (item >= n_items) break;
+        const double2 v = history_item<W>(J, item, err, completed, valid, visits);
+        if (J.log) J.log[item] = cmul(J.scale, v);
+        acc.x += v.x;
+        acc.y += v.y;
+        if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
+            J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
+            acc = make_double2(0.0, 0.0);
+        }
+    }
+    if (lg >= 3) {
+        const int lps = lg >= 8 ? 32 : (1 << (lg - 3));   // lanes per pair segment
+        acc = group_sum(acc, lps);
+        if ((lane & (lps - 1)) == 0 && first < n_items) {
+            const uint64_t p = first >> lg;
+            const uint64_t l = first & ((1ull << lg) - 1ull);
+            J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = acc;
+        }
+    }
     completed = warp_sum_u64(completed);
     valid = warp_sum_u64(valid);
     visits = warp_sum_u64(visits);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0 && (completed | valid | visits)) {
         atomicAdd(&J.stats[0], completed);
         atomicAdd(&J.stats[1], valid);
         atomicAdd(&J.stats[2], visits);
     }
-    // fixed-order segmented reduction: a segment is one pair's items in the tile
-    const int seg_log2 = J.log2_ipp < TILE_LOG2 ? J.log2_ipp : TILE_LOG2;
-    if (seg_log2 < 5) {
-        const int seg = 1 << seg_log2;
-        for (int off = seg >> 1; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
-        if (active && (lane & (seg - 1)) == 0) J.partials[pair] = acc;
-    } else {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
-        if (lane == 0) s_warp[warp] = acc;
-        __syncthreads();
-        const int wps = 1 << (seg_log2 - 5);          // warps per segment
-        const int nseg = TILE >> seg_log2;
-        if ((int)threadIdx.x < nseg) {
-            const uint64_t first = tile * TILE + (uint64_t)threadIdx.x * (1ull << seg_log2);
-            if (first < n_items) {
-                double2 t = s_warp[threadIdx.x * wps];
-                for (int k = 1; k < wps; ++k) {
-                    t.x += s_warp[threadIdx.x * wps + k].x;
-                    t.y += s_warp[threadIdx.x * wps + k].y;
-                }
-                const uint64_t p = first >> J.log2_ipp;
-                const uint64_t l = first & ((1ull << J.log2_ipp) - 1ull);
-                J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = t;
-            }
-        }
-    }
 }
 
+// Persistent warps pull 256-item tiles off the queue with one atomicAdd each
+// (the next index is fetched while the current tile runs).
 __global__ void __launch_bounds__(TILE) history_kernel(const JobDev* __restrict__ jobs,
                                                        const uint2* __restrict__ tiles, uint64_t n_tiles,
                                                        unsigned int* counter, uint32_t* err)
 {
-    __shared__ unsigned int s_tile;
-    __shared__ double2 s_warp[TILE / 32];
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
-        __syncthreads();
-        const unsigned int t = s_tile;
-        __syncthreads();
-        if ((uint64_t)t >= n_tiles) break;
+    const int lane = threadIdx.x & 31;
+    unsigned int t = 0u, next = 0u;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    while ((uint64_t)t < n_tiles) {
+        if (lane == 0) next = atomicAdd(counter, 1u);
         const uint2 td = tiles[t];
         const JobDev& J = jobs[td.x];
-        if (J.W == 1) history_tile<1>(J, td.y, err, s_warp);
-        else if (J.W == 2) history_tile<2>(J, td.y, err, s_warp);
-        else history_tile<4>(J, td.y, err, s_warp);
+        if (J.W == 1) history_tile<1>(J, td.y, err);
+        else if (J.W == 2) history_tile<2>(J, td.y, err);
+        else history_tile<4>(J, td.y, err);
+        t = __shfl_sync(0xffffffffu, next, 0);
     }
 }
 
@@ -478,7 +541,7 @@ __global__ void __launch_bounds__(TILE) history_kernel(const JobDev* __restrict_
 // order: count per block, exclusive scan of the block counts, write.
 __device__ __forceinline__ bool entry_live(const JobDev& J, uint64_t e)
 {
-    return !isnan(reinterpret_cast<const double2*>(reinterpret_cast<const uint4*>(J.table + e) + 1)->x);
+    return !is_bottom(reinterpret_cast<const double2*>(reinterpret_cast<const uint4*>(J.table + e) + 1)->x);
 }
 
 __global__ void __launch_bounds__(256) compact_count_kernel(const JobDev* __restrict__ jobp)
@@ -591,8 +654,8 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
     const uint64_t e = J.live[i >> J.Ar];
     const uint64_t hr = i & ((1ull << J.Ar) - 1ull);
     const uint64_t pair = e >> J.Ap;
-    const uint64_t o = pair / (uint64_t)J.S;
-    const uint64_t s = pair - o * (uint64_t)J.S;
+    uint64_t s;
+    const uint64_t o = pair_split(pair, (uint32_t)J.S, s);
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
     double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
@@ -628,16 +691,12 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
 }
 
 // Subtree sums of one warp's 32 consecutive items: with A_r >= 5 they share a
-// live entry and one fixed butterfly leaves one partial per warp (esum[i /
-// 32]); otherwise each item keeps its own (esum[i]).
+// live entry and group_sum leaves one partial per warp (esum[i / 32]);
+// otherwise each item keeps its own (esum[i]).
 __device__ __forceinline__ void store_esum(const JobDev& J, uint64_t i, double2 acc, bool active)
 {
     if (J.Ar >= 5) {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
+        acc = group_sum(acc, 32);
         if ((threadIdx.x & 31) == 0 && active) J.esum[i >> 5] = acc;
     } else if (active) {
         J.esum[i] = acc;
@@ -760,13 +819,15 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
         const int s_max = (int)__reduce_max_sync(0xffffffffu, small ? (unsigned)S : 0u);
         double2 amp = make_double2(0.0, 0.0);
         for (int s = 0; s < s_max; ++s) {
-            const bool act = small && s < S;
+            uint64_t lo = 0, hi = 0;
+            const double2* src = nullptr;
+            if (small && s < S) src = pair_items(J, o * (uint64_t)S + (uint64_t)s, lo, hi);
+            const bool act = hi > lo;   // pairs with no items add exactly zero
+            // FP64 instructions cost the same for every lane: skip them when
+            // no pair of this warp has items
+            if (!__any_sync(0xffffffffu, act)) continue;
             double2 t = make_double2(0.0, 0.0);
-            if (act) {
-                uint64_t lo, hi;
-                const double2* src = pair_items(J, o * (uint64_t)S + (uint64_t)s, lo, hi);
-                t = strided_sum(src, lo + (uint64_t)sub, hi, RED_LPO);
-            }
+            if (act) t = strided_sum(src, lo + (uint64_t)sub, hi, RED_LPO);
 #pragma unroll
             for (int off = RED_LPO / 2; off >= 1; off >>= 1) {
                 t.x += __shfl_xor_sync(0xffffffffu, t.x, off);

@@ -388,10 +388,21 @@ __device__ __forceinline__ void entry_features_of(const JobDev& J, const Entry& 
                                                   const FeatureSpec& sp, float* out)
 {
     const unsigned long long pair = local >> J.Ap;
-    const unsigned long long o = pair / (unsigned long long)J.S;
-    const unsigned long long sidx = pair - o * (unsigned long long)J.S;
+    unsigned long long sidx, o;
+    if (J.S == 1) {   // the 64-bit division routine would use the FP64 pipe
+        o = pair;
+        sidx = 0;
+    } else if (pair < (1ull << 32)) {
+        const uint32_t p32 = (uint32_t)pair, o32 = p32 / (uint32_t)J.S;
+        o = o32;
+        sidx = p32 - o32 * (uint32_t)J.S;
+    } else {
+        o = pair / (unsigned long long)J.S;
+        sidx = pair - o * (unsigned long long)J.S;
+    }
+    (void)o;
     const uint32_t* bin = J.ins + 4 * sidx;
-    if (isnan(e.amp.x)) {
+    if (((unsigned long long)__double_as_longlong(e.amp.x) << 1) > 0xffe0000000000000ull) {   // bottom (NaN)
         for (int k = 0; k < 16; ++k) out[k] = 0.f;
         out[0] = __int_as_float(0x7fc00000);
         return;
