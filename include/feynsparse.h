@@ -249,10 +249,11 @@ FS_API int fs_batch_engine(const fs_batch* b, uint32_t* engine, double* compile_
 /* Total outputs over the jobs added so far. */
 FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
 
-/* Number of kernel launches fs_batch_run enqueues (prefix, reduce, the tiled
- * history kernel when any job is exact, and per pruned job a learned-prune
- * launch if attached plus count/scan/write compaction, the per-pair live
- * ranges and the history over live entries). */
+/* Number of kernel launches fs_batch_run enqueues (prefix levels or the
+ * flat prefix, the two reduction kernels, the tiled history kernel when any
+ * job is exact, and per pruned job a learned-prune launch if attached plus
+ * count/scan/write compaction (the write also records each pair's live
+ * range) and the history over live entries). */
 FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
 
 /* Average duration of the history kernel of the last fs_batch_run that

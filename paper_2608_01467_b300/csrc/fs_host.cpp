@@ -1154,7 +1154,7 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         flat_prefix |= j.levels.empty();
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
-        if (j.compact) k += 5;                  // count, scan, write, pair ranges, history over live entries
+        if (j.compact) k += 4;                  // count, scan, write (with pair ranges), history over live entries
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
@@ -1253,7 +1253,6 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         if (!j.compact) continue;
-        CUDA_TRY(cudaMemsetAsync(base + j.o_prange, 0, 2 * j.pairs * sizeof(uint64_t), s));
         CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[1], s));

@@ -136,6 +136,21 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
+// acc += v inside a branch the compiler may not flatten: flattened, the add
+// would run on every lane with v replaced by zero, and FP64 instructions are
+// scarce on this part while most leaves are invalid and most items zero.
+__device__ __forceinline__ void add_kept(double2& acc, double2 v)
+{
+    asm volatile("" ::: "memory");
+    acc.x += v.x;
+    acc.y += v.y;
+}
+
+__device__ __forceinline__ bool nonzero(double2 v)
+{
+    return ((((unsigned long long)__double_as_longlong(v.x)) | ((unsigned long long)__double_as_longlong(v.y))) << 1) != 0ull;
+}
+
 // bottom entries carry a NaN real part; tested on the bits (integer pipe)
 __device__ __forceinline__ bool is_bottom(double x)
 {
@@ -183,8 +198,7 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 item, u64& comp
                 for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
                 if (d == 0) {
                     ++valid;
-                    acc.x += amp2.x;
-                    acc.y += amp2.y;
+                    add_kept(acc, amp2);
                 }
                 ++hs;
             } else {
@@ -214,8 +228,7 @@ __device__ void tile_body(const JobDev& J, u64 tile)
         if (item >= n_items) break;
         const double2 v = item_sum<T>(J, item, completed, valid, visits);
         if (J.log) J.log[item] = cmul(J.scale, v);
-        acc.x += v.x;
-        acc.y += v.y;
+        if (nonzero(v)) add_kept(acc, v);
         if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
             J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
             acc = make_double2(0.0, 0.0);
@@ -275,8 +288,7 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
                 for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
                 if (d == 0) {
                     ++valid;
-                    acc.x += amp2.x;
-                    acc.y += amp2.y;
+                    add_kept(acc, amp2);
                 }
                 ++hs;
             } else {

@@ -100,6 +100,21 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
+// acc += v inside a branch the compiler may not flatten: flattened, the add
+// would run on every lane with v replaced by zero, and FP64 instructions are
+// scarce on this part while most leaves are invalid and most items zero.
+__device__ __forceinline__ void add_kept(double2& acc, double2 v)
+{
+    asm volatile("" ::: "memory");
+    acc.x += v.x;
+    acc.y += v.y;
+}
+
+__device__ __forceinline__ bool nonzero(double2 v)
+{
+    return ((((unsigned long long)__double_as_longlong(v.x)) | ((unsigned long long)__double_as_longlong(v.y))) << 1) != 0ull;
+}
+
 // A bottom entry (its prefix met an exactly zero factor) carries a NaN real
 // part; tested on the bits (a double compare would use the FP64 pipe).
 __device__ __forceinline__ bool is_bottom(double x)
@@ -456,8 +471,7 @@ __device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, u
                 ++completed;
                 if (same<W>(st2, bin)) {
                     ++valid;
-                    acc.x += amp2.x;
-                    acc.y += amp2.y;
+                    add_kept(acc, amp2);
                 }
                 ++hs;
             } else {
@@ -488,8 +502,7 @@ __device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err)
         if (item >= n_items) break;
         const double2 v = history_item<W>(J, item, err, completed, valid, visits);
         if (J.log) J.log[item] = cmul(J.scale, v);
-        acc.x += v.x;
-        acc.y += v.y;
+        if (nonzero(v)) add_kept(acc, v);
         if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
             J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
             acc = make_double2(0.0, 0.0);
@@ -624,21 +637,19 @@ __global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __rest
     unsigned woff = 0;
     for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) woff += s_w[w];
     uint64_t pos = (uint64_t)J.blk[blockIdx.x] + woff + x - c;
+    // pos is the number of live entries before e: at the first entry of a
+    // pair it opens that pair's range and closes the previous one's
+    const uint64_t pmask = (1ull << J.Ap) - 1ull;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (lv[k]) J.live[pos++] = base + (uint64_t)threadIdx.x * 4 + k;
-}
-
-// Each pair's range [lo, hi) in the live list (zeroed beforehand: pairs
-// without live entries keep an empty range).
-__global__ void __launch_bounds__(256) pair_range_kernel(const JobDev* __restrict__ jobp)
-{
-    const JobDev& J = *jobp;
-    const uint64_t nlive = J.stats[6];
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlive; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t p = J.live[i] >> J.Ap;
-        if (i == 0 || (J.live[i - 1] >> J.Ap) != p) J.prange[2 * p] = i;
-        if (i + 1 == nlive || (J.live[i + 1] >> J.Ap) != p) J.prange[2 * p + 1] = i + 1;
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
+        if (e < J.n_entries && (e & pmask) == 0ull) {
+            const uint64_t p = e >> J.Ap;
+            J.prange[2 * p] = pos;
+            if (p) J.prange[2 * p - 1] = pos;
+        }
+        if (lv[k]) J.live[pos++] = e;
+        if (e + 1ull == J.n_entries) J.prange[2 * (e >> J.Ap) + 1] = pos;
     }
 }
 
@@ -678,8 +689,7 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
                 ++completed;
                 if (same<W>(st2, bin)) {
                     ++valid;
-                    acc.x += amp2.x;
-                    acc.y += amp2.y;
+                    add_kept(acc, amp2);
                 }
                 ++hs;
             } else {
@@ -783,7 +793,7 @@ __device__ __forceinline__ double2 strided_sum(const double2* __restrict__ src, 
 }
 
 constexpr int RED_LPO = 4;            // lanes per output in the common path
-constexpr uint64_t RED_SMALL = 1024;  // outputs with more items go to reduce_big_kernel
+constexpr uint64_t RED_SMALL = 64;    // outputs with more items go to reduce_big_kernel
 constexpr int RED_BIG_THREADS = 256;
 
 // FP64 is scarce on this part (about 2 FMA per clock per SM), so the
@@ -1008,9 +1018,6 @@ cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t
     compact_count_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
     compact_scan_kernel<<<1, 1024, 0, s>>>(d_job, (uint32_t)nblk);
     compact_write_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
-    uint64_t rblocks = (n_entries + 255) / 256;
-    if (rblocks > 148ull * 8) rblocks = 148ull * 8;
-    pair_range_kernel<<<(unsigned)rblocks, 256, 0, s>>>(d_job);
     return cudaGetLastError();
 }
 
