@@ -35,13 +35,15 @@ def workload_jobs(name, rank=0, outputs=None, seed_shift=0):
     # autotuned cuts
     walk_cuts = [(4, 8), (5, 7), (6, 6), (7, 6)]
     if name == "qw100":
-        n_out = qw_out if seed_shift == 0 else 512
+        # training request 512 outputs; validation the bench's size, so that
+        # the candidate cuts are timed at the size they will run at
+        n_out = 512 if seed_shift == 100 else qw_out
         w = qw_workload(n_out=n_out, seed=0x5EED0005 + rank + seed_shift)
         w.meta["learned_cut"] = walk_cuts
         return [w], {"workload": f"qw100_t16_{qw_out}out", "qubits": 100, "steps": 16,
                      "outputs": qw_out, "input_support": 2}
     if name == "qw100+qaoa16":
-        n_qw = qw_out if seed_shift == 0 else 512
+        n_qw = 512 if seed_shift == 100 else qw_out
         n_qa = 4 if seed_shift == 0 else 32
         ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift),
               qaoa_workload(16, 2, n_out=n_qa, seed=0x5EED0003 + rank + seed_shift)]
@@ -275,7 +277,7 @@ def train_pruner(fs, args, w_train, w_val, dev, stream, plain_stats):
             continue
         tau, F, bl = chosen
         ms = []
-        for _ in range(5):
+        for _ in range(10):
             e0, e1 = torch_event(), torch_event()
             e0.record(stream)
             bl.run(stream)

@@ -1087,6 +1087,17 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.Ap = j.sp.Ap; d.Ar = j.sp.Ar; d.As = j.sp.As;
         d.W = j.W;
         d.S = (int32_t)j.ins.size();
+        // division by S on the device: l = ceil(log2 S), multiplier
+        // floor(2^32 (2^l - S) / S) + 1 (Granlund and Montgomery 1994, Fig. 4.1)
+        d.s_shift = 0;
+        d.s_magic = 0;
+        if (j.ins.size() >= 2) {
+            const uint64_t S = j.ins.size();
+            int l = 0;
+            while ((1ull << l) < S) ++l;
+            d.s_shift = l;
+            d.s_magic = (uint32_t)((((1ull << l) - S) << 32) / S + 1ull);
+        }
         d.M = (int32_t)j.outs.size();
         d.log2_ipp = j.log2_ipp;
         d.log2_spp = j.log2_spp;

@@ -99,7 +99,7 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     int32_t M;                                                                \
     int32_t log2_ipp;          /* Ap + Ar */                                  \
     int32_t log2_spp;          /* max(0, log2_ipp - TILE_LOG2) */             \
-    int32_t pad0;                                                             \
+    uint32_t s_magic;          /* division by S: multiplier (see fs_host.cpp) */ \
     uint64_t n_pairs;          /* S * M */                                    \
     uint64_t prefix_begin;     /* offset of this job in the flat prefix index space */ \
     uint64_t out_begin;        /* offset of this job's outputs in amp_out */ \
@@ -107,7 +107,7 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     double eps2;               /* eps^2 (0: exact) */                         \
     double2* log;              /* optional: per-item subtree sums (logging runs) */     \
     int32_t compact;           /* 1: history over the compacted live entries */         \
-    int32_t pad1;                                                             \
+    int32_t s_shift;           /* division by S: ceil(log2 S) */                 \
     uint64_t* live;            /* compacted live entry indices, table order */            \
     double2* esum;             /* subtree sums of live items: per 32 (A_r >= 5) or per item */ \
     uint32_t* blk;             /* per compaction block: live count, then offset */       \

@@ -79,20 +79,31 @@ __device__ __forceinline__ u64 warp_sum_u64(u64 v)
     return v;
 }
 
-// (output, input) of a pair index, pair = o * S + s, without the 64-bit
-// division routine (it runs through the scarce FP64 pipe): S = 1, or
-// 32-bit division for pair indices below 2^32.
-__device__ __forceinline__ u64 pair_split(u64 pair, u32 S, u64& s)
+// (output, input) of a pair index, pair = o * S + s.  Integer division by a
+// runtime value goes through the scarce FP64 pipe on this part, so the
+// quotient comes from the job's precomputed multiplier (division by an
+// invariant integer, Granlund and Montgomery 1994, Fig. 4.1) for pair
+// indices below 2^32.
+__device__ __forceinline__ u64 pair_split(u64 pair, const JobDev& J, u64& s)
 {
+    const u32 S = (u32)J.S;
     if (S == 1u) { s = 0; return pair; }
     if (pair < (1ull << 32)) {
-        const u32 p = (u32)pair, o = p / S;
+        const u32 p = (u32)pair, t = __umulhi(J.s_magic, p);
+        const u32 o = (t + ((p - t) >> 1)) >> (J.s_shift - 1);
         s = p - o * S;
         return o;
     }
     const u64 o = pair / S;
     s = pair - o * S;
     return o;
+}
+
+// 32-bit word tests (64-bit integer operations run through the FP64 pipe)
+__device__ __forceinline__ bool nonzero(double2 v)
+{
+    return (((unsigned)__double2hiint(v.x) | (unsigned)__double2hiint(v.y)) << 1 |
+            (unsigned)__double2loint(v.x) | (unsigned)__double2loint(v.y)) != 0u;
 }
 
 // Sum of acc over each aligned group of seg lanes (seg a power of two, at
@@ -106,8 +117,7 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool nz = ((((unsigned long long)__double_as_longlong(acc.x)) |
-                      ((unsigned long long)__double_as_longlong(acc.y))) << 1) != 0ull;
+    const bool nz = nonzero(acc);
     const unsigned m = __ballot_sync(full, nz);
     if (m == 0u) return make_double2(0.0, 0.0);
     const unsigned gmask = seg >= 32 ? full : (((1u << seg) - 1u) << (lane & ~(seg - 1)));
@@ -146,30 +156,34 @@ __device__ __forceinline__ void add_kept(double2& acc, double2 v)
     acc.y += v.y;
 }
 
-__device__ __forceinline__ bool nonzero(double2 v)
-{
-    return ((((unsigned long long)__double_as_longlong(v.x)) | ((unsigned long long)__double_as_longlong(v.y))) << 1) != 0ull;
-}
+
+// Loop counter type: 32-bit when the count fits (64-bit integer operations
+// run through the FP64 pipe on this part).
+template <bool Fits32> struct CounterType { typedef u64 type; };
+template <> struct CounterType<true> { typedef u32 type; };
 
 // bottom entries carry a NaN real part; tested on the bits (integer pipe)
 __device__ __forceinline__ bool is_bottom(double x)
 {
-    return ((u64)__double_as_longlong(x) << 1) > 0xffe0000000000000ull;
+    const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+    return hi > 0x7ff00000u || (hi == 0x7ff00000u && (unsigned)__double2loint(x) != 0u);
 }
 
 // Sum over the valid leaves of one (prefix, root) item: the root once, the
 // suffix for every h_s (skipping cut subtrees), the chi test at the input.
 template <class T>
-__device__ __forceinline__ double2 item_sum(const JobDev& J, u64 item, u64& completed, u64& valid, u64& visits)
+__device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
+                                            typename CounterType<(T::Ap + T::Ar <= 32)>::type local,
+                                            u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
     double2 acc = make_double2(0.0, 0.0);
-    const u64 pair = item >> J.log2_ipp;
-    const u64 local = item & ((1ull << J.log2_ipp) - 1ull);
-    const u64 hp = local >> T::Ar;
-    const u64 hr = local & ((1ull << T::Ar) - 1ull);
+    typedef typename CounterType<(T::Ap + T::Ar <= 32)>::type loc_t;
+    // (the shift counts stay below the type's width in every instantiation)
+    const loc_t hp = T::Ap == 0 ? (loc_t)0 : (loc_t)(local >> (T::Ar % (8 * (int)sizeof(loc_t))));
+    const loc_t hr = local & (loc_t)((1ull << T::Ar) - 1ull);
     u64 s;
-    const u64 o = pair_split(pair, (u32)J.S, s);
+    const u64 o = pair_split(pair, J, s);
     (void)o;
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
     const uint4 sv = __ldg(ent);
@@ -183,14 +197,15 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 item, u64& comp
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 amp = a0;
     if (T::root(st, amp, hr, bin, visits) < 0) {
-        const u64 ns = 1ull << T::As;
-        u64 hs = 0;
+        typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
+        const hs_t ns = (hs_t)1 << T::As;
+        hs_t hs = 0;
         while (hs < ns) {
             u32 st2[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) st2[j] = st[j];
             double2 amp2 = amp;
-            const int r2 = T::suffix(st2, amp2, hs, bin, visits);
+            const int r2 = T::suffix(st2, amp2, (u64)hs, bin, visits);
             if (r2 < 0) {
                 ++completed;
                 u32 d = 0;
@@ -202,7 +217,7 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 item, u64& comp
                 }
                 ++hs;
             } else {
-                hs = ((hs >> r2) + 1ull) << r2;
+                hs = ((hs >> r2) + (hs_t)1) << r2;
             }
         }
     }
@@ -217,21 +232,31 @@ template <class T>
 __device__ void tile_body(const JobDev& J, u64 tile)
 {
     const int lane = threadIdx.x & 31;
-    const u64 n_items = J.n_pairs << J.log2_ipp;
-    const int lg = J.log2_ipp;
+    constexpr int lg = T::Ap + T::Ar;   // items per pair: 2^lg
+    typedef typename CounterType<(lg <= 32)>::type loc_t;
+    const u64 n_items = J.n_pairs << lg;
     const u64 first = tile * TILE + (u64)lane * 8u;
     u64 completed = 0, valid = 0, visits = 0;
     double2 acc = make_double2(0.0, 0.0);
+    // the lane's items as (pair, index within the pair), advanced in place
+    // (the index stays 32-bit where it fits)
+    u64 pair = first >> lg;
+    loc_t local = (loc_t)(first & ((1ull << lg) - 1ull));
+    const int kn = first >= n_items ? 0 : (n_items - first < 8u ? (int)(n_items - first) : 8);
 #pragma unroll 1
-    for (int k = 0; k < 8; ++k) {
-        const u64 item = first + (u64)k;
-        if (item >= n_items) break;
-        const double2 v = item_sum<T>(J, item, completed, valid, visits);
-        if (J.log) J.log[item] = cmul(J.scale, v);
+    for (int k = 0; k < kn; ++k) {
+        const double2 v = item_sum<T>(J, pair, local, completed, valid, visits);
+        if (J.log) {   // logging runs only: keep the product out of the common path
+            asm volatile("" ::: "memory");
+            J.log[first + (u64)k] = cmul(J.scale, v);
+        }
         if (nonzero(v)) add_kept(acc, v);
-        if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
-            J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
+        ++local;
+        if (lg < 3 && local == ((loc_t)1 << (lg < 3 ? lg : 0))) {
+            J.partials[pair] = acc;   // a pair of at most 4 items ends here
             acc = make_double2(0.0, 0.0);
+            ++pair;
+            local = 0;
         }
     }
     if (lg >= 3) {
@@ -258,10 +283,11 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
 {
     constexpr int W = T::W;
     const u64 e = J.live[i >> T::Ar];
-    const u64 hr = i & ((1ull << T::Ar) - 1ull);
+    typedef typename CounterType<(T::Ar <= 32)>::type hr_t;   // 32-bit when it fits
+    const hr_t hr = (hr_t)i & (hr_t)((1ull << T::Ar) - 1ull);
     const u64 pair = e >> T::Ap;
     u64 sidx;
-    const u64 o = pair_split(pair, (u32)J.S, sidx);
+    const u64 o = pair_split(pair, J, sidx);
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
     double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
@@ -273,14 +299,15 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 acc = make_double2(0.0, 0.0);
     if (T::root(st, amp, hr, bin, visits) < 0) {
-        const u64 ns = 1ull << T::As;
-        u64 hs = 0;
+        typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
+        const hs_t ns = (hs_t)1 << T::As;
+        hs_t hs = 0;
         while (hs < ns) {
             u32 st2[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) st2[j] = st[j];
             double2 amp2 = amp;
-            const int r2 = T::suffix(st2, amp2, hs, bin, visits);
+            const int r2 = T::suffix(st2, amp2, (u64)hs, bin, visits);
             if (r2 < 0) {
                 ++completed;
                 u32 d = 0;
@@ -292,7 +319,7 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
                 }
                 ++hs;
             } else {
-                hs = ((hs >> r2) + 1ull) << r2;
+                hs = ((hs >> r2) + (hs_t)1) << r2;
             }
         }
     }
@@ -321,7 +348,7 @@ __device__ __forceinline__ bool lv_load(const JobDev& J, int a_prev, int a_next,
     const u64 pair = idx >> a_next;
     const u64 child = idx & ((1ull << a_next) - 1ull);
     u64 sidx;
-    const u64 o = pair_split(pair, (u32)J.S, sidx);
+    const u64 o = pair_split(pair, J, sidx);
     const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
     const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
     uint4 sv;
@@ -368,7 +395,7 @@ __device__ __forceinline__ void prefix_body(const JobDev& J, u64 local, u64& vis
     const u64 pair = local >> T::Ap;
     const u64 hp = local & ((1ull << T::Ap) - 1ull);
     u64 sidx;
-    const u64 o = pair_split(pair, (u32)J.S, sidx);
+    const u64 o = pair_split(pair, J, sidx);
     const uint4 ov = __ldg(reinterpret_cast<const uint4*>(J.outs + 4 * o));
     const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
     const u32 otmp[4] = {ov.x, ov.y, ov.z, ov.w};
@@ -554,7 +581,8 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         const double2* F = J.fac + op.aux;
         const std::string visits_cut = "{ visits += " + std::to_string(e - e0 + 1) + "ull; return low; }";
         auto srcbit = [&](int sidx, int q) {
-            return sidx >= 0 ? "((u32)(h >> " + std::to_string(sidx) + ") & 1u)"
+            if (sidx >= 32) return "((u32)(h >> " + std::to_string(sidx) + ") & 1u)";
+            return sidx >= 0 ? "((h32 >> " + std::to_string(sidx) + ") & 1u)"
                              : "((bin[" + std::to_string(q >> 5) + "] >> " + std::to_string(q & 31) + ") & 1u)";
         };
         std::string c;
@@ -669,6 +697,9 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         }
         if (!c.empty()) body += "    " + c + "\n";
     }
+    // 64-bit integer operations run through the FP64 pipe on this part:
+    // the enumeration word is read as 32 bits wherever its bits allow
+    out += "    const u32 h32 = (u32)h;\n    (void)h32;\n";
     out += "    int low = " + std::to_string(nbits) + ";\n";
     for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
     out += body;

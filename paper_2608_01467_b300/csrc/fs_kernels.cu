@@ -42,21 +42,31 @@ __device__ __forceinline__ double2 ldf(const double2* p)
     return __ldg(p);
 }
 
-// (output, input) of a pair index: pair = o * S + s.  64-bit integer
-// division runs through the FP64 pipe, which is scarce on this part, so the
-// common cases avoid it: S = 1, and pair indices below 2^32 (32-bit
-// division).
-__device__ __forceinline__ uint64_t pair_split(uint64_t pair, uint32_t S, uint64_t& s)
+// (output, input) of a pair index, pair = o * S + s.  Integer division by a
+// runtime value goes through the scarce FP64 pipe on this part, so the
+// quotient comes from the job's precomputed multiplier (division by an
+// invariant integer, Granlund and Montgomery 1994, Fig. 4.1) for pair
+// indices below 2^32.
+__device__ __forceinline__ uint64_t pair_split(uint64_t pair, const JobDev& J, uint64_t& s)
 {
+    const uint32_t S = (uint32_t)J.S;
     if (S == 1u) { s = 0; return pair; }
     if (pair < (1ull << 32)) {
-        const uint32_t p = (uint32_t)pair, o = p / S;
+        const uint32_t p = (uint32_t)pair, t = __umulhi(J.s_magic, p);
+        const uint32_t o = (t + ((p - t) >> 1)) >> (J.s_shift - 1);
         s = p - o * S;
         return o;
     }
     const uint64_t o = pair / S;
     s = pair - o * S;
     return o;
+}
+
+// 32-bit word tests (64-bit integer operations run through the FP64 pipe)
+__device__ __forceinline__ bool nonzero(double2 v)
+{
+    return (((unsigned)__double2hiint(v.x) | (unsigned)__double2hiint(v.y)) << 1 |
+            (unsigned)__double2loint(v.x) | (unsigned)__double2loint(v.y)) != 0u;
 }
 
 // Sum of acc over each aligned group of seg lanes (seg a power of two, at
@@ -70,8 +80,7 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool nz = ((((unsigned long long)__double_as_longlong(acc.x)) |
-                      ((unsigned long long)__double_as_longlong(acc.y))) << 1) != 0ull;
+    const bool nz = nonzero(acc);
     const unsigned m = __ballot_sync(full, nz);
     if (m == 0u) return make_double2(0.0, 0.0);
     const unsigned gmask = seg >= 32 ? full : (((1u << seg) - 1u) << (lane & ~(seg - 1)));
@@ -110,16 +119,13 @@ __device__ __forceinline__ void add_kept(double2& acc, double2 v)
     acc.y += v.y;
 }
 
-__device__ __forceinline__ bool nonzero(double2 v)
-{
-    return ((((unsigned long long)__double_as_longlong(v.x)) | ((unsigned long long)__double_as_longlong(v.y))) << 1) != 0ull;
-}
 
 // A bottom entry (its prefix met an exactly zero factor) carries a NaN real
 // part; tested on the bits (a double compare would use the FP64 pipe).
 __device__ __forceinline__ bool is_bottom(double x)
 {
-    return ((unsigned long long)__double_as_longlong(x) << 1) > 0xffe0000000000000ull;
+    const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+    return hi > 0x7ff00000u || (hi == 0x7ff00000u && (unsigned)__double2loint(x) != 0u);
 }
 
 template <int W>
@@ -321,7 +327,7 @@ __device__ void prefix_one(const JobDev& J, uint64_t local, uint32_t* err,
     const uint64_t pair = local >> J.Ap;
     const uint64_t hp = local & ((1ull << J.Ap) - 1ull);
     uint64_t s;
-    const uint64_t o = pair_split(pair, (uint32_t)J.S, s);
+    const uint64_t o = pair_split(pair, J, s);
     uint32_t st[W], bin[W];
     load_bits<W>(J.outs + 4 * o, st);
     load_bits<W>(J.ins + 4 * s, bin);
@@ -383,7 +389,7 @@ __device__ void prefix_level_one(const JobDev& J, const PrefixLevel& L, const En
     const uint64_t pair = idx >> L.a_next;
     const uint64_t child = idx & ((1ull << L.a_next) - 1ull);
     uint64_t s;
-    const uint64_t o = pair_split(pair, (uint32_t)J.S, s);
+    const uint64_t o = pair_split(pair, J, s);
     uint32_t st[W], bin[W];
     load_bits<W>(J.ins + 4 * s, bin);
     double2 amp = make_double2(1.0, 0.0);
@@ -447,7 +453,7 @@ __device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, u
     const uint64_t hp = local >> J.Ar;
     const uint64_t hr = local & ((1ull << J.Ar) - 1ull);
     uint64_t s;
-    pair_split(pair, (uint32_t)J.S, s);
+    pair_split(pair, J, s);
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << J.Ap) + hp);
     const uint4 sv = __ldg(ent);
     const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
@@ -501,7 +507,10 @@ __device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err)
         const uint64_t item = first + (uint64_t)k;
         if (item >= n_items) break;
         const double2 v = history_item<W>(J, item, err, completed, valid, visits);
-        if (J.log) J.log[item] = cmul(J.scale, v);
+        if (J.log) {   // logging runs only: keep the product out of the common path
+            asm volatile("" ::: "memory");
+            J.log[item] = cmul(J.scale, v);
+        }
         if (nonzero(v)) add_kept(acc, v);
         if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
             J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
@@ -666,7 +675,7 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
     const uint64_t hr = i & ((1ull << J.Ar) - 1ull);
     const uint64_t pair = e >> J.Ap;
     uint64_t s;
-    const uint64_t o = pair_split(pair, (uint32_t)J.S, s);
+    const uint64_t o = pair_split(pair, J, s);
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
     double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));

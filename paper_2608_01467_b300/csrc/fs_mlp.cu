@@ -392,8 +392,9 @@ __device__ __forceinline__ void entry_features_of(const JobDev& J, const Entry& 
     if (J.S == 1) {   // the 64-bit division routine would use the FP64 pipe
         o = pair;
         sidx = 0;
-    } else if (pair < (1ull << 32)) {
-        const uint32_t p32 = (uint32_t)pair, o32 = p32 / (uint32_t)J.S;
+    } else if (pair < (1ull << 32)) {   // multiplier division (the job's s_magic, s_shift)
+        const uint32_t p32 = (uint32_t)pair, t = __umulhi(J.s_magic, p32);
+        const uint32_t o32 = (t + ((p32 - t) >> 1)) >> (J.s_shift - 1);
         o = o32;
         sidx = p32 - o32 * (uint32_t)J.S;
     } else {

@@ -335,6 +335,22 @@ def test_incrementer_cascades_match_oracle(n, f0, L, common, inc, msb):
     assert s1[0]["valid"] == int(cnt["valid"].sum())
 
 
+@pytest.mark.parametrize("S", [3, 5])
+def test_input_support_not_a_power_of_two(S):
+    """Sparse inputs of 3 and 5 basis states (Eq. 2): pair indices are split
+    into (output, input) by a precomputed multiplier; exact, threshold and
+    learned-free compacted runs against the oracle."""
+    c = random_small_circuit(9, 50, 900 + S)
+    rng = SplitMix64(S)
+    ins = [(rng.bits(9), complex(0.3 * (k + 1), 0.1 * k)) for k in range(S)]
+    outs = [rng.bits(9) for _ in range(37)]
+    for eps in (0.0, 0.05):
+        (a,), st, _ = run_batch([(c, ins, outs, eps)])
+        o, cnt = oracle_counts(c, ins, outs, eps=eps, c1=st[0]["c1"], c2=st[0]["c2"])
+        close(a, o)
+        assert st[0]["valid"] == int(cnt["valid"].sum())
+
+
 def test_deterministic_and_host_path_bitwise():
     w = qaoa_workload(8, 2, n_out=40, seed=9)
     (a1,), _, b = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
