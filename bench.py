@@ -382,7 +382,7 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
         peak = peaks["bf16_tflops"] * 1e12
         r = {"bound": "tensor", "achieved": work["prune"][1] / t / 1e12, "peak": peak / 1e12,
              "unit": "TFLOP/s", "frac": work["prune"][1] / t / peak,
-             "peak_note": "bf16 cuBLAS burst of measured peaks; the MLP runs mma.sync m16n8k16"}
+             "peak_note": "bf16 cuBLAS burst of measured peaks; the scoring MLP runs tcgen05.mma (BF16, FP32 accumulate in tensor memory)"}
     else:
         i_frac = work[dom][0] / t / int_peak
         f_frac = work[dom][1] / t / peaks["dfma_per_s"]

@@ -627,14 +627,39 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     uint32_t* tmem_slot = (uint32_t*)(sm + SM_BAR + 16);
     volatile uint32_t* abort_flag = (volatile uint32_t*)(sm + SM_BAR + 20) + grp;
 
-    // weights as the B operands (B[n][k] = W[k][n]), biases, bf16-rounded w3
-    for (int i = tid; i < F * H; i += TC_THREADS) {
-        const int k = i / H, n = i % H;
-        *(__nv_bfloat16*)(sm + SM_W1 + kmajor_off(n, k, 256)) = __float2bfloat16_rn(P[OFF_W1 + i]);
-    }
-    for (int i = tid; i < H * H; i += TC_THREADS) {
-        const int k = i / H, n = i % H;
-        *(__nv_bfloat16*)(sm + SM_W2 + kmajor_off(n, k, 2048)) = __float2bfloat16_rn(P[OFF_W2 + i]);
+    // weights as the B operands (B[n][k] = W[k][n]), biases, bf16-rounded w3;
+    // 16-byte loads, eight in flight per thread (the staging is on every
+    // CTA's critical path)
+    if (((uintptr_t)P & 15u) == 0u) {
+        const float4* P4 = reinterpret_cast<const float4*>(P);
+#pragma unroll 2
+        for (int i = tid; i < F * H / 4; i += TC_THREADS) {
+            const float4 v = __ldg(P4 + OFF_W1 / 4 + i);
+            const int k = (4 * i) / H, n = (4 * i) % H;
+            const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                *(__nv_bfloat16*)(sm + SM_W1 + kmajor_off(n + u, k, 256)) = __float2bfloat16_rn(f[u]);
+        }
+#pragma unroll 8
+        for (int i = tid; i < H * H / 4; i += TC_THREADS) {
+            const float4 v = __ldg(P4 + OFF_W2 / 4 + i);
+            const int k = (4 * i) / H, n = (4 * i) % H;
+            const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                *(__nv_bfloat16*)(sm + SM_W2 + kmajor_off(n + u, k, 2048)) = __float2bfloat16_rn(f[u]);
+        }
+    } else {
+        for (int i = tid; i < F * H; i += TC_THREADS) {
+            const int k = i / H, n = i % H;
+            *(__nv_bfloat16*)(sm + SM_W1 + kmajor_off(n, k, 256)) = __float2bfloat16_rn(P[OFF_W1 + i]);
+        }
+#pragma unroll 8
+        for (int i = tid; i < H * H; i += TC_THREADS) {
+            const int k = i / H, n = i % H;
+            *(__nv_bfloat16*)(sm + SM_W2 + kmajor_off(n, k, 2048)) = __float2bfloat16_rn(P[OFF_W2 + i]);
+        }
     }
     for (int i = tid; i < H; i += TC_THREADS) {
         vb1[i] = P[OFF_B1 + i];
