@@ -802,16 +802,17 @@ __device__ __forceinline__ double2 strided_sum(const double2* __restrict__ src, 
 }
 
 constexpr int RED_LPO = 4;            // lanes per output in the common path
-constexpr uint64_t RED_SMALL = 64;    // outputs with more items go to reduce_big_kernel
+constexpr uint64_t RED_SMALL = 64;    // outputs with more items take the whole warp
+constexpr uint64_t RED_WARP = 4096;   // outputs with more items go to reduce_big_kernel
 constexpr int RED_BIG_THREADS = 256;
 
 // FP64 is scarce on this part (about 2 FMA per clock per SM), so the
 // reduction keeps FP64 instructions per output low: each warp takes 8
 // outputs, 4 lanes each (lane-strided sums, a 2-level butterfly), then adds
 // c_in * alpha over the input support in order (Eq. 2).  An output with more
-// than RED_SMALL items is listed for reduce_big_kernel instead.  The order
-// of every sum depends only on the item counts, so results are run-to-run
-// identical.
+// than RED_SMALL items is summed by the whole warp, one with more than
+// RED_WARP is listed for reduce_big_kernel.  The order of every sum depends
+// only on the item counts, so results are run-to-run identical.
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
                                                                 const uint64_t* __restrict__ begin,
                                                                 int n_jobs, uint64_t total, double2* amp_out,
@@ -821,8 +822,10 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
     const int lane = threadIdx.x & 31, sub = lane & (RED_LPO - 1), slot = lane / RED_LPO;
     const uint64_t warp = ((uint64_t)blockIdx.x * REDUCE_THREADS + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * REDUCE_THREADS) >> 5;
-    for (uint64_t g0 = warp * OPW; g0 < total; g0 += nwarp * OPW) {
-        const uint64_t g = g0 + (uint64_t)slot;
+    // a warp's 8 outputs are nwarp apart, so that runs of large outputs
+    // (requests list the likely ones first) spread over warps
+    for (uint64_t g0 = warp; g0 < total; g0 += nwarp * OPW) {
+        const uint64_t g = g0 + (uint64_t)slot * nwarp;
         const bool have = g < total;
         const int j = have ? find_job(begin, n_jobs, g) : 0;
         const JobDev& J = jobs[j];
@@ -858,9 +861,36 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
                 amp.y += w.y;
             }
         }
+        // medium outputs: the whole warp, one output at a time (32-lane
+        // stride, 5-level butterfly); larger ones go to reduce_big_kernel
+        unsigned mid = __ballot_sync(0xffffffffu, have && !small && n <= RED_WARP && sub == 0);
+        while (mid) {
+            const int b = __ffs(mid) - 1;
+            mid &= mid - 1u;
+            const uint64_t gb = __shfl_sync(0xffffffffu, g, b);
+            const int jb = __shfl_sync(0xffffffffu, j, b);
+            const JobDev& JB = jobs[jb];
+            const uint64_t ob = gb - JB.out_begin;
+            double2 ab = make_double2(0.0, 0.0);
+            for (int s = 0; s < JB.S; ++s) {
+                uint64_t lo, hi;
+                const double2* src = pair_items(JB, ob * (uint64_t)JB.S + (uint64_t)s, lo, hi);
+                if (hi == lo) continue;   // warp-uniform: the same pair for every lane
+                double2 t = strided_sum(src, lo + (uint64_t)lane, hi, 32);
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+                    t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+                }
+                const double2 w = cmul(__ldg(JB.coef + s), t);
+                ab.x += w.x;
+                ab.y += w.y;
+            }
+            if (lane == b) amp_out[gb] = ab;
+        }
         if (have && sub == 0) {
             if (small) amp_out[g] = amp;
-            else big_list[atomicAdd(big_count, 1u)] = g;
+            else if (n > RED_WARP) big_list[atomicAdd(big_count, 1u)] = g;
         }
     }
 }

@@ -252,17 +252,21 @@ def test_mixed_batch_one_launch():
 
 
 def test_reduction_large_and_small_outputs_in_one_warp():
-    """Outputs with thousands of per-tile partials (the whole-warp path of
-    the reduction) next to outputs with a handful, with input supports of
-    1 and 2 terms, in one batch; every amplitude against the oracle."""
-    big = qaoa_workload(10, 2, n_out=3, seed=5)            # A = 20
+    """Outputs with thousands of per-tile partials (the whole-warp and the
+    block-per-output paths of the reduction) next to outputs with a handful,
+    with input supports of 1 and 2 terms, in one batch; every amplitude
+    against the oracle."""
+    big = qaoa_workload(10, 2, n_out=3, seed=5)            # A = 20: 4096 partials, one warp each
+    hc = random_small_circuit(8, 70, 701)                   # A = 22: 16384 partials, one block each
+    hrng = SplitMix64(701)
     small = qft_workload(8)
     c = random_small_circuit(6, 30, 606)
     rng = SplitMix64(606)
     two = (c, [(rng.bits(6), 0.6), (rng.bits(6), 0.8j)], list(range(64)), 0.0)
     jobs = [(small.circuit, small.inputs, small.outputs[:5], 0.0),
             (big.circuit, big.inputs, big.outputs, 0.0), two,
-            (small.circuit, small.inputs, small.outputs[5:40], 0.0)]
+            (small.circuit, small.inputs, small.outputs[5:40], 0.0),
+            (hc, [(hrng.bits(8), 1.0)], [hrng.bits(8) for _ in range(2)], 0.0)]
     b = fs.Batch()
     circs = []
     for circ, ins, outs, eps in jobs:
@@ -271,12 +275,13 @@ def test_reduction_large_and_small_outputs_in_one_warp():
         circs.append(C)
         b.add(C, outs, eps)
     b.set_cuts(1, 0, len(big.circuit.gates))   # one region: 2^20 items, 4096 partials per output
+    b.set_cuts(4, 0, len(hc.gates))           # one region: 2^22 items
     b.plan()
     b.allocate()
     b.upload()
     b.run()
     st = b.finish()
-    assert st[1]["A_r"] == 20
+    assert st[1]["A_r"] == 20 and st[4]["A_r"] == 22
     amp = b.amp.cpu().numpy()
     for (circ, ins, outs, eps), sl in zip(jobs, b.job_slices()):
         o, _ = oracle_counts(circ, ins, outs)
