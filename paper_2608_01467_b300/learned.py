@@ -111,4 +111,9 @@ def train(x: torch.Tensor, t: torch.Tensor, init: np.ndarray, steps: int = 400, 
 
 
 def attach(batch: Batch, job: int, params: torch.Tensor, tau: float):
+    """The library reads the parameters at every run: the batch keeps a
+    reference so that the device buffer outlives it."""
     check(_lib.load().fs_batch_set_pruner(batch._h, job, _vp(params), float(tau)))
+    if not hasattr(batch, "_pruner_params"):
+        batch._pruner_params = {}
+    batch._pruner_params[job] = params
