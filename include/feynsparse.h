@@ -66,7 +66,7 @@ extern "C" {
 #define FS_ERR_NONUNITARY (-4)     /* explicit matrix with |U^+U - I| > 1e-12 */
 #define FS_ERR_NOMEM (-5)
 #define FS_ERR_CUDA (-6)           /* a CUDA runtime call failed; see fs_last_error() */
-#define FS_ERR_TIMEOUT (-7)        /* reserved: a bounded device wait gave up */
+#define FS_ERR_TIMEOUT (-7)        /* a bounded device wait gave up (tensor-core scoring) */
 #define FS_ERR_BAD_PROGRAM (-8)    /* the device found an opcode it does not know */
 #define FS_ERR_TOO_LARGE (-9)      /* 2^A histories cannot be enumerated (A > 62) or
                                       the work exceeds the library's index range */
@@ -296,7 +296,9 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
  * partial history after the prefix of Algorithm 2) by the predicted
  * log10 |exact subtree sum| of its root and suffix completions; entries
  * scoring below tau are cut and every other entry is enumerated exactly (with
- * eps pruning as configured).  BF16 tensor-core operands, FP32 accumulation.
+ * eps pruning as configured).  BF16 tensor-core operands, FP32 accumulation:
+ * scoring (fs_mlp_forward and the prune step of fs_batch_run) on tcgen05.mma
+ * with accumulators in tensor memory, training (fs_mlp_grad) on mma.sync.
  * Parameters: FS_MLP_PARAMS FP32 values in device memory, laid out W1[16][128],
  * b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][n]: input k to output n).
  * Features (16 FP32 per entry): |beta|, log10|beta|, Re beta/|beta|,
@@ -306,7 +308,9 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
  * artificial sources after the prefix. */
 #define FS_MLP_PARAMS 18817
 
-/* y[i] = MLP(x[i]) for n rows of 16 FP32 features (device pointers). */
+/* y[i] = MLP(x[i]) for n rows of 16 FP32 features (device pointers; x rows
+ * 16-byte aligned).  Returns FS_ERR_CUDA on a launch error; a scoring wait
+ * that gives up writes no y for its tile (see FS_ERR_TIMEOUT). */
 FS_API int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream);
 
 /* Loss mean((y - target)^2) and its gradient: d_grad receives FS_MLP_PARAMS
