@@ -745,6 +745,7 @@ int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, 
 int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream)
 {
     if (!d_params || (n && (!d_x || !d_y))) return fail(FS_ERR_INVALID, "NULL argument");
+    if (((uintptr_t)d_x) & 15) return fail(FS_ERR_INVALID, "feature rows must be 16-byte aligned");
     CUDA_TRY(fs::mlp_prepare());
     CUDA_TRY(fs::mlp_forward(d_params, d_x, (long long)n, d_y, (cudaStream_t)stream));
     return FS_OK;

@@ -177,6 +177,13 @@ def test_plan_layout_and_fixed_split_errors():
     assert st_levels >= 2
 
 
+def test_mlp_forward_rejects_misaligned_features_before_any_device_work():
+    L = fs._lib.load()
+    rc = L.fs_mlp_forward(ctypes.c_void_p(256), ctypes.c_void_p(256 + 8), 1, ctypes.c_void_p(512), None)
+    assert rc == -1 and b"16-byte" in L.fs_last_error()
+    assert L.fs_mlp_forward(None, ctypes.c_void_p(256), 1, ctypes.c_void_p(512), None) == -1
+
+
 def test_run_before_upload_is_a_state_error():
     C = fs.Circuit(qft(3))
     b = fs.Batch()
