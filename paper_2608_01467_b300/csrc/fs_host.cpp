@@ -1166,7 +1166,7 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         flat_prefix |= j.levels.empty();
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
-        if (j.compact) k += 4;                  // count, scan, write (with pair ranges), history over live entries
+        if (j.compact) k += j.d_pruner ? 3 : 4; // [count,] scan, write (with pair ranges), history over live entries
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
@@ -1257,15 +1257,18 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     if (b->timing) CUDA_TRY(record(b->ev[4], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
-        if (j.d_pruner)
+        if (j.d_pruner) {
+            // the prune step counts the entries it leaves live per compaction block
+            CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries,
                                            (uint32_t*)(base + b->o_err), s));
+        }
     }
     if (b->timing) CUDA_TRY(record(b->ev[5], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         if (!j.compact) continue;
-        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, s));
+        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, j.d_pruner != nullptr, s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[1], s));
     if (b->tiles.empty()) {

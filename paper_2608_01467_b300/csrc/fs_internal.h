@@ -171,7 +171,9 @@ cudaError_t launch_prefix_level(const JobDev* d_job, const PrefixLevel& L, const
                                 uint64_t n_dst, bool last, uint32_t* d_err, cudaStream_t s);
 cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job, int level, const PrefixLevel& L,
                                     const Entry* src, Entry* dst, uint64_t n_dst, bool last, cudaStream_t s);
-cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t s);
+// counted: the per-block live counts are already in blk (the learned prune
+// step writes them), so only the scan and the write run.
+cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, bool counted, cudaStream_t s);
 cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s);
 int compact_grid_size(int device);
 cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s);

@@ -1050,11 +1050,11 @@ cudaError_t launch_prefix_level(const JobDev* d_job, const PrefixLevel& L, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, cudaStream_t s)
+cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, bool counted, cudaStream_t s)
 {
     const uint64_t nblk = (n_entries + COMPACT_BLOCK - 1) / COMPACT_BLOCK;
     if (nblk == 0) return cudaSuccess;
-    compact_count_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
+    if (!counted) compact_count_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
     compact_scan_kernel<<<1, 1024, 0, s>>>(d_job, (uint32_t)nblk);
     compact_write_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
     return cudaGetLastError();

@@ -789,10 +789,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         tc_fence_before();   // TMEM reads complete before the next tile's MMA
         const float y = (__uint_as_float((uint32_t)acc2) + __uint_as_float((uint32_t)(acc2 >> 32))) + b3;
         if (PRUNE) {
-            if (live && y < tau) {
+            const bool cut = live && y < tau;
+            if (cut) {
                 J->table[row].amp.x = __longlong_as_double(0x7ff8000000000000ll);
                 ++cuts;
             }
+            // entries left live, counted per compaction block (the warp's 32
+            // rows lie in one block); the compaction's own count pass is skipped
+            const unsigned keep = __ballot_sync(0xffffffffu, live && !cut);
+            if ((tid & 31) == 0 && keep)
+                atomicAdd(&J->blk[(unsigned long long)(tile * 128 + (r & ~31)) / COMPACT_BLOCK], (unsigned)__popc(keep));
         } else if (row < n) {
             Y[row] = y;
         }
