@@ -704,25 +704,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         const long long row0 = ((long long)blockIdx.x * 2 + grp) * 128 + r;
         if (PRUNE && row0 < n) cur = J->table[row0];
     }
-    for (long long tile = (long long)blockIdx.x * 2 + grp; tile < tiles; tile += tstride) {
-        const long long row = tile * 128 + r;
+    // features of one row (bf16) into this group's X operand; false: the row
+    // is outside the table or a bottom entry (zero features, never cut)
+    auto stage_x = [&](long long row_, const Entry& e) -> bool {
         float fv[16];
-        bool live = false;
-        if (row < n) {
+        bool lv = false;
+        if (row_ < n) {
             if (PRUNE) {
-                entry_features_of(*J, cur, (unsigned long long)row, sp, fv);
-                live = !isnan(fv[0]);
+                entry_features_of(*J, e, (unsigned long long)row_, sp, fv);
+                lv = !isnan(fv[0]);
             } else {
-                const float4* x4 = reinterpret_cast<const float4*>(X + row * F);
+                const float4* x4 = reinterpret_cast<const float4*>(X + row_ * F);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float4 v = x4[q];
                     fv[4 * q] = v.x; fv[4 * q + 1] = v.y; fv[4 * q + 2] = v.z; fv[4 * q + 3] = v.w;
                 }
-                live = true;
+                lv = true;
             }
         }
-        if (!live) {
+        if (!lv) {
 #pragma unroll
             for (int k = 0; k < F; ++k) fv[k] = 0.f;
         }
@@ -730,6 +731,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                                                            pack_bf16(fv[4], fv[5]), pack_bf16(fv[6], fv[7]));
         *(uint4*)(xs + kmajor_off(r, 8, 256)) = make_uint4(pack_bf16(fv[8], fv[9]), pack_bf16(fv[10], fv[11]),
                                                            pack_bf16(fv[12], fv[13]), pack_bf16(fv[14], fv[15]));
+        return lv;
+    };
+    // the features of tile i + 1 are computed while tile i's layer-2 MMAs run
+    long long tile = (long long)blockIdx.x * 2 + grp;
+    bool live = tile < tiles ? stage_x(tile * 128 + r, cur) : false;
+    for (; tile < tiles; tile += tstride) {
+        const long long row = tile * 128 + r;
+        const long long nrow = row + tstride * 128;
         fence_async_smem();
         group_sync(grp);
         if (r == 0) {
@@ -737,10 +746,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             tc_mma(tmem, sdesc(sx, 256), sdesc(sw1, 256), 0u);
             tc_commit(bar);
         }
-        if (PRUNE) {
-            const long long nrow = row + tstride * 128;
-            if (nrow < n) cur = J->table[nrow];
-        }
+        if (PRUNE && nrow < n) cur = J->table[nrow];
         if (!group_wait(bar, phase, abort_flag, r, grp, err)) break;
         phase ^= 1u;
         // epilogue 1: h1 = bf16(relu(x W1 + b1)) into the layer-2 A operand
@@ -771,6 +777,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 tc_mma(tmem, sdesc(sh + 256u * kt, 2048), sdesc(sw2 + 256u * kt, 2048), kt ? 1u : 0u);
             tc_commit(bar);
         }
+        // next tile's X (the layer-1 MMA that read X has completed)
+        const bool live_next = tile + tstride < tiles ? stage_x(nrow, cur) : false;
         if (!group_wait(bar, phase, abort_flag, r, grp, err)) break;
         phase ^= 1u;
         // epilogue 2: y = relu(h1 W2 + b2) . bf16(w3) + b3
@@ -802,6 +810,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         } else if (row < n) {
             Y[row] = y;
         }
+        live = live_next;
     }
     if (PRUNE) {
         cuts = warp_sum_cuts(cuts);
