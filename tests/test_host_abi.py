@@ -228,3 +228,41 @@ def test_options_and_cut_validation():
         b.plan()                       # c2 beyond the gate count
     assert L.fs_batch_set_cuts(b._h, 0, -1, -1) == 0
     assert b.plan() > 0
+
+
+def _walk_like(n, f0, L, msb_first):
+    """H on the coin (qubit 0), then +1 on qubits f0 .. f0+L-1 controlled on
+    the coin, as multi-controlled X gates most (or least) significant first."""
+    g = [Gate("H", (0,))]
+    ks = range(L - 1, -1, -1) if msb_first else range(L)
+    for k in ks:
+        g.append(Gate("X", (f0 + k,), ((0, 1),) + tuple((f0 + j, 1) for j in range(k))))
+    return WCircuit(n, g, "inc")
+
+
+def test_work_model_counts_fused_incrementers_for_the_generated_engine():
+    """The straight-line engine replaces a controlled +-1 written as an MCX
+    cascade (most significant gate first, i.e. least significant first in the
+    output-to-input evaluation order) by one borrow chain; the work model
+    counts it that way for that engine only, and a cascade in the other
+    order is left gate by gate."""
+    for msb_first, fused in ((True, True), (False, False)):
+        c = _walk_like(40, 3, 30, msb_first)
+        C = fs.Circuit(c)
+        C.set_input([(0, 1.0)])
+        work = {}
+        for engine in ("straight", "interp"):
+            b = fs.Batch(split="fixed", c1=0, c2=len(c.gates), engine=engine)
+            b.add(C, [0, 1])
+            b.plan()
+            work[engine] = b.region_work(0)[0][1]   # root region integer ops
+        if fused:
+            # H deferred (3 + 1 class count) + its unit-phase class applied as a
+            # sign flip (3) + the cascade: common-control test on 1 word (2)
+            # and 5 per register word of the field (2 words)
+            assert work["straight"] == 4 + 3 + 2 + 10
+            assert work["straight"] < work["interp"] / 4
+        else:
+            # gate by gate in both engines; they differ only in the H: 4 integer
+            # ops + 2 FP64 literally, 4 + 3 (sign flip) deferred and hoisted
+            assert work["straight"] == work["interp"] + 3
