@@ -266,3 +266,26 @@ def test_work_model_counts_fused_incrementers_for_the_generated_engine():
             # gate by gate in both engines; they differ only in the H: 4 integer
             # ops + 2 FP64 literally, 4 + 3 (sign flip) deferred and hoisted
             assert work["straight"] == work["interp"] + 3
+
+
+def test_automatic_prefix_segmentation_is_between_flat_and_per_source():
+    """prefix="auto" keeps some of the per-source level boundaries: never more
+    launches than one level per source op, never fewer than the flat prefix;
+    on the 100-qubit walk with A_p = 10 it splits (large table), with A_p = 2
+    it keeps the flat prefix (the extra launches cost more than they save)."""
+    w = qw_workload(n_out=512)
+    G = len(w.circuit.gates)
+    src_gate = {sid: g for g, q, sid in fs.Circuit(w.circuit).branch_vars() if sid >= 0}
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    counts = {}
+    for ap in (2, 10):
+        c1 = G - src_gate[ap - 1]
+        for mode in ("single", "levels", "auto"):
+            b = fs.Batch(split="fixed", c1=c1, c2=c1, prefix=mode)
+            b.add(C, w.outputs)
+            b.plan()
+            counts[(ap, mode)] = b.launch_count()
+        assert counts[(ap, "single")] <= counts[(ap, "auto")] <= counts[(ap, "levels")]
+    assert counts[(2, "auto")] == counts[(2, "single")]
+    assert counts[(10, "auto")] > counts[(10, "single")]
