@@ -154,6 +154,20 @@ def test_aa_fig8_ablation_rows_agree():
         assert st["gate_visits"] == 10 * cost
 
 
+def test_aa12x1_config_all_outputs_vs_dense():
+    """Amplitude amplification on 12 data qubits (10 ancillas, 22 qubits),
+    one iteration (A = 24): the 64 requested outputs, autotuned split, against
+    the dense state vector; the marked string carries the Grover amplitude
+    sin(3 theta), sin(theta) = 2^-6."""
+    w = aa_workload(n=12, iters=1)
+    (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)])
+    assert feynman.analyze(w.circuit)["A"] == 24
+    close(a, dense.amplitudes(w.circuit, w.inputs, w.outputs))
+    theta = math.asin(2.0 ** -6)
+    assert abs(abs(a[0]) - math.sin(3 * theta)) < 1e-12
+    assert st[0]["completed"] == 64 * (1 << 24)
+
+
 def test_qaoa8_exact_vs_dense_and_oracle_counts():
     w = qaoa_workload(8, 2, n_out=64, seed=31)
     (a,), st, _ = run_batch([(w.circuit, w.inputs, w.outputs, 0.0)], prefix="single")
