@@ -237,6 +237,14 @@ FS_API int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream
  * (fs_stats array of capacity cap, host) of the last run. */
 FS_API int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size_t cap);
 
+/* The CUDA C++ source of the straight-line engine for the planned batch:
+ * the regions of Algorithm 2 (Sec. IV-C) of every job as generated code,
+ * what the next fs_batch_upload compiles (NVRTC, sm_103a).  No CUDA call.
+ * Writes at most cap - 1 characters and a terminating NUL into buf (host;
+ * NULL with cap 0 only queries), the full length into *len.
+ * FS_ERR_STATE before fs_batch_plan. */
+FS_API int fs_batch_generated_source(const fs_batch* b, char* buf, size_t cap, size_t* len);
+
 /* Bytes fs_batch_upload copies host-to-device (programs, bit strings,
  * descriptors, tile list) for the planned batch. */
 FS_API int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes);

@@ -81,6 +81,7 @@ SIGNATURES = {
     "fs_batch_finish": (ctypes.c_int, [vp, vp, vp, P(fs_stats), ctypes.c_size_t]),
     "fs_batch_total_outputs": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
     "fs_batch_upload_bytes": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
+    "fs_batch_generated_source": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
     "fs_batch_engine": (ctypes.c_int, [vp, P(ctypes.c_uint32), P(ctypes.c_double)]),
     "fs_batch_launch_count": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
     "fs_batch_time_kernels": (ctypes.c_int, [vp, ctypes.c_int]),

@@ -259,6 +259,15 @@ class Batch:
                          for k in _lib.OPCODES if arr[r * _lib.N_OPCODES + k]}
         return out
 
+    def generated_source(self) -> str:
+        """CUDA C++ of the straight-line engine for the planned batch."""
+        L = _lib.load()
+        n = ctypes.c_size_t(0)
+        check(L.fs_batch_generated_source(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        check(L.fs_batch_generated_source(self._h, buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode()
+
     def region_work(self, job: int):
         """Per single execution: ([prefix, root, suffix, per-leaf] integer ops,
         [prefix, root, suffix, per-valid-leaf] FP64 instructions)."""

@@ -997,6 +997,32 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     return FS_OK;
 }
 
+static std::vector<fs::JitJobSpec> jit_specs(const fs_batch* b)
+{
+    std::vector<fs::JitJobSpec> specs(b->jobs.size());
+    for (size_t ji = 0; ji < b->jobs.size(); ++ji) {
+        const Job& j = b->jobs[ji];
+        specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
+                                   j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
+                                   j.sp.As, j.eps * j.eps, j.compact, j.levels};
+    }
+    return specs;
+}
+
+int fs_batch_generated_source(const fs_batch* b, char* buf, size_t cap, size_t* len)
+{
+    if (!b || !len) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    const std::string src = fs::jit_source(jit_specs(b));
+    *len = src.size();
+    if (buf && cap) {
+        const size_t n = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), n);
+        buf[n] = '\0';
+    }
+    return FS_OK;
+}
+
 int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
 {
     if (!b || !d_ws) return fail(FS_ERR_INVALID, "NULL argument");
@@ -1049,13 +1075,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
     // the straight-line kernel is built first: it reports the constant factor
     // each job's generated root and suffix leave out (folded into c_in below)
     if (b->opt.engine == 0 && !b->jit && nj) {
-        std::vector<fs::JitJobSpec> specs(nj);
-        for (size_t ji = 0; ji < nj; ++ji) {
-            const Job& j = b->jobs[ji];
-            specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
-                                       j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
-                                       j.sp.As, j.eps * j.eps, j.compact, j.levels};
-        }
+        const std::vector<fs::JitJobSpec> specs = jit_specs(b);
         std::string err, src;
         const char* dump = getenv("FS_JIT_DUMP");   // optional: write the generated source here
         std::vector<double2> scales;

@@ -197,6 +197,9 @@ struct JitJobSpec {
     bool compact;
     std::vector<PrefixLevel> levels;   // empty: single-region prefix
 };
+// The generated source for these jobs (what jit_build compiles), without
+// compiling it.
+std::string jit_source(const std::vector<JitJobSpec>& jobs);
 // scales (per job): the constant factor the generated root and suffix
 // leave out of every history (applied through the input coefficients).
 int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,

@@ -764,7 +764,10 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         structs += "  }\n";
         structs += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
         emit_region(structs, globals, js + "s", J, J.c2, J.G, J.As, true, &hoisted);
-        if (scales) (*scales)[j] = make_double2((double)hoisted.real(), (double)hoisted.imag());
+        const double2 sc = make_double2((double)hoisted.real(), (double)hoisted.imag());
+        if (scales) (*scales)[j] = sc;
+        structs += "// J" + js + ": constant factor of the root and suffix, applied through c_in: (" + hexd(sc.x) +
+                   ", " + hexd(sc.y) + ")\n";
         structs += "  }\n};\n";
     }
     src += globals;
@@ -853,6 +856,12 @@ struct JitModule {
 };
 
 }  // namespace
+
+std::string jit_source(const std::vector<JitJobSpec>& jobs)
+{
+    std::vector<double2> scales(jobs.size());
+    return generate(jobs, &scales);
+}
 
 int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* err, double* compile_ms,
               std::string* source_out, std::vector<double2>* scales)

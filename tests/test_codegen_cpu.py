@@ -1,0 +1,243 @@
+"""The straight-line engine's generated region code, compiled for the host.
+
+`fs_batch_generated_source` returns the CUDA C++ the next upload would
+compile.  Its region functions (prefix, root and suffix of Algorithm 2 for
+each job) are plain integer and FP64 code; here they are extracted, compiled
+with g++ against small stand-ins for the few CUDA intrinsics they use, and
+driven by a literal Algorithm 2 loop on the host.  The amplitudes must match
+the oracle: this checks the code generator itself (fused incrementers,
+deferred and hoisted factor classes, threshold cuts) without a GPU."""
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from workloads import (Gate, Circuit as WCircuit, SplitMix64, aa_workload, qaoa_workload, qft,
+                       quantum_walk, random_small_circuit)
+from oracle import feynman
+import paper_2608_01467_b300 as fs
+
+SHIM = r"""
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+typedef unsigned int u32;
+typedef int i32;
+typedef unsigned long long u64;
+struct double2 { double x, y; };
+static inline double2 make_double2(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
+#define __device__
+#define __forceinline__ inline
+#define __ldg(p) (*(p))
+static inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
+static inline double __dmul_rn(double a, double b) { return a * b; }
+static inline int __double2hiint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u >> 32); }
+static inline int __double2loint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u & 0xffffffffu); }
+static inline double __hiloint2double(int hi, int lo)
+{
+    uint64_t u = ((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo;
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+}
+"""
+
+DRIVER = r"""
+int main()
+{
+    const int M = %(M)d, S = %(S)d;
+    static const u32 outs[%(Mp)d][4] = {%(outs)s};
+    static const u32 ins[%(Sp)d][4] = {%(ins)s};
+    static const double cre_[%(Sp)d] = {%(cre)s}, cim_[%(Sp)d] = {%(cim)s};
+    const double2 scale = make_double2(%(sx)s, %(sy)s);
+    constexpr int W = J0::W;
+    for (int o = 0; o < M; ++o) {
+        double ar = 0.0, ai = 0.0;
+        for (int s = 0; s < S; ++s) {
+            u32 bin[W];
+            for (int j = 0; j < W; ++j) bin[j] = ins[s][j];
+            double sr = 0.0, si = 0.0;
+            u64 visits = 0;
+            for (u64 hp = 0; hp < (1ull << J0::Ap); ++hp) {
+                u32 st[W];
+                for (int j = 0; j < W; ++j) st[j] = outs[o][j];
+                double2 a = make_double2(1.0, 0.0);
+                if (J0::prefix(st, a, hp, bin, visits) >= 0) continue;
+                for (u64 hr = 0; hr < (1ull << J0::Ar); ++hr) {
+                    u32 st2[W];
+                    for (int j = 0; j < W; ++j) st2[j] = st[j];
+                    double2 a2 = a;
+                    if (J0::root(st2, a2, hr, bin, visits) >= 0) continue;
+                    for (u64 hs = 0; hs < (1ull << J0::As); ++hs) {
+                        u32 st3[W];
+                        for (int j = 0; j < W; ++j) st3[j] = st2[j];
+                        double2 a3 = a2;
+                        if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
+                        bool ok = true;
+                        for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
+                        if (ok) { sr += a3.x; si += a3.y; }
+                    }
+                }
+            }
+            // c_in times the constant left out of the root and suffix
+            const double cr = cre_[s] * scale.x - cim_[s] * scale.y, ci = cre_[s] * scale.y + cim_[s] * scale.x;
+            ar += cr * sr - ci * si;
+            ai += cr * si + ci * sr;
+        }
+        std::printf("%%.17g %%.17g\n", ar, ai);
+    }
+    return 0;
+}
+"""
+
+
+def _words(v, W):
+    return "{" + ", ".join(f"{(v >> (32 * j)) & 0xffffffff}u" for j in range(4)) + "}"
+
+
+def _extract(src):
+    i = src.index("__device__ __forceinline__ double2 cmul")
+    j = src.index("__device__ __forceinline__ double2 sel2")
+    j = src.index("\n", j) + 1
+    helpers = src[i:j]
+    k = min(x for x in (src.find("__device__ const double2 T_"), src.find("struct J0 {")) if x >= 0)
+    e = src.index('extern "C"', k)
+    body = src[k:e]
+    scale_line = [l for l in body.splitlines() if "J0: constant factor" in l][0]
+    sx, sy = scale_line.split("(")[-1].rstrip(")").split(",")
+    return helpers, body, sx.strip(), sy.strip()
+
+
+def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp):
+    C = fs.Circuit(circ)
+    C.set_input(inputs)
+    b = fs.Batch(split="fixed", c1=c1, c2=c2, prefix="single")
+    b.add(C, outputs, eps)
+    b.plan()
+    helpers, body, sx, sy = _extract(b.generated_source())
+    W = 4
+    drv = DRIVER % dict(M=len(outputs), S=len(inputs), Mp=max(len(outputs), 1), Sp=max(len(inputs), 1),
+                        outs=", ".join(_words(v, W) for v in outputs),
+                        ins=", ".join(_words(v, W) for v, _ in inputs),
+                        cre=", ".join(repr(complex(c).real) for _, c in inputs),
+                        cim=", ".join(repr(complex(c).imag) for _, c in inputs), sx=sx, sy=sy)
+    path = os.path.join(tmp, "gen.cpp")
+    with open(path, "w") as f:
+        f.write(SHIM + helpers + body + drv)
+    exe = os.path.join(tmp, "gen")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-w", "-o", exe, path])
+    out = subprocess.check_output([exe]).decode().split()
+    v = np.array([float(x) for x in out]).reshape(-1, 2)
+    return v[:, 0] + 1j * v[:, 1]
+
+
+def _close(got, want):
+    err = np.abs(np.asarray(got) - np.asarray(want))
+    assert np.all(err <= 1e-12 + 1e-10 * np.abs(want)), err.max()
+
+
+def _cascade(n, f0, L, common, inc):
+    g = [Gate("H", (f0,)), Gate("H", (f0 + L - 1,))] + [Gate("H", (q,)) for q, _ in common]
+    v = 1 if inc else 0
+    for k in range(L - 1, -1, -1):
+        ctr = tuple(common) + tuple((f0 + j, v) for j in range(k))
+        g.append(Gate("X", (f0 + k,), ctr) if ctr else Gate("X", (f0 + k,)))
+    g += [Gate("S", (f0,)), Gate("H", (f0,))]
+    return WCircuit(n, g, "cascade")
+
+
+def _embed():
+    """A 6-qubit random circuit on qubits spread over three register words
+    of a 70-qubit register; outputs with nonzero amplitude from its dense
+    simulation."""
+    from oracle import dense
+    act = [3, 31, 32, 40, 63, 66]
+    small = random_small_circuit(6, 30, 707)
+    gates = [Gate(g.kind, tuple(act[q] for q in g.qubits), tuple((act[q], v) for q, v in g.controls),
+                  g.theta, g.matrix) for g in small.gates]
+    big = WCircuit(70, gates, "embed70")
+    amp = dense.amplitudes(small, [(5, 1.0)], list(range(64)))
+    top = [int(i) for i in np.argsort(-np.abs(amp))[:5]]
+    spread = lambda y: sum(((y >> j) & 1) << q for j, q in enumerate(act))
+    return big, [(spread(5), 1.0)], [spread(y) for y in top]
+
+
+def _cascade_case(n, f0, L, common, inc):
+    """The cascade circuit and outputs reachable from a seeded input: any
+    flips of the H qubits, the field moved by one where the common controls
+    hold, either value of the last H qubit."""
+    c = _cascade(n, f0, L, common, inc)
+    b = SplitMix64(n + L).bits(n)
+    hq = [f0, f0 + L - 1] + [q for q, _ in common]
+    outs = []
+    for k in range(1 << len(hq)):
+        y = b
+        for j, q in enumerate(hq):
+            if (k >> j) & 1:
+                y ^= 1 << q
+        if all(((y >> q) & 1) == v for q, v in common):
+            x = (y >> f0) & ((1 << L) - 1)
+            x = (x + (1 if inc else -1)) % (1 << L)
+            y = (y & ~(((1 << L) - 1) << f0)) | (x << f0)
+        outs.append(y & ~(1 << f0))
+        outs.append(y | (1 << f0))
+    return c, [(b, 1.0)], outs[:6]
+
+
+def _walk():
+    from workloads import qw_workload
+    w = qw_workload(steps=5, n_out=6, pos_bits=8)
+    return w.circuit, w.inputs, w.outputs
+
+
+def _qaoa():
+    w = qaoa_workload(6, 2, n_out=5, seed=3)
+    return w.circuit, w.inputs, w.outputs
+
+
+def _aa():
+    w = aa_workload(n=4, iters=1, all_outputs=True)
+    return w.circuit, w.inputs, w.outputs[:6]
+
+
+CASES = {
+    "random7": lambda: (random_small_circuit(7, 40, 4249), 2),
+    "random9": lambda: (random_small_circuit(9, 50, 905), 3),
+    "embed70": _embed,
+    "qft5": lambda: (qft(5), 1),
+    "qaoa6": _qaoa,
+    "aa4": _aa,
+    "walk": _walk,
+    "cascade_inc": lambda: _cascade_case(45, 27, 12, ((1, 0),), True),
+    "cascade_dec": lambda: _cascade_case(70, 5, 60, ((0, 1), (68, 0)), False),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("eps", [0.0, 0.05])
+def test_generated_regions_match_the_oracle(case, eps, tmp_path):
+    spec = CASES[case]()
+    circ = spec[0]
+    n = circ.n_qubits
+    G = len(circ.gates)
+    A = feynman.analyze(circ)["A"]
+    assert A <= 14, A
+    if len(spec) == 3:
+        inputs, outputs = spec[1], spec[2]
+    else:
+        rng = SplitMix64(len(case) * 131 + n)
+        inputs = [(rng.bits(n), complex(0.6 + 0.1 * k, 0.2 * k)) for k in range(spec[1])]
+        outputs = [rng.bits(n) for _ in range(5)]
+        if n <= 9:   # small registers: outputs that carry amplitude
+            from oracle import dense
+            amp = dense.amplitudes(circ, inputs, list(range(1 << n)))
+            outputs = [int(i) for i in np.argsort(-np.abs(amp))[:5]] + outputs[:2]
+    c1, c2 = G // 3, (2 * G) // 3
+    got = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path))
+    want, _ = feynman.run(circ, inputs, outputs, eps=eps, c1=c1, c2=c2)
+    _close(got, want)
+    if eps == 0.0:
+        assert np.abs(want).max() > 0.05   # the case exercises nonzero amplitudes
