@@ -754,6 +754,9 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         else structs += "    (void)s; (void)a; (void)visits;\n    return -1;   // expanded level by level\n";
         structs += "  }\n";
         for (size_t k = 0; k < J.levels.size(); ++k) {
+            structs += "  // level " + std::to_string(k) + ": ops [" + std::to_string(J.levels[k].e0) + ", " +
+                       std::to_string(J.levels[k].e1) + "), sources [" + std::to_string(J.levels[k].a_prev) + ", " +
+                       std::to_string(J.levels[k].a_next) + ")\n";
             structs += "  static __device__ __forceinline__ int lv" + std::to_string(k) + sig + " {\n    (void)h; (void)bin;\n";
             emit_region(structs, globals, js + "l" + std::to_string(k), J, J.levels[k].e0, J.levels[k].e1, J.Ap);
             structs += "  }\n";

@@ -4,7 +4,8 @@
 compile.  Its region functions (prefix, root and suffix of Algorithm 2 for
 each job) are plain integer and FP64 code; here they are extracted, compiled
 with g++ against small stand-ins for the few CUDA intrinsics they use, and
-driven by a literal Algorithm 2 loop on the host.  The amplitudes must match
+driven by a literal Algorithm 2 loop on the host, with the prefix either as
+one region or expanded level by level as the level kernels do.  The amplitudes must match
 the oracle: this checks the code generator itself (fused incrementers,
 deferred and hoisted factor classes, threshold cuts) without a GPU."""
 import os
@@ -94,6 +95,84 @@ int main()
 """
 
 
+DRIVER_LEVELS = r"""
+#include <vector>
+struct Ent { u32 st[4]; double2 a; bool live; };
+int main()
+{
+    const int M = %(M)d, S = %(S)d;
+    static const u32 outs[%(Mp)d][4] = {%(outs)s};
+    static const u32 ins[%(Sp)d][4] = {%(ins)s};
+    static const double cre_[%(Sp)d] = {%(cre)s}, cim_[%(Sp)d] = {%(cim)s};
+    const double2 scale = make_double2(%(sx)s, %(sy)s);
+    constexpr int W = J0::W;
+    static const int lv_prev[] = {%(aprev)s}, lv_next[] = {%(anext)s};
+    const int L = %(L)d;
+    for (int o = 0; o < M; ++o) {
+        double ar = 0.0, ai = 0.0;
+        for (int s = 0; s < S; ++s) {
+            u32 bin[W];
+            for (int j = 0; j < W; ++j) bin[j] = ins[s][j];
+            u64 visits = 0;
+            // level k extends entry p (a_prev bits) by the level's new bits
+            // c into child (p << new) | c, evaluated with h = child << (A_p - a_next)
+            std::vector<Ent> cur(1);
+            for (int j = 0; j < 4; ++j) cur[0].st[j] = outs[o][j];
+            cur[0].a = make_double2(1.0, 0.0);
+            cur[0].live = true;
+            for (int k = 0; k < L; ++k) {
+                const int nb = lv_next[k] - lv_prev[k];
+                std::vector<Ent> nxt(cur.size() << nb);
+                for (u64 p = 0; p < cur.size(); ++p)
+                    for (u64 c = 0; c < (1ull << nb); ++c) {
+                        const u64 child = (p << nb) | c;
+                        Ent e = cur[p];
+                        if (e.live) {
+                            u32 st[W];
+                            for (int j = 0; j < W; ++j) st[j] = e.st[j];
+                            const u64 h = child << (J0::Ap - lv_next[k]);
+                            int r = -1;
+                            switch (k) {
+%(cases)s
+                            default: break;
+                            }
+                            e.live = r < 0;
+                            for (int j = 0; j < W; ++j) e.st[j] = st[j];
+                        }
+                        nxt[child] = e;
+                    }
+                cur.swap(nxt);
+            }
+            double sr = 0.0, si = 0.0;
+            for (u64 hp = 0; hp < cur.size(); ++hp) {
+                if (!cur[hp].live) continue;
+                for (u64 hr = 0; hr < (1ull << J0::Ar); ++hr) {
+                    u32 st2[W];
+                    for (int j = 0; j < W; ++j) st2[j] = cur[hp].st[j];
+                    double2 a2 = cur[hp].a;
+                    if (J0::root(st2, a2, hr, bin, visits) >= 0) continue;
+                    for (u64 hs = 0; hs < (1ull << J0::As); ++hs) {
+                        u32 st3[W];
+                        for (int j = 0; j < W; ++j) st3[j] = st2[j];
+                        double2 a3 = a2;
+                        if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
+                        bool ok = true;
+                        for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
+                        if (ok) { sr += a3.x; si += a3.y; }
+                    }
+                }
+            }
+            const double cr = cre_[s] * scale.x - cim_[s] * scale.y, ci = cre_[s] * scale.y + cim_[s] * scale.x;
+            ar += cr * sr - ci * si;
+            ai += cr * si + ci * sr;
+        }
+        std::printf("%%.17g %%.17g\n", ar, ai);
+    }
+    return 0;
+}
+"""
+
+
 def _words(v, W):
     return "{" + ", ".join(f"{(v >> (32 * j)) & 0xffffffff}u" for j in range(4)) + "}"
 
@@ -111,19 +190,28 @@ def _extract(src):
     return helpers, body, sx.strip(), sy.strip()
 
 
-def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp):
+def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
     C = fs.Circuit(circ)
     C.set_input(inputs)
-    b = fs.Batch(split="fixed", c1=c1, c2=c2, prefix="single")
+    b = fs.Batch(split="fixed", c1=c1, c2=c2, prefix=prefix)
     b.add(C, outputs, eps)
     b.plan()
-    helpers, body, sx, sy = _extract(b.generated_source())
+    src = b.generated_source()
+    helpers, body, sx, sy = _extract(src)
     W = 4
-    drv = DRIVER % dict(M=len(outputs), S=len(inputs), Mp=max(len(outputs), 1), Sp=max(len(inputs), 1),
-                        outs=", ".join(_words(v, W) for v in outputs),
-                        ins=", ".join(_words(v, W) for v, _ in inputs),
-                        cre=", ".join(repr(complex(c).real) for _, c in inputs),
-                        cim=", ".join(repr(complex(c).imag) for _, c in inputs), sx=sx, sy=sy)
+    fields = dict(M=len(outputs), S=len(inputs), Mp=max(len(outputs), 1), Sp=max(len(inputs), 1),
+                  outs=", ".join(_words(v, W) for v in outputs),
+                  ins=", ".join(_words(v, W) for v, _ in inputs),
+                  cre=", ".join(repr(complex(c).real) for _, c in inputs),
+                  cim=", ".join(repr(complex(c).imag) for _, c in inputs), sx=sx, sy=sy)
+    levels = [l.split("sources [")[1].rstrip(")").split(", ") for l in src.splitlines() if "  // level " in l]
+    if levels:
+        fields.update(L=len(levels), aprev=", ".join(a for a, _ in levels), anext=", ".join(b_ for _, b_ in levels),
+                      cases="\n".join(f"                            case {k}: r = J0::lv{k}(st, e.a, h, bin, visits); break;"
+                                      for k in range(len(levels))))
+        drv = DRIVER_LEVELS % fields
+    else:
+        drv = DRIVER % fields
     path = os.path.join(tmp, "gen.cpp")
     with open(path, "w") as f:
         f.write(SHIM + helpers + body + drv)
@@ -217,8 +305,8 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("eps", [0.0, 0.05])
-def test_generated_regions_match_the_oracle(case, eps, tmp_path):
+@pytest.mark.parametrize("eps,prefix", [(0.0, "single"), (0.05, "single"), (0.0, "levels"), (0.05, "levels")])
+def test_generated_regions_match_the_oracle(case, eps, prefix, tmp_path):
     spec = CASES[case]()
     circ = spec[0]
     n = circ.n_qubits
@@ -236,7 +324,7 @@ def test_generated_regions_match_the_oracle(case, eps, tmp_path):
             amp = dense.amplitudes(circ, inputs, list(range(1 << n)))
             outputs = [int(i) for i in np.argsort(-np.abs(amp))[:5]] + outputs[:2]
     c1, c2 = G // 3, (2 * G) // 3
-    got = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path))
+    got = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path), prefix)
     want, _ = feynman.run(circ, inputs, outputs, eps=eps, c1=c1, c2=c2)
     _close(got, want)
     if eps == 0.0:
