@@ -150,11 +150,12 @@ def sum_over_ranks(v, world, device):
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_sample(jobs, budget_s=15.0, max_outputs=None):
+def oracle_sample(jobs, budget_s=15.0, max_outputs=None, threads=None):
     """Times the C oracle (Algorithm 2 at its own autotuned cuts, all host
-    threads) on a bounded sample of each job's outputs; returns rates."""
+    threads unless given) on a bounded sample of each job's outputs; returns
+    rates."""
     from oracle import feynman
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     tot_out = 0
     tot_hist = 0
     tot_time = 0.0
@@ -531,9 +532,12 @@ def run_ours(args):
         line["learned"] = [{k: v for k, v in p.items() if k != "params"} for p in learned_info]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samp = oracle_sample(jobs, budget_s=args.cpu_seconds)
+        one = oracle_sample(jobs, budget_s=max(2.0, args.cpu_seconds / 4), threads=1)
         line["cpu_baseline"] = {"value": samp["amplitudes_per_s"], "unit": "amplitudes/s",
                                 "cores": samp["cores"], "kind": "oracle", "sample": samp["sample"],
-                                "histories_per_s": samp["histories_per_s"]}
+                                "histories_per_s": samp["histories_per_s"],
+                                "single_thread": {"value": one["amplitudes_per_s"], "sample": one["sample"],
+                                                  "histories_per_s": one["histories_per_s"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
