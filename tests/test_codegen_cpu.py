@@ -57,6 +57,7 @@ int main()
     constexpr int W = J0::W;
     for (int o = 0; o < M; ++o) {
         double ar = 0.0, ai = 0.0;
+        u64 completed = 0, valid = 0;
         for (int s = 0; s < S; ++s) {
             u32 bin[W];
             for (int j = 0; j < W; ++j) bin[j] = ins[s][j];
@@ -77,9 +78,10 @@ int main()
                         for (int j = 0; j < W; ++j) st3[j] = st2[j];
                         double2 a3 = a2;
                         if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
+                        ++completed;
                         bool ok = true;
                         for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
-                        if (ok) { sr += a3.x; si += a3.y; }
+                        if (ok) { sr += a3.x; si += a3.y; ++valid; }
                     }
                 }
             }
@@ -88,7 +90,7 @@ int main()
             ar += cr * sr - ci * si;
             ai += cr * si + ci * sr;
         }
-        std::printf("%%.17g %%.17g\n", ar, ai);
+        std::printf("%%.17g %%.17g %%llu %%llu\n", ar, ai, completed, valid);
     }
     return 0;
 }
@@ -110,6 +112,7 @@ int main()
     const int L = %(L)d;
     for (int o = 0; o < M; ++o) {
         double ar = 0.0, ai = 0.0;
+        u64 completed = 0, valid = 0;
         for (int s = 0; s < S; ++s) {
             u32 bin[W];
             for (int j = 0; j < W; ++j) bin[j] = ins[s][j];
@@ -156,9 +159,10 @@ int main()
                         for (int j = 0; j < W; ++j) st3[j] = st2[j];
                         double2 a3 = a2;
                         if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
+                        ++completed;
                         bool ok = true;
                         for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
-                        if (ok) { sr += a3.x; si += a3.y; }
+                        if (ok) { sr += a3.x; si += a3.y; ++valid; }
                     }
                 }
             }
@@ -166,7 +170,7 @@ int main()
             ar += cr * sr - ci * si;
             ai += cr * si + ci * sr;
         }
-        std::printf("%%.17g %%.17g\n", ar, ai);
+        std::printf("%%.17g %%.17g %%llu %%llu\n", ar, ai, completed, valid);
     }
     return 0;
 }
@@ -217,9 +221,9 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
         f.write(SHIM + helpers + body + drv)
     exe = os.path.join(tmp, "gen")
     subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-w", "-o", exe, path])
-    out = subprocess.check_output([exe]).decode().split()
-    v = np.array([float(x) for x in out]).reshape(-1, 2)
-    return v[:, 0] + 1j * v[:, 1]
+    rows = [l.split() for l in subprocess.check_output([exe]).decode().splitlines()]
+    amp = np.array([float(r[0]) + 1j * float(r[1]) for r in rows])
+    return amp, np.array([int(r[2]) for r in rows]), np.array([int(r[3]) for r in rows])
 
 
 def _close(got, want):
@@ -324,8 +328,12 @@ def test_generated_regions_match_the_oracle(case, eps, prefix, tmp_path):
             amp = dense.amplitudes(circ, inputs, list(range(1 << n)))
             outputs = [int(i) for i in np.argsort(-np.abs(amp))[:5]] + outputs[:2]
     c1, c2 = G // 3, (2 * G) // 3
-    got = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path), prefix)
-    want, _ = feynman.run(circ, inputs, outputs, eps=eps, c1=c1, c2=c2)
+    got, completed, valid = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path), prefix)
+    want, cnt = feynman.run(circ, inputs, outputs, eps=eps, c1=c1, c2=c2)
     _close(got, want)
+    # the same factors in the same order: every pruning decision, hence every
+    # leaf count, is the oracle's exactly
+    assert np.array_equal(completed, cnt["completed"].astype(np.int64))
+    assert np.array_equal(valid, cnt["valid"].astype(np.int64))
     if eps == 0.0:
         assert np.abs(want).max() > 0.05   # the case exercises nonzero amplitudes
