@@ -317,8 +317,11 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
 #define FS_MLP_PARAMS 18817
 
 /* y[i] = MLP(x[i]) for n rows of 16 FP32 features (device pointers; x rows
- * 16-byte aligned).  Returns FS_ERR_CUDA on a launch error; a scoring wait
- * that gives up writes no y for its tile (see FS_ERR_TIMEOUT). */
+ * 16-byte aligned, else FS_ERR_INVALID).  Asynchronous on stream; returns
+ * FS_ERR_CUDA on a launch error.  The scoring kernel bounds its waits on the
+ * tensor cores; in the batch path a wait that gives up is reported as
+ * FS_ERR_TIMEOUT by fs_batch_finish, here (no status word) it leaves the
+ * rows of the tiles it did not finish unwritten. */
 FS_API int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream);
 
 /* Loss mean((y - target)^2) and its gradient: d_grad receives FS_MLP_PARAMS
