@@ -377,6 +377,10 @@ FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params,
  *     counters that must start at zero are cleared by each call.  Calls whose
  *     GPU work overlaps (other host threads, or several streams) race on the
  *     array: serialise them.
+ *   - It runs the library's precompiled kernels (the interpreter engine), so
+ *     no code is generated or loaded onto the device at call time; exact-mode
+ *     amplitudes agree with fs_amplitudes' generated code within rounding
+ *     (1e-12 absolute + 1e-10 relative), threshold-mode ones bit for bit.
  *   - stream: a cudaStream_t (NULL = legacy default stream); the call
  *     synchronises it before returning. */
 #define FS_NOALLOC_SCRATCH_BYTES (16u << 20)

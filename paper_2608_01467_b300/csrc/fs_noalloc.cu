@@ -67,6 +67,9 @@ extern "C" FS_API int fs_amplitudes_noalloc(fs_circuit* c, const uint64_t* outpu
     fs_options opt = {};
     opt.table_budget_bytes = FS_NOALLOC_SCRATCH_BYTES / 4;
     opt.max_items = FS_NOALLOC_SCRATCH_BYTES / 4 / 16;
+    // the precompiled kernels: the generated engine would load a freshly
+    // compiled module onto the device, which allocates
+    opt.engine = 1;
     rc = fs_batch_set_options(b, &opt);
     if (!rc) rc = fs_batch_add(b, c, outputs, n_out, eps, nullptr);
     if (!rc) rc = fs_batch_plan(b, &ws);
