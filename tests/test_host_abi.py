@@ -289,3 +289,19 @@ def test_automatic_prefix_segmentation_is_between_flat_and_per_source():
         assert counts[(ap, "single")] <= counts[(ap, "auto")] <= counts[(ap, "levels")]
     assert counts[(2, "auto")] == counts[(2, "single")]
     assert counts[(10, "auto")] > counts[(10, "single")]
+
+
+def test_generated_source_requires_a_plan_and_reports_its_length():
+    C = fs.Circuit(qft(3))
+    b = fs.Batch()
+    b.add(C, [0, 1])
+    L = fs._lib.load()
+    n = ctypes.c_size_t(0)
+    assert L.fs_batch_generated_source(b._h, None, 0, ctypes.byref(n)) == -10   # FS_ERR_STATE
+    b.plan()
+    assert L.fs_batch_generated_source(b._h, None, 0, ctypes.byref(n)) == 0 and n.value > 1000
+    small = ctypes.create_string_buffer(16)
+    assert L.fs_batch_generated_source(b._h, small, 16, ctypes.byref(n)) == 0
+    assert len(small.value) == 15 and n.value > 1000   # truncated, NUL-terminated
+    src = b.generated_source()
+    assert len(src) == n.value and "struct J0" in src and "fs_jit_history" in src
