@@ -970,8 +970,6 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     b->o_bigcount = take(sizeof(unsigned int));
     b->o_err = take(sizeof(uint32_t));   // last of the words zeroed at the start of every run
     b->o_biglist = take(b->total_out * sizeof(uint64_t));
-    const size_t zero_end = off;
-    (void)zero_end;
     for (Job& j : b->jobs) {
         j.o_table = take(j.table_entries * sizeof(fs::Entry));
         j.o_part = take(j.n_partials * sizeof(double2));
