@@ -211,7 +211,9 @@ FS_API int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, siz
 FS_API int fs_batch_set_cuts(fs_batch* b, uint32_t job, int32_t c1, int32_t c2);
 
 /* Compiles every job (programs, autotuned cuts, tile queue) and reports the
- * device workspace size in bytes (256-byte aligned sub-buffers). */
+ * device workspace size in bytes (256-byte aligned sub-buffers).  Planning
+ * again releases the generated kernel of the previous plan: graphs captured
+ * from fs_batch_run before must be captured again after the next upload. */
 FS_API int fs_batch_plan(fs_batch* b, size_t* workspace_bytes);
 
 /* Copies the planned static data (programs, bit strings, tile list) into the
