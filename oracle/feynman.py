@@ -148,6 +148,19 @@ def run(circuit, inputs, outputs, eps=0.0, c1=0, c2=0, threads=1):
     input [(basis, coeff)] (Eq. 2) by Algorithm 2 with cuts (c1, c2), or
     Algorithm 1 when c1 = c2 = 0; plus per-output counts
     {completed, valid, visits} and A."""
+    return _run(circuit, inputs, outputs, eps, c1, c2, threads)
+
+
+def run_dfs(circuit, inputs, outputs, eps=0.0, threads=1):
+    """As run(), by a depth-first search over the artificial sources in
+    backward order that drops a subtree as soon as its branch is cut (any A;
+    cost proportional to the surviving tree, not to 2^A).  Same leaves and
+    counts {completed, valid} as Algorithm 1/2 with the same eps; visits
+    count the gates the search evaluated."""
+    return _run(circuit, inputs, outputs, eps, -1, -1, threads)
+
+
+def _run(circuit, inputs, outputs, eps, c1, c2, threads):
     ins = _words([b for b, _ in inputs])
     coef = np.array([[complex(c).real, complex(c).imag] for _, c in inputs], np.float64).reshape(-1)
     outs = _words(list(outputs))

@@ -306,6 +306,73 @@ static cplx pair_amplitude(const ocirc* C, const uint64_t b_in[2], const uint64_
     return cx(sr.s + sr.c, si.s + si.c);
 }
 
+/* alpha^{b_in, b_out} as a depth-first search over the artificial sources in
+ * the order the backward sweep meets them (the per-source limit of the
+ * checkpointing of Sec. IV-C: every gate is evaluated once per assignment of
+ * the sources met before it).  At a branching gate carrying artificial
+ * sources each value of those sources is tried in turn; a branch whose
+ * factor is exactly zero, or whose |beta| falls below eps right after that
+ * factor (Sec. IV-A, Observation 3), is dropped with its whole subtree.
+ * The surviving leaves, their chi test and their products are those of
+ * Algorithm 1 / Algorithm 2 with the same threshold. */
+typedef struct {
+    const ocirc* C;
+    const uint64_t* b_in;
+    double eps;
+    uint8_t* h;
+    ocount* cnt;
+    neum sr, si;
+} dfs_ctx;
+
+static void dfs(dfs_ctx* D, int e, const uint64_t st_in[2], cplx amp)
+{
+    const ocirc* C = D->C;
+    uint64_t st[2] = {st_in[0], st_in[1]};
+    for (; e < C->G; e++) {
+        const ogate* g = &C->g[C->G - 1 - e];
+        int srcs[2], ns = 0;
+        if (g->role == ROLE_BR)
+            for (int t = 0; t < g->k; t++)
+                if (g->src[t] >= 0) srcs[ns++] = g->src[t];
+        if (ns == 0) {
+            int has_src;
+            D->cnt->visits++;
+            if (!step_gate(g, st, &amp, D->h, D->b_in, &has_src)) return;
+            continue;
+        }
+        for (int v = 0; v < (1 << ns); v++) {
+            for (int j = 0; j < ns; j++) D->h[srcs[j]] = (uint8_t)((v >> j) & 1);
+            uint64_t s2[2] = {st[0], st[1]};
+            cplx a2 = amp;
+            int has_src;
+            D->cnt->visits++;
+            if (!step_gate(g, s2, &a2, D->h, D->b_in, &has_src)) continue;
+            if (D->eps > 0.0 && below_eps(a2, D->eps)) continue;
+            dfs(D, e + 1, s2, a2);
+        }
+        return;
+    }
+    D->cnt->completed++;
+    if (st[0] == D->b_in[0] && st[1] == D->b_in[1]) {
+        D->cnt->valid++;
+        neum_add(&D->sr, amp.re);
+        neum_add(&D->si, amp.im);
+    }
+}
+
+static cplx pair_amplitude_dfs(const ocirc* C, const uint64_t b_in[2], const uint64_t b_out[2], double eps,
+                               ocount* cnt)
+{
+    dfs_ctx D;
+    D.C = C; D.b_in = b_in; D.eps = eps; D.cnt = cnt;
+    D.h = (uint8_t*)calloc((size_t)C->A + 1, 1);
+    D.sr.s = D.sr.c = D.si.s = D.si.c = 0.0;
+    const uint64_t st[2] = {b_out[0], b_out[1]};
+    dfs(&D, 0, st, cx(1, 0));
+    free(D.h);
+    return cx(D.sr.s + D.sr.c, D.si.s + D.si.c);
+}
+
 /* ---- exported API ------------------------------------------------------- */
 
 static int make_circ(const orc_gate_in* gates, int G, int n, ocirc* C)
@@ -395,6 +462,7 @@ typedef struct {
     const uint64_t* ins; const double* coef; int S;
     const uint64_t* outs; int M;
     double eps; int c1, c2;
+    int dfs;          /* 1: per-source depth-first search instead of Algorithm 2 */
     double* amp; uint64_t* counts;
     int next;
     pthread_mutex_t mu;
@@ -412,7 +480,8 @@ static void* worker(void* arg)
         ocount tot = {0, 0, 0};
         for (int s = 0; s < J->S; s++) {
             ocount cnt = {0, 0, 0};
-            cplx a = pair_amplitude(J->C, &J->ins[2 * s], &J->outs[2 * o], J->eps, J->c1, J->c2, &cnt);
+            cplx a = J->dfs ? pair_amplitude_dfs(J->C, &J->ins[2 * s], &J->outs[2 * o], J->eps, &cnt)
+                            : pair_amplitude(J->C, &J->ins[2 * s], &J->outs[2 * o], J->eps, J->c1, J->c2, &cnt);
             cplx w = cmul(cx(J->coef[2 * s], J->coef[2 * s + 1]), a);
             neum_add(&ar, w.re);
             neum_add(&ai, w.im);
@@ -477,7 +546,8 @@ int orc_checkpoints(const orc_gate_in* gates, int G, int n, const uint64_t* b_in
 }
 
 /* Amplitudes of M requested outputs for a sparse input of S basis states
- * (Eq. 2), with checkpoints (c1, c2) (c1 = c2 = 0: Algorithm 1), threshold
+ * (Eq. 2), with checkpoints (c1, c2) (c1 = c2 = 0: Algorithm 1; c1 = -1:
+ * the per-source depth-first search), threshold
  * eps (0 = exact) on n_threads host threads.  counts: per output
  * {completed leaves, valid histories, gate visits}. */
 int orc_run(const orc_gate_in* gates, int G, int n,
@@ -488,11 +558,14 @@ int orc_run(const orc_gate_in* gates, int G, int n,
     ocirc C;
     int rc = make_circ(gates, G, n, &C);
     if (rc) return rc;
-    if (c1 < 0 || c2 < c1 || c2 > G || C.A > 62) { free(C.g); return -1; }
+    /* c1 = -1: the per-source depth-first search (any A); otherwise
+     * Algorithm 2 with cuts (c1, c2), which enumerates 2^A per pair */
+    const int use_dfs = c1 == -1;
+    if (!use_dfs && (c1 < 0 || c2 < c1 || c2 > G || C.A > 62)) { free(C.g); return -1; }
     *A_out = C.A;
     job_t J;
     J.C = &C; J.ins = ins; J.coef = coef; J.S = S; J.outs = outs; J.M = M;
-    J.eps = eps; J.c1 = c1; J.c2 = c2; J.amp = amp; J.counts = counts; J.next = 0;
+    J.eps = eps; J.c1 = c1; J.c2 = c2; J.dfs = use_dfs; J.amp = amp; J.counts = counts; J.next = 0;
     pthread_mutex_init(&J.mu, NULL);
     if (n_threads < 1) n_threads = 1;
     pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));

@@ -351,3 +351,76 @@ def test_multithreaded_oracle_is_deterministic():
     a1, c1 = feynman.run(w.circuit, w.inputs, w.outputs, threads=1)
     a4, c4 = feynman.run(w.circuit, w.inputs, w.outputs, threads=4)
     assert np.array_equal(a1, a4) and np.array_equal(c1["valid"], c4["valid"])
+
+
+# ------------------------------------------------ per-source depth-first search
+
+@pytest.mark.parametrize("seed", [3, 17, 29])
+def test_depth_first_search_equals_algorithms_1_and_2(seed):
+    """The per-source search visits the same leaves as Algorithm 1 (and as
+    Algorithm 2 at any cuts) and sums the same histories: equal amplitudes,
+    equal completed and valid counts, exact and thresholded; its gate visits
+    are Eq. 8 generalised to one region per source, never more than
+    Algorithm 2's."""
+    c = random_small_circuit(8, 45, 900 + seed)
+    rng = SplitMix64(seed)
+    inputs = [(rng.bits(8), 0.6), (rng.bits(8), 0.8j)]
+    outputs = [rng.bits(8) for _ in range(6)]
+    G = len(c.gates)
+    for eps in (0.0, 0.05, 0.2):
+        a1, k1 = feynman.run(c, inputs, outputs, eps=eps)
+        a2, k2 = feynman.run(c, inputs, outputs, eps=eps, c1=G // 3, c2=2 * G // 3)
+        ad, kd = feynman.run_dfs(c, inputs, outputs, eps=eps)
+        assert np.max(np.abs(ad - a1)) < 1e-14 and np.max(np.abs(ad - a2)) < 1e-14
+        for k in (k1, k2):
+            assert np.array_equal(kd["completed"], k["completed"])
+            assert np.array_equal(kd["valid"], k["valid"])
+        assert np.all(kd["visits"] <= k2["visits"])
+
+
+def _qaoa_closed_form_leaves(n, angles, eps):
+    """Leaves of one (output, input) pair of QAOA MaxCut that survive the
+    threshold eps: RZZ factors have modulus 1 and RX factors modulus
+    |cos(beta/2)| (input = output value) or |sin(beta/2)| whatever the state,
+    and every factor has modulus <= 1, so a history survives iff the product
+    of its RX moduli is >= eps; with k_l sine choices in layer l there are
+    prod_l C(n, k_l) such histories.  Also returns the smallest distance of a
+    log-product to log(eps)."""
+    layers = []
+    for _, beta in angles:
+        c, s = abs(math.cos(beta / 2)), abs(math.sin(beta / 2))
+        layers.append([((n - k) * math.log(c) + k * math.log(s), math.comb(n, k)) for k in range(n + 1)])
+    states = [(0.0, 1)]
+    for layer in layers:
+        states = [(a + b, x * y) for a, x in states for b, y in layer]
+    return (sum(cnt for lg, cnt in states if lg >= math.log(eps)),
+            min(abs(lg - math.log(eps)) for lg, _ in states))
+
+
+@pytest.mark.parametrize("n,p,eps", [(8, 2, 1e-2), (10, 2, 1e-3), (10, 3, 1e-3), (12, 2, 1e-4)])
+def test_threshold_leaf_count_matches_the_qaoa_closed_form(n, p, eps):
+    w = qaoa_workload(n, p, n_out=4, seed=77 + n)
+    want, margin = _qaoa_closed_form_leaves(n, w.meta["angles"], eps)
+    assert margin > 1e-9          # no product within rounding of eps
+    a, cnt = feynman.run_dfs(w.circuit, w.inputs, w.outputs, eps=eps, threads=4)
+    assert list(cnt["completed"]) == [want] * len(w.outputs)
+    assert list(cnt["valid"]) == [want] * len(w.outputs)   # chi = 1: the H layer reads b_in
+    if n * p <= 24:
+        a1, _ = feynman.run(w.circuit, w.inputs, w.outputs, eps=eps)
+        assert np.max(np.abs(a - a1)) < 1e-14
+
+
+def test_golden_qaoa_threshold_file_is_consistent():
+    """The stored QAOA samples (written by tests/golden/make_qaoa_golden.py
+    from the oracle) against the closed form and the seeded requests."""
+    g = gold("qaoa_threshold.json")
+    for r in g["requests"]:
+        w = qaoa_workload(r["n"], r["p"], n_out=r["n_out"], seed=r["seed"])
+        assert [int(x) for x in w.outputs[:4]] == r["outputs_head"]
+        amp = np.asarray(r["exact_re"]) + 1j * np.asarray(r["exact_im"])
+        assert len(amp) == r["n_out"] and np.all(np.abs(amp) <= 1.0)
+    for s in g["samples"]:
+        w = qaoa_workload(s["n"], s["p"], n_out=4, seed=s["seed"])
+        want, margin = _qaoa_closed_form_leaves(s["n"], w.meta["angles"], s["eps"])
+        assert s["closed_form_leaves"] == want and margin > 1e-9
+        assert s["completed"] == [want] * len(s["index"]) == s["valid"]
