@@ -148,10 +148,12 @@ typedef struct fs_stats {
     uint64_t live_entries;    /* checkpoint entries enumerated by the history kernel */
 } fs_stats;
 
-/* Thread-local message of the last failing call on this thread. */
+/* Thread-local message of the last failing call on this thread (library
+ * plumbing; the paper has no counterpart).  Never NULL; owned by the
+ * library and valid until the next failing call on the same thread. */
 FS_API const char* fs_last_error(void);
 
-/* Library version string. */
+/* Library version string (static storage; no counterpart in the paper). */
 FS_API const char* fs_version(void);
 
 /* Copies n_gates gates (host memory) into a new circuit on n_qubits qubits,
@@ -163,6 +165,9 @@ FS_API const char* fs_version(void);
 FS_API int fs_circuit_create(const fs_gate* gates, size_t n_gates, uint32_t n_qubits,
                       fs_circuit** out);
 
+/* Frees a circuit made by fs_circuit_create (NULL is accepted).  The circuit
+ * of the statement of the problem (Sec. II, Eq. 1); batches that hold jobs
+ * of it must be destroyed or re-planned without it first. */
 FS_API int fs_circuit_destroy(fs_circuit* c);
 
 /* Analysis for the basis input input_bits (2 words, host): fills *out with
@@ -171,7 +176,9 @@ FS_API int fs_circuit_destroy(fs_circuit* c);
  * (S = 1, coefficient 1) until fs_set_input replaces it.  Sec. IV-A/IV-C. */
 FS_API int fs_analyze(fs_circuit* c, const uint64_t* input_bits, fs_analysis* out);
 
-/* Lists the branching variables in backward-sweep order: per entry the gate
+/* Branching variables and artificial sources of the analysis (Sec. IV-A,
+ * Eq. 7; Fig. 2 lists them for the four-qubit example).  Lists the
+ * branching variables in backward-sweep order: per entry the gate
  * index (circuit order), the qubit, and the artificial source id or -1 for a
  * natural source.  Arrays of capacity cap (host); *count receives the total
  * (entries beyond cap are not written). */
@@ -182,41 +189,68 @@ FS_API int fs_branch_vars(const fs_circuit* c, int32_t* gate_index, int32_t* qub
  * words and S complex coefficients (re, im), host memory, copied. */
 FS_API int fs_set_input(fs_circuit* c, const uint64_t* support_bits, const double* coeffs, size_t S);
 
-/* Amplitudes <out|C|psi> of n_out requested outputs (n_out x 2 words, host)
- * into amp_out (2*n_out doubles, re/im, host, caller-owned), with threshold
- * eps (0 = exact).  Synchronous: plans, copies to the device, runs the
- * kernels on the default stream and copies back.  Device memory is
- * allocated and freed inside the call. */
+/* Amplitudes <out|C|psi> = sum_in c_in alpha^{in,out} (Eqs. 1-2) of n_out
+ * requested outputs (n_out x 2 words, host) into amp_out (2*n_out doubles,
+ * re/im, host, caller-owned), each alpha the reduced history sum of Eq. 7
+ * evaluated by Algorithm 2 at autotuned cuts (Eq. 8), with threshold eps
+ * (0 = exact; eps > 0 drops branches below eps, Sec. IV-A Observation 3).
+ * Synchronous: plans, copies to the device, runs the kernels on the legacy
+ * default stream of the current device and copies back.  Device memory is
+ * allocated and freed inside the call.  Errors: FS_ERR_INVALID (NULL
+ * pointers, bits beyond the register), FS_ERR_TOO_LARGE (2^A not
+ * enumerable), FS_ERR_NOMEM / FS_ERR_CUDA. */
 FS_API int fs_amplitudes(fs_circuit* c, const uint64_t* outputs, size_t n_out, double eps,
                   double* amp_out);
 
-/* ---- batches: many circuits and outputs in one persistent launch ---- */
+/* ---- batches: many circuits and outputs in one persistent launch --------
+ * A batch is the device form of the paper's output decomposition (Sec.
+ * IV-D, Observations 5-6): every (output, input) pair of every job is an
+ * independent work unit, and one persistent kernel drains a cost-sorted
+ * tile queue in place of the server-worker balancer. */
 
+/* New empty batch in *out (host object, freed by fs_batch_destroy): the
+ * request queue of Sec. IV-D. */
 FS_API int fs_batch_create(fs_batch** out);
+/* Frees a batch of Sec. IV-D (NULL accepted); device workspaces stay the
+ * caller's. */
 FS_API int fs_batch_destroy(fs_batch* b);
 
-/* Batch options (may be NULL for defaults); call before fs_batch_plan. */
+/* CUDA device of the batch (Sec. IV-D: output shards may live on different
+ * devices): plan, upload, run, finish and the feature query make it current
+ * for their CUDA calls and restore the caller's device afterwards.  -1 (the
+ * default) uses whatever device is current at each call.  Changing it drops
+ * the plan.  FS_ERR_INVALID for a device index out of range. */
+FS_API int fs_batch_set_device(fs_batch* b, int32_t device);
+
+/* Batch options (may be NULL for defaults); call before fs_batch_plan.  The
+ * split is the checkpoint partition of Sec. IV-C (autotuned on Eq. 8, fixed,
+ * or none = Algorithm 1). */
 FS_API int fs_batch_set_options(fs_batch* b, const fs_options* opt);
 
-/* Adds a job: circuit c (its current input state), n_out outputs (host,
- * copied), threshold eps.  *job_id receives the job's index; its amplitudes
+/* Adds a job (Eq. 2 for one circuit): circuit c (its current input state),
+ * n_out outputs (host, copied), threshold eps (Sec. IV-A, Observation 3).  *job_id receives the job's index; its amplitudes
  * occupy amp_out[2*offset .. 2*(offset+n_out)) where offset is the sum of
  * n_out over earlier jobs. */
 FS_API int fs_batch_add(fs_batch* b, fs_circuit* c, const uint64_t* outputs, size_t n_out,
                  double eps, uint32_t* job_id);
 
-/* Fixes the cuts (c1, c2) of one job, overriding the batch's split option
+/* Fixes the checkpoint cuts (c1, c2) of one job (Sec. IV-C, Algorithm 2),
+ * overriding the batch's split option
  * (both -1 restores it); 0 <= c1 <= c2 <= n_gates is checked at plan time.
  * Call before fs_batch_plan. */
 FS_API int fs_batch_set_cuts(fs_batch* b, uint32_t job, int32_t c1, int32_t c2);
 
-/* Compiles every job (programs, autotuned cuts, tile queue) and reports the
+/* Compiles every job -- evaluation-order program of the backward sweep
+ * (Sec. IV-A), cuts autotuned on Eq. 8 under the device's memory bounds
+ * (Sec. IV-C), cost-sorted tile queue (Observation 6) -- and reports the
  * device workspace size in bytes (256-byte aligned sub-buffers).  Planning
  * again releases the generated kernel of the previous plan: graphs captured
  * from fs_batch_run before must be captured again after the next upload. */
 FS_API int fs_batch_plan(fs_batch* b, size_t* workspace_bytes);
 
-/* Copies the planned static data (programs, bit strings, tile list) into the
+/* Staging of the boundary data (Sec. IV-D; the per-pair input and output
+ * bit strings of Algorithm 2's InitializeState): copies the planned static
+ * data (programs, bit strings, tile list) into the
  * caller's device workspace d_ws (at least workspace_bytes, 256-byte
  * aligned) on stream (a cudaStream_t, NULL = legacy default stream).  The
  * first upload of a plan builds the straight-line kernel (engine 0), stages
@@ -227,7 +261,8 @@ FS_API int fs_batch_plan(fs_batch* b, size_t* workspace_bytes);
  * the same plan. */
 FS_API int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream);
 
-/* Enqueues one evaluation of every job on stream: counter reset, prefix
+/* Algorithm 2 for every (output, input) pair of every job, summed per
+ * output by Eq. 2.  Enqueues one evaluation of every job on stream: counter reset, prefix
  * expansion (checkpoint table), persistent history kernel over the atomic
  * tile queue, fixed-order reduction into d_amp_out (device, 2 * total
  * outputs doubles).  Asynchronous and free of host synchronisation, so it
@@ -236,7 +271,10 @@ FS_API int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* strea
 FS_API int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream);
 
 /* Waits for stream, reads the device error word and the per-job counters
- * (fs_stats array of capacity cap, host) of the last run. */
+ * (fs_stats array of capacity cap, host) of the last run: the candidate,
+ * completed and valid history counts of Eq. 7 and the gate visits of
+ * Eq. 8.  Errors found on the device: FS_ERR_BAD_PROGRAM (an opcode the
+ * interpreter does not know), FS_ERR_TIMEOUT (a bounded wait gave up). */
 FS_API int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size_t cap);
 
 /* The CUDA C++ source of the straight-line engine for the planned batch:
@@ -248,33 +286,42 @@ FS_API int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stat
 FS_API int fs_batch_generated_source(const fs_batch* b, char* buf, size_t cap, size_t* len);
 
 /* Bytes fs_batch_upload copies host-to-device (programs, bit strings,
- * descriptors, tile list) for the planned batch. */
+ * descriptors, tile list) for the planned batch: the boundary staging of
+ * Sec. IV-D, reported for end-to-end throughput. */
 FS_API int fs_batch_upload_bytes(const fs_batch* b, size_t* bytes);
 
 /* Engine actually used by the last fs_batch_upload (0 straight-line, 1
  * interpreter) and the milliseconds spent generating and compiling the
- * straight-line kernel. */
+ * straight-line kernel (the AdvanceCheckpoint regions of Algorithm 2 as
+ * generated code).  FS_ERR_STATE before the first upload. */
 FS_API int fs_batch_engine(const fs_batch* b, uint32_t* engine, double* compile_ms);
 
-/* Total outputs over the jobs added so far. */
+/* Total outputs over the jobs added so far (the requested set B_out of
+ * Sec. IV-D, summed over jobs). */
 FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
 
-/* Number of kernel launches fs_batch_run enqueues (prefix levels or the
+/* Launch accounting of Algorithm 2's stages: the number of kernel launches
+ * fs_batch_run enqueues (prefix levels or the
  * flat prefix, the two reduction kernels, the tiled history kernel when any
  * job is exact, and per pruned job a learned-prune launch if attached plus
  * count/scan/write compaction (the write also records each pair's live
  * range) and the history over live entries). */
 FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
 
-/* Average duration of the history kernel of the last fs_batch_run that
- * recorded events (enabled by fs_batch_time_kernels), in milliseconds. */
+/* Stage timing (the paper times its kernel per output, Fig. 11; here per
+ * stage of Algorithm 2).  enable != 0 makes fs_batch_run record CUDA events
+ * around its stages (as event nodes when the stream is being captured). */
 FS_API int fs_batch_time_kernels(fs_batch* b, int enable);
 /* Milliseconds of the five stages of the last timed run: prefix expansion,
- * learned pruning, compaction, history, reduction (ms: 5 floats, host). */
+ * learned pruning, compaction, history, reduction (ms: 5 floats, host).
+ * FS_ERR_STATE when no timed run was recorded. */
 FS_API int fs_batch_stage_ms(fs_batch* b, float* ms);
+/* Milliseconds of the last timed run's prefix expansion, history and
+ * reduction stages (each pointer may be NULL). */
 FS_API int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, float* reduce_ms);
 
-/* Per-region opcode histogram of a planned job: counts[r * FS_N_OPCODES + k]
+/* Per-region opcode histogram of a planned job (the G_p, G_r, G_s of Eq. 8
+ * broken down by gate role, Sec. II-A): counts[r * FS_N_OPCODES + k]
  * for region r (0 prefix, 1 root, 2 suffix) and opcode k, into a host array
  * of 3 * FS_N_OPCODES uint32_t.  Opcode numbering is the library's internal
  * one (1 = X, 2 = MCX, 3 = SWAP, 4 = PERM1, 5 = PERM2, 6 = DIAG1, 7 = PH1,
@@ -283,7 +330,8 @@ FS_API int fs_batch_kernel_ms(fs_batch* b, float* prefix_ms, float* history_ms, 
 #define FS_N_OPCODES 16
 FS_API int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* counts);
 
-/* Algorithmic work of one execution of each region (0 prefix, 1 root,
+/* Algorithmic work (Eq. 8 counts gate visits; this weighs each visit by
+ * its instructions) of one execution of each region (0 prefix, 1 root,
  * 2 suffix) of a planned job, as integer instructions on the register state
  * and FP64 instructions, from the job's program (control-mask words that are
  * not all zero, factor forms); index 3 is the work per completed leaf (chi
@@ -292,10 +340,12 @@ FS_API int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* coun
  * FP64 rooflines. */
 FS_API int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, double* fp64_ops);
 
-/* Register width (32-bit words: 1, 2 or 4) of a planned job's state. */
+/* Register width (32-bit words: 1, 2 or 4) of a planned job's state (the
+ * internal-wire values of Sec. II-A held as a bit register). */
 FS_API int fs_batch_job_words(const fs_batch* b, uint32_t job, uint32_t* words);
 
-/* Measures, on the current device, the sustained FP64 FMA rate (FMA/s) and
+/* Roofline denominators (no counterpart in the paper).  Measures, on the
+ * current device, the sustained FP64 FMA rate (FMA/s) and
  * the 32-bit integer logic rate (ops/s) with short probe kernels, and
  * reports the SM count.  Allocates and frees 256 bytes of device memory. */
 FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms);
@@ -318,7 +368,9 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
  * artificial sources after the prefix. */
 #define FS_MLP_PARAMS 18817
 
-/* y[i] = MLP(x[i]) for n rows of 16 FP32 features (device pointers; x rows
+/* Scoring (learned pruning has no counterpart in the paper; it scores the
+ * checkpoint entries of Algorithm 2, Sec. IV-C).
+ * y[i] = MLP(x[i]) for n rows of 16 FP32 features (device pointers; x rows
  * 16-byte aligned, else FS_ERR_INVALID).  Asynchronous on stream; returns
  * FS_ERR_CUDA on a launch error.  The scoring kernel bounds its waits on the
  * tensor cores; in the batch path a wait that gives up is reported as
@@ -326,36 +378,75 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
  * rows of the tiles it did not finish unwritten. */
 FS_API int fs_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream);
 
-/* Loss mean((y - target)^2) and its gradient: d_grad receives FS_MLP_PARAMS
+/* Training of the pruner (no counterpart in the paper; targets are exact
+ * subtree sums of Algorithm 2's checkpoint entries, Sec. IV-C).
+ * Loss mean((y - target)^2) and its gradient: d_grad receives FS_MLP_PARAMS
  * gradient values followed by the loss (device, FS_MLP_PARAMS + 1 floats;
  * zeroed by the call).  Gradients are accumulated with atomics (summation
  * order not fixed). */
 FS_API int fs_mlp_grad(const float* d_params, const float* d_x, const float* d_target, uint64_t n,
                        float* d_grad, void* stream);
 
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 parameters with
+/* Training of the pruner (no counterpart in the paper).
+ * One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 parameters with
  * moment buffers d_m, d_v (device, FS_MLP_PARAMS floats each); step >= 1. */
 FS_API int fs_mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_grad, float lr, int32_t step,
                        void* stream);
 
-/* Features of every checkpoint entry of a job after a run (entries = pairs x
+/* Pruner inputs (no counterpart in the paper) of the checkpoint entries
+ * (sigma_p, beta_p) of Algorithm 2 (Sec. IV-C).
+ * Features of every checkpoint entry of a job after a run (entries = pairs x
  * 2^A_p, 16 floats each, device; bottom entries get NaN in feature 0). */
 FS_API int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, void* stream);
 
-/* Logging runs: makes the history kernel write each (prefix, root) item's
+/* Training targets of the pruner (no counterpart in the paper; S_i is the
+ * exact sum over one checkpoint entry's root and suffix completions,
+ * Algorithm 2): d_target[i] = max(log10 |S_i|, floor_log10)
+ * for n logged subtree sums S_i (d_sums: n x (re, im) doubles, device, as
+ * written by a logging run; d_target: n floats, device), computed in FP64
+ * and rounded to FP32; an exactly zero sum gives the floor.  Asynchronous on
+ * stream.  FS_ERR_INVALID for NULL pointers or a non-finite floor. */
+FS_API int fs_mlp_targets(const double* d_sums, uint64_t n, double floor_log10, float* d_target, void* stream);
+
+/* Logging runs (no counterpart in the paper; the items are Algorithm 2's
+ * (h_p, h_r) loop iterations, Sec. IV-C): makes the history kernel write each (prefix, root) item's
  * exact subtree sum (re, im doubles) into d_log (device, 2 x items doubles,
  * items from fs_batch_log_items).  With a fixed split c1 = c2 the items are
  * the checkpoint entries.  Call before fs_batch_upload; NULL turns it off. */
 FS_API int fs_batch_log_subtrees(fs_batch* b, uint32_t job, double* d_log);
+/* Items of a planned job: pairs x 2^(A_p + A_r), the (h_p, h_r) iterations
+ * of Algorithm 2 (Sec. IV-C), i.e. the length of its logging buffer.
+ * FS_ERR_STATE before fs_batch_plan. */
 FS_API int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items);
 
-/* Attaches a trained pruner (device parameters, threshold tau on the
+/* Learned pruning at the checkpoint boundary of Algorithm 2 (no counterpart
+ * in the paper; an alternative to the threshold of Sec. IV-A Observation 3).
+ * Attaches a trained pruner (device parameters, threshold tau on the
  * predicted log10 |subtree sum|) to a job; fs_batch_run then scores and cuts
  * checkpoint entries between the prefix and history kernels.  Call before
  * fs_batch_plan (it changes the job's layout); NULL detaches it.  Jobs with a
  * pruner or eps > 0 run the history over the compacted list of live
  * checkpoint entries, so cut entries cost nothing downstream. */
 FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau);
+
+/* ---- failure detection (no counterpart in the paper) ----------------------
+ * Bounded device waits: every wait of the tensor-core scoring kernel on an
+ * MMA-completion barrier gives up after `polls` polls, records
+ * FS_ERR_TIMEOUT for fs_batch_finish, issues no further MMA and waits
+ * (bounded) for the MMAs already committed before releasing its tensor
+ * memory, so the context stays usable.  polls < 0 restores the default
+ * (2^22); 0 makes every wait give up at once (a test of that path).
+ * Process-wide; set it while no batch is running.  FS_ERR_INVALID above
+ * 2^32 - 1. */
+FS_API int fs_set_wait_limit(int64_t polls);
+
+/* Byte offset of a planned job's op program (16-byte ops in the evaluation
+ * order of the backward sweep, Sec. IV-A)
+ * inside the workspace, and its op count: lets a caller inspect the uploaded
+ * program, or corrupt it on purpose to test the device-side opcode check
+ * (the interpreter engine reports an unknown opcode as FS_ERR_BAD_PROGRAM
+ * from fs_batch_finish).  FS_ERR_STATE before fs_batch_plan. */
+FS_API int fs_batch_program_offset(const fs_batch* b, uint32_t job, size_t* offset, size_t* n_ops);
 
 /* ---- allocation-free variant ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
@@ -374,7 +465,10 @@ FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params,
  * message giving both sizes.
  *   - The first call on a device looks up that array's device address (once
  *     per device, with the device current); make that first call before any
- *     stream capture.
+ *     stream capture.  Under CUDA's lazy module loading that first call may
+ *     also load this part of the library onto the device, which is when the
+ *     device footprint grows by the array and the kernel code; later calls
+ *     leave free device memory unchanged.
  *   - Every call uses the same array and leaves its contents behind; the
  *     counters that must start at zero are cleared by each call.  Calls whose
  *     GPU work overlaps (other host threads, or several streams) race on the

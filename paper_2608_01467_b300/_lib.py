@@ -102,6 +102,10 @@ SIGNATURES = {
     "fs_batch_set_pruner": (ctypes.c_int, [vp, ctypes.c_uint32, vp, ctypes.c_float]),
     "fs_amplitudes_noalloc": (ctypes.c_int, [vp, P(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_double,
                                              P(ctypes.c_double), vp]),
+    "fs_batch_set_device": (ctypes.c_int, [vp, ctypes.c_int32]),
+    "fs_batch_program_offset": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_size_t), P(ctypes.c_size_t)]),
+    "fs_mlp_targets": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, vp, vp]),
+    "fs_set_wait_limit": (ctypes.c_int, [ctypes.c_int64]),
 }
 NOALLOC_SCRATCH_BYTES = 16 << 20
 MLP_PARAMS = 18817

@@ -140,11 +140,13 @@ class Batch:
 
     def __init__(self, split: str = "auto", c1: int = 0, c2: int = 0,
                  table_budget_bytes: int = 0, min_items: int = 0, max_items: int = 0,
-                 engine: str = "straight", prefix: str = "auto"):
+                 engine: str = "straight", prefix: str = "auto", device: int = -1):
         L = _lib.load()
         h = ctypes.c_void_p()
         check(L.fs_batch_create(ctypes.byref(h)))
         self._h = h
+        if device >= 0:
+            check(L.fs_batch_set_device(self._h, int(device)))
         opt = fs_options()
         opt.split = {"auto": 0, "fixed": 1, "none": 2}[split]
         opt.c1, opt.c2 = c1, c2
@@ -258,6 +260,12 @@ class Batch:
             out[name] = {_lib.OPCODES[k]: arr[r * _lib.N_OPCODES + k]
                          for k in _lib.OPCODES if arr[r * _lib.N_OPCODES + k]}
         return out
+
+    def program_offset(self, job: int):
+        """(byte offset in the workspace, op count) of a planned job's program."""
+        off, n = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        check(_lib.load().fs_batch_program_offset(self._h, job, ctypes.byref(off), ctypes.byref(n)))
+        return off.value, n.value
 
     def generated_source(self) -> str:
         """CUDA C++ of the straight-line engine for the planned batch."""

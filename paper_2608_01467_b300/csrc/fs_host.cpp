@@ -431,6 +431,26 @@ struct Job {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Makes a device current for the lifetime of the guard and restores the
+// caller's device afterwards (no-op for device < 0 or when it already is).
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int device)
+    {
+        if (device < 0) return;
+        int cur = 0;
+        err = cudaGetDevice(&cur);
+        if (err != cudaSuccess || cur == device) return;
+        err = cudaSetDevice(device);
+        if (err == cudaSuccess) prev = cur;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 struct fs_batch {
@@ -455,6 +475,7 @@ struct fs_batch {
     size_t h_words_bytes = 0;
     uint64_t n_finishes = 0;
     bool no_host_alloc = false;         // set by the allocation-free entry point
+    int device = -1;                    // CUDA device of the batch (-1: the caller's current one)
     std::vector<uint2> tiles;
     uint64_t total_prefix = 0, total_out = 0;
     int grid = 0, compact_grid = 0;
@@ -734,6 +755,8 @@ int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float 
 int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, void* stream)
 {
     if (!b || !d_ws || !d_features) return fail(FS_ERR_INVALID, "NULL argument");
+    DeviceGuard dg_(b->device);
+    if (dg_.err != cudaSuccess) return cuda_fail(dg_.err, "cudaSetDevice(batch device)");
     if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "no run on this workspace");
     if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
     const Job& j = b->jobs[job];
@@ -793,8 +816,9 @@ int fs_batch_total_outputs(const fs_batch* b, size_t* n)
     return FS_OK;
 }
 
-static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused,
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, int dfrom, bool fused,
                         bool hoisted = false);
+static int job_defer_from(const Job& j, bool straight);
 
 // Rates of the prefix cost model (work-model integer ops and FP64
 // instructions per second, HBM bytes per second, seconds per launch),
@@ -804,6 +828,8 @@ constexpr double kModelIntOps = 2.5e13, kModelFp64Ops = 5.0e11, kModelBytes = 5.
 int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
 {
     if (!b || !workspace_bytes) return fail(FS_ERR_INVALID, "NULL argument");
+    DeviceGuard dg_(b->device);
+    if (dg_.err != cudaSuccess) return cuda_fail(dg_.err, "cudaSetDevice(batch device)");
     const uint64_t budget = b->opt.table_budget_bytes ? b->opt.table_budget_bytes : (4ull << 30);
     const uint64_t max_items = b->opt.max_items ? b->opt.max_items : (1ull << 28);
     // the parallelism floor never exceeds the ceiling
@@ -819,7 +845,11 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     for (size_t ji = 0; ji < b->jobs.size(); ++ji) {
         Job& j = b->jobs[ji];
         const fs_circuit& C = *j.c;
-        if (C.A > 62) return fail(FS_ERR_TOO_LARGE, "job %zu: A = %d artificial sources: 2^A histories cannot be enumerated", ji, C.A);
+        // exact jobs enumerate 2^A histories per pair; a threshold lets the
+        // suffix skip cut subtrees, so only each region's word must fit
+        if (C.A > 62 && j.eps == 0.0)
+            return fail(FS_ERR_TOO_LARGE, "job %zu: A = %d artificial sources: 2^A histories cannot be enumerated "
+                                          "exactly (a threshold eps > 0 allows up to 102)", ji, C.A);
         j.W = words_for(C.n);
         j.pairs = (uint64_t)j.outs.size() * j.ins.size();
         const int G = (int)C.g.size();
@@ -845,11 +875,18 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
             const uint64_t per_pair = j.pairs ? share / (j.pairs * entry_bytes) : share;
             const int max_ap = per_pair ? std::min(ilog2_floor(per_pair), 40) : 0;
             const int min_apr = j.pairs ? ilog2_ceil((min_items + j.pairs - 1) / j.pairs) : 0;
-            const int max_apr = std::max(0, std::min(40, ilog2_floor(max_items)) -
-                                            ilog2_ceil(std::max<uint64_t>(j.pairs, 1)));
+            int max_apr = std::max(0, std::min(40, ilog2_floor(max_items)) -
+                                      ilog2_ceil(std::max<uint64_t>(j.pairs, 1)));
+            // with a threshold most (prefix, root) items of a live entry are
+            // cut at the first sources of the root: the root adds no more
+            // assignments than the parallelism floor needs, and the suffix
+            // enumerates the rest, skipping cut subtrees
+            if (j.eps > 0.0) max_apr = std::min(max_apr, std::max(max_ap, min_apr));
             if (!autotune(C, max_ap, min_apr, max_apr, j.sp))
                 return fail(FS_ERR_TOO_LARGE, "job %zu: no partition fits the table budget", ji);
         }
+        if (j.sp.As > 62)
+            return fail(FS_ERR_TOO_LARGE, "job %zu: %d artificial sources in the suffix (at most 62)", ji, j.sp.As);
         if (j.sp.Ap + j.sp.Ar + ilog2_ceil(std::max<uint64_t>(j.pairs, 1)) > 40)
             return fail(FS_ERR_TOO_LARGE, "job %zu: too many (prefix, root) items", ji);
         compile(C, j.W, j.sp, j.prog);
@@ -878,13 +915,14 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
                 // boundaries (i, k] runs its ops once per entry of level k,
                 // reads level i and writes level k (32 B per entry) and costs
                 // one launch; a single segment is the flat prefix
-                const bool deferred = b->opt.engine == 0 && j.eps == 0.0, fused = b->opt.engine == 0;
+                const int dfrom = job_defer_from(j, b->opt.engine == 0);
+                const bool fused = b->opt.engine == 0;
                 std::vector<double> best(m + 1, 1e300);
                 best[0] = 0.0;
                 for (size_t k = 1; k <= m; ++k)
                     for (size_t i = 0; i < k; ++i) {
                         double io = 0, fo = 0;
-                        region_work(j, E[i], E[k], io, fo, deferred, fused);
+                        region_work(j, E[i], E[k], io, fo, dfrom, fused);
                         const double n_out = std::ldexp((double)j.pairs, Abits[k]);
                         const double n_in = i ? std::ldexp((double)j.pairs, Abits[i]) : 0.0;
                         const double t = n_out * (io / kModelIntOps + fo / kModelFp64Ops) +
@@ -1024,6 +1062,8 @@ int fs_batch_generated_source(const fs_batch* b, char* buf, size_t cap, size_t* 
 int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
 {
     if (!b || !d_ws) return fail(FS_ERR_INVALID, "NULL argument");
+    DeviceGuard dg_(b->device);
+    if (dg_.err != cudaSuccess) return cuda_fail(dg_.err, "cudaSetDevice(batch device)");
     if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
     if (ws_bytes < b->ws_bytes) return fail(FS_ERR_INVALID, "workspace of %zu bytes < %zu needed", ws_bytes, b->ws_bytes);
     if (((uintptr_t)d_ws) & 255) return fail(FS_ERR_INVALID, "workspace must be 256-byte aligned");
@@ -1193,6 +1233,8 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
 int fs_batch_time_kernels(fs_batch* b, int enable)
 {
     if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    DeviceGuard dg_(b->device);
+    if (dg_.err != cudaSuccess) return cuda_fail(dg_.err, "cudaSetDevice(batch device)");
     if (enable && !b->ev[0])
         for (auto& e : b->ev) CUDA_TRY(cudaEventCreate(&e));
     b->timing = enable != 0;
@@ -1241,6 +1283,8 @@ int fs_batch_stage_ms(fs_batch* b, float* ms)
 int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
 {
     if (!b || !d_ws || (!d_amp_out && b->total_out)) return fail(FS_ERR_INVALID, "NULL argument");
+    DeviceGuard dg_(b->device);
+    if (dg_.err != cudaSuccess) return cuda_fail(dg_.err, "cudaSetDevice(batch device)");
     if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "fs_batch_upload on this workspace must come first");
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char* base = (unsigned char*)d_ws;
@@ -1316,6 +1360,8 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
 int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size_t cap)
 {
     if (!b || !d_ws) return fail(FS_ERR_INVALID, "NULL argument");
+    DeviceGuard dg_(b->device);
+    if (dg_.err != cudaSuccess) return cuda_fail(dg_.err, "cudaSetDevice(batch device)");
     if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "no run on this workspace");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nj = b->jobs.size();
@@ -1406,12 +1452,30 @@ static void factor_cost(double2 f, double& iops, double& fops)
 
 static bool same2(double2 a, double2 b) { return a.x == b.x && a.y == b.y; }
 
-// deferred: the straight-line engine in exact mode, where two-valued factors
-// are counted per class (1 integer add) and applied once per region (one
-// complex product per class).
+// First evaluation position whose two-valued factors the straight-line
+// engine defers (counts per class, one product per region): 0 in exact
+// mode, after the last |beta| test with a threshold, none for the
+// interpreter (G + 1).
+static int job_defer_from(const Job& j, bool straight)
+{
+    const int G = (int)j.prog.ops.size();
+    if (!straight) return G + 1;
+    if (j.eps == 0.0) return 0;
+    int last = -1;
+    for (int e = 0; e < G; ++e) {
+        const fs::Op& op = j.prog.ops[e];
+        const bool br = op.code == fs::OP_H || op.code == fs::OP_BR1 || op.code == fs::OP_BR2;
+        if (br && (op.s0 >= 0 || (op.code == fs::OP_BR2 && op.s1 >= 0))) last = e;
+    }
+    return last + 1;
+}
+
+// Ops at positions >= dfrom are deferred: the straight-line engine counts
+// their two-valued factors per class (1 integer add) and applies each class
+// once per region (one complex product per class).
 // hoisted: the straight-line root and suffix, where a class whose factors
 // differ by a unit phase is applied as sign flips and swaps (integer pipe).
-static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, bool deferred, bool fused,
+static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, int dfrom, bool fused,
                         bool hoisted)
 {
     const int W = j.W;
@@ -1436,7 +1500,7 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
             e += run.len - 1;
             continue;
         }
-        if (deferred) {
+        if (e >= dfrom) {
             const double2* F = j.prog.fac.data() + op0.aux;
             bool z = false;
             switch (op0.code) {
@@ -1481,7 +1545,13 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
         case fs::OP_MCNEG: iops += test + 1; break;
         case fs::OP_DIAG2: iops += 3; fops += 4; break;
         case fs::OP_H: iops += 4; fops += 2; break;
-        case fs::OP_BR1: iops += 5; fops += 4; break;
+        case fs::OP_BR1: {
+            const bool sym = same2(F[0], F[3]) && same2(F[1], F[2]);
+            const bool ri = (F[0].x == 0.0 || F[0].y == 0.0) && (F[1].x == 0.0 || F[1].y == 0.0);
+            if (sym && ri) { iops += 7; fops += 2; }   // one real scalar product and a rotation
+            else { iops += 5; fops += 4; }
+            break;
+        }
         case fs::OP_BR2: iops += 10; fops += 4; break;
         default: break;
         }
@@ -1503,11 +1573,11 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
     const Job& j = b->jobs[job];
     const int G = (int)j.prog.ops.size();
     const int cuts[4] = {0, j.sp.c1, j.sp.c2, G};
-    const bool deferred = b->opt.engine == 0 && j.eps == 0.0;
+    const int dfrom = job_defer_from(j, b->opt.engine == 0);
     const bool fused = b->opt.engine == 0;   // the straight-line engine fuses incrementer cascades
     for (int r = 0; r < 3; ++r) {
         double i = 0, f = 0;
-        region_work(j, cuts[r], cuts[r + 1], i, f, deferred, fused, r > 0 && deferred);
+        region_work(j, cuts[r], cuts[r + 1], i, f, dfrom, fused, r > 0 && dfrom <= G);
         int_ops[r] = i;
         fp64_ops[r] = f;
     }
@@ -1517,7 +1587,7 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
         double i = 0, f = 0;
         for (const fs::PrefixLevel& L : j.levels) {
             double li = 0, lf = 0;
-            region_work(j, L.e0, L.e1, li, lf, deferred, fused);
+            region_work(j, L.e0, L.e1, li, lf, dfrom, fused);
             i += li * std::ldexp(1.0, L.a_next - j.sp.Ap);
             f += lf * std::ldexp(1.0, L.a_next - j.sp.Ap);
         }
@@ -1545,6 +1615,49 @@ int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms)
     int n = 0;
     CUDA_TRY(fs::probe_peaks(dfma_per_s, int_ops_per_s, &n));
     *sms = n;
+    return FS_OK;
+}
+
+int fs_batch_set_device(fs_batch* b, int32_t device)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (device < -1) return fail(FS_ERR_INVALID, "device must be >= 0 (or -1: the current device)");
+    if (device >= 0) {
+        int n = 0;
+        const cudaError_t e = cudaGetDeviceCount(&n);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+        if (device >= n) return fail(FS_ERR_INVALID, "device %d out of range (%d devices)", device, n);
+    }
+    if (device != b->device) {
+        b->device = device;
+        b->planned = b->uploaded = false;   // grid sizes and the generated module are per device
+        b->drop_jit();
+    }
+    return FS_OK;
+}
+
+int fs_batch_program_offset(const fs_batch* b, uint32_t job, size_t* offset, size_t* n_ops)
+{
+    if (!b || !offset || !n_ops) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!b->planned) return fail(FS_ERR_STATE, "fs_batch_plan must come first");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    *offset = b->jobs[job].o_ops;
+    *n_ops = b->jobs[job].prog.ops.size();
+    return FS_OK;
+}
+
+int fs_mlp_targets(const double* d_sums, uint64_t n, double floor_log10, float* d_target, void* stream)
+{
+    if (n && (!d_sums || !d_target)) return fail(FS_ERR_INVALID, "NULL argument");
+    if (!std::isfinite(floor_log10)) return fail(FS_ERR_INVALID, "the floor must be finite");
+    CUDA_TRY(fs::mlp_targets(d_sums, (unsigned long long)n, floor_log10, d_target, (cudaStream_t)stream));
+    return FS_OK;
+}
+
+int fs_set_wait_limit(int64_t polls)
+{
+    if (polls > 0xffffffffll) return fail(FS_ERR_INVALID, "at most 2^32 - 1 polls");
+    fs::mlp_set_wait_limit(polls < 0 ? fs::mlp_default_wait_limit() : (uint32_t)polls);
     return FS_OK;
 }
 

@@ -145,6 +145,11 @@ cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, f
                          unsigned long long n_entries, cudaStream_t s);
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
                               float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s);
+cudaError_t mlp_targets(const double* d_sums, unsigned long long n, double floor_v, float* d_t, cudaStream_t s);
+// Polls of a bounded tensor-core wait before it gives up (process-wide;
+// change it only while no scoring kernel is being launched).
+void mlp_set_wait_limit(uint32_t polls);
+uint32_t mlp_default_wait_limit();
 // Raises the dynamic shared-memory limit of the tensor-core scoring kernels
 // (outside any stream capture, before their first launch).
 cudaError_t mlp_prepare();

@@ -69,7 +69,21 @@ __device__ __forceinline__ double2 qrot(double2 a, u32 r)
 }
 __device__ __forceinline__ double2 cre(double2 a, double r) { return make_double2(__dmul_rn(a.x, r), __dmul_rn(a.y, r)); }
 __device__ __forceinline__ double2 cim(double2 a, double s) { return make_double2(dneg(__dmul_rn(a.y, s)), __dmul_rn(a.x, s)); }
-__device__ __forceinline__ bool cut(double2 a, double eps2) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)) < eps2; }
+// |a|^2 < eps2, with |a|^2 formed as fma(re, re, im * im); both sides are
+// non-negative doubles, so their bit patterns compare like the values (an
+// integer compare instead of an FP64 one)
+__device__ __forceinline__ bool cut(double2 a, double eps2)
+{
+    const double m = __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y));
+    return __double_as_longlong(m) < __double_as_longlong(eps2);
+}
+// a * f for a real f, then times i when rot: the product by a purely real or
+// purely imaginary factor, the same doubles as cmul by (f, 0) or (0, f)
+__device__ __forceinline__ double2 crot(double2 a, double f, bool rot)
+{
+    const double2 p = make_double2(__dmul_rn(a.x, f), __dmul_rn(a.y, f));
+    return rot ? make_double2(dneg(p.y), p.x) : p;
+}
 __device__ __forceinline__ double2 sel2(bool c, double2 a, double2 b) { return c ? a : b; }
 
 __device__ __forceinline__ u64 warp_sum_u64(u64 v)
@@ -169,6 +183,85 @@ __device__ __forceinline__ bool is_bottom(double x)
     return hi > 0x7ff00000u || (hi == 0x7ff00000u && (unsigned)__double2loint(x) != 0u);
 }
 
+// Leaves of one root checkpoint (state st, amplitude amp): the suffix for
+// every h_s in increasing order, skipping the subtree of a cut history, the
+// chi test at the input boundary.  A stacked suffix (threshold jobs) keeps
+// the state after each of its source ops (a checkpoint per source, the
+// per-source limit of Algorithm 2's regions) and restarts the next history
+// at the first source whose bit changed, instead of at the region's start.
+template <class T>
+__device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp, const u32 (&bin)[T::W],
+                                              u64& completed, u64& valid, u64& visits)
+{
+    constexpr int W = T::W;
+    double2 acc = make_double2(0.0, 0.0);
+    typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
+    const hs_t ns = (hs_t)1 << T::As;
+    hs_t hs = 0;
+    if constexpr (T::STACKED) {
+        u32 sst[T::As][W];
+        double2 sam[T::As];
+        int start = 0;
+        while (hs < ns) {
+            u32 st2[W];
+            double2 amp2;
+            if (start == 0) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) st2[j] = st[j];
+                amp2 = amp;
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) st2[j] = sst[start - 1][j];
+                amp2 = sam[start - 1];
+            }
+            const int r2 = T::suffix_from(start, st2, amp2, (u64)hs, bin, visits, sst, sam);
+            hs_t nx;
+            if (r2 < 0) {
+                ++completed;
+                u32 d = 0;
+#pragma unroll
+                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
+                if (d == 0) {
+                    ++valid;
+                    add_kept(acc, amp2);
+                }
+                nx = hs + (hs_t)1;
+            } else {
+                nx = ((hs >> r2) + (hs_t)1) << r2;
+            }
+            if (nx < ns) {
+                // the highest bit that changes names the first source to redo
+                const int msb = sizeof(hs_t) == 4 ? 31 - __clz((u32)(hs ^ nx))
+                                                  : 63 - __clzll((long long)(u64)(hs ^ nx));
+                start = T::As - 1 - msb;
+            }
+            hs = nx;
+        }
+    } else {
+        while (hs < ns) {
+            u32 st2[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) st2[j] = st[j];
+            double2 amp2 = amp;
+            const int r2 = T::suffix(st2, amp2, (u64)hs, bin, visits);
+            if (r2 < 0) {
+                ++completed;
+                u32 d = 0;
+#pragma unroll
+                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
+                if (d == 0) {
+                    ++valid;
+                    add_kept(acc, amp2);
+                }
+                ++hs;
+            } else {
+                hs = ((hs >> r2) + (hs_t)1) << r2;
+            }
+        }
+    }
+    return acc;
+}
+
 // Sum over the valid leaves of one (prefix, root) item: the root once, the
 // suffix for every h_s (skipping cut subtrees), the chi test at the input.
 template <class T>
@@ -196,31 +289,7 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
 #pragma unroll
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 amp = a0;
-    if (T::root(st, amp, hr, bin, visits) < 0) {
-        typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
-        const hs_t ns = (hs_t)1 << T::As;
-        hs_t hs = 0;
-        while (hs < ns) {
-            u32 st2[W];
-#pragma unroll
-            for (int j = 0; j < W; ++j) st2[j] = st[j];
-            double2 amp2 = amp;
-            const int r2 = T::suffix(st2, amp2, (u64)hs, bin, visits);
-            if (r2 < 0) {
-                ++completed;
-                u32 d = 0;
-#pragma unroll
-                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
-                if (d == 0) {
-                    ++valid;
-                    add_kept(acc, amp2);
-                }
-                ++hs;
-            } else {
-                hs = ((hs >> r2) + (hs_t)1) << r2;
-            }
-        }
-    }
+    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T>(st, amp, bin, completed, valid, visits);
     return acc;
 }
 
@@ -298,31 +367,7 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
 #pragma unroll
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 acc = make_double2(0.0, 0.0);
-    if (T::root(st, amp, hr, bin, visits) < 0) {
-        typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
-        const hs_t ns = (hs_t)1 << T::As;
-        hs_t hs = 0;
-        while (hs < ns) {
-            u32 st2[W];
-#pragma unroll
-            for (int j = 0; j < W; ++j) st2[j] = st[j];
-            double2 amp2 = amp;
-            const int r2 = T::suffix(st2, amp2, (u64)hs, bin, visits);
-            if (r2 < 0) {
-                ++completed;
-                u32 d = 0;
-#pragma unroll
-                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
-                if (d == 0) {
-                    ++valid;
-                    add_kept(acc, amp2);
-                }
-                ++hs;
-            } else {
-                hs = ((hs >> r2) + (hs_t)1) << r2;
-            }
-        }
-    }
+    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T>(st, amp, bin, completed, valid, visits);
     return acc;
 }
 
@@ -556,13 +601,53 @@ std::string emit_cascade(const CascadeRun& r, int W)
 // unit phase (B = A, -A, iA or -iA) is applied as that phase to the k-th
 // power (sign flips and swaps on the integer pipe) and its constant A^n is
 // multiplied into *hoist, to be applied once per (output, input) pair.
+// First evaluation position from which factors may be deferred: 0 in exact
+// mode; with a threshold, the position after the last op that tests |beta|
+// (no later test reads the running amplitude, so the remaining factors may
+// be reassociated).
+int defer_from(const JitJobSpec& J)
+{
+    if (J.eps2 == 0.0) return 0;
+    int last = -1;
+    for (int e = 0; e < J.G; ++e) {
+        const Op& op = J.ops[e];
+        const bool br = op.code == OP_H || op.code == OP_BR1 || op.code == OP_BR2;
+        if (br && (op.s0 >= 0 || (op.code == OP_BR2 && op.s1 >= 0))) last = e;
+    }
+    return last + 1;
+}
+
+// Product by a two-valued factor selected by `sel` (0: A, 1: B) when each
+// of A and B is purely real or purely imaginary: one real scalar product
+// and an exact rotation, instead of a general complex product.
+bool real_or_imag(double2 f) { return f.y == 0.0 || f.x == 0.0; }
+std::string mul_two_valued(double2 A, double2 B, const std::string& sel)
+{
+    auto part = [](double2 f) { return f.y == 0.0 ? f.x : f.y; };
+    const bool ra = A.y == 0.0, rb = B.y == 0.0;   // real (else imaginary)
+    std::string rot;
+    if (ra && rb) rot = "false";
+    else if (!ra && !rb) rot = "true";
+    else rot = ra ? "(" + sel + ") != 0u" : "(" + sel + ") == 0u";
+    return "a = crot(a, (" + sel + ") ? " + hexd(part(B)) + " : " + hexd(part(A)) + ", " + rot + ");";
+}
+
+// stacked: the region is cut into segments that each end with an op
+// carrying artificial sources; the generated function (suffix_from) runs
+// the segments from `start` on, saving the state after each segment in
+// sst / sam, so that the next history can restart at the first source whose
+// bit changed.  `low` then starts at the bit of the last source before
+// `start`, and visits count the ops run in this call.
 void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
-                 int e0, int e1, int nbits, bool chi_only = false, std::complex<long double>* hoist = nullptr)
+                 int e0, int e1, int nbits, bool chi_only = false, std::complex<long double>* hoist = nullptr,
+                 bool stacked = false)
 {
     const int W = J.W;
-    const bool defer = J.eps2 == 0.0;
+    const int dfrom = defer_from(J);
     std::vector<FactorClass> cls;
     std::string body;
+    int seg = 0, seg_e0 = e0;   // current segment and its first op
+    if (stacked) body += "    if (start <= 0) {\n";
     auto count = [&](double2 A, double2 B, const std::string& bexpr) {
         const int c = class_of(cls, A, B);
         return "k" + std::to_string(c) + " += (" + bexpr + ");";
@@ -579,7 +664,8 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         const Op& op = J.ops[e];
         const int q0 = op.q0, q1 = op.q1;
         const double2* F = J.fac + op.aux;
-        const std::string visits_cut = "{ visits += " + std::to_string(e - e0 + 1) + "ull; return low; }";
+        const bool defer = e >= dfrom;
+        const std::string visits_cut = "{ visits += " + std::to_string(e - seg_e0 + 1) + "ull; return low; }";
         auto srcbit = [&](int sidx, int q) {
             if (sidx >= 32) return "((u32)(h >> " + std::to_string(sidx) + ") & 1u)";
             return sidx >= 0 ? "((h32 >> " + std::to_string(sidx) + ") & 1u)"
@@ -658,6 +744,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             const bool sym = same_d2(F[0], F[3]) && same_d2(F[1], F[2]);
             c = "{ const u32 o = " + bitexpr(q0) + "; const u32 i = " + srcbit(op.s0, q0) + "; ";
             if (defer && sym && !any_zero) c += count(F[0], F[1], "o ^ i") + " ";
+            else if (sym && real_or_imag(F[0]) && real_or_imag(F[1])) c += mul_two_valued(F[0], F[1], "o ^ i") + " ";
             else c += "a = cmul(a, " + select_factor(F, 4, "(o << 1) | i") + "); ";
             c += flip(q0, "o ^ i");
             if (op.s0 >= 0) c += " low = " + std::to_string(op.s0) + ";";
@@ -696,11 +783,25 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             break;
         }
         if (!c.empty()) body += "    " + c + "\n";
+        const bool carries = (op.code == OP_H || op.code == OP_BR1 || op.code == OP_BR2) &&
+                             (op.s0 >= 0 || (op.code == OP_BR2 && op.s1 >= 0));
+        if (stacked && carries) {
+            // close the segment: checkpoint after this source op
+            const std::string k = std::to_string(seg);
+            for (int j = 0; j < W; ++j)
+                body += "    sst[" + k + "][" + std::to_string(j) + "] = s[" + std::to_string(j) + "];";
+            body += " sam[" + k + "] = a; visits += " + std::to_string(e - seg_e0 + 1) + "ull;\n    }\n";
+            ++seg;
+            seg_e0 = e + 1;
+            if (seg < nbits) body += "    if (start <= " + std::to_string(seg) + ") {\n";
+        }
     }
+    if (stacked && seg < nbits) body += "    }\n";   // (a region whose last op carries no source)
     // 64-bit integer operations run through the FP64 pipe on this part:
     // the enumeration word is read as 32 bits wherever its bits allow
     out += "    const u32 h32 = (u32)h;\n    (void)h32;\n";
-    out += "    int low = " + std::to_string(nbits) + ";\n";
+    out += stacked ? "    int low = " + std::to_string(nbits) + " - start;\n"
+                   : "    int low = " + std::to_string(nbits) + ";\n";
     for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
     out += body;
     if (chi_only && !cls.empty()) {
@@ -735,7 +836,22 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         out += "    a = cmul(a, __ldg(&" + name + "[" + kv + "]));\n";
     }
     if (chi_only && !cls.empty()) out += "    }\n";
-    out += "    visits += " + std::to_string(e1 - e0) + "ull;\n    (void)low;\n    return -1;\n";
+    out += "    visits += " + std::to_string(e1 - seg_e0) + "ull;\n    (void)low;\n    return -1;\n";
+}
+
+// Threshold jobs whose suffix carries at least two artificial sources, one
+// per op, run the stacked suffix (a checkpoint after every source op).
+bool stacked_suffix(const JitJobSpec& J)
+{
+    if (J.eps2 == 0.0 || J.As < 2) return false;
+    int n = 0;
+    for (int e = J.c2; e < J.G; ++e) {
+        const Op& op = J.ops[e];
+        if (op.code == OP_BR2 && op.s0 >= 0 && op.s1 >= 0) return false;
+        const bool br = op.code == OP_H || op.code == OP_BR1 || op.code == OP_BR2;
+        if (br && (op.s0 >= 0 || op.s1 >= 0)) ++n;
+    }
+    return n == J.As;
 }
 
 std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* scales)
@@ -745,9 +861,11 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
     for (size_t j = 0; j < jobs.size(); ++j) {
         const JitJobSpec& J = jobs[j];
         const std::string W = std::to_string(J.W), js = std::to_string(j);
+        const bool stacked = stacked_suffix(J);
         structs += "struct J" + js + " {\n";
         structs += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
                    std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
+        structs += std::string("  static constexpr bool STACKED = ") + (stacked ? "true" : "false") + ";\n";
         const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
         structs += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
         if (J.levels.empty()) emit_region(structs, globals, js + "p", J, 0, J.c1, J.Ap);
@@ -765,6 +883,17 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         std::complex<long double> hoisted(1.0L, 0.0L);
         emit_region(structs, globals, js + "r", J, J.c1, J.c2, J.Ar, false, &hoisted);
         structs += "  }\n";
+        if (stacked) {
+            // the same suffix as per-source segments (its hoisted constant is
+            // the one of `suffix` below: the same tail classes)
+            std::complex<long double> h2(1.0L, 0.0L);
+            structs += "  static __device__ __forceinline__ int suffix_from(int start, u32 (&s)[" + W +
+                       "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits, u32 (&sst)[" +
+                       std::to_string(J.As) + "][" + W + "], double2 (&sam)[" + std::to_string(J.As) +
+                       "]) {\n    (void)h; (void)bin;\n";
+            emit_region(structs, globals, js + "t", J, J.c2, J.G, J.As, true, &h2, true);
+            structs += "  }\n";
+        }
         structs += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
         emit_region(structs, globals, js + "s", J, J.c2, J.G, J.As, true, &hoisted);
         const double2 sc = make_double2((double)hoisted.real(), (double)hoisted.imag());

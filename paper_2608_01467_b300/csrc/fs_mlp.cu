@@ -435,6 +435,20 @@ __device__ void entry_features(const JobDev& J, unsigned long long local, const 
     entry_features_of(J, J.table[local], local, sp, out);
 }
 
+// Training target of one logged subtree sum S (re, im): log10 |S| in FP64,
+// floored (an exactly zero sum gives the floor), rounded to FP32.
+__global__ void targets_kernel(const double2* __restrict__ sums, unsigned long long n, double floor_v,
+                               float* __restrict__ t)
+{
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const double2 v = sums[i];
+        const double mag = hypot(v.x, v.y);
+        const double lg = mag > 0.0 ? log10(mag) : floor_v;
+        t[i] = (float)(lg > floor_v ? lg : floor_v);
+    }
+}
+
 __global__ void features_kernel(const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float* __restrict__ feat,
                                 unsigned long long n)
 {
@@ -461,7 +475,8 @@ __global__ void features_kernel(const JobDev* __restrict__ jobs, int job, Featur
 
 constexpr int TC_THREADS = 256;
 constexpr uint32_t TC_COLS = 256;             // TMEM columns per CTA, 128 per warpgroup
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;  // mbarrier polls before a wait gives up
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;  // default mbarrier polls before a wait gives up
+constexpr uint32_t TC_DRAIN_LIMIT = 1u << 24; // polls for the commit left pending by a give-up
 constexpr int SM_W1 = 0;                      // B of layer 1: 128 n x 16 k
 constexpr int SM_W2 = SM_W1 + 4096;           // B of layer 2: 128 n x 128 k
 constexpr int SM_X = SM_W2 + 32768;           // per warpgroup: 128 rows x 16 k
@@ -591,15 +606,17 @@ __device__ __forceinline__ uint32_t relu_bf16x2(uint64_t a)
     return d;
 }
 
-// Thread 0 of the warpgroup polls the MMA-completion barrier (bounded); the
-// group then learns the outcome together.  False: the wait gave up, the
-// error word has DEV_ERR_TIMEOUT and the group stops.
+// Thread 0 of the warpgroup polls the MMA-completion barrier (at most
+// `limit` polls); the group then learns the outcome together.  False: the
+// wait gave up, the error word has DEV_ERR_TIMEOUT and the group issues no
+// further MMA (the commit it stopped waiting for is drained before the
+// tensor memory is released, see the end of mlp_tc_kernel).
 __device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag, int r,
-                                           int grp, uint32_t* err)
+                                           int grp, uint32_t* err, uint32_t limit)
 {
     if (r == 0) {
         bool ok = false;
-        for (uint32_t i = 0; i < TC_WAIT_LIMIT && !ok; ++i) ok = mbar_try_wait(bar, parity);
+        for (uint32_t i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(bar, parity);
         if (!ok) {
             *abort_flag = 1u;
             if (err) atomicOr(err, DEV_ERR_TIMEOUT);
@@ -616,7 +633,8 @@ __device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t parity, volati
 template <bool PRUNE>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     mlp_tc_kernel(const float* __restrict__ P, const float* __restrict__ X, long long n_rows, float* __restrict__ Y,
-                  const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err)
+                  const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err,
+                  uint32_t wait_limit)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, grp = tid >> 7, r = tid & 127, warp = tid >> 5;
@@ -747,7 +765,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             tc_commit(bar);
         }
         if (PRUNE && nrow < n) cur = J->table[nrow];
-        if (!group_wait(bar, phase, abort_flag, r, grp, err)) break;
+        if (!group_wait(bar, phase, abort_flag, r, grp, err, wait_limit)) break;
         phase ^= 1u;
         // epilogue 1: h1 = bf16(relu(x W1 + b1)) into the layer-2 A operand
 #pragma unroll
@@ -779,7 +797,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         }
         // next tile's X (the layer-1 MMA that read X has completed)
         const bool live_next = tile + tstride < tiles ? stage_x(nrow, cur) : false;
-        if (!group_wait(bar, phase, abort_flag, r, grp, err)) break;
+        if (!group_wait(bar, phase, abort_flag, r, grp, err, wait_limit)) break;
         phase ^= 1u;
         // epilogue 2: y = relu(h1 W2 + b2) . bf16(w3) + b3
         uint64_t acc2 = 0;   // two FP32 partial sums (even, odd columns)
@@ -816,6 +834,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         cuts = warp_sum_cuts(cuts);
         if ((tid & 31) == 0 && cuts) atomicAdd(&J->stats[5], cuts);
     }
+    // A group that gave up left one commit pending (parity `phase`): its MMAs
+    // may still read shared memory and write this group's tensor-memory
+    // columns, so thread 0 of the group waits for that commit (bounded)
+    // before the CTA releases the tensor memory.
+    if (*abort_flag != 0u && r == 0) {
+        bool done = false;
+        for (uint32_t i = 0; i < TC_DRAIN_LIMIT && !done; ++i) done = mbar_try_wait(bar, phase);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -825,6 +851,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     }
 }
 
+// Polls of a bounded tensor-core wait before it gives up (process-wide).
+uint32_t g_wait_limit = TC_WAIT_LIMIT;
+
 template <bool PRUNE>
 cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y, const JobDev* jobs, int job,
                       const FeatureSpec& sp, float tau, uint32_t* err, unsigned long long rows, cudaStream_t s)
@@ -832,7 +861,8 @@ cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y
     const unsigned long long tiles = (rows + 127) / 128;
     unsigned long long blocks = (tiles + 1) / 2;
     if (blocks > 148 * 2) blocks = 148 * 2;
-    mlp_tc_kernel<PRUNE><<<(unsigned)blocks, TC_THREADS, TC_SMEM, s>>>(P, X, n_rows, Y, jobs, job, sp, tau, err);
+    mlp_tc_kernel<PRUNE><<<(unsigned)blocks, TC_THREADS, TC_SMEM, s>>>(P, X, n_rows, Y, jobs, job, sp, tau, err,
+                                                                       g_wait_limit);
     return cudaGetLastError();
 }
 
@@ -878,12 +908,24 @@ cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, f
     return cudaGetLastError();
 }
 
+cudaError_t mlp_targets(const double* d_sums, unsigned long long n, double floor_v, float* d_t, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    unsigned long long blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    targets_kernel<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const double2*>(d_sums), n, floor_v, d_t);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
                               float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s)
 {
     if (n_entries == 0) return cudaSuccess;
     return launch_tc<true>(d_params, nullptr, 0, nullptr, d_jobs, job, sp, tau, d_err, n_entries, s);
 }
+
+void mlp_set_wait_limit(uint32_t polls) { g_wait_limit = polls; }
+uint32_t mlp_default_wait_limit() { return TC_WAIT_LIMIT; }
 
 cudaError_t mlp_prepare()
 {

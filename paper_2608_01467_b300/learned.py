@@ -52,9 +52,12 @@ def adam_step(params, m, v, g, lr: float, step: int):
 
 
 def subtree_targets(log_sums: torch.Tensor) -> torch.Tensor:
-    """log10 |S| of complex subtree sums (re, im pairs), floored."""
-    mag = torch.sqrt(log_sums[:, 0] ** 2 + log_sums[:, 1] ** 2)
-    return torch.clamp(torch.log10(mag + 1e-300), min=TARGET_FLOOR).float()
+    """max(log10 |S|, TARGET_FLOOR) of complex subtree sums (re, im pairs),
+    computed by the library (fs_mlp_targets)."""
+    sums = log_sums.contiguous()
+    t = torch.empty(sums.shape[0], dtype=torch.float32, device=sums.device)
+    check(_lib.load().fs_mlp_targets(_vp(sums), sums.shape[0], TARGET_FLOOR, _vp(t), _stream()))
+    return t
 
 
 def table_data(circuit, inputs, outputs, cut: int, device="cuda"):

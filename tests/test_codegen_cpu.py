@@ -37,6 +37,7 @@ static inline double __fma_rn(double a, double b, double c) { return std::fma(a,
 static inline double __dmul_rn(double a, double b) { return a * b; }
 static inline int __double2hiint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u >> 32); }
 static inline int __double2loint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u & 0xffffffffu); }
+static inline long long __double_as_longlong(double x) { long long u; std::memcpy(&u, &x, 8); return u; }
 static inline double __hiloint2double(int hi, int lo)
 {
     uint64_t u = ((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo;
@@ -73,16 +74,7 @@ int main()
                     for (int j = 0; j < W; ++j) st2[j] = st[j];
                     double2 a2 = a;
                     if (J0::root(st2, a2, hr, bin, visits) >= 0) continue;
-                    for (u64 hs = 0; hs < (1ull << J0::As); ++hs) {
-                        u32 st3[W];
-                        for (int j = 0; j < W; ++j) st3[j] = st2[j];
-                        double2 a3 = a2;
-                        if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
-                        ++completed;
-                        bool ok = true;
-                        for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
-                        if (ok) { sr += a3.x; si += a3.y; ++valid; }
-                    }
+%(suffix_loop)s
                 }
             }
             // c_in times the constant left out of the root and suffix
@@ -154,16 +146,7 @@ int main()
                     for (int j = 0; j < W; ++j) st2[j] = cur[hp].st[j];
                     double2 a2 = cur[hp].a;
                     if (J0::root(st2, a2, hr, bin, visits) >= 0) continue;
-                    for (u64 hs = 0; hs < (1ull << J0::As); ++hs) {
-                        u32 st3[W];
-                        for (int j = 0; j < W; ++j) st3[j] = st2[j];
-                        double2 a3 = a2;
-                        if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
-                        ++completed;
-                        bool ok = true;
-                        for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
-                        if (ok) { sr += a3.x; si += a3.y; ++valid; }
-                    }
+%(suffix_loop)s
                 }
             }
             const double cr = cre_[s] * scale.x - cim_[s] * scale.y, ci = cre_[s] * scale.y + cim_[s] * scale.x;
@@ -175,6 +158,50 @@ int main()
     return 0;
 }
 """
+
+
+# the suffix enumeration of the driver: every h_s tried in turn (the
+# generated `suffix` returns at a cut), or, for a stacked suffix, the
+# device's restart loop: skip the subtree of a cut history and restart the
+# next one at the first source whose bit changed, from the saved state
+SUFFIX_PLAIN = """
+                    for (u64 hs = 0; hs < (1ull << J0::As); ++hs) {
+                        u32 st3[W];
+                        for (int j = 0; j < W; ++j) st3[j] = st2[j];
+                        double2 a3 = a2;
+                        if (J0::suffix(st3, a3, hs, bin, visits) >= 0) continue;
+                        ++completed;
+                        bool ok = true;
+                        for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
+                        if (ok) { sr += a3.x; si += a3.y; ++valid; }
+                    }"""
+SUFFIX_STACKED = """
+                    {
+                        u32 sst[J0::As][W];
+                        double2 sam[J0::As];
+                        int start = 0;
+                        const u64 ns = 1ull << J0::As;
+                        u64 hs = 0;
+                        while (hs < ns) {
+                            u32 st3[W];
+                            double2 a3;
+                            for (int j = 0; j < W; ++j) st3[j] = start ? sst[start - 1][j] : st2[j];
+                            a3 = start ? sam[start - 1] : a2;
+                            const int r2 = J0::suffix_from(start, st3, a3, hs, bin, visits, sst, sam);
+                            u64 nx;
+                            if (r2 < 0) {
+                                ++completed;
+                                bool ok = true;
+                                for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
+                                if (ok) { sr += a3.x; si += a3.y; ++valid; }
+                                nx = hs + 1;
+                            } else {
+                                nx = ((hs >> r2) + 1) << r2;
+                            }
+                            if (nx < ns) start = J0::As - 1 - (63 - __builtin_clzll(hs ^ nx));
+                            hs = nx;
+                        }
+                    }"""
 
 
 def _words(v, W):
@@ -208,6 +235,8 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
                   ins=", ".join(_words(v, W) for v, _ in inputs),
                   cre=", ".join(repr(complex(c).real) for _, c in inputs),
                   cim=", ".join(repr(complex(c).imag) for _, c in inputs), sx=sx, sy=sy)
+    stacked = "STACKED = true" in src
+    fields["suffix_loop"] = SUFFIX_STACKED if stacked else SUFFIX_PLAIN
     levels = [l.split("sources [")[1].rstrip(")").split(", ") for l in src.splitlines() if "  // level " in l]
     if levels:
         fields.update(L=len(levels), aprev=", ".join(a for a, _ in levels), anext=", ".join(b_ for _, b_ in levels),
@@ -223,6 +252,7 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
     subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-w", "-o", exe, path])
     rows = [l.split() for l in subprocess.check_output([exe]).decode().splitlines()]
     amp = np.array([float(r[0]) + 1j * float(r[1]) for r in rows])
+    _host_amplitudes.stacked = stacked
     return amp, np.array([int(r[2]) for r in rows]), np.array([int(r[3]) for r in rows])
 
 
@@ -337,3 +367,32 @@ def test_generated_regions_match_the_oracle(case, eps, prefix, tmp_path):
     assert np.array_equal(valid, cnt["valid"].astype(np.int64))
     if eps == 0.0:
         assert np.abs(want).max() > 0.05   # the case exercises nonzero amplitudes
+
+
+@pytest.mark.parametrize("family,eps", [("qaoa", 1e-2), ("qaoa", 1e-3), ("qaoa", 3e-4), ("walk", 0.3),
+                                        ("random", 0.05)])
+def test_stacked_suffix_matches_the_oracle(family, eps, tmp_path):
+    """Threshold jobs with several artificial sources in the suffix run it
+    as per-source segments with a saved state after each source op; the next
+    history restarts at the first source whose bit changed.  Driven on the
+    host by the device's restart loop, amplitudes and leaf counts must be the
+    oracle's (the same factors in the same order: identical pruning)."""
+    if family == "qaoa":
+        w = qaoa_workload(8, 2, n_out=6, seed=5)
+        circ, inputs, outputs = w.circuit, w.inputs, w.outputs
+        c1 = c2 = 8                              # 8 sources before, 8 in the suffix
+    elif family == "walk":
+        circ, inputs, outputs = _walk()
+        c1 = c2 = len(circ.gates) // 4
+    else:
+        circ = random_small_circuit(9, 60, 9093)   # one source per branching op in the suffix
+        rng = SplitMix64(9093)
+        inputs = [(rng.bits(9), 0.8), (rng.bits(9), 0.6j)]
+        outputs = [rng.bits(9) for _ in range(5)]
+        c1 = c2 = len(circ.gates) // 3
+    got, completed, valid = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path))
+    assert _host_amplitudes.stacked
+    want, cnt = feynman.run(circ, inputs, outputs, eps=eps, c1=c1, c2=c2)
+    _close(got, want)
+    assert np.array_equal(completed, cnt["completed"].astype(np.int64))
+    assert np.array_equal(valid, cnt["valid"].astype(np.int64))

@@ -305,3 +305,78 @@ def test_generated_source_requires_a_plan_and_reports_its_length():
     assert len(small.value) == 15 and n.value > 1000   # truncated, NUL-terminated
     src = b.generated_source()
     assert len(src) == n.value and "struct J0" in src and "fs_jit_history" in src
+
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "feynsparse.h")
+CITATION = re.compile(r"(Sec\. [IV]|Eqs?\. ?\d|Algorithm \d|Observation \d|Fig\. \d|Table \d|no counterpart)")
+
+
+def test_every_exported_call_cites_its_passage():
+    """Each FS_API declaration of the header is preceded by a comment that
+    names the passage of the paper it follows (section, equation, algorithm,
+    observation, figure or table) or says that the paper has no counterpart."""
+    lines = open(HEADER).read().split("\n")
+    missing = []
+    for i, line in enumerate(lines):
+        if not line.startswith("FS_API"):
+            continue
+        j, block = i - 1, []
+        while j >= 0 and (lines[j].startswith(("FS_API", "#define")) or lines[j].strip().startswith(("/*", "*"))
+                          or lines[j].startswith(" " * 8)):
+            block.append(lines[j])
+            j -= 1
+        if not CITATION.search("\n".join(block)):
+            missing.append(line)
+    assert not missing, missing
+    names = set(re.findall(r"FS_API [^(]*?\b(fs_\w+)\(", open(HEADER).read()))
+    assert names == set(_lib.exported_symbols()), names ^ set(_lib.exported_symbols())
+
+
+def test_device_wait_limit_program_offset_and_targets_argument_checks():
+    L = _lib.load()
+    b = fs.Batch()
+    assert L.fs_batch_set_device(b._h, -2) == -1
+    assert L.fs_batch_set_device(b._h, -1) == 0
+    w = qaoa_workload(6, 2, n_out=4, seed=9)
+    C = fs.Circuit(w.circuit)
+    b.add(C, w.outputs)
+    off, n = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert L.fs_batch_program_offset(b._h, 0, ctypes.byref(off), ctypes.byref(n)) == -10
+    b.plan()
+    o, k = b.program_offset(0)
+    assert k == len(w.circuit.gates) and o % 256 == 0
+    assert L.fs_batch_program_offset(b._h, 1, ctypes.byref(off), ctypes.byref(n)) == -1
+    assert L.fs_set_wait_limit(1 << 33) == -1
+    assert L.fs_set_wait_limit(-1) == 0
+    assert L.fs_mlp_targets(ctypes.c_void_p(256), 4, float("nan"), ctypes.c_void_p(512), None) == -1
+    assert L.fs_mlp_targets(None, 4, -12.0, ctypes.c_void_p(512), None) == -1
+
+
+def test_threshold_jobs_plan_beyond_62_sources_and_keep_the_root_narrow():
+    """An exact job with A = 72 (QAOA-24, p = 3) is refused (2^72 histories
+    per pair); with a threshold the suffix skips cut subtrees, so it plans
+    with every region's word within 62 bits.  A threshold job's root adds no
+    more assignments than the parallelism floor needs, and its cuts are the
+    oracle's Eq. 8 argmin under the same bounds."""
+    w = qaoa_workload(24, 3, n_out=1024, seed=0x5EED0004)
+    C = fs.Circuit(w.circuit)
+    b = fs.Batch()
+    b.add(C, w.outputs, 0.0)
+    with pytest.raises(_lib.FsError) as e:
+        b.plan()
+    assert e.value.code == -9
+    for n, p, A in ((24, 3, 72), (16, 2, 32)):
+        w = qaoa_workload(n, p, n_out=1024, seed=0x5EED0004)
+        C = fs.Circuit(w.circuit)
+        b = fs.Batch()
+        b.add(C, w.outputs, 1e-6)
+        b.plan()
+        iw, _ = b.region_work(0)
+        assert all(x >= 0 for x in iw)
+        # budget 4 GiB / (1024 pairs x 40 B) -> A_p <= 16; floor 2^19 items -> A_p + A_r >= 9
+        max_ap, min_apr, max_apr = 16, 9, 16
+        c1, c2, cost = feynman.autotune(w.circuit, max_ap=max_ap, min_apr=min_apr, max_apr=max_apr)
+        (Gp, Gr, Gs, Ap, Ar, As), _ = feynman.region_counts(w.circuit, c1, c2)
+        assert Ap + Ar + As == A and As <= 62 and Ap + Ar <= max_apr
+        hist = b.op_histogram(0)
+        assert sum(hist["prefix"].values()) == Gp and sum(hist["root"].values()) == Gr
