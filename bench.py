@@ -211,9 +211,10 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def make_batch(fs, jobs, engine, dev, stream, pruners=None):
+def make_batch(fs, jobs, engine, dev, stream, pruners=None, bounds=None):
     """Plans, allocates and uploads a batch; pruners: per job (params, tau,
-    c1, c2) or None (exact, autotuned cuts)."""
+    c1, c2) or None (exact, autotuned cuts); bounds: per job (c1, c2) for the
+    exact reachability bound at that checkpoint, or None."""
     circs = []
     b = fs.Batch(engine=engine)
     for ji, w in enumerate(jobs):
@@ -225,6 +226,9 @@ def make_batch(fs, jobs, engine, dev, stream, pruners=None):
             from paper_2608_01467_b300 import learned
             learned.attach(b, ji, pruners[ji][0], pruners[ji][1])
             b.set_cuts(ji, pruners[ji][2], pruners[ji][3])
+        if bounds and bounds[ji] is not None:
+            b.set_exact_bound(ji)
+            b.set_cuts(ji, bounds[ji][0], bounds[ji][1])
     b._keep = circs
     ws = b.plan()
     b.allocate(dev)
@@ -297,6 +301,32 @@ def train_pruner(fs, args, w_train, w_val, dev, stream, plain_stats):
         c1, c2 = plain_stats["c1"], plain_stats["c2"]
         best = {"params": None, "tau": -1e30, "val_fidelity": 1.0, "c1": c1, "c2": c2, "cut": None}
     best["search"] = search
+    return best
+
+
+def pick_bound_cut(fs, args, w, dev, stream, plain_stats):
+    """The exact reachability bound needs no training and no validation (it
+    only cuts entries whose subtree sum is exactly zero): each candidate cut
+    is timed on the request itself and the fastest is kept."""
+    cands = w.meta.get("learned_cut") or [None]
+    best = None
+    for cut in cands:
+        if cut is None:
+            c1, c2 = plain_stats["c1"], plain_stats["c2"]
+        else:
+            c1 = source_cut(w.circuit, cut[0])
+            c2 = source_cut(w.circuit, cut[0] + cut[1])
+        bb, _ = make_batch(fs, [w], args.engine, dev, stream, bounds=[(c1, c2)])
+        ms = []
+        for _ in range(6):
+            e0, e1 = torch_event(), torch_event()
+            e0.record(stream)
+            bb.run(stream)
+            e1.record(stream)
+            bb.finish(stream)
+            ms.append(e0.elapsed_time(e1))
+        if best is None or min(ms) < best["ms"]:
+            best = {"c1": c1, "c2": c2, "cut": list(cut) if cut else None, "ms": min(ms)}
     return best
 
 
@@ -434,6 +464,18 @@ def run_ours(args):
     stats_plain = bp.finish(stream)
     n_out = bp.total_outputs
 
+    # exact reachability bound at the checkpoint (fair exact baseline for the
+    # learned pruner: cuts only entries whose subtree sums are exactly zero)
+    bound_info = None
+    if not args.no_bound:
+        bound_info = [pick_bound_cut(fs, args, w, dev, stream, sp) for w, sp in zip(jobs, stats_plain)]
+        bb, _ = make_batch(fs, jobs, args.engine, dev, stream, bounds=[(p["c1"], p["c2"]) for p in bound_info])
+        bb.pruned = None
+        for _ in range(max(args.warmup, 3)):
+            bb.run(stream)
+            bb.finish(stream)
+        stats_bound = bb.finish(stream)
+
     # learned: a pruner per job trained on separately seeded requests
     tr_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 100)
     va_jobs, _ = workload_jobs(args.workload, rank, args.outputs, 200)
@@ -456,6 +498,7 @@ def run_ours(args):
 
     graph_p = None if args.no_graph else capture(bp, stream)
     graph_l = None if (args.no_graph or not learned_info) else capture(bl, stream)
+    graph_b = None if (args.no_graph or not bound_info) else capture(bb, stream)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -463,6 +506,10 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     plain_ms, plain_stage, plain_completed, _ = timed_steps(bp, args.steps, stream, flush, "plain_step", graph_p)
     plain_amp = bp.amp.cpu().numpy()
+    if bound_info:
+        bound_ms, bound_stage, bound_completed, stats_bound = timed_steps(bb, args.steps, stream, flush,
+                                                                          "bound_step", graph_b)
+        bound_amp = bb.amp.cpu().numpy()
     if learned_info:
         learned_ms, learned_stage, learned_completed, stats_learned = timed_steps(bl, args.steps, stream, flush,
                                                                                   "learned_step", graph_l)
@@ -530,6 +577,18 @@ def run_ours(args):
             "roofline": roof}
     if learned_info:
         line["learned"] = [{k: v for k, v in p.items() if k != "params"} for p in learned_info]
+    if bound_info:
+        bv, bh, bs = rates(bound_ms, bound_completed)
+        line["exact_bound"] = {"value": bv, "unit": "amplitudes/s", "histories_per_s": bh, "ms_per_step": bs,
+                               "fidelity_vs_exact": fidelity(plain_amp[:n_out], bound_amp[:n_out]),
+                               "max_abs_diff_vs_exact": float(abs(plain_amp[:n_out] - bound_amp[:n_out]).max()),
+                               "bound_cuts": int(sum(x["bound_cuts"] for x in stats_bound)),
+                               "live_entries": int(sum(x["live_entries"] for x in stats_bound)),
+                               "cut_sources": [p["cut"] for p in bound_info],
+                               "stage_ms": {k: round(v, 4) for k, v in bound_stage.items()},
+                               "speedup_vs_plain": bv / plain_value}
+        if learned_info:
+            line["learned_vs_exact_bound"] = value / bv
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samp = oracle_sample(jobs, budget_s=args.cpu_seconds)
         one = oracle_sample(jobs, budget_s=max(2.0, args.cpu_seconds / 4), threads=1)
@@ -562,6 +621,7 @@ def main():
                     help="A_p,A_r: artificial sources before the learned cut and in the root after it")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bound", action="store_true", help="skip the exact-bound arm")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -146,6 +146,7 @@ typedef struct fs_stats {
     uint32_t A_p, A_r, A_s;
     uint64_t learned_cuts;    /* checkpoint entries cut by the learned pruner */
     uint64_t live_entries;    /* checkpoint entries enumerated by the history kernel */
+    uint64_t bound_cuts;      /* checkpoint entries cut by the exact reachability bound */
 } fs_stats;
 
 /* Thread-local message of the last failing call on this thread (library
@@ -349,6 +350,21 @@ FS_API int fs_batch_job_words(const fs_batch* b, uint32_t job, uint32_t* words);
  * the 32-bit integer logic rate (ops/s) with short probe kernels, and
  * reports the SM count.  Allocates and frees 256 bytes of device memory. */
 FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sms);
+
+/* Exact pruning at the checkpoint (Sec. IV-A Observation 3: a history that
+ * cannot reach b_in contributes exactly zero; here decided for a whole
+ * subtree at once).  With enable != 0, fs_batch_run cuts every checkpoint
+ * entry (sigma_p, beta_p) of the job whose state provably cannot reach the
+ * input b_in through the ops after the cut: a qubit that no remaining op
+ * targets must already hold b_in's value, and a field of contiguous qubits
+ * changed only by controlled +-1 cascades of multi-controlled X gates (an
+ * incrementer / decrementer) moves by at most the number of such cascades
+ * left, so a field value farther than that (cyclically) from b_in's is
+ * unreachable.  Cut entries are counted in fs_stats.bound_cuts; the job runs
+ * the history over the compacted live entries, so amplitudes are the exact
+ * ones.  Call before fs_batch_plan; FS_ERR_UNSUPPORTED from the plan when
+ * more than 4 disjoint cascade fields follow the cut. */
+FS_API int fs_batch_set_exact_bound(fs_batch* b, uint32_t job, int32_t enable);
 
 /* ---- learned pruning at the checkpoint boundary ---------------------------
  * Not in the paper: a proposal built on its checkpoint boundary (Sec. IV-C).

@@ -54,7 +54,8 @@ class fs_stats(ctypes.Structure):
                 ("history_visits", ctypes.c_uint64),
                 ("table_entries", ctypes.c_uint64), ("c1", ctypes.c_int32), ("c2", ctypes.c_int32),
                 ("A_p", ctypes.c_uint32), ("A_r", ctypes.c_uint32), ("A_s", ctypes.c_uint32),
-                ("learned_cuts", ctypes.c_uint64), ("live_entries", ctypes.c_uint64)]
+                ("learned_cuts", ctypes.c_uint64), ("live_entries", ctypes.c_uint64),
+                ("bound_cuts", ctypes.c_uint64)]
 
 
 P = ctypes.POINTER
@@ -106,6 +107,7 @@ SIGNATURES = {
     "fs_batch_program_offset": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_size_t), P(ctypes.c_size_t)]),
     "fs_mlp_targets": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, vp, vp]),
     "fs_set_wait_limit": (ctypes.c_int, [ctypes.c_int64]),
+    "fs_batch_set_exact_bound": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.c_int32]),
 }
 NOALLOC_SCRATCH_BYTES = 16 << 20
 MLP_PARAMS = 18817

@@ -182,6 +182,10 @@ class Batch:
         self._circuits.append(circuit)
         return jid.value
 
+    def set_exact_bound(self, job: int, enable: bool = True):
+        """Cut checkpoint entries that provably cannot reach the input (exact)."""
+        check(_lib.load().fs_batch_set_exact_bound(self._h, job, 1 if enable else 0))
+
     def set_cuts(self, job: int, c1: int, c2: int):
         """Fixed cuts for one job (both -1: back to the batch's split)."""
         check(_lib.load().fs_batch_set_cuts(self._h, job, c1, c2))

@@ -419,8 +419,11 @@ struct Job {
     const float* d_pruner = nullptr;
     float tau = 0;
     fs::FeatureSpec fspec{};
-    // pruned jobs (eps > 0 or a learned pruner) run over compacted live entries
+    // pruned jobs (eps > 0, a learned pruner or the exact bound) run over
+    // compacted live entries
     bool compact = false;
+    bool bound = false;                   // exact reachability bound at the checkpoint
+    fs::BoundSpec bspec{};
     int fixed_c1 = -1, fixed_c2 = -1;     // per-job cuts overriding the batch split
     std::vector<fs::PrefixLevel> levels;  // per-source prefix expansion (empty: single region)
     double2 scale = make_double2(1.0, 0.0);   // constant left out by the generated root and suffix
@@ -752,6 +755,16 @@ int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float 
     return FS_OK;
 }
 
+int fs_batch_set_exact_bound(fs_batch* b, uint32_t job, int32_t enable)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    b->jobs[job].bound = enable != 0;
+    b->planned = b->uploaded = false;   // the job's layout changes: plan again
+    b->drop_jit();
+    return FS_OK;
+}
+
 int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, void* stream)
 {
     if (!b || !d_ws || !d_features) return fail(FS_ERR_INVALID, "NULL argument");
@@ -819,6 +832,7 @@ int fs_batch_total_outputs(const fs_batch* b, size_t* n)
 static void region_work(const Job& j, int e0, int e1, double& iops, double& fops, int dfrom, bool fused,
                         bool hoisted = false);
 static int job_defer_from(const Job& j, bool straight);
+static bool make_bound(Job& j, int n_qubits);
 
 // Rates of the prefix cost model (work-model integer ops and FP64
 // instructions per second, HBM bytes per second, seconds per launch),
@@ -871,7 +885,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         } else {
             const uint64_t share = all_pairs ? (uint64_t)((long double)budget * j.pairs / all_pairs) : budget;
             // pruned jobs also keep a compacted live list (8 B per entry)
-            const uint64_t entry_bytes = sizeof(fs::Entry) + ((j.eps > 0.0 || j.d_pruner) ? 8 : 0);
+            const uint64_t entry_bytes = sizeof(fs::Entry) + ((j.eps > 0.0 || j.d_pruner || j.bound) ? 8 : 0);
             const uint64_t per_pair = j.pairs ? share / (j.pairs * entry_bytes) : share;
             const int max_ap = per_pair ? std::min(ilog2_floor(per_pair), 40) : 0;
             const int min_apr = j.pairs ? ilog2_ceil((min_items + j.pairs - 1) / j.pairs) : 0;
@@ -961,7 +975,10 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
                     if (gi.src[t] >= 0) f.next_qubits[nk++] = gi.q[t];
             }
         }
-        j.compact = j.eps > 0.0 || j.d_pruner != nullptr;
+        j.compact = j.eps > 0.0 || j.d_pruner != nullptr || j.bound;
+        if (j.bound) {
+            if (!make_bound(j, (int)C.n)) return fail(FS_ERR_UNSUPPORTED, "job %zu: more than %d cascade fields after the cut", ji, fs::MAX_BOUND_FIELDS);
+        }
         j.log2_ipp = j.sp.Ap + j.sp.Ar;
         j.log2_spp = std::max(0, j.log2_ipp - fs::TILE_LOG2);
         j.table_entries = j.pairs << j.sp.Ap;
@@ -1031,6 +1048,69 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     b->grid = fs::history_grid_size(dev);
     b->compact_grid = fs::compact_grid_size(dev);
     return FS_OK;
+}
+
+// The exact reachability bound of a planned job (cuts at sp.c1): qubits no
+// op in [c1, G) can change, and fields moved only by +-1 cascades with the
+// number of such cascades as the radius.
+static bool make_bound(Job& j, int n_qubits)
+{
+    const int G = (int)j.prog.ops.size(), W = j.W;
+    uint32_t freem[4] = {0, 0, 0, 0};
+    struct F { int t0, len; uint32_t runs; bool ok; };
+    std::vector<F> fields;
+    auto setq = [&](int q) { freem[q >> 5] |= 1u << (q & 31); };
+    for (int e = j.sp.c1; e < G; ++e) {
+        fs::CascadeRun run;
+        if (fs::find_cascade(j.prog.ops.data(), j.prog.masks.data(), W, e, G, run)) {
+            bool found = false;
+            for (F& f : fields)
+                if (f.t0 == run.t0 && f.len == run.len) { f.runs++; found = true; }
+            if (!found) fields.push_back({run.t0, run.len, 1u, true});
+            e += run.len - 1;
+            continue;
+        }
+        const fs::Op& op = j.prog.ops[e];
+        switch (op.code) {
+        case fs::OP_X: case fs::OP_MCX: case fs::OP_PERM1: case fs::OP_H: case fs::OP_BR1:
+            setq(op.q0);
+            break;
+        case fs::OP_SWAP: case fs::OP_PERM2: case fs::OP_BR2:
+            setq(op.q0);
+            setq(op.q1);
+            break;
+        default:   // wire-preserving: the state does not change
+            break;
+        }
+    }
+    uint32_t fmask[4] = {0, 0, 0, 0};
+    for (F& f : fields) {
+        for (int q = f.t0; q < f.t0 + f.len; ++q) {
+            if ((freem[q >> 5] >> (q & 31)) & 1u) f.ok = false;
+            for (const F& g : fields)   // overlapping fields: no bound from either
+                if (&g != &f && q >= g.t0 && q < g.t0 + g.len) f.ok = false;
+        }
+    }
+    fs::BoundSpec& sp = j.bspec;
+    std::memset(&sp, 0, sizeof sp);
+    for (F& f : fields) {
+        for (int q = f.t0; q < f.t0 + f.len; ++q) fmask[q >> 5] |= 1u << (q & 31);
+        if (!f.ok) {
+            for (int q = f.t0; q < f.t0 + f.len; ++q) setq(q);
+            continue;
+        }
+        if (sp.n_fields == fs::MAX_BOUND_FIELDS) return false;
+        sp.t0[sp.n_fields] = f.t0;
+        sp.len[sp.n_fields] = f.len;
+        sp.radius[sp.n_fields] = f.runs;
+        sp.n_fields++;
+    }
+    for (int w = 0; w < 4; ++w) {
+        const int lo = 32 * w;
+        const uint32_t valid = n_qubits >= lo + 32 ? 0xffffffffu : (n_qubits > lo ? ((1u << (n_qubits - lo)) - 1u) : 0u);
+        sp.frozen[w] = valid & ~freem[w] & ~fmask[w];
+    }
+    return true;
 }
 
 static std::vector<fs::JitJobSpec> jit_specs(const fs_batch* b)
@@ -1224,7 +1304,8 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         flat_prefix |= j.levels.empty();
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
-        if (j.compact) k += j.d_pruner ? 3 : 4; // [count,] scan, write (with pair ranges), history over live entries
+        if (j.bound) k += 1;                    // exact bound
+        if (j.compact) k += (j.d_pruner || j.bound) ? 3 : 4;   // [count,] scan, write (with pair ranges), history over live entries
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
@@ -1319,18 +1400,20 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     if (b->timing) CUDA_TRY(record(b->ev[4], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
-        if (j.d_pruner) {
-            // the prune step counts the entries it leaves live per compaction block
-            CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
+        // the last checkpoint step (exact bound, then learned pruner) counts
+        // the entries it leaves live per compaction block
+        if (j.bound || j.d_pruner) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
+        if (j.bound)
+            CUDA_TRY(fs::launch_bound_prune(jobs, ji, j.bspec, j.table_entries, j.d_pruner == nullptr, s));
+        if (j.d_pruner)
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries,
                                            (uint32_t*)(base + b->o_err), s));
-        }
     }
     if (b->timing) CUDA_TRY(record(b->ev[5], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         if (!j.compact) continue;
-        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, j.d_pruner != nullptr, s));
+        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, j.d_pruner != nullptr || j.bound, s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[1], s));
     if (b->tiles.empty()) {
@@ -1409,6 +1492,7 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
             o.history_visits = q[2];
             o.table_entries = q[3];
             o.learned_cuts = q[5];
+            o.bound_cuts = q[8];
             o.live_entries = j.compact ? q[6] : q[3];
             o.c1 = j.sp.c1; o.c2 = j.sp.c2;
             o.A_p = (uint32_t)j.sp.Ap; o.A_r = (uint32_t)j.sp.Ar; o.A_s = (uint32_t)j.sp.As;

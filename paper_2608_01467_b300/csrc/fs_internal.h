@@ -122,10 +122,32 @@ struct JobDev {
 constexpr int TILE_LOG2 = 8;             // items per tile = threads per CTA
 constexpr int TILE = 1 << TILE_LOG2;
 constexpr int REDUCE_THREADS = 128;
-constexpr int STATS_PER_JOB = 8;   // completed, valid, hist visits, entries, prefix visits, learned cuts,
-                                   // live entries after compaction, compact work counter
+constexpr int STATS_PER_JOB = 9;   // completed, valid, hist visits, entries, prefix visits, learned cuts,
+                                   // live entries after compaction, compact work counter, bound cuts
 constexpr int COMPACT_BLOCK = 1024;   // entries per compaction block (256 threads x 4)
 constexpr int MLP_PARAMS = 18817;
+
+// Exact reachability bound at the checkpoint: what the ops after the cut can
+// still change.  Qubits in `frozen` are targeted by no remaining op, so a
+// checkpoint state that differs from b_in there reaches the input with no
+// valid history; a field of contiguous qubits changed only by controlled
+// +-1 cascades (find_cascade) moves by at most `radius` (the number of
+// remaining cascades on it), so a state whose field value is farther than
+// that from b_in's (cyclically, modulo 2^len) has an exactly zero subtree
+// sum too.
+constexpr int MAX_BOUND_FIELDS = 4;
+struct BoundSpec {
+    uint32_t frozen[4];
+    int n_fields;
+    int t0[MAX_BOUND_FIELDS];
+    int len[MAX_BOUND_FIELDS];
+    uint32_t radius[MAX_BOUND_FIELDS];
+};
+// Cuts (bottom) every live entry of a job's checkpoint table that the
+// bound proves unreachable (counted in stats[8]); with count_blocks, also
+// counts the live entries per compaction block (blk, zeroed by the caller).
+cudaError_t launch_bound_prune(const JobDev* d_jobs, int job, const BoundSpec& sp, unsigned long long n_entries,
+                               bool count_blocks, cudaStream_t s);
 
 // Per-job constants of the learned pruner's features.
 struct FeatureSpec {

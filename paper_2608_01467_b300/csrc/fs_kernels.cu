@@ -939,6 +939,60 @@ __global__ void __launch_bounds__(RED_BIG_THREADS) reduce_big_kernel(const JobDe
     }
 }
 
+// ---------------------------------------------------------------- exact bound
+
+// One warp covers 32 consecutive entries, inside one compaction block.
+__global__ void __launch_bounds__(256) bound_prune_kernel(const JobDev* __restrict__ jobs, int job, BoundSpec sp,
+                                                          unsigned long long n, int count_blocks)
+{
+    const JobDev& J = jobs[job];
+    unsigned long long cuts = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const unsigned long long e = base + threadIdx.x;
+        bool live = false, cut = false;
+        if (e < n) {
+            uint4* ent = reinterpret_cast<uint4*>(J.table + e);
+            const uint4 sv = ent[0];
+            const double2 a = reinterpret_cast<const double2*>(ent + 1)[0];
+            live = !is_bottom(a.x);
+            if (live) {
+                uint64_t sidx;
+                pair_split(e >> J.Ap, J, sidx);
+                const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
+                const uint32_t st[4] = {sv.x, sv.y, sv.z, sv.w}, bi[4] = {bv.x, bv.y, bv.z, bv.w};
+                uint32_t d = 0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) d |= (st[w] ^ bi[w]) & sp.frozen[w];
+                cut = d != 0u;
+                const unsigned __int128 s128 = ((unsigned __int128)(((uint64_t)st[3] << 32) | st[2]) << 64) |
+                                               (((uint64_t)st[1] << 32) | st[0]);
+                const unsigned __int128 b128 = ((unsigned __int128)(((uint64_t)bi[3] << 32) | bi[2]) << 64) |
+                                               (((uint64_t)bi[1] << 32) | bi[0]);
+                for (int f = 0; f < sp.n_fields && !cut; ++f) {
+                    const unsigned __int128 m = sp.len[f] >= 128 ? ~(unsigned __int128)0
+                                                                 : (((unsigned __int128)1 << sp.len[f]) - 1);
+                    const unsigned __int128 x = (s128 >> sp.t0[f]) & m, y = (b128 >> sp.t0[f]) & m;
+                    const unsigned __int128 up = (x - y) & m, down = (y - x) & m;   // cyclic distances
+                    const unsigned __int128 dist = up < down ? up : down;
+                    cut = dist > (unsigned __int128)sp.radius[f];
+                }
+                if (cut) {
+                    reinterpret_cast<double2*>(ent + 1)->x = __longlong_as_double(0x7ff8000000000000ll);
+                    ++cuts;
+                }
+            }
+        }
+        if (count_blocks) {
+            const unsigned keep = __ballot_sync(0xffffffffu, live && !cut);
+            if ((threadIdx.x & 31) == 0 && keep)
+                atomicAdd(&J.blk[(base + (threadIdx.x & ~31u)) / COMPACT_BLOCK], (unsigned)__popc(keep));
+        }
+    }
+    cuts = warp_sum_u64(cuts);
+    if ((threadIdx.x & 31) == 0 && cuts) atomicAdd(&J.stats[8], cuts);
+}
+
 // ---------------------------------------------------------------- peak probes
 
 // FP64 FMA throughput: 8 independent dependency chains per thread.
@@ -1071,6 +1125,16 @@ int compact_grid_size(int device)
 cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s)
 {
     history_compact_kernel<<<grid, 256, 0, s>>>(d_job, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_prune(const JobDev* d_jobs, int job, const BoundSpec& sp, unsigned long long n_entries,
+                               bool count_blocks, cudaStream_t s)
+{
+    if (n_entries == 0) return cudaSuccess;
+    unsigned long long blocks = (n_entries + 255) / 256;
+    if (blocks > 148ull * 16) blocks = 148ull * 16;
+    bound_prune_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, job, sp, n_entries, count_blocks ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -424,3 +424,35 @@ def test_golden_qaoa_threshold_file_is_consistent():
         want, margin = _qaoa_closed_form_leaves(s["n"], w.meta["angles"], s["eps"])
         assert s["closed_form_leaves"] == want and margin > 1e-9
         assert s["completed"] == [want] * len(s["index"]) == s["valid"]
+
+
+def test_walk_checkpoints_beyond_the_remaining_steps_have_zero_subtree_sums():
+    """The reading behind the exact reachability bound at the checkpoint: on
+    the coined walk a checkpoint state whose position is farther from the
+    input's than the steps left after the cut (each step moves it by one)
+    has no valid completion, so its exact subtree sum is 0 -- and so is any
+    state whose untouched ancilla differs from the input's.  Checked on the
+    oracle's checkpoint tables (exact subtree sums by enumeration)."""
+    steps, pos_bits = 6, 8
+    w = qw_workload(steps=steps, n_out=24, pos_bits=pos_bits)
+    c = w.circuit
+    G = len(c.gates)
+    per_step = G // steps
+    mask = (1 << pos_bits) - 1
+    seen = 0
+    for k_prefix in (2, 3, 4):
+        c1 = k_prefix * per_step                   # the last k_prefix steps are the prefix
+        left = steps - k_prefix
+        for b_in, _ in w.inputs:
+            for b_out in w.outputs[:12]:
+                t = feynman.checkpoints(c, b_in, b_out, c1)
+                for st, live, sub in zip(t["state"], t["live"], t["subtree"]):
+                    if not live:
+                        continue
+                    x, y = (st >> 1) & mask, (b_in >> 1) & mask
+                    dist = min((x - y) & mask, (y - x) & mask)
+                    anc_differs = ((st ^ b_in) >> (pos_bits + 3)) & 1
+                    if dist > left or anc_differs:
+                        assert sub == 0, (k_prefix, st, sub)
+                        seen += 1
+    assert seen > 0

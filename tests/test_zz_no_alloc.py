@@ -77,3 +77,25 @@ def test_noalloc_refuses_requests_larger_than_its_scratch():
     rc, got = call_noalloc(C, w.outputs[:4])
     assert rc == 0
     check_close(got, C.amplitudes(w.outputs[:4]))
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    """After the first call on a device (which may load this part of the
+    library, the static array included, under lazy module loading), further
+    calls allocate nothing: the free device memory reported by the driver is
+    the same before and after each of them."""
+    import torch
+    w = qw_workload(steps=6, n_out=48, pos_bits=8)
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    for eps in (0.0, 0.02):          # first calls: exact and threshold kernels loaded
+        rc, _ = call_noalloc(C, w.outputs, eps)
+        assert rc == 0
+    torch.cuda.synchronize()
+    for eps in (0.0, 0.0, 0.02, 0.02):
+        free0, _ = torch.cuda.mem_get_info()
+        rc, got = call_noalloc(C, w.outputs, eps)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert rc == 0 and free1 == free0, (free0, free1)
+    check_close(got, C.amplitudes(w.outputs, eps=0.02))
