@@ -262,12 +262,23 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
     return acc;
 }
 
+// The checkpoint entry and input bits of the item a lane is on: consecutive
+// items of a lane share them whenever they share (pair, h_p), so they are
+// loaded once per change instead of once per item.
+template <class T>
+struct EntryCache {
+    u64 pair, hp;
+    u32 st[T::W], bin[T::W];
+    double2 amp;
+    bool bottom;
+};
+
 // Sum over the valid leaves of one (prefix, root) item: the root once, the
 // suffix for every h_s (skipping cut subtrees), the chi test at the input.
 template <class T>
 __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
                                             typename CounterType<(T::Ap + T::Ar <= 32)>::type local,
-                                            u64& completed, u64& valid, u64& visits)
+                                            EntryCache<T>& c, u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
     double2 acc = make_double2(0.0, 0.0);
@@ -275,21 +286,31 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
     // (the shift counts stay below the type's width in every instantiation)
     const loc_t hp = T::Ap == 0 ? (loc_t)0 : (loc_t)(local >> (T::Ar % (8 * (int)sizeof(loc_t))));
     const loc_t hr = local & (loc_t)((1ull << T::Ar) - 1ull);
-    u64 s;
-    const u64 o = pair_split(pair, J, s);
-    (void)o;
-    const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
-    const uint4 sv = __ldg(ent);
-    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
-    if (is_bottom(a0.x)) return acc;
-    u32 st[W], bin[W];
-    const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
-    const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * s));
-    const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+    if (pair != c.pair) {
+        u64 s;
+        pair_split(pair, J, s);
+        const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * s));
+        const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-    for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
-    double2 amp = a0;
-    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T>(st, amp, bin, completed, valid, visits);
+        for (int j = 0; j < W; ++j) c.bin[j] = btmp[j];
+    }
+    if (pair != c.pair || (u64)hp != c.hp) {
+        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
+        const uint4 sv = __ldg(ent);
+        c.amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
+        c.bottom = is_bottom(c.amp.x);
+        const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+        for (int j = 0; j < W; ++j) c.st[j] = tmp[j];
+        c.pair = pair;
+        c.hp = hp;
+    }
+    if (c.bottom) return acc;
+    u32 st[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) st[j] = c.st[j];
+    double2 amp = c.amp;
+    if (T::root(st, amp, hr, c.bin, visits) < 0) acc = suffix_sum<T>(st, amp, c.bin, completed, valid, visits);
     return acc;
 }
 
@@ -312,9 +333,12 @@ __device__ void tile_body(const JobDev& J, u64 tile)
     u64 pair = first >> lg;
     loc_t local = (loc_t)(first & ((1ull << lg) - 1ull));
     const int kn = first >= n_items ? 0 : (n_items - first < 8u ? (int)(n_items - first) : 8);
+    EntryCache<T> cache;
+    cache.pair = ~0ull;
+    cache.hp = ~0ull;
 #pragma unroll 1
     for (int k = 0; k < kn; ++k) {
-        const double2 v = item_sum<T>(J, pair, local, completed, valid, visits);
+        const double2 v = item_sum<T>(J, pair, local, cache, completed, valid, visits);
         if (J.log) {   // logging runs only: keep the product out of the common path
             asm volatile("" ::: "memory");
             J.log[first + (u64)k] = cmul(J.scale, v);

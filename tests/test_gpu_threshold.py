@@ -1,0 +1,106 @@
+"""Threshold pruning (Sec. IV-A, Observation 3) at the sizes of the QAOA
+MaxCut requests: three seeded 3-regular graphs at 16, 20 and 24 qubits,
+p = 2, 1024 requested outputs each, eps in {1e-4, 1e-6}, and QAOA-24 at
+p = 3 (A = 72) at eps = 1e-4 (at 1e-6 its pruned search would keep about
+1e11 leaves per output).
+
+The stored values (tests/golden/qaoa_threshold.json, written by
+tests/golden/make_qaoa_golden.py from oracle/ only) are the dense state
+vector's exact amplitudes of every requested output and, for sampled
+outputs, the oracle's per-source depth-first search with the same
+threshold: pruned amplitudes and completed / valid leaf counts.  Each test
+runs the whole 1024-output request on the GPU (large compacted checkpoint
+tables, the block-per-output reduction), compares the sampled amplitudes
+with the oracle's element by element, checks the job's leaf count against
+the closed form, runs the sampled outputs alone with the same cuts for
+bit-exact per-output counts, and reports the fidelity against the exact
+amplitudes."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from workloads import qaoa_workload
+from oracle import closed_forms
+import paper_2608_01467_b300 as fs
+
+pytestmark = pytest.mark.gpu
+
+ATOL, RTOL = 1e-12, 1e-10
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "qaoa_threshold.json")
+
+
+def _gold():
+    with open(GOLD) as f:
+        return json.load(f)
+
+
+def _request(g, n, p):
+    r = next(r for r in g["requests"] if r["n"] == n and r["p"] == p)
+    w = qaoa_workload(n, p, n_out=r["n_out"], seed=r["seed"])
+    assert [int(x) for x in w.outputs[:4]] == r["outputs_head"]
+    exact = np.asarray(r["exact_re"]) + 1j * np.asarray(r["exact_im"])
+    return w, exact
+
+
+def _run(w, outputs, eps, cuts=None):
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    b = fs.Batch()
+    b.add(C, outputs, eps)
+    if cuts is not None:
+        b.set_cuts(0, *cuts)
+    b.plan()
+    b.allocate()
+    b.upload()
+    b.run()
+    st = b.finish()[0]
+    return b.amp.cpu().numpy()[:len(outputs)], st
+
+
+CASES = [(16, 2, 1e-4), (16, 2, 1e-6), (20, 2, 1e-4), (20, 2, 1e-6), (24, 2, 1e-4), (24, 3, 1e-4)]
+
+
+@pytest.mark.parametrize("n,p,eps", CASES)
+def test_qaoa_threshold_request_matches_the_oracle(n, p, eps):
+    g = _gold()
+    w, exact = _request(g, n, p)
+    smp = next(s for s in g["samples"] if s["n"] == n and s["p"] == p and s["eps"] == eps)
+    A = fs.Circuit(w.circuit).analyze(0)["A"]
+    assert A == n * p                                        # Table 1: QAOA A = sn
+    amp, st = _run(w, w.outputs, eps)
+    idx = smp["index"]
+    want = np.asarray(smp["re"]) + 1j * np.asarray(smp["im"])
+    err = np.abs(amp[idx] - want)
+    assert np.all(err <= ATOL + RTOL * np.abs(want)), err.max()
+    # every pair of this request keeps the same leaves (the RX moduli do not
+    # depend on the state): the closed-form count, and chi = 1 for all of them
+    assert smp["closed_form_margin"] > 1e-9
+    assert smp["completed"] == [smp["closed_form_leaves"]] * len(idx)
+    assert st["completed"] == len(w.outputs) * smp["closed_form_leaves"]
+    assert st["valid"] == st["completed"]
+    assert st["candidates"] == (len(w.outputs) << A if A + 10 < 64 else (1 << 64) - 1)
+    # the sampled outputs alone with the same cuts: per-output counts equal
+    # to the oracle's, amplitudes bit-identical to the full request's
+    amp2, st2 = _run(w, [w.outputs[i] for i in idx], eps, (st["c1"], st["c2"]))
+    assert st2["completed"] == sum(smp["completed"]) and st2["valid"] == sum(smp["valid"])
+    assert np.array_equal(amp2, amp[idx])
+    F = closed_forms.fidelity(exact, amp)
+    weight = float(np.vdot(amp, amp).real / np.vdot(exact, exact).real)
+    print(f"QAOA-{n} p={p} eps={eps:g}: A={A} (A_p, A_r, A_s)=({st['A_p']}, {st['A_r']}, {st['A_s']}) "
+          f"live entries {st['live_entries']} leaves {st['completed']} fidelity {F:.6f} weight {weight:.6f}")
+    assert 0.0 <= F <= 1.0 + 1e-12
+
+
+def test_threshold_request_exercises_large_tables_and_the_block_reduction():
+    """QAOA-16, eps = 1e-4: the compacted checkpoint table has far more
+    entries than one compaction block and the scan's block count exceeds one
+    pass of its 1024 threads; every output has more than 4096 live entries,
+    so the block-per-output reduction sums them."""
+    g = _gold()
+    w, exact = _request(g, 16, 2)
+    amp, st = _run(w, w.outputs, 1e-4)
+    entries = len(w.outputs) << st["A_p"]
+    assert entries // 1024 > 1024                  # compaction blocks > scan threads
+    assert st["A_r"] <= 5 and st["live_entries"] // len(w.outputs) > 4096
