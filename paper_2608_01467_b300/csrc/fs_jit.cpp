@@ -160,14 +160,24 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
-// acc += v inside a branch the compiler may not flatten: flattened, the add
-// would run on every lane with v replaced by zero, and FP64 instructions are
-// scarce on this part while most leaves are invalid and most items zero.
-__device__ __forceinline__ void add_kept(double2& acc, double2 v)
+// acc += v in the lanes where keep holds.  FP64 instructions occupy the
+// scarce FP64 pipe of this part even when every lane of the warp is
+// predicated off, and most leaves are invalid and most items zero, so the
+// two adds sit behind a warp-uniform branch (bra.uni on a vote of the active
+// lanes) that the warp skips when no lane keeps its value.
+__device__ __forceinline__ void add_kept(double2& acc, double2 v, bool keep)
 {
-    asm volatile("" ::: "memory");
-    acc.x += v.x;
-    acc.y += v.y;
+    const unsigned any = __any_sync(__activemask(), keep) ? 1u : 0u;
+    asm volatile(
+        "{\n\t.reg .pred pa, pk;\n\t"
+        "setp.ne.u32 pa, %4, 0;\n\t"
+        "setp.ne.u32 pk, %5, 0;\n\t"
+        "@!pa bra.uni FS_ADD_SKIP;\n\t"
+        "@pk add.rn.f64 %0, %0, %2;\n\t"
+        "@pk add.rn.f64 %1, %1, %3;\n"
+        "FS_ADD_SKIP:\n\t}\n"
+        : "+d"(acc.x), "+d"(acc.y)
+        : "d"(v.x), "d"(v.y), "r"(any), "r"(keep ? 1u : 0u));
 }
 
 
@@ -221,9 +231,10 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
                 u32 d = 0;
 #pragma unroll
                 for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
-                if (d == 0) {
-                    ++valid;
-                    add_kept(acc, amp2);
+                {
+                    const bool ok = d == 0u;
+                    valid += ok ? 1u : 0u;
+                    add_kept(acc, amp2, ok);
                 }
                 nx = hs + (hs_t)1;
             } else {
@@ -249,9 +260,10 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
                 u32 d = 0;
 #pragma unroll
                 for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
-                if (d == 0) {
-                    ++valid;
-                    add_kept(acc, amp2);
+                {
+                    const bool ok = d == 0u;
+                    valid += ok ? 1u : 0u;
+                    add_kept(acc, amp2, ok);
                 }
                 ++hs;
             } else {
@@ -343,7 +355,7 @@ __device__ void tile_body(const JobDev& J, u64 tile)
             asm volatile("" ::: "memory");
             J.log[first + (u64)k] = cmul(J.scale, v);
         }
-        if (nonzero(v)) add_kept(acc, v);
+        add_kept(acc, v, nonzero(v));
         ++local;
         if (lg < 3 && local == ((loc_t)1 << (lg < 3 ? lg : 0))) {
             J.partials[pair] = acc;   // a pair of at most 4 items ends here
@@ -831,7 +843,9 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
     if (chi_only && !cls.empty()) {
         out += "    u32 dchi = 0u;\n";
         for (int j = 0; j < W; ++j) out += "    dchi |= s[" + std::to_string(j) + "] ^ bin[" + std::to_string(j) + "];\n";
-        out += "    if (dchi == 0u) {\n";
+        // the class products only for valid leaves, behind a vote so that
+        // a warp with no valid leaf issues none of their FP64 instructions
+        out += "    if (__any_sync(__activemask(), dchi == 0u)) if (dchi == 0u) {\n";
     }
     for (size_t k = 0; k < cls.size(); ++k) {
         const FactorClass& f = cls[k];

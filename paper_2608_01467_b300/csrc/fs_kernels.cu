@@ -109,14 +109,24 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
-// acc += v inside a branch the compiler may not flatten: flattened, the add
-// would run on every lane with v replaced by zero, and FP64 instructions are
-// scarce on this part while most leaves are invalid and most items zero.
-__device__ __forceinline__ void add_kept(double2& acc, double2 v)
+// acc += v in the lanes where keep holds.  FP64 instructions occupy the
+// scarce FP64 pipe of this part even when every lane of the warp is
+// predicated off, and most leaves are invalid and most items zero, so the
+// two adds sit behind a warp-uniform branch (bra.uni on a vote of the active
+// lanes) that the warp skips when no lane keeps its value.
+__device__ __forceinline__ void add_kept(double2& acc, double2 v, bool keep)
 {
-    asm volatile("" ::: "memory");
-    acc.x += v.x;
-    acc.y += v.y;
+    const unsigned any = __any_sync(__activemask(), keep) ? 1u : 0u;
+    asm volatile(
+        "{\n\t.reg .pred pa, pk;\n\t"
+        "setp.ne.u32 pa, %4, 0;\n\t"
+        "setp.ne.u32 pk, %5, 0;\n\t"
+        "@!pa bra.uni FS_ADD_SKIP;\n\t"
+        "@pk add.rn.f64 %0, %0, %2;\n\t"
+        "@pk add.rn.f64 %1, %1, %3;\n"
+        "FS_ADD_SKIP:\n\t}\n"
+        : "+d"(acc.x), "+d"(acc.y)
+        : "d"(v.x), "d"(v.y), "r"(any), "r"(keep ? 1u : 0u));
 }
 
 
@@ -475,9 +485,10 @@ __device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, u
             const int r2 = run_ops<W>(J, J.c2, J.G, st2, amp2, hs, J.As, bin, visits, err);
             if (r2 < 0) {
                 ++completed;
-                if (same<W>(st2, bin)) {
-                    ++valid;
-                    add_kept(acc, amp2);
+                {
+                    const bool ok = same<W>(st2, bin);
+                    valid += ok ? 1u : 0u;
+                    add_kept(acc, amp2, ok);
                 }
                 ++hs;
             } else {
@@ -511,7 +522,7 @@ __device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err)
             asm volatile("" ::: "memory");
             J.log[item] = cmul(J.scale, v);
         }
-        if (nonzero(v)) add_kept(acc, v);
+        add_kept(acc, v, nonzero(v));
         if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
             J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
             acc = make_double2(0.0, 0.0);
@@ -696,9 +707,10 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
             const int r2 = run_ops<W>(J, J.c2, J.G, st2, amp2, hs, J.As, bin, visits, err);
             if (r2 < 0) {
                 ++completed;
-                if (same<W>(st2, bin)) {
-                    ++valid;
-                    add_kept(acc, amp2);
+                {
+                    const bool ok = same<W>(st2, bin);
+                    valid += ok ? 1u : 0u;
+                    add_kept(acc, amp2, ok);
                 }
                 ++hs;
             } else {

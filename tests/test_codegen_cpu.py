@@ -37,6 +37,8 @@ static inline double __fma_rn(double a, double b, double c) { return std::fma(a,
 static inline double __dmul_rn(double a, double b) { return a * b; }
 static inline int __double2hiint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u >> 32); }
 static inline int __double2loint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u & 0xffffffffu); }
+static inline unsigned __activemask() { return 0xffffffffu; }
+static inline bool __any_sync(unsigned, bool p) { return p; }   // one lane on the host
 static inline long long __double_as_longlong(double x) { long long u; std::memcpy(&u, &x, 8); return u; }
 static inline double __hiloint2double(int hi, int lo)
 {

@@ -426,10 +426,12 @@ def test_edge_cases_ragged_and_empty():
 
 @pytest.mark.parametrize("case", ["qaoa_exact", "qaoa_eps", "qw", "qw96", "rand7", "rand70", "aa"])
 def test_engines_bitwise_equal(case):
-    """The generated straight-line kernel and the interpreter agree: to the
-    bit in threshold mode (same factors, same order), within the exact-mode
-    tolerance when the generated code defers two-valued factors into
-    per-class tables (exact mode); counters always exactly."""
+    """The generated straight-line kernel and the interpreter agree within
+    the exact-mode tolerance (the generated code defers two-valued factors
+    into per-class tables: in exact mode everywhere, with a threshold after
+    the last |beta| test), and their counters exactly: with a threshold every
+    test sees the same double in both engines, so every pruning decision is
+    the same."""
     if case.startswith("qaoa"):
         w = qaoa_workload(8, 2, n_out=40, seed=77)
         jobs = [(w.circuit, w.inputs, w.outputs, 0.05 if case == "qaoa_eps" else 0.0)]
@@ -452,10 +454,7 @@ def test_engines_bitwise_equal(case):
     a2, s2, b2 = run_batch(jobs, engine="interp")
     assert b1.engine()[0] == "straight" and b2.engine()[0] == "interp"
     for x, y in zip(a1, a2):
-        if jobs[0][3] > 0:
-            assert np.array_equal(x, y)
-        else:
-            close(x, y)
+        close(x, y)
     for x, y in zip(s1, s2):
         for k in ("completed", "valid", "gate_visits", "table_entries"):
             assert x[k] == y[k], k
