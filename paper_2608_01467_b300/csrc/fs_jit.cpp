@@ -420,6 +420,36 @@ __device__ __forceinline__ void store_esum(const JobDev& J, u64 i, double2 acc, 
     }
 }
 
+// History over the compacted live entries of one job.  With A_r < 5 every
+// (live entry, h_r) item keeps its own subtree sum, and each lane takes its
+// next item on its own: the subtrees of a threshold job differ widely in
+// size, and a lane never waits for the rest of its warp.  Otherwise a warp
+// takes 32 consecutive items (one live entry) and adds their sums.
+template <class T>
+__device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u64& valid, u64& visits)
+{
+    const u64 nlive = J.stats[6] << T::Ar;
+    if constexpr (T::Ar < 5) {
+        for (;;) {
+            const u64 i = atomicAdd(&J.stats[7], 1ull);
+            if (i >= nlive) break;
+            J.esum[i] = compact_body<T>(J, i, completed, valid, visits);
+        }
+    } else {
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            u64 base = 0;
+            if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= nlive) break;
+            const u64 i = base + lane;
+            double2 acc = make_double2(0.0, 0.0);
+            if (i < nlive) acc = compact_body<T>(J, i, completed, valid, visits);
+            store_esum(J, i, acc, i < nlive);
+        }
+    }
+}
+
 // Level expansion prologue / epilogue (per-source prefix levels).
 template <class T>
 __device__ __forceinline__ bool lv_load(const JobDev& J, int a_prev, int a_next, const Entry* __restrict__ src,
@@ -956,17 +986,13 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
                std::to_string(j) + "], td.y); break;\n";
     src += "        default: break;\n        }\n        t = __shfl_sync(0xffffffffu, next, 0);\n    }\n}\n";
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job)\n{\n"
-           "    const JobDev& J = jobs[job];\n    const u64 nlive = J.stats[6] << J.Ar;\n    const int lane = threadIdx.x & 31;\n"
-           "    u64 completed = 0, valid = 0, visits = 0;\n    for (;;) {\n"
-           "        u64 base = 0;\n        if (lane == 0) base = atomicAdd(&J.stats[7], 32ull);\n"
-           "        base = __shfl_sync(0xffffffffu, base, 0);\n        if (base >= nlive) break;\n"
-           "        const u64 i = base + lane;\n        double2 acc = make_double2(0.0, 0.0);\n"
-           "        if (i < nlive) {\n            switch (job) {\n";
+           "    const JobDev& J = jobs[job];\n    const int lane = threadIdx.x & 31;\n"
+           "    u64 completed = 0, valid = 0, visits = 0;\n    switch (job) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
         if (jobs[j].compact)
-            src += "            case " + std::to_string(j) + ": acc = compact_body<J" + std::to_string(j) +
-                   ">(J, i, completed, valid, visits); break;\n";
-    src += "            default: break;\n            }\n        }\n        store_esum(J, i, acc, i < nlive);\n    }\n"
+            src += "    case " + std::to_string(j) + ": compact_loop<J" + std::to_string(j) +
+                   ">(J, completed, valid, visits); break;\n";
+    src += "    default: break;\n    }\n"
            "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
            "    if (lane == 0 && (completed | valid | visits)) {\n"
            "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
