@@ -445,6 +445,18 @@ FS_API int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items);
  * checkpoint entries, so cut entries cost nothing downstream. */
 FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau);
 
+/* ---- output sharding across devices or processes -----------------------
+ * Outputs are independent (Sec. IV-D, Observation 5) but their costs differ
+ * (Observation 6).  fs_lpt_assign splits n work units with predicted costs
+ * cost[i] (>= 0, host; e.g. S x Eq. 8 of each output's circuit) over n_ranks
+ * ranks by longest-processing-time-first: units in descending cost (ties by
+ * index) each go to the least loaded rank (ties to the lowest).  rank[i]
+ * (host, n entries) receives unit i's rank and load (host, n_ranks entries,
+ * may be NULL) the summed cost per rank.  No CUDA call; deterministic, so
+ * every process computes the same assignment.  FS_ERR_INVALID for NULL
+ * arrays, n_ranks = 0 or a cost that is negative or not finite. */
+FS_API int fs_lpt_assign(const double* cost, size_t n, uint32_t n_ranks, uint32_t* rank, double* load);
+
 /* ---- failure detection (no counterpart in the paper) ----------------------
  * Bounded device waits: every wait of the tensor-core scoring kernel on an
  * MMA-completion barrier gives up after `polls` polls, records

@@ -1738,6 +1738,30 @@ int fs_mlp_targets(const double* d_sums, uint64_t n, double floor_log10, float* 
     return FS_OK;
 }
 
+int fs_lpt_assign(const double* cost, size_t n, uint32_t n_ranks, uint32_t* rank, double* load)
+{
+    if (n && (!cost || !rank)) return fail(FS_ERR_INVALID, "NULL argument");
+    if (n_ranks == 0) return fail(FS_ERR_INVALID, "n_ranks must be >= 1");
+    for (size_t i = 0; i < n; ++i)
+        if (!(cost[i] >= 0.0) || std::isinf(cost[i])) return fail(FS_ERR_INVALID, "cost %zu is not finite and >= 0", i);
+    // longest processing time first: units by descending cost (ties by
+    // index), each to the least loaded rank (ties to the lowest rank)
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return cost[a] > cost[c]; });
+    std::vector<double> ld(n_ranks, 0.0);
+    for (size_t i : order) {
+        uint32_t best = 0;
+        for (uint32_t r = 1; r < n_ranks; ++r)
+            if (ld[r] < ld[best]) best = r;
+        rank[i] = best;
+        ld[best] += cost[i];
+    }
+    if (load)
+        for (uint32_t r = 0; r < n_ranks; ++r) load[r] = ld[r];
+    return FS_OK;
+}
+
 int fs_set_wait_limit(int64_t polls)
 {
     if (polls > 0xffffffffll) return fail(FS_ERR_INVALID, "at most 2^32 - 1 polls");
