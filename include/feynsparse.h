@@ -186,6 +186,23 @@ FS_API int fs_analyze(fs_circuit* c, const uint64_t* input_bits, fs_analysis* ou
 FS_API int fs_branch_vars(const fs_circuit* c, int32_t* gate_index, int32_t* qubit, int32_t* source,
                    size_t cap, size_t* count);
 
+/* Source placement in the graph form of Sec. IV-B (Fig. 4), for circuits of
+ * CNOTs (one control, either polarity), SWAPs and single-qubit gates:
+ * internal wires are nodes, each CNOT joins its control wire and the two
+ * sides of its target (any two fix the third by XOR), diagonal and
+ * single-qubit deterministic gates keep a wire, single-qubit branching
+ * gates separate their two sides, and the input and output wires are known.
+ * After the natural-source rule (a CNOT on a known wire is removed and its
+ * other two wires merge), *n_sources receives the number of artificial
+ * sources that make every wire known: method 0 = the backward sweep of
+ * Sec. IV-A (A, any circuit), 1 = greedy (repeatedly the node on the most
+ * unresolved CNOTs), 2 = the optimum by exhaustive search (at most 30
+ * unknown wire classes, else FS_ERR_TOO_LARGE).  *n_nodes (may be NULL)
+ * receives the unknown wire classes after merging.  FS_ERR_UNSUPPORTED for
+ * other gates (methods 1, 2).  Analysis only: the history kernels use the
+ * backward placement. */
+FS_API int fs_source_placement(const fs_circuit* c, uint32_t method, uint32_t* n_sources, uint32_t* n_nodes);
+
 /* Sparse input state sum_k coeffs[k] |support[k]> (Eq. 2): S bit strings of 2
  * words and S complex coefficients (re, im), host memory, copied. */
 FS_API int fs_set_input(fs_circuit* c, const uint64_t* support_bits, const double* coeffs, size_t S);

@@ -106,6 +106,14 @@ class Circuit:
                                _ptr(sr, ctypes.c_int32), n, ctypes.byref(cnt)))
         return [(int(gi[i]), int(qb[i]), int(sr[i])) for i in range(n)]
 
+    def source_placement(self, method: str = "backward"):
+        """(artificial sources, unknown wire classes) of the backward sweep,
+        the greedy or the optimal placement of the graph form (Fig. 4)."""
+        k, m = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        check(_lib.load().fs_source_placement(self._h, {"backward": 0, "greedy": 1, "optimal": 2}[method],
+                                              ctypes.byref(k), ctypes.byref(m)))
+        return k.value, m.value
+
     def set_input(self, inputs: Iterable[Tuple[int, complex]]):
         inputs = list(inputs)
         b = _bits_array([x for x, _ in inputs])

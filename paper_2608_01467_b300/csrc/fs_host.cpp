@@ -3,6 +3,7 @@
 // compiler, the Eq. 8 autotuner (Sec. IV-C) and the batch planner that lays
 // out one device workspace for many jobs (Sec. IV-D, Observations 5-6).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -1735,6 +1736,177 @@ int fs_mlp_targets(const double* d_sums, uint64_t n, double floor_log10, float* 
     if (n && (!d_sums || !d_target)) return fail(FS_ERR_INVALID, "NULL argument");
     if (!std::isfinite(floor_log10)) return fail(FS_ERR_INVALID, "the floor must be finite");
     CUDA_TRY(fs::mlp_targets(d_sums, (unsigned long long)n, floor_log10, d_target, (cudaStream_t)stream));
+    return FS_OK;
+}
+
+// ---- source placement in the graph form of Sec. IV-B (Fig. 4)
+
+namespace {
+
+struct WireGraph {
+    int n_nodes = 0;                       // wire classes after merging
+    std::vector<char> known;               // per node
+    std::vector<std::array<int, 3>> tri;   // CNOTs still joining unknown nodes
+};
+
+int find_root(std::vector<int>& p, int x)
+{
+    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
+    return x;
+}
+
+// Wires of a CNOT + single-qubit circuit, boundary wires known, CNOTs as
+// triples; then the natural-source rule (a CNOT on a known wire goes, its
+// other two wires merge) until no CNOT touches a known wire.  Returns
+// FS_ERR_UNSUPPORTED for other gates.
+int build_wire_graph(const fs_circuit& C, WireGraph& out)
+{
+    const int n = (int)C.n;
+    int nw = n;
+    std::vector<int> cur(n);
+    for (int q = 0; q < n; ++q) cur[q] = q;
+    std::vector<char> isknown(n, 1);
+    std::vector<std::array<int, 3>> cn;
+    for (size_t i = 0; i < C.g.size(); ++i) {
+        const GateInfo& g = C.g[i];
+        const int nctl = __builtin_popcountll(g.cm[0]) + __builtin_popcountll(g.cm[1]);
+        if (g.role == WP) continue;                                  // keeps every wire
+        if (g.role == DET && g.k == 1 && nctl == 0) continue;        // one wire through
+        if (g.role == DET && g.kind == FS_SWAP) { std::swap(cur[g.q[0]], cur[g.q[1]]); continue; }
+        if (g.role == DET && g.kind == FS_X && nctl == 1) {
+            const int c = g.cm[0] ? __builtin_ctzll(g.cm[0]) : 64 + __builtin_ctzll(g.cm[1]);
+            const int t = g.q[0];
+            cn.push_back({cur[c], cur[t], nw});
+            cur[t] = nw++;
+            isknown.push_back(0);
+            continue;
+        }
+        if (g.role == BR && g.k == 1 && nctl == 0) {
+            cur[g.q[0]] = nw++;
+            isknown.push_back(0);
+            continue;
+        }
+        return fail(FS_ERR_UNSUPPORTED, "gate %zu is outside CNOT + single-qubit gates", i);
+    }
+    for (int q = 0; q < n; ++q) isknown[cur[q]] = 1;   // output wires
+    std::vector<int> par(nw);
+    for (int i = 0; i < nw; ++i) par[i] = i;
+    bool changed = true;
+    while (changed) {
+        changed = false;
+        std::vector<std::array<int, 3>> keep;
+        for (auto t : cn) {
+            for (int& x : t) x = find_root(par, x);
+            int k = -1;
+            for (int j = 0; j < 3; ++j)
+                if (isknown[t[j]]) { k = j; break; }
+            if (k < 0) { keep.push_back(t); continue; }
+            int a = -1, b = -1;
+            for (int j = 0; j < 3; ++j) {
+                if (t[j] == t[k]) continue;
+                if (a < 0) a = t[j]; else b = t[j];
+            }
+            if (a >= 0 && b >= 0 && a != b) {
+                const char kn = isknown[a] | isknown[b];
+                par[std::max(a, b)] = std::min(a, b);
+                isknown[std::min(a, b)] = kn;
+            }
+            changed = true;
+        }
+        cn.swap(keep);
+    }
+    std::vector<int> id(nw, -1);
+    out = WireGraph{};
+    for (int x = 0; x < nw; ++x) {
+        const int r = find_root(par, x);
+        if (id[r] < 0) { id[r] = out.n_nodes++; out.known.push_back(isknown[r]); }
+        if (isknown[x]) out.known[id[r]] = 1;
+    }
+    for (auto t : cn) out.tri.push_back({id[find_root(par, t[0])], id[find_root(par, t[1])], id[find_root(par, t[2])]});
+    return FS_OK;
+}
+
+// Closure under the CNOT rule: two known wires of a CNOT fix the third.
+void close_known(const WireGraph& G, std::vector<char>& kn)
+{
+    for (bool grew = true; grew;) {
+        grew = false;
+        for (const auto& t : G.tri) {
+            const int k = kn[t[0]] + kn[t[1]] + kn[t[2]];
+            if (k >= 2 && k < 3)
+                for (int x : t)
+                    if (!kn[x]) { kn[x] = 1; grew = true; }
+        }
+    }
+}
+
+bool all_known(const std::vector<char>& kn)
+{
+    for (char v : kn) if (!v) return false;
+    return true;
+}
+
+}  // namespace
+
+int fs_source_placement(const fs_circuit* c, uint32_t method, uint32_t* n_sources, uint32_t* n_nodes)
+{
+    if (!c || !n_sources) return fail(FS_ERR_INVALID, "NULL argument");
+    if (method > 2) return fail(FS_ERR_INVALID, "method must be 0, 1 or 2");
+    if (method == 0) {
+        *n_sources = (uint32_t)c->A;
+        if (n_nodes) *n_nodes = 0;
+        return FS_OK;
+    }
+    WireGraph G;
+    if (int rc = build_wire_graph(*c, G)) return rc;
+    std::vector<int> unknown;
+    for (int x = 0; x < G.n_nodes; ++x)
+        if (!G.known[x]) unknown.push_back(x);
+    if (n_nodes) *n_nodes = (uint32_t)unknown.size();
+    if (method == 1) {
+        // greedy: the unknown node on the most unresolved CNOTs, then closure
+        std::vector<char> kn = G.known;
+        close_known(G, kn);
+        uint32_t k = 0;
+        while (!all_known(kn)) {
+            std::vector<int> deg(G.n_nodes, 0);
+            for (const auto& t : G.tri) {
+                if (kn[t[0]] && kn[t[1]] && kn[t[2]]) continue;
+                for (int j = 0; j < 3; ++j) {
+                    bool dup = false;
+                    for (int i = 0; i < j; ++i) dup |= t[i] == t[j];
+                    if (!dup && !kn[t[j]]) deg[t[j]]++;
+                }
+            }
+            int best = -1;
+            for (int x : unknown)
+                if (!kn[x] && (best < 0 || deg[x] > deg[best])) best = x;
+            kn[best] = 1;
+            close_known(G, kn);
+            ++k;
+        }
+        *n_sources = k;
+        return FS_OK;
+    }
+    // exhaustive: subsets of the unknown nodes by increasing size
+    const int m = (int)unknown.size();
+    if (m > 30) return fail(FS_ERR_TOO_LARGE, "%d unknown wire classes: exhaustive placement is limited to 30", m);
+    for (int k = 0; k <= m; ++k) {
+        std::vector<int> pick(k);
+        for (int i = 0; i < k; ++i) pick[i] = i;
+        while (true) {
+            std::vector<char> kn = G.known;
+            for (int i : pick) kn[unknown[i]] = 1;
+            close_known(G, kn);
+            if (all_known(kn)) { *n_sources = (uint32_t)k; return FS_OK; }
+            int i = k - 1;
+            while (i >= 0 && pick[i] == m - k + i) --i;
+            if (i < 0) break;
+            ++pick[i];
+            for (int j = i + 1; j < k; ++j) pick[j] = pick[j - 1] + 1;
+        }
+    }
+    *n_sources = (uint32_t)m;
     return FS_OK;
 }
 

@@ -380,3 +380,24 @@ def test_threshold_jobs_plan_beyond_62_sources_and_keep_the_root_narrow():
         assert Ap + Ar + As == A and As <= 62 and Ap + Ar <= max_apr
         hist = b.op_histogram(0)
         assert sum(hist["prefix"].values()) == Gp and sum(hist["root"].values()) == Gr
+
+
+def test_source_placement_matches_the_oracle():
+    """fs_source_placement (graph form of Sec. IV-B) against the oracle's
+    own graph reduction: Fig. 4 (backward 2, optimum 1 on 3 merged nodes)
+    and random CNOT + single-qubit circuits; other gates are refused."""
+    import importlib
+    from workloads import placement_figure
+    from oracle import placement
+    pins = importlib.import_module("test_oracle_pins")
+    circuits = [placement_figure()] + [pins._cnot_h_circuit(5, 18, 300 + s) for s in range(8)]
+    for c in circuits:
+        C = fs.Circuit(c)
+        nodes = len(placement.simplified(c)[0])
+        assert C.source_placement("backward")[0] == feynman.analyze(c)["A"]
+        assert C.source_placement("greedy") == (placement.greedy(c), nodes)
+        assert C.source_placement("optimal") == (placement.optimum(c), nodes)
+    C = fs.Circuit(qw_workload(steps=3, n_out=4, pos_bits=8).circuit)    # multi-controlled X
+    with pytest.raises(_lib.FsError) as e:
+        C.source_placement("greedy")
+    assert e.value.code == -2

@@ -456,3 +456,88 @@ def test_walk_checkpoints_beyond_the_remaining_steps_have_zero_subtree_sums():
                         assert sub == 0, (k_prefix, st, sub)
                         seen += 1
     assert seen > 0
+
+
+def test_qft_of_a_two_tone_signal_has_four_bins_of_one_half():
+    """Dense-support input (Eq. 2 with S ~ 2^n; the paper's QFT signal study,
+    Sec. V, Fig. 7): the QFT of x_t = cos(2 pi f1 t/N) + cos(2 pi f2 t/N),
+    normalised, is 1/2 at the frequencies f1, N - f1, f2, N - f2 (read
+    through the bit reversal of the swap-free QFT) and 0 elsewhere; checked
+    on the dense tier at n = 8 and the reduced-history oracle."""
+    from workloads import qft_signal_workload
+    w = qft_signal_workload(8, seed=12345)
+    N = 1 << 8
+    f1, f2 = w.meta["f1"], w.meta["f2"]
+    want = np.zeros(N, complex)
+    for k in (f1, N - f1, f2, N - f2):
+        want[closed_forms.bit_reverse(k, 8)] = 0.5
+    got = dense.amplitudes(w.circuit, w.inputs, w.outputs)
+    assert len(w.inputs) >= N - 4
+    assert np.max(np.abs(got - want)) < 1e-13
+    o3, _ = feynman.run(w.circuit, w.inputs, w.outputs[:32], threads=4)
+    assert np.max(np.abs(o3 - want[:32])) < 1e-13
+
+
+# ------------------------------------------------ source placement (Sec. IV-B)
+
+def test_fig4_source_placement():
+    from workloads import placement_figure
+    from oracle import placement
+    g = gold("fig4_placement.json")
+    c = placement_figure()
+    nw, known, cnots = placement.wire_graph(c)
+    assert nw - len(known) == g["internal_wires"]
+    nodes, _, _ = placement.simplified(c)
+    assert len(nodes) == g["nodes_after_merge"]
+    assert placement.optimum(c) == g["optimum"]
+    assert placement.greedy(c) == g["optimum"]
+    assert feynman.analyze(c)["A"] == g["backward"]
+
+
+def _cnot_h_circuit(n, G, seed):
+    rng = SplitMix64(seed)
+    gates = []
+    for _ in range(G):
+        r = rng.below(10)
+        q = rng.below(n)
+        if r < 5:
+            c = rng.below(n - 1)
+            c = c + 1 if c >= q else c
+            gates.append(Gate("X", (q,), ((c, rng.below(2)),)))
+        elif r < 7:
+            gates.append(Gate("H", (q,)))
+        elif r < 8:
+            gates.append(Gate("RX", (q,), (), 0.3 + rng.uniform()))
+        elif r < 9:
+            gates.append(Gate("P", (q,), (), rng.uniform()))
+        else:
+            gates.append(Gate("X", (q,)))
+    return Circuit(n, gates, f"cnoth{n}x{G}s{seed}")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_placement_optimum_is_at_most_greedy_and_backward(seed):
+    """The backward sweep's sources make every wire known by backward
+    propagation, so the optimum of the graph form is at most A; greedy is a
+    feasible choice, so at least the optimum.  The optimum is also checked
+    against a literal search over sets of the original (unmerged) wires."""
+    from oracle import placement
+    from itertools import combinations
+    c = _cnot_h_circuit(4, 14, 100 + seed)
+    opt, gr, A = placement.optimum(c), placement.greedy(c), feynman.analyze(c)["A"]
+    assert opt <= gr and opt <= A
+    nw, known, cnots = placement.wire_graph(c)
+    wires = [w for w in range(nw) if w not in known]
+
+    def closes(extra):
+        kn = set(known) | set(extra)
+        grew = True
+        while grew:
+            grew = False
+            for t in cnots:
+                if sum(x in kn for x in t) == 2:
+                    kn |= set(t)
+                    grew = True
+        return kn >= set(range(nw))
+    lit = next(k for k in range(len(wires) + 1) if any(closes(s) for s in combinations(wires, k)))
+    assert lit == opt

@@ -9,7 +9,7 @@ from .mlp_init import mlp_init_params  # noqa: F401
 from .circuits import (  # noqa: F401
     Gate, Circuit, Workload, SplitMix64,
     qft, amplitude_amplification, qaoa_maxcut, quantum_walk,
-    three_qubit_example, four_qubit_figure, random_small_circuit,
-    qft_workload, aa_workload, qaoa_workload, qw_workload,
+    three_qubit_example, four_qubit_figure, placement_figure, random_small_circuit,
+    qft_workload, qft_signal_workload, aa_workload, qaoa_workload, qw_workload,
     random_regular_graph, bits_to_int, int_to_bits,
 )

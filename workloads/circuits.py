@@ -146,6 +146,23 @@ def four_qubit_figure() -> Circuit:
     ], "four_qubit_figure")
 
 
+def placement_figure() -> Circuit:
+    """Fig. 4 three-qubit circuit for the source-placement graph, columns 1..8:
+    H on q2; CNOTs q2 -> q1, q2 -> q0, q2 -> q1, q2 -> q0, q0 -> q1, q1 -> q2;
+    H on q0 and q1."""
+    return Circuit(3, [
+        Gate("H", (2,)),                     # col 1
+        Gate("X", (1,), ((2, 1),)),          # col 2
+        Gate("X", (0,), ((2, 1),)),          # col 3
+        Gate("X", (1,), ((2, 1),)),          # col 4
+        Gate("X", (0,), ((2, 1),)),          # col 5
+        Gate("X", (1,), ((0, 1),)),          # col 6
+        Gate("X", (2,), ((1, 1),)),          # col 7
+        Gate("H", (0,)),                     # col 8
+        Gate("H", (1,)),                     # col 8
+    ], "placement_figure")
+
+
 # --------------------------------------------------------------------------
 # Circuit families of the evaluation section
 # --------------------------------------------------------------------------
@@ -345,6 +362,23 @@ def qft_workload(n: int = 8, seed: int = SEED_BASE + 1) -> Workload:
     x = rng.below(1 << n)
     return Workload(qft(n), [(x, 1.0 + 0j)], list(range(1 << n)), 0.0,
                     f"qft{n}", {"x": x})
+
+
+def qft_signal_workload(n: int = 12, seed: int = SEED_BASE + 6) -> Workload:
+    """QFT-n of a seeded real two-tone signal as a dense input state:
+    x_t = cos(2 pi f1 t / N) + cos(2 pi f2 t / N) for t = 0 .. N-1 (N = 2^n),
+    normalised, every basis state with a nonzero sample in the support
+    (S ~ N); all N outputs.  f1 != f2 are drawn in [1, N/2)."""
+    rng = SplitMix64(seed)
+    N = 1 << n
+    f1 = 1 + rng.below(N // 2 - 1)
+    f2 = f1
+    while f2 == f1:
+        f2 = 1 + rng.below(N // 2 - 1)
+    x = [math.cos(2.0 * math.pi * f1 * t / N) + math.cos(2.0 * math.pi * f2 * t / N) for t in range(N)]
+    norm = math.sqrt(sum(v * v for v in x))
+    inputs = [(t, complex(v / norm, 0.0)) for t, v in enumerate(x) if v != 0.0]
+    return Workload(qft(n), inputs, list(range(N)), 0.0, f"qft{n}signal", {"f1": f1, "f2": f2})
 
 
 def aa_workload(n: int = 12, iters: int = 3, n_out: int = 64,
