@@ -1122,6 +1122,11 @@ static std::vector<fs::JitJobSpec> jit_specs(const fs_batch* b)
         specs[ji] = fs::JitJobSpec{j.prog.ops.data(), (int)j.prog.ops.size(), j.prog.masks.data(),
                                    j.prog.fac.data(), j.W, j.sp.c1, j.sp.c2, j.sp.Ap, j.sp.Ar,
                                    j.sp.As, j.eps * j.eps, j.compact, j.levels};
+        // the generated prefix applies the exact bound where it writes the
+        // table and, without a learned pruner, counts the live entries
+        specs[ji].bound = j.bound;
+        specs[ji].bound_counts = j.bound && !j.d_pruner;
+        specs[ji].bspec = j.bspec;
     }
     return specs;
 }
@@ -1305,7 +1310,7 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         flat_prefix |= j.levels.empty();
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
-        if (j.bound) k += 1;                    // exact bound
+        if (j.bound && b->opt.engine == 1) k += 1;   // exact bound (inside the generated prefix otherwise)
         if (j.compact) k += (j.d_pruner || j.bound) ? 3 : 4;   // [count,] scan, write (with pair ranges), history over live entries
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
@@ -1373,6 +1378,13 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     const int nj = (int)b->jobs.size();
     const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
     CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
+    // the generated prefix of a job with the exact bound and no learned
+    // pruner counts the live entries per compaction block as it writes them
+    if (b->jit)
+        for (int ji = 0; ji < nj; ++ji) {
+            const Job& j = b->jobs[ji];
+            if (j.bound && !j.d_pruner) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
+        }
     if (b->timing) CUDA_TRY(record(b->ev[0], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
@@ -1402,9 +1414,11 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
         // the last checkpoint step (exact bound, then learned pruner) counts
-        // the entries it leaves live per compaction block
-        if (j.bound || j.d_pruner) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
-        if (j.bound)
+        // the entries it leaves live per compaction block; the generated
+        // prefix has applied the bound already
+        const bool bound_kernel = j.bound && !b->jit;
+        if (bound_kernel || j.d_pruner) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
+        if (bound_kernel)
             CUDA_TRY(fs::launch_bound_prune(jobs, ji, j.bspec, j.table_entries, j.d_pruner == nullptr, s));
         if (j.d_pruner)
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries,

@@ -223,6 +223,11 @@ struct JitJobSpec {
     double eps2;
     bool compact;
     std::vector<PrefixLevel> levels;   // empty: single-region prefix
+    // exact reachability bound applied where the table is written; with
+    // bound_counts the same kernel counts the live entries per compaction
+    // block (the job has no learned pruner to do it)
+    bool bound = false, bound_counts = false;
+    BoundSpec bspec{};
 };
 // The generated source for these jobs (what jit_build compiles), without
 // compiling it.

@@ -199,7 +199,14 @@ __device__ __forceinline__ bool is_bottom(double x)
 // the state after each of its source ops (a checkpoint per source, the
 // per-source limit of Algorithm 2's regions) and restarts the next history
 // at the first source whose bit changed, instead of at the region's start.
-template <class T>
+//
+// WARP (stacked suffixes with at least 5 sources): the 32 lanes of a warp
+// share one root checkpoint; lane L takes the histories whose last 5
+// sources are the bits of L, and the warp walks the other sources together.
+// Those are the same for every lane, so are the state, the amplitude and
+// every cut decision above the last 5 sources: the walk is one converged
+// loop, and only the last 5 segments differ between lanes.
+template <class T, bool WARP = false>
 __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp, const u32 (&bin)[T::W],
                                               u64& completed, u64& valid, u64& visits)
 {
@@ -208,6 +215,51 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
     typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
     const hs_t ns = (hs_t)1 << T::As;
     hs_t hs = 0;
+    if constexpr (WARP) {
+        static_assert(T::STACKED && T::As >= 5, "warp walk needs a stacked suffix of at least 5 sources");
+        constexpr int LB = 5;
+        const hs_t lane = (hs_t)(threadIdx.x & 31);
+        u32 sst[T::As][W];
+        double2 sam[T::As];
+        int start = 0;
+        hs = lane;
+        while (hs < ns) {
+            u32 st2[W];
+            double2 amp2;
+            if (start == 0) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) st2[j] = st[j];
+                amp2 = amp;
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) st2[j] = sst[start - 1][j];
+                amp2 = sam[start - 1];
+            }
+            const int r2 = T::suffix_from(start, st2, amp2, (u64)hs, bin, visits, sst, sam);
+            hs_t nx;
+            if (r2 < 0) {
+                ++completed;
+                u32 d = 0;
+#pragma unroll
+                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
+                const bool ok = d == 0u;
+                valid += ok ? 1u : 0u;
+                add_kept(acc, amp2, ok);
+                nx = hs + (hs_t)32;
+            } else if (r2 >= LB) {
+                nx = (((hs >> r2) + (hs_t)1) << r2) | lane;   // every lane was cut here
+            } else {
+                nx = hs + (hs_t)32;                           // only this lane's history
+            }
+            if (nx < ns) {
+                const int msb = sizeof(hs_t) == 4 ? 31 - __clz((u32)(hs ^ nx))
+                                                  : 63 - __clzll((long long)(u64)(hs ^ nx));
+                start = T::As - 1 - msb;
+            }
+            hs = nx;
+        }
+        return acc;
+    }
     if constexpr (T::STACKED) {
         u32 sst[T::As][W];
         double2 sam[T::As];
@@ -383,7 +435,7 @@ __device__ void tile_body(const JobDev& J, u64 tile)
     }
 }
 
-template <class T>
+template <class T, bool WARP = false>
 __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
@@ -403,7 +455,7 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
 #pragma unroll
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 acc = make_double2(0.0, 0.0);
-    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T>(st, amp, bin, completed, valid, visits);
+    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T, WARP>(st, amp, bin, completed, valid, visits);
     return acc;
 }
 
@@ -429,7 +481,19 @@ template <class T>
 __device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u64& valid, u64& visits)
 {
     const u64 nlive = J.stats[6] << T::Ar;
-    if constexpr (T::Ar < 5) {
+    if constexpr (T::STACKED && T::As >= 5 && T::Ar < 5) {
+        // a warp per item: the lanes split its last 5 suffix sources
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            u64 i = 0;
+            if (lane == 0) i = atomicAdd(&J.stats[7], 1ull);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= nlive) break;
+            double2 acc = compact_body<T, true>(J, i, completed, valid, visits);
+            acc = group_sum(acc, 32);
+            if (lane == 0) J.esum[i] = acc;
+        }
+    } else if constexpr (T::Ar < 5) {
         for (;;) {
             const u64 i = atomicAdd(&J.stats[7], 1ull);
             if (i >= nlive) break;
@@ -500,7 +564,7 @@ __device__ __forceinline__ int find_job(const u64* __restrict__ begin, int n_job
 }
 
 template <class T>
-__device__ __forceinline__ void prefix_body(const JobDev& J, u64 local, u64& visits, u64& entries)
+__device__ __forceinline__ bool prefix_body(const JobDev& J, u64 local, u64& visits, u64& entries, u64& bcuts)
 {
     constexpr int W = T::W;
     const u64 pair = local >> T::Ap;
@@ -519,11 +583,32 @@ __device__ __forceinline__ void prefix_body(const JobDev& J, u64 local, u64& vis
     u32 w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int j = 0; j < W; ++j) w[j] = st[j];
-    if (r >= 0) amp.x = __longlong_as_double(0x7ff8000000000000ll);
-    else entries += 1;
+    bool live = r < 0;
+    if (live) entries += 1;
+    if constexpr (T::BOUND) {
+        if (live && T::bound_cut(st, bin)) {   // exact: this entry cannot reach b_in
+            live = false;
+            ++bcuts;
+        }
+    }
+    if (!live) amp.x = __longlong_as_double(0x7ff8000000000000ll);
     uint4* dst = reinterpret_cast<uint4*>(J.table + local);
     dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
     reinterpret_cast<double2*>(dst + 1)[0] = amp;
+    return live;
+}
+
+// Live entries of a compaction block, counted by the warp that wrote them
+// (one atomic when its 32 lanes lie in one block of one job).
+__device__ __forceinline__ void count_live(const JobDev& J, u64 local, bool live, bool uniform)
+{
+    const unsigned keep = __ballot_sync(0xffffffffu, live);
+    const u64 first = __shfl_sync(0xffffffffu, local, 0), last = __shfl_sync(0xffffffffu, local, 31);
+    if (uniform && (first >> 10) == (last >> 10) && last == first + 31u) {
+        if ((threadIdx.x & 31) == 0 && keep) atomicAdd(&J.blk[first >> 10], (unsigned)__popc(keep));
+    } else if (live) {
+        atomicAdd(&J.blk[local >> 10], 1u);
+    }
 }
 )PRE";
 
@@ -643,10 +728,15 @@ std::string emit_cascade(const CascadeRun& r, int W)
         char buf[64];
         snprintf(buf, sizeof buf, "0x%08xu", F);
         const std::string ws = std::to_string(w);
+        // a borrow leaves the first word only when its part of the field is
+        // all ones (x - 1) or all zeros (x + 1): the later words sit behind
+        // a vote, so a warp in which no lane borrows skips them
+        if (w == w0 + 1) c += "if (__any_sync(__activemask(), b != 0u)) { ";
         c += "{ const u32 y = " + std::string(r.dec ? "" : "~") + "s[" + ws + "] & " + buf + "; const u32 d = y - b; ";
         if (w < w1) c += "b = (y < b) ? 1u : 0u; ";
         c += "s[" + ws + "] ^= (y ^ d) & " + buf + "; } ";
     }
+    if (w1 > w0) c += "} ";
     c += "}";
     bool any = false;
     for (int j = 0; j < W; ++j) any |= r.cm[j] != 0;
@@ -907,6 +997,61 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
     out += "    visits += " + std::to_string(e1 - seg_e0) + "ull;\n    (void)low;\n    return -1;\n";
 }
 
+// The exact reachability bound of a job as code (the BoundSpec as
+// immediates): true when the checkpoint state s cannot reach bin.
+std::string emit_bound(const JitJobSpec& J)
+{
+    const int W = J.W;
+    std::string c = "  static __device__ __forceinline__ bool bound_cut(const u32 (&s)[" + std::to_string(W) +
+                    "], const u32 (&bin)[" + std::to_string(W) + "]) {\n";
+    if (!J.bound) return c + "    (void)s; (void)bin;\n    return false;\n  }\n";
+    c += "    u32 d = 0u;\n";
+    for (int j = 0; j < W; ++j)
+        if (J.bspec.frozen[j]) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "    d |= (s[%d] ^ bin[%d]) & 0x%08xu;\n", j, j, J.bspec.frozen[j]);
+            c += buf;
+        }
+    c += "    if (d) return true;\n";
+    // a field: its value in 32-bit words (funnel shifts at fixed offsets),
+    // both cyclic differences by borrow chains, each compared with the radius
+    for (int f = 0; f < J.bspec.n_fields; ++f) {
+        const int t0 = J.bspec.t0[f], len = J.bspec.len[f], FW = (len + 31) / 32;
+        const uint32_t top = (len % 32) ? ((1u << (len % 32)) - 1u) : 0xffffffffu;
+        c += "    {\n";
+        auto word = [&](const std::string& v, int k) {
+            const int pos = t0 + 32 * k, w = pos >> 5, sh = pos & 31;
+            const std::string lo = w < W ? v + "[" + std::to_string(w) + "]" : "0u";
+            const std::string hi = w + 1 < W ? v + "[" + std::to_string(w + 1) + "]" : "0u";
+            return sh ? "__funnelshift_r(" + lo + ", " + hi + ", " + std::to_string(sh) + "u)" : lo;
+        };
+        for (int k = 0; k < FW; ++k) {
+            char m[32];
+            snprintf(m, sizeof m, "0x%08xu", k == FW - 1 ? top : 0xffffffffu);
+            c += "      const u32 a" + std::to_string(k) + " = " + word("s", k) + " & " + m + ", b" + std::to_string(k) +
+                 " = " + word("bin", k) + " & " + m + ";\n";
+        }
+        for (const char* dir : {"u", "v"}) {   // u = a - b, v = b - a (mod 2^len)
+            const bool ab = dir[0] == 'u';
+            c += "      u32 " + std::string(dir) + "br = 0u;\n";
+            for (int k = 0; k < FW; ++k) {
+                const std::string x = (ab ? "a" : "b") + std::to_string(k), y = (ab ? "b" : "a") + std::to_string(k);
+                char m[32];
+                snprintf(m, sizeof m, "0x%08xu", k == FW - 1 ? top : 0xffffffffu);
+                c += "      const u32 " + std::string(dir) + std::to_string(k) + " = (" + x + " - " + y + " - " + dir +
+                     "br) & " + m + "; " + dir + "br = (" + x + " < " + y + ") || (" + x + " == " + y + " && " + dir +
+                     "br) ? 1u : 0u;\n";
+            }
+            std::string hiw = "0u";
+            for (int k = 1; k < FW; ++k) hiw += " | " + std::string(dir) + std::to_string(k);
+            c += "      const bool " + std::string(dir) + "far = (" + hiw + ") != 0u || " + dir + "0 > " +
+                 std::to_string(J.bspec.radius[f]) + "u;\n";
+        }
+        c += "      if (ufar && vfar) return true;\n    }\n";
+    }
+    return c + "    return false;\n  }\n";
+}
+
 // Threshold jobs whose suffix carries at least two artificial sources, one
 // per op, run the stacked suffix (a checkpoint after every source op).
 bool stacked_suffix(const JitJobSpec& J)
@@ -934,6 +1079,9 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         structs += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
                    std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
         structs += std::string("  static constexpr bool STACKED = ") + (stacked ? "true" : "false") + ";\n";
+        structs += std::string("  static constexpr bool BOUND = ") + (J.bound ? "true" : "false") +
+                   ", COUNTB = " + (J.bound && J.bound_counts ? "true" : "false") + ";\n";
+        structs += emit_bound(J);
         const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
         structs += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
         if (J.levels.empty()) emit_region(structs, globals, js + "p", J, 0, J.c1, J.Ap);
@@ -1002,40 +1150,58 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_lv_" + js +
                "(const JobDev* __restrict__ jobs, int level, int a_prev, int a_next, const Entry* __restrict__ src, "
                "Entry* __restrict__ dst, u64 n, int last)\n{\n"
-               "    const JobDev& J = jobs[" + js + "];\n    u64 visits = 0, entries = 0;\n"
-               "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (u64)gridDim.x * blockDim.x) {\n"
+               "    const JobDev& J = jobs[" + js + "];\n    u64 visits = 0, entries = 0, bcuts = 0;\n"
+               "    for (u64 base = (u64)blockIdx.x * blockDim.x; base < n; base += (u64)gridDim.x * blockDim.x) {\n"
+               "        const u64 idx = base + threadIdx.x;\n"
+               "        bool live = false;\n"
+               "        if (idx < n) {\n"
                "        u32 st[" + T + "::W], bin[" + T + "::W];\n        double2 a;\n"
-               "        bool live = lv_load<" + T + ">(J, a_prev, a_next, src, idx, st, bin, a);\n"
+               "        live = lv_load<" + T + ">(J, a_prev, a_next, src, idx, st, bin, a);\n"
                "        if (live) {\n            const u64 h = (idx & ((1ull << a_next) - 1ull)) << (" + T + "::Ap - a_next);\n"
                "            int r = -1;\n            switch (level) {\n";
         for (size_t k = 0; k < jobs[j].levels.size(); ++k)
             src += "            case " + std::to_string(k) + ": r = " + T + "::lv" + std::to_string(k) + "(st, a, h, bin, visits); break;\n";
         src += "            default: break;\n            }\n            live = r < 0;\n        }\n"
                "        if (live && last) ++entries;\n"
-               "        lv_store<" + T + ">(dst, idx, st, a, live);\n    }\n"
-               "    visits = warp_sum_u64(visits);\n    entries = warp_sum_u64(entries);\n"
+               "        if (" + T + "::BOUND && last && live && " + T + "::bound_cut(st, bin)) { live = false; ++bcuts; }\n"
+               "        lv_store<" + T + ">(dst, idx, st, a, live);\n"
+               "        }\n";
+        // every lane of the warp reaches the one count (its ballot is warp-wide)
+        if (jobs[j].bound && jobs[j].bound_counts)
+            src += "        if (last) count_live(J, idx, live, true);\n";
+        src += "    }\n"
+               "    visits = warp_sum_u64(visits);\n    entries = warp_sum_u64(entries);\n    bcuts = warp_sum_u64(bcuts);\n"
                "    if ((threadIdx.x & 31) == 0) {\n        if (visits) atomicAdd(&J.stats[4], visits);\n"
-               "        if (entries) atomicAdd(&J.stats[3], entries);\n    }\n}\n";
+               "        if (entries) atomicAdd(&J.stats[3], entries);\n        if (bcuts) atomicAdd(&J.stats[8], bcuts);\n    }\n}\n";
     }
+    bool any_count = false;
+    for (const JitJobSpec& J : jobs) any_count |= J.bound && J.bound_counts && J.levels.empty();
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_prefix(const JobDev* __restrict__ jobs, "
            "const u64* __restrict__ begin, int n_jobs, u64 total)\n{\n"
            "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (u64)gridDim.x * blockDim.x) {\n"
            "        if (!__any_sync(0xffffffffu, idx < total)) break;\n"
-           "        u64 visits = 0, entries = 0;\n        int j = 0;\n"
+           "        u64 visits = 0, entries = 0, bcuts = 0, local = 0;\n        int j = 0;\n"
+           "        bool live = false, counts = false;\n"
            "        if (idx < total) {\n            j = find_job(begin, n_jobs, idx);\n"
-           "            const u64 local = idx - jobs[j].prefix_begin;\n            switch (j) {\n";
+           "            local = idx - jobs[j].prefix_begin;\n            switch (j) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
-        src += "            case " + std::to_string(j) + ": prefix_body<J" + std::to_string(j) + ">(jobs[" +
-               std::to_string(j) + "], local, visits, entries); break;\n";
+        src += "            case " + std::to_string(j) + ": live = prefix_body<J" + std::to_string(j) + ">(jobs[" +
+               std::to_string(j) + "], local, visits, entries, bcuts); counts = J" + std::to_string(j) +
+               "::COUNTB; break;\n";
     src += "            default: break;\n            }\n        }\n"
            "        const unsigned act = __ballot_sync(0xffffffffu, idx < total);\n"
            "        const unsigned same = __match_any_sync(0xffffffffu, idx < total ? j : -1);\n"
-           "        if (act == 0xffffffffu && same == 0xffffffffu) {\n"
-           "            const u64 v = warp_sum_u64(visits), en = warp_sum_u64(entries);\n"
-           "            if ((threadIdx.x & 31) == 0) { atomicAdd(&jobs[j].stats[4], v); atomicAdd(&jobs[j].stats[3], en); }\n"
+           "        const bool uniform = act == 0xffffffffu && same == 0xffffffffu;\n";
+    if (any_count)
+        src += "        if (__any_sync(0xffffffffu, counts)) count_live(jobs[j], local, live && counts, uniform && counts);\n";
+    src += "        if (uniform) {\n"
+           "            const u64 v = warp_sum_u64(visits), en = warp_sum_u64(entries), bc = warp_sum_u64(bcuts);\n"
+           "            if ((threadIdx.x & 31) == 0) { atomicAdd(&jobs[j].stats[4], v); atomicAdd(&jobs[j].stats[3], en);\n"
+           "                                           if (bc) atomicAdd(&jobs[j].stats[8], bc); }\n"
            "        } else if (idx < total) {\n"
            "            if (visits) atomicAdd(&jobs[j].stats[4], visits);\n"
            "            if (entries) atomicAdd(&jobs[j].stats[3], entries);\n"
+           "            if (bcuts) atomicAdd(&jobs[j].stats[8], bcuts);\n"
            "        }\n    }\n}\n";
     return src;
 }

@@ -38,6 +38,11 @@ static inline double __dmul_rn(double a, double b) { return a * b; }
 static inline int __double2hiint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u >> 32); }
 static inline int __double2loint(double x) { uint64_t u; std::memcpy(&u, &x, 8); return (int)(u & 0xffffffffu); }
 static inline unsigned __activemask() { return 0xffffffffu; }
+static inline unsigned __funnelshift_r(unsigned lo, unsigned hi, unsigned s)
+{
+    s &= 31u;
+    return s ? (lo >> s) | (hi << (32u - s)) : lo;
+}
 static inline bool __any_sync(unsigned, bool p) { return p; }   // one lane on the host
 static inline long long __double_as_longlong(double x) { long long u; std::memcpy(&u, &x, 8); return u; }
 static inline double __hiloint2double(int hi, int lo)
@@ -178,12 +183,16 @@ SUFFIX_PLAIN = """
                         if (ok) { sr += a3.x; si += a3.y; ++valid; }
                     }"""
 SUFFIX_STACKED = """
-                    {
+                    for (u64 lane = 0; lane < ((J0::As >= 5 && J0::Ar < 5) ? 32u : 1u); ++lane) {
+                        // with 5 or more suffix sources the device runs a warp per
+                        // root checkpoint, lane L taking the histories whose last 5
+                        // sources are the bits of L; lanes are independent here
+                        const bool warp = J0::As >= 5 && J0::Ar < 5;
                         u32 sst[J0::As][W];
                         double2 sam[J0::As];
                         int start = 0;
                         const u64 ns = 1ull << J0::As;
-                        u64 hs = 0;
+                        u64 hs = warp ? lane : 0;
                         while (hs < ns) {
                             u32 st3[W];
                             double2 a3;
@@ -196,9 +205,11 @@ SUFFIX_STACKED = """
                                 bool ok = true;
                                 for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
                                 if (ok) { sr += a3.x; si += a3.y; ++valid; }
-                                nx = hs + 1;
+                                nx = warp ? hs + 32 : hs + 1;
+                            } else if (warp && r2 < 5) {
+                                nx = hs + 32;
                             } else {
-                                nx = ((hs >> r2) + 1) << r2;
+                                nx = (((hs >> r2) + 1) << r2) | (warp ? lane : 0);
                             }
                             if (nx < ns) start = J0::As - 1 - (63 - __builtin_clzll(hs ^ nx));
                             hs = nx;
@@ -398,3 +409,58 @@ def test_stacked_suffix_matches_the_oracle(family, eps, tmp_path):
     _close(got, want)
     assert np.array_equal(completed, cnt["completed"].astype(np.int64))
     assert np.array_equal(valid, cnt["valid"].astype(np.int64))
+
+
+def test_generated_exact_bound_matches_the_reachability_rule(tmp_path):
+    """The exact reachability bound as generated code (bound_cut of the job,
+    compiled for the host): on the walk the remaining ops move the position
+    by at most two per remaining step (a +1 and a -1 cascade) and never touch
+    the third ancilla, so a state is cut iff that ancilla differs from the
+    input's or the cyclic position distance exceeds twice the remaining
+    steps.  Checked on 96-bit positions (fields across register words) and
+    8-bit ones, on random states near and far from the input."""
+    from workloads import qw_workload
+    for pos_bits, steps, k_prefix in ((96, 6, 2), (8, 6, 3)):
+        w = qw_workload(steps=steps, n_out=8, pos_bits=pos_bits)
+        G = len(w.circuit.gates)
+        c1 = k_prefix * (G // steps)
+        radius = 2 * (steps - k_prefix)
+        C = fs.Circuit(w.circuit)
+        C.set_input(w.inputs)
+        b = fs.Batch(split="fixed", c1=c1, c2=c1)
+        b.add(C, w.outputs)
+        b.set_exact_bound(0)
+        b.plan()
+        src = b.generated_source()
+        helpers, body, _, _ = _extract(src)
+        W = 4 if pos_bits > 32 else 1
+        mask = (1 << pos_bits) - 1
+        rng = SplitMix64(pos_bits)
+        b_in = w.inputs[0][0]
+        cases = []
+        for _ in range(400):
+            d = rng.below(4 * radius + 5) - 2 * radius - 2
+            if rng.below(4) == 0:
+                d = rng.bits(pos_bits)
+            pos = (((b_in >> 1) & mask) + d) & mask
+            s = (b_in & ~(mask << 1)) | (pos << 1) | rng.below(2) | (rng.below(4) << (pos_bits + 1))
+            if rng.below(8) == 0:
+                s ^= 1 << (pos_bits + 3)
+            cases.append(s)
+        words = lambda v: "{" + ", ".join(f"{(v >> (32 * j)) & 0xffffffff}u" for j in range(W)) + "}"
+        drv = ("int main() {\n    static const u32 st[][%d] = {%s};\n    const u32 bin[%d] = %s;\n"
+               "    for (unsigned i = 0; i < %d; ++i) std::printf(\"%%d\\n\", J0::bound_cut(st[i], bin) ? 1 : 0);\n"
+               "    return 0;\n}\n") % (W, ", ".join(words(s) for s in cases), W, words(b_in), len(cases))
+        path = os.path.join(str(tmp_path), f"bound{pos_bits}.cpp")
+        with open(path, "w") as f:
+            f.write(SHIM + helpers + body + drv)
+        exe = path[:-4]
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-w", "-o", exe, path])
+        got = [int(x) for x in subprocess.check_output([exe]).decode().split()]
+        want = []
+        for s in cases:
+            x, y = (s >> 1) & mask, (b_in >> 1) & mask
+            dist = min((x - y) & mask, (y - x) & mask)
+            want.append(int(dist > radius or (((s ^ b_in) >> (pos_bits + 3)) & 1) == 1))
+        assert got == want
+        assert 0 < sum(want) < len(want)

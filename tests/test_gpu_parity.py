@@ -456,8 +456,14 @@ def test_engines_bitwise_equal(case):
     for x, y in zip(a1, a2):
         close(x, y)
     for x, y in zip(s1, s2):
-        for k in ("completed", "valid", "gate_visits", "table_entries"):
+        for k in ("completed", "valid", "table_entries"):
             assert x[k] == y[k], k
+        # a threshold job's stacked suffix restarts at the changed source
+        # instead of the region start: it evaluates fewer gates
+        if jobs[0][3] > 0:
+            assert x["gate_visits"] <= y["gate_visits"]
+        else:
+            assert x["gate_visits"] == y["gate_visits"]
     o, _ = oracle_counts(*jobs[0][:3], eps=jobs[0][3])
     close(a1[0], o)
 
