@@ -42,15 +42,47 @@ def workload_jobs(name, rank=0, outputs=None, seed_shift=0):
         w.meta["learned_cut"] = walk_cuts
         return [w], {"workload": f"qw100_t16_{qw_out}out", "qubits": 100, "steps": 16,
                      "outputs": qw_out, "input_support": 2}
-    if name == "qw100+qaoa16":
+    if name == "qw100+qaoa":
+        # the walk batched with the QAOA MaxCut requests (16/20/24 qubits,
+        # p = 2, 1024 outputs each, threshold eps) in one captured graph
         n_qw = 512 if seed_shift == 100 else qw_out
-        n_qa = 4 if seed_shift == 0 else 32
-        ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift),
-              qaoa_workload(16, 2, n_out=n_qa, seed=0x5EED0003 + rank + seed_shift)]
+        ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift)]
         ws[0].meta["learned_cut"] = walk_cuts
-        ws[1].meta["learned_cut"] = None
-        return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_p2_4out", "outputs": qw_out + 4}
+        for n in (16, 20, 24):
+            q = qaoa_workload(n, 2, n_out=1024, eps=QAOA_EPS, seed=0x5EED0003 + rank + seed_shift)
+            q.meta["learned_cut"] = None
+            ws.append(q)
+        return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_20_24_p2_1024out_eps{QAOA_EPS:g}",
+                    "outputs": qw_out + 3 * 1024}
     raise SystemExit(f"unknown workload {name}")
+
+
+QAOA_EPS = 1e-4   # threshold of the QAOA requests in the batched workload
+
+
+def family_jobs(name, rank=0, outputs=None):
+    """Workloads timed as they are (exact or threshold), with no learned arm:
+    the QAOA threshold requests, amplitude amplification (the checkpoint
+    ablation and the 36-source row), the QFT rows."""
+    from workloads import aa_workload, qaoa_workload, qft_signal_workload, qft_workload
+    if name == "qaoa_thr":
+        ws = [qaoa_workload(n, 2, n_out=outputs or 1024, eps=QAOA_EPS, seed=0x5EED0003 + rank) for n in (16, 20, 24)]
+        return ws, {"workload": f"qaoa16_20_24_p2_{outputs or 1024}out_eps{QAOA_EPS:g}", "outputs": 3 * (outputs or 1024)}
+    if name == "aa6x3":
+        w = aa_workload(n=6, iters=3, n_out=outputs or 64, seed=0x5EED0002 + rank)
+        return [w], {"workload": f"aa6x3_{len(w.outputs)}out", "qubits": 10, "outputs": len(w.outputs)}
+    if name == "aa4x3":
+        w = aa_workload(n=4, iters=3, n_out=10, seed=0x5EED0002 + rank, all_outputs=True)
+        w = type(w)(w.circuit, w.inputs, w.outputs[:10], 0.0, w.name, w.meta)
+        return [w], {"workload": "aa4x3_lowest10out", "qubits": 6, "outputs": 10}
+    if name == "qft8":
+        w = qft_workload(8, seed=0x5EED0001 + rank)
+        return [w], {"workload": "qft8_256out", "qubits": 8, "outputs": 256}
+    if name == "qft12signal":
+        w = qft_signal_workload(12, seed=0x5EED0006 + rank)
+        return [w], {"workload": "qft12_two_tone_signal_4096out", "qubits": 12, "outputs": 4096,
+                     "input_support": len(w.inputs)}
+    return None, None
 
 
 def source_cut(circuit, k):
@@ -170,7 +202,10 @@ def oracle_sample(jobs, budget_s=15.0, max_outputs=None, threads=None):
         while t_used < per_job_budget and done < len(w.outputs):
             outs = w.outputs[done:done + k]
             t0 = time.perf_counter()
-            _, cnt = feynman.run(w.circuit, w.inputs, outs, eps=w.eps, c1=c1, c2=c2, threads=threads)
+            if w.eps > 0.0:   # threshold: the per-source search skips cut subtrees
+                _, cnt = feynman.run_dfs(w.circuit, w.inputs, outs, eps=w.eps, threads=threads)
+            else:
+                _, cnt = feynman.run(w.circuit, w.inputs, outs, eps=w.eps, c1=c1, c2=c2, threads=threads)
             dt = time.perf_counter() - t0
             t_used += dt
             done += len(outs)
@@ -185,11 +220,143 @@ def oracle_sample(jobs, budget_s=15.0, max_outputs=None, threads=None):
             "seconds": tot_time, "cores": threads, "sample": "; ".join(desc)}
 
 
+def exact_reference(w):
+    """Exact amplitudes of a QAOA request from the stored oracle values (the
+    dense state vector), when the request is one of them; else None."""
+    path = os.path.join(ROOT, "tests", "golden", "qaoa_threshold.json")
+    if not w.name.startswith("qaoa") or not os.path.exists(path):
+        return None
+    import numpy as np
+    with open(path) as f:
+        g = json.load(f)
+    for r in g["requests"]:
+        if w.name == f"qaoa{r['n']}p{r['p']}" and len(w.outputs) <= r["n_out"] and \
+                [int(x) for x in w.outputs[:4]] == r["outputs_head"][:len(w.outputs[:4])]:
+            return (np.asarray(r["exact_re"]) + 1j * np.asarray(r["exact_im"]))[:len(w.outputs)]
+    return None
+
+
+def run_family(args, jobs, cfg):
+    """Exact or threshold requests timed as they are (no learned arm):
+    graph replay, L2 flushed between steps, CUDA events on the launch stream;
+    for the checkpoint ablation three partitions of the same request."""
+    import numpy as np
+    import torch
+    import paper_2608_01467_b300 as fs
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    peaks = fs.api.probe_peaks()
+    try:
+        peaks["bf16_tflops"] = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1800.0)
+    except Exception:
+        peaks["bf16_tflops"] = 1800.0
+    n_out = sum(len(w.outputs) for w in jobs)
+
+    def build(split="auto", c1=0, c2=0):
+        b = fs.Batch(split=split, c1=c1, c2=c2, engine=args.engine)
+        keep = []
+        for w in jobs:
+            C = fs.Circuit(w.circuit)
+            C.set_input(w.inputs)
+            keep.append(C)
+            b.add(C, w.outputs, w.eps)
+        b._keep = keep
+        b.pruned = None
+        b.plan()
+        b.allocate(dev)
+        b.upload(stream)
+        b.time_kernels(True)
+        for _ in range(max(args.warmup, 3)):
+            b.run(stream)
+            b.finish(stream)
+        return b
+
+    ablation = None
+    if args.workload == "aa4x3":
+        G = len(jobs[0].circuit.gates)
+        times = {}
+        for name, kw in (("none", dict(split="none")), ("thirds", dict(split="fixed", c1=G // 3, c2=2 * G // 3)),
+                         ("autotuned", {})):
+            bb = build(**kw)
+            g = None if args.no_graph else capture(bb, stream)
+            ms, _, _, st = timed_steps(bb, args.steps, stream, flush, f"aa_{name}", g)
+            times[name] = {"ms_per_step": statistics.mean(ms), "gate_visits": int(st[0]["gate_visits"]),
+                           "cuts": [st[0]["c1"], st[0]["c2"]]}
+        ablation = {k: dict(v, speedup_vs_none=times["none"]["ms_per_step"] / v["ms_per_step"],
+                            visits_ratio_vs_none=times["none"]["gate_visits"] / v["gate_visits"])
+                    for k, v in times.items()}
+    b = build()
+    g = None if args.no_graph else capture(b, stream)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ms, stage, completed, st = timed_steps(b, args.steps, stream, flush, "family_step", g)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    amp = b.amp.cpu().numpy()
+    t = max_over_ranks(sum(ms) / 1000.0, world, dev)
+    value = sum_over_ranks(n_out * args.steps, world, dev) / t
+    hist = sum_over_ranks(completed, world, dev) / t
+    roof = stage_roofline(fs, b, jobs, st, stage, peaks, clocks)
+    per_job, off = [], 0
+    for w, s0 in zip(jobs, st):
+        a = amp[off:off + len(w.outputs)]
+        off += len(w.outputs)
+        ex = exact_reference(w)
+        per_job.append({"job": w.name, "eps": w.eps, "completed": int(s0["completed"]), "valid": int(s0["valid"]),
+                        "cuts": [s0["c1"], s0["c2"]], "A_p_r_s": [s0["A_p"], s0["A_r"], s0["A_s"]],
+                        "fidelity_vs_exact": fidelity(ex, a) if ex is not None else None})
+    # end to end: the request uploaded from pinned memory, the graph, the
+    # amplitudes back to pinned memory, every step
+    host_amp = torch.empty(b.amp.shape, dtype=b.amp.dtype, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.upload(stream)
+        if g is not None:
+            g.replay()
+        else:
+            b.run(stream)
+        host_amp.copy_(b.amp, non_blocking=True)
+        b.finish(stream)
+    torch.cuda.synchronize(dev)
+    e2e = sum_over_ranks(n_out * args.steps, world, dev) / max_over_ranks(time.perf_counter() - t0, world, dev)
+    line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded circuits and requests)",
+            "config": dict(cfg, mode="exact" if all(w.eps == 0 for w in jobs) else "threshold",
+                           launch="one CUDA graph per step" if not args.no_graph else "stream launches",
+                           l2="flushed between steps (512 MiB write)", engine=args.engine),
+            "histories_per_s": hist, "jobs": per_job, "clocks": clocks,
+            "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": int(b.static_bytes()),
+                    "d2h_bytes_per_step": int(16 * n_out)},
+            "gpu_launches": b.launch_count() * args.steps, "roofline": roof}
+    if ablation:
+        line["checkpoint_ablation"] = ablation
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        samp = oracle_sample(jobs, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": samp["amplitudes_per_s"], "unit": "amplitudes/s", "cores": samp["cores"],
+                                "kind": "oracle", "sample": samp["sample"], "histories_per_s": samp["histories_per_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     rank, world, local = dist_setup(args)
     if rank != 0:
         return
-    jobs, cfg = workload_jobs(args.workload, 0, args.outputs)
+    jobs, cfg = family_jobs(args.workload, 0, args.outputs)
+    if jobs is None:
+        jobs, cfg = workload_jobs(args.workload, 0, args.outputs)
     for _ in range(args.warmup):
         oracle_sample(jobs, budget_s=2.0, max_outputs=1)
     rates = []
@@ -221,7 +388,7 @@ def make_batch(fs, jobs, engine, dev, stream, pruners=None, bounds=None):
         C = fs.Circuit(w.circuit)
         C.set_input(w.inputs)
         circs.append(C)
-        b.add(C, w.outputs, 0.0)
+        b.add(C, w.outputs, w.eps)
         if pruners and pruners[ji] is not None:
             from paper_2608_01467_b300 import learned
             learned.attach(b, ji, pruners[ji][0], pruners[ji][1])
@@ -468,8 +635,11 @@ def run_ours(args):
     # learned pruner: cuts only entries whose subtree sums are exactly zero)
     bound_info = None
     if not args.no_bound:
-        bound_info = [pick_bound_cut(fs, args, w, dev, stream, sp) for w, sp in zip(jobs, stats_plain)]
-        bb, _ = make_batch(fs, jobs, args.engine, dev, stream, bounds=[(p["c1"], p["c2"]) for p in bound_info])
+        # the bound applies to the jobs with candidate cuts (the walk)
+        bound_info = [pick_bound_cut(fs, args, w, dev, stream, sp) if w.meta.get("learned_cut") else None
+                      for w, sp in zip(jobs, stats_plain)]
+        bb, _ = make_batch(fs, jobs, args.engine, dev, stream,
+                           bounds=[(p["c1"], p["c2"]) if p else None for p in bound_info])
         bb.pruned = None
         for _ in range(max(args.warmup, 3)):
             bb.run(stream)
@@ -484,12 +654,15 @@ def run_ours(args):
             w.meta["learned_cut"] = w0.meta.get("learned_cut")
     learned_info = None
     if not args.plain_only:
-        pr = [train_pruner(fs, args, tr, va, dev, stream, sp) for tr, va, sp in zip(tr_jobs, va_jobs, stats_plain)]
+        # a pruner for the jobs with candidate cuts; threshold jobs without
+        # candidates (the QAOA requests) run as they are in both arms
+        pr = [train_pruner(fs, args, tr, va, dev, stream, sp) if tr.meta.get("learned_cut") else None
+              for tr, va, sp in zip(tr_jobs, va_jobs, stats_plain)]
         learned_info = pr
         bl, ws_learned = make_batch(fs, jobs, args.engine, dev, stream,
-                                    [(p["params"], p["tau"], p["c1"], p["c2"]) if p["params"] is not None
+                                    [(p["params"], p["tau"], p["c1"], p["c2"]) if p and p["params"] is not None
                                      else None for p in pr])
-        cfg["learned_cut_sources"] = [p["cut"] for p in pr]
+        cfg["learned_cut_sources"] = [p["cut"] if p else None for p in pr]
         bl.pruned = [True] * len(jobs)
         for _ in range(max(args.warmup, 3)):
             bl.run(stream)
@@ -556,6 +729,27 @@ def run_ours(args):
     t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e = sum_over_ranks(n_out * args.steps, world, dev) / t_e2e
 
+    # one call through the host-buffer entry point on the first job: plan,
+    # generated-code compile, allocation, upload, run and copy back -- what a
+    # new request of this size costs end to end
+    w0 = jobs[0]
+    C0 = fs.Circuit(w0.circuit)
+    C0.set_input(w0.inputs)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    C0.amplitudes(w0.outputs, w0.eps)
+    t_one = time.perf_counter() - t0
+    one_shot = {"call": "fs_amplitudes", "job": w0.name, "outputs": len(w0.outputs), "seconds": t_one,
+                "value": len(w0.outputs) / t_one, "unit": "amplitudes/s", "mode": "exact" if w0.eps == 0 else "threshold"}
+    per_job, off = [], 0
+    head_amp = learned_amp if learned_info else plain_amp
+    for w in jobs:
+        ex = exact_reference(w)
+        if ex is not None:
+            per_job.append({"job": w.name, "eps": w.eps,
+                            "fidelity_vs_exact": fidelity(ex, head_amp[off:off + len(w.outputs)])})
+        off += len(w.outputs)
+
     line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -574,9 +768,11 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(head.static_bytes()),
                     "d2h_bytes_per_step": int(16 * n_out)},
             "gpu_launches": head.launch_count() * args.steps,
-            "roofline": roof}
+            "roofline": roof, "one_shot": one_shot}
+    if per_job:
+        line["threshold_jobs"] = per_job
     if learned_info:
-        line["learned"] = [{k: v for k, v in p.items() if k != "params"} for p in learned_info]
+        line["learned"] = [{k: v for k, v in p.items() if k != "params"} for p in learned_info if p]
     if bound_info:
         bv, bh, bs = rates(bound_ms, bound_completed)
         line["exact_bound"] = {"value": bv, "unit": "amplitudes/s", "histories_per_s": bh, "ms_per_step": bs,
@@ -584,7 +780,7 @@ def run_ours(args):
                                "max_abs_diff_vs_exact": float(abs(plain_amp[:n_out] - bound_amp[:n_out]).max()),
                                "bound_cuts": int(sum(x["bound_cuts"] for x in stats_bound)),
                                "live_entries": int(sum(x["live_entries"] for x in stats_bound)),
-                               "cut_sources": [p["cut"] for p in bound_info],
+                               "cut_sources": [p["cut"] for p in bound_info if p],
                                "stage_ms": {k: round(v, 4) for k, v in bound_stage.items()},
                                "speedup_vs_plain": bv / plain_value}
         if learned_info:
@@ -625,6 +821,13 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    jobs, cfg = family_jobs(args.workload, 0, args.outputs)
+    if jobs is not None:
+        rank = int(os.environ.get("RANK", "0"))
+        if rank:
+            jobs, cfg = family_jobs(args.workload, rank, args.outputs)
+        run_family(args, jobs, cfg)
     else:
         run_ours(args)
 

@@ -541,3 +541,22 @@ def test_placement_optimum_is_at_most_greedy_and_backward(seed):
         return kn >= set(range(nw))
     lit = next(k for k in range(len(wires) + 1) if any(closes(s) for s in combinations(wires, k)))
     assert lit == opt
+
+
+def test_pruner_features_against_values_derived_by_hand():
+    """The oracle's learned-pruner features (oracle.features) against values
+    derived by hand from the feature definition for two checkpoint tables:
+    a 3-step walk on 4 position qubits and a 2-qubit QAOA layer (stored with
+    the derivation in tests/golden/features_by_hand.json)."""
+    from oracle import features as ofeat
+    g = gold("features_by_hand.json")
+    cases = {"walk": quantum_walk(3, pos_bits=4),
+             "qaoa2": Circuit(2, [Gate("H", (0,)), Gate("H", (1,)), Gate("RZZ", (0, 1), (), 0.7),
+                                  Gate("RX", (0,), (), 1.1), Gate("RX", (1,), (), 1.1)], "qaoa2")}
+    for name, c in cases.items():
+        d = g[name]
+        assert len(c.gates) == (45 if name == "walk" else 5)
+        F, _, Ap = ofeat.table_features(c, d["input"], d["output"], d["c1"])
+        assert Ap == d["A_p"] and feynman.analyze(c)["A"] == d["A"]
+        for h, want in d["entries"].items():
+            assert np.max(np.abs(F[int(h)] - np.asarray(want))) < 1e-12, (name, h, F[int(h)], want)
