@@ -1591,11 +1591,13 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
         const fs::Op& op0 = j.prog.ops[e];
         fs::CascadeRun run;
         if (fused && fs::find_cascade(j.prog.ops.data(), j.prog.masks.data(), W, e, e1, run)) {
-            // common-control test, then per field word: mask, subtract, borrow, xor-and, flip
+            // common-control test, then the first field word: mask, subtract,
+            // borrow, xor-and, flip; later words only when a lane borrows
+            // (practically never), behind a vote (2)
             int nz = 0;
             for (int w = 0; w < W; ++w) nz += (run.cm[w] | run.cv[w]) != 0;
-            iops += (nz ? nz + (nz > 1 ? nz / 2 : 0) + 1 : 0) +
-                    5.0 * (((run.t0 + run.len - 1) >> 5) - (run.t0 >> 5) + 1);
+            const bool multi = ((run.t0 + run.len - 1) >> 5) != (run.t0 >> 5);
+            iops += (nz ? nz + (nz > 1 ? nz / 2 : 0) + 1 : 0) + 5.0 + (multi ? 2.0 : 0.0);
             e += run.len - 1;
             continue;
         }

@@ -84,6 +84,9 @@ __device__ __forceinline__ double2 crot(double2 a, double f, bool rot)
     const double2 p = make_double2(__dmul_rn(a.x, f), __dmul_rn(a.y, f));
     return rot ? make_double2(dneg(p.y), p.x) : p;
 }
+// a * t[0], out of line (see fs_add_ool): the per-class products of valid
+// leaves, which most warps never need
+__device__ __noinline__ double2 fs_cmul_ool(double2 a, const double2* t) { return cmul(a, __ldg(t)); }
 __device__ __forceinline__ double2 sel2(bool c, double2 a, double2 b) { return c ? a : b; }
 
 __device__ __forceinline__ u64 warp_sum_u64(u64 v)
@@ -160,24 +163,23 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
-// acc += v in the lanes where keep holds.  FP64 instructions occupy the
-// scarce FP64 pipe of this part even when every lane of the warp is
-// predicated off, and most leaves are invalid and most items zero, so the
-// two adds sit behind a warp-uniform branch (bra.uni on a vote of the active
-// lanes) that the warp skips when no lane keeps its value.
+// The FP64 adds of add_kept, out of line: a call that no lane makes issues
+// none of the callee's instructions, where an inlined add would be
+// if-converted into FP64 instructions predicated off in every lane -- and
+// those still occupy the scarce FP64 pipe of this part.
+__device__ __noinline__ double2 fs_add_ool(double2 a, double2 b)
+{
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+
+// acc += v in the lanes where keep holds.  Most leaves are invalid and most
+// items zero, so the adds run only when some active lane keeps its value.
 __device__ __forceinline__ void add_kept(double2& acc, double2 v, bool keep)
 {
-    const unsigned any = __any_sync(__activemask(), keep) ? 1u : 0u;
-    asm volatile(
-        "{\n\t.reg .pred pa, pk;\n\t"
-        "setp.ne.u32 pa, %4, 0;\n\t"
-        "setp.ne.u32 pk, %5, 0;\n\t"
-        "@!pa bra.uni FS_ADD_SKIP;\n\t"
-        "@pk add.rn.f64 %0, %0, %2;\n\t"
-        "@pk add.rn.f64 %1, %1, %3;\n"
-        "FS_ADD_SKIP:\n\t}\n"
-        : "+d"(acc.x), "+d"(acc.y)
-        : "d"(v.x), "d"(v.y), "r"(any), "r"(keep ? 1u : 0u));
+    if (__any_sync(__activemask(), keep)) {
+        const double2 t = fs_add_ool(acc, v);
+        if (keep) acc = t;
+    }
 }
 
 
@@ -199,14 +201,8 @@ __device__ __forceinline__ bool is_bottom(double x)
 // the state after each of its source ops (a checkpoint per source, the
 // per-source limit of Algorithm 2's regions) and restarts the next history
 // at the first source whose bit changed, instead of at the region's start.
-//
-// WARP (stacked suffixes with at least 5 sources): the 32 lanes of a warp
-// share one root checkpoint; lane L takes the histories whose last 5
-// sources are the bits of L, and the warp walks the other sources together.
-// Those are the same for every lane, so are the state, the amplitude and
-// every cut decision above the last 5 sources: the walk is one converged
-// loop, and only the last 5 segments differ between lanes.
-template <class T, bool WARP = false>
+
+template <class T>
 __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp, const u32 (&bin)[T::W],
                                               u64& completed, u64& valid, u64& visits)
 {
@@ -215,51 +211,6 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
     typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
     const hs_t ns = (hs_t)1 << T::As;
     hs_t hs = 0;
-    if constexpr (WARP) {
-        static_assert(T::STACKED && T::As >= 5, "warp walk needs a stacked suffix of at least 5 sources");
-        constexpr int LB = 5;
-        const hs_t lane = (hs_t)(threadIdx.x & 31);
-        u32 sst[T::As][W];
-        double2 sam[T::As];
-        int start = 0;
-        hs = lane;
-        while (hs < ns) {
-            u32 st2[W];
-            double2 amp2;
-            if (start == 0) {
-#pragma unroll
-                for (int j = 0; j < W; ++j) st2[j] = st[j];
-                amp2 = amp;
-            } else {
-#pragma unroll
-                for (int j = 0; j < W; ++j) st2[j] = sst[start - 1][j];
-                amp2 = sam[start - 1];
-            }
-            const int r2 = T::suffix_from(start, st2, amp2, (u64)hs, bin, visits, sst, sam);
-            hs_t nx;
-            if (r2 < 0) {
-                ++completed;
-                u32 d = 0;
-#pragma unroll
-                for (int j = 0; j < W; ++j) d |= st2[j] ^ bin[j];
-                const bool ok = d == 0u;
-                valid += ok ? 1u : 0u;
-                add_kept(acc, amp2, ok);
-                nx = hs + (hs_t)32;
-            } else if (r2 >= LB) {
-                nx = (((hs >> r2) + (hs_t)1) << r2) | lane;   // every lane was cut here
-            } else {
-                nx = hs + (hs_t)32;                           // only this lane's history
-            }
-            if (nx < ns) {
-                const int msb = sizeof(hs_t) == 4 ? 31 - __clz((u32)(hs ^ nx))
-                                                  : 63 - __clzll((long long)(u64)(hs ^ nx));
-                start = T::As - 1 - msb;
-            }
-            hs = nx;
-        }
-        return acc;
-    }
     if constexpr (T::STACKED) {
         u32 sst[T::As][W];
         double2 sam[T::As];
@@ -435,7 +386,7 @@ __device__ void tile_body(const JobDev& J, u64 tile)
     }
 }
 
-template <class T, bool WARP = false>
+template <class T>
 __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
@@ -455,7 +406,7 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
 #pragma unroll
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 acc = make_double2(0.0, 0.0);
-    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T, WARP>(st, amp, bin, completed, valid, visits);
+    if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T>(st, amp, bin, completed, valid, visits);
     return acc;
 }
 
@@ -481,19 +432,7 @@ template <class T>
 __device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u64& valid, u64& visits)
 {
     const u64 nlive = J.stats[6] << T::Ar;
-    if constexpr (T::STACKED && T::As >= 5 && T::Ar < 5) {
-        // a warp per item: the lanes split its last 5 suffix sources
-        const int lane = threadIdx.x & 31;
-        for (;;) {
-            u64 i = 0;
-            if (lane == 0) i = atomicAdd(&J.stats[7], 1ull);
-            i = __shfl_sync(0xffffffffu, i, 0);
-            if (i >= nlive) break;
-            double2 acc = compact_body<T, true>(J, i, completed, valid, visits);
-            acc = group_sum(acc, 32);
-            if (lane == 0) J.esum[i] = acc;
-        }
-    } else if constexpr (T::Ar < 5) {
+    if constexpr (T::Ar < 5) {
         for (;;) {
             const u64 i = atomicAdd(&J.stats[7], 1ull);
             if (i >= nlive) break;
@@ -965,7 +904,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         for (int j = 0; j < W; ++j) out += "    dchi |= s[" + std::to_string(j) + "] ^ bin[" + std::to_string(j) + "];\n";
         // the class products only for valid leaves, behind a vote so that
         // a warp with no valid leaf issues none of their FP64 instructions
-        out += "    if (__any_sync(__activemask(), dchi == 0u)) if (dchi == 0u) {\n";
+        out += "    if (__any_sync(__activemask(), dchi == 0u)) {\n";
     }
     for (size_t k = 0; k < cls.size(); ++k) {
         const FactorClass& f = cls[k];
@@ -991,7 +930,8 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         }
         const std::string name = "T_" + tag + "_" + std::to_string(k);
         emit_class_table(globals, name, f);
-        out += "    a = cmul(a, __ldg(&" + name + "[" + kv + "]));\n";
+        out += chi_only ? "    a = fs_cmul_ool(a, &" + name + "[" + kv + "]);\n"
+                        : "    a = cmul(a, __ldg(&" + name + "[" + kv + "]));\n";
     }
     if (chi_only && !cls.empty()) out += "    }\n";
     out += "    visits += " + std::to_string(e1 - seg_e0) + "ull;\n    (void)low;\n    return -1;\n";

@@ -109,24 +109,23 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
-// acc += v in the lanes where keep holds.  FP64 instructions occupy the
-// scarce FP64 pipe of this part even when every lane of the warp is
-// predicated off, and most leaves are invalid and most items zero, so the
-// two adds sit behind a warp-uniform branch (bra.uni on a vote of the active
-// lanes) that the warp skips when no lane keeps its value.
+// The FP64 adds of add_kept, out of line: a call that no lane makes issues
+// none of the callee's instructions, where an inlined add would be
+// if-converted into FP64 instructions predicated off in every lane -- and
+// those still occupy the scarce FP64 pipe of this part.
+__device__ __noinline__ double2 fs_add_ool(double2 a, double2 b)
+{
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+
+// acc += v in the lanes where keep holds.  Most leaves are invalid and most
+// items zero, so the adds run only when some active lane keeps its value.
 __device__ __forceinline__ void add_kept(double2& acc, double2 v, bool keep)
 {
-    const unsigned any = __any_sync(__activemask(), keep) ? 1u : 0u;
-    asm volatile(
-        "{\n\t.reg .pred pa, pk;\n\t"
-        "setp.ne.u32 pa, %4, 0;\n\t"
-        "setp.ne.u32 pk, %5, 0;\n\t"
-        "@!pa bra.uni FS_ADD_SKIP;\n\t"
-        "@pk add.rn.f64 %0, %0, %2;\n\t"
-        "@pk add.rn.f64 %1, %1, %3;\n"
-        "FS_ADD_SKIP:\n\t}\n"
-        : "+d"(acc.x), "+d"(acc.y)
-        : "d"(v.x), "d"(v.y), "r"(any), "r"(keep ? 1u : 0u));
+    if (__any_sync(__activemask(), keep)) {
+        const double2 t = fs_add_ool(acc, v);
+        if (keep) acc = t;
+    }
 }
 
 

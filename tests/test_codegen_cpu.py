@@ -32,6 +32,7 @@ struct double2 { double x, y; };
 static inline double2 make_double2(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
 #define __device__
 #define __forceinline__ inline
+#define __noinline__
 #define __ldg(p) (*(p))
 static inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
 static inline double __dmul_rn(double a, double b) { return a * b; }
@@ -183,16 +184,12 @@ SUFFIX_PLAIN = """
                         if (ok) { sr += a3.x; si += a3.y; ++valid; }
                     }"""
 SUFFIX_STACKED = """
-                    for (u64 lane = 0; lane < ((J0::As >= 5 && J0::Ar < 5) ? 32u : 1u); ++lane) {
-                        // with 5 or more suffix sources the device runs a warp per
-                        // root checkpoint, lane L taking the histories whose last 5
-                        // sources are the bits of L; lanes are independent here
-                        const bool warp = J0::As >= 5 && J0::Ar < 5;
+                    {
                         u32 sst[J0::As][W];
                         double2 sam[J0::As];
                         int start = 0;
                         const u64 ns = 1ull << J0::As;
-                        u64 hs = warp ? lane : 0;
+                        u64 hs = 0;
                         while (hs < ns) {
                             u32 st3[W];
                             double2 a3;
@@ -205,11 +202,9 @@ SUFFIX_STACKED = """
                                 bool ok = true;
                                 for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
                                 if (ok) { sr += a3.x; si += a3.y; ++valid; }
-                                nx = warp ? hs + 32 : hs + 1;
-                            } else if (warp && r2 < 5) {
-                                nx = hs + 32;
+                                nx = hs + 1;
                             } else {
-                                nx = (((hs >> r2) + 1) << r2) | (warp ? lane : 0);
+                                nx = ((hs >> r2) + 1) << r2;
                             }
                             if (nx < ns) start = J0::As - 1 - (63 - __builtin_clzll(hs ^ nx));
                             hs = nx;
