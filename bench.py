@@ -49,15 +49,17 @@ def workload_jobs(name, rank=0, outputs=None, seed_shift=0):
         ws = [qw_workload(n_out=n_qw, seed=0x5EED0005 + rank + seed_shift)]
         ws[0].meta["learned_cut"] = walk_cuts
         for n in (16, 20, 24):
-            q = qaoa_workload(n, 2, n_out=1024, eps=QAOA_EPS, seed=0x5EED0003 + rank + seed_shift)
+            q = qaoa_workload(n, 2, n_out=QAOA_BATCHED_OUT, eps=QAOA_EPS, seed=0x5EED0003 + rank + seed_shift)
             q.meta["learned_cut"] = None
             ws.append(q)
-        return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_20_24_p2_1024out_eps{QAOA_EPS:g}",
-                    "outputs": qw_out + 3 * 1024}
+        return ws, {"workload": f"qw100_t16_{qw_out}out+qaoa16_20_24_p2_{QAOA_BATCHED_OUT}out_eps{QAOA_EPS:g}",
+                    "outputs": qw_out + 3 * QAOA_BATCHED_OUT}
     raise SystemExit(f"unknown workload {name}")
 
 
-QAOA_EPS = 1e-4   # threshold of the QAOA requests in the batched workload
+QAOA_EPS = 1e-4          # threshold of the QAOA requests in the batched workload
+QAOA_BATCHED_OUT = 128   # outputs per QAOA request batched with the walk (the first
+                         # 128 of each seeded 1024-output request)
 
 
 def family_jobs(name, rank=0, outputs=None):
