@@ -253,9 +253,12 @@ def run_family(args, jobs, cfg):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     peaks = fs.api.probe_peaks()
     try:
-        peaks["bf16_tflops"] = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1800.0)
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks["bf16_tflops"] = mp.get("bf16_tflops", 1800.0)
+        peaks["hbm_gbs"] = mp.get("hbm_gbs", 6400.0)
     except Exception:
         peaks["bf16_tflops"] = 1800.0
+        peaks["hbm_gbs"] = 6400.0
     n_out = sum(len(w.outputs) for w in jobs)
 
     def build(split="auto", c1=0, c2=0):
@@ -439,7 +442,8 @@ def train_pruner(fs, args, w_train, w_val, dev, stream, plain_stats):
         t_train = time.perf_counter() - t0
         chosen = None
         for tau in (-6.0, -7.0, -8.0, -9.0, -10.0, -11.0):
-            bl, _ = make_batch(fs, [w_val], args.engine, dev, stream, [(params, tau, c1, c2)])
+            bl, _ = make_batch(fs, [w_val], args.engine, dev, stream, [(params, tau, c1, c2)],
+                               bounds=None if args.no_bound else [(c1, c2)])
             bl.run(stream)
             bl.finish(stream)
             F = fidelity(exact, bl.amp.cpu().numpy()[:len(w_val.outputs)])
@@ -559,16 +563,29 @@ def timed_steps(b, steps, stream, flush, name, graph=None):
 
 def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
     """Roofline of the dominant stage of a step: algorithmic work per launch
-    (the library's per-region work model x executions, or MLP FLOPs) over the
-    stage's mean device time."""
+    over the stage's mean device time (CUDA events on the launch stream).
+
+    * history / prefix (integer code, no dense contraction): the library's
+      work model (fs_batch_region_work, instructions per region execution of
+      the generated code) times the executions of the step, as warp
+      instructions (32 lanes each), against the issue rate of the part:
+      SMs x 4 schedulers x one warp instruction per clock x the maximum SM
+      clock.  The model is calibrated against ncu's smsp__inst_executed of
+      the same kernel (ratio stated with the profile).
+    * prune (the scoring MLP on the tensor cores): its FLOPs per scored entry
+      against the measured bf16 peak.
+    Beside it, the checkpoint table's HBM rate: 32 B written per entry by the
+    prefix stage against the measured copy bandwidth."""
     sm_max = (clocks or {}).get("sm_max_mhz") or 2032.0
-    int_peak = peaks["sms"] * 128 * sm_max * 1e6
+    issue_peak = peaks["sms"] * 4 * sm_max * 1e6                 # warp instructions / s
     work = {"prefix": [0.0, 0.0], "history": [0.0, 0.0], "prune": [0.0, 0.0]}
+    table_bytes = 0.0
     for ji, w in enumerate(jobs):
         iw, fw = b.region_work(ji)
         s0 = stats[ji]
         pairs = len(w.outputs) * len(w.inputs)
         entries = pairs << s0["A_p"]
+        table_bytes += 32.0 * entries
         work["prefix"][0] += iw[0] * entries
         work["prefix"][1] += fw[0] * entries
         root_runs = s0["live_entries"] << s0["A_r"]
@@ -584,17 +601,18 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
              "unit": "TFLOP/s", "frac": work["prune"][1] / t / peak,
              "peak_note": "bf16 cuBLAS burst of measured peaks; the scoring MLP runs tcgen05.mma (BF16, FP32 accumulate in tensor memory)"}
     else:
-        i_frac = work[dom][0] / t / int_peak
-        f_frac = work[dom][1] / t / peaks["dfma_per_s"]
-        if i_frac >= f_frac:
-            r = {"bound": "alu", "achieved": work[dom][0] / t / 1e9, "peak": int_peak / 1e9,
-                 "unit": "Gop/s", "frac": i_frac,
-                 "peak_note": "derived: SMs x 128 lanes x max SM clock (issue rate)"}
-        else:
-            r = {"bound": "alu", "achieved": work[dom][1] / t / 1e9, "peak": peaks["dfma_per_s"] / 1e9,
-                 "unit": "GFP64-inst/s", "frac": f_frac, "peak_note": "measured FP64 FMA rate (fs_probe_peaks)"}
-        r.update({"int_frac": i_frac, "fp64_frac": f_frac})
+        warp_inst = (work[dom][0] + work[dom][1]) / 32.0
+        r = {"bound": "alu", "achieved": warp_inst / t / 1e9, "peak": issue_peak / 1e9,
+             "unit": "G warp-instructions/s", "frac": warp_inst / t / issue_peak,
+             "peak_note": "derived: SMs x 4 schedulers x 1 warp instruction per clock x max SM clock (issue slots)",
+             "fp64_pipe_frac": work[dom][1] / t / peaks["dfma_per_s"]}
     r.update({"kernel": dom, "traffic": None, "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}})
+    tp = stage_ms.get("prefix", 0.0) / 1000.0
+    if tp > 0:
+        hbm = peaks.get("hbm_gbs", 6497.4)
+        r["table"] = {"bound": "hbm", "achieved": table_bytes / tp / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": table_bytes / tp / 1e9 / hbm, "bytes": table_bytes,
+                      "note": "checkpoint table written by the prefix stage, 32 B per entry"}
     return r
 
 
@@ -620,8 +638,10 @@ def run_ours(args):
     try:
         mp = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         peaks["bf16_tflops"] = mp.get("bf16_tflops", 1800.0)
+        peaks["hbm_gbs"] = mp.get("hbm_gbs", 6400.0)
     except Exception:
         peaks["bf16_tflops"] = 1800.0
+        peaks["hbm_gbs"] = 6400.0
 
     # plain: exact, autotuned cuts
     bp, ws_plain = make_batch(fs, jobs, args.engine, dev, stream)
@@ -661,9 +681,14 @@ def run_ours(args):
         pr = [train_pruner(fs, args, tr, va, dev, stream, sp) if tr.meta.get("learned_cut") else None
               for tr, va, sp in zip(tr_jobs, va_jobs, stats_plain)]
         learned_info = pr
+        # the pruner acts on top of the exact reachability bound (the bound
+        # cuts the entries whose subtree sums are exactly zero, the network
+        # scores the rest)
         bl, ws_learned = make_batch(fs, jobs, args.engine, dev, stream,
                                     [(p["params"], p["tau"], p["c1"], p["c2"]) if p and p["params"] is not None
-                                     else None for p in pr])
+                                     else None for p in pr],
+                                    bounds=None if args.no_bound else
+                                    [(p["c1"], p["c2"]) if p and p["params"] is not None else None for p in pr])
         cfg["learned_cut_sources"] = [p["cut"] if p else None for p in pr]
         bl.pruned = [True] * len(jobs)
         for _ in range(max(args.warmup, 3)):
@@ -756,7 +781,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded circuits and requests)",
-            "config": dict(cfg, mode="learned pruning vs plain exact" if learned_info else "plain exact",
+            "config": dict(cfg, mode=("learned pruning" + ("" if args.no_bound else " on the exact reachability bound") +
+                                      " vs plain exact") if learned_info else "plain exact",
                            launch="one CUDA graph per step" if not args.no_graph else "stream launches",
                            l2="flushed between steps (512 MiB write)",
                            parallelism=f"outputs sharded, {world} replica(s)", engine=engine,

@@ -1125,7 +1125,7 @@ static std::vector<fs::JitJobSpec> jit_specs(const fs_batch* b)
         // the generated prefix applies the exact bound where it writes the
         // table and, without a learned pruner, counts the live entries
         specs[ji].bound = j.bound;
-        specs[ji].bound_counts = j.bound && !j.d_pruner;
+        specs[ji].bound_counts = j.bound;
         specs[ji].bspec = j.bspec;
     }
     return specs;
@@ -1378,12 +1378,12 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     const int nj = (int)b->jobs.size();
     const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
     CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
-    // the generated prefix of a job with the exact bound and no learned
-    // pruner counts the live entries per compaction block as it writes them
+    // the generated prefix of a job with the exact bound counts the live
+    // entries per compaction block as it writes them
     if (b->jit)
         for (int ji = 0; ji < nj; ++ji) {
             const Job& j = b->jobs[ji];
-            if (j.bound && !j.d_pruner) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
+            if (j.bound) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
         }
     if (b->timing) CUDA_TRY(record(b->ev[0], s));
     for (int ji = 0; ji < nj; ++ji) {
@@ -1413,22 +1413,28 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     if (b->timing) CUDA_TRY(record(b->ev[4], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
-        // the last checkpoint step (exact bound, then learned pruner) counts
-        // the entries it leaves live per compaction block; the generated
-        // prefix has applied the bound already
-        const bool bound_kernel = j.bound && !b->jit;
-        if (bound_kernel || j.d_pruner) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
-        if (bound_kernel)
-            CUDA_TRY(fs::launch_bound_prune(jobs, ji, j.bspec, j.table_entries, j.d_pruner == nullptr, s));
-        if (j.d_pruner)
+        // Checkpoint cuts.  With the exact bound (applied and counted by the
+        // generated prefix, or by its own kernel for the interpreter) the
+        // table is compacted first and a learned pruner scores only the
+        // live entries, marking its cuts in place (the history skips them);
+        // a pruner alone scores every entry and counts the live ones per
+        // compaction block for the compaction that follows.
+        if (j.bound && !b->jit) {
+            CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
+            CUDA_TRY(fs::launch_bound_prune(jobs, ji, j.bspec, j.table_entries, true, s));
+        }
+        if (j.bound) CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, true, s));
+        if (j.d_pruner) {
+            if (!j.bound) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries,
-                                           (uint32_t*)(base + b->o_err), s));
+                                           (uint32_t*)(base + b->o_err), s, j.bound));
+        }
     }
     if (b->timing) CUDA_TRY(record(b->ev[5], s));
     for (int ji = 0; ji < nj; ++ji) {
         const Job& j = b->jobs[ji];
-        if (!j.compact) continue;
-        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, j.d_pruner != nullptr || j.bound, s));
+        if (!j.compact || j.bound) continue;   // (bound jobs were compacted before scoring)
+        CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, j.d_pruner != nullptr, s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[1], s));
     if (b->tiles.empty()) {
@@ -1509,6 +1515,8 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
             o.learned_cuts = q[5];
             o.bound_cuts = q[8];
             o.live_entries = j.compact ? q[6] : q[3];
+            // with the bound, the pruner's cuts are marked in the compacted list
+            if (j.bound && j.d_pruner) o.live_entries = q[6] - q[5];
             o.c1 = j.sp.c1; o.c2 = j.sp.c2;
             o.A_p = (uint32_t)j.sp.Ap; o.A_r = (uint32_t)j.sp.Ar; o.A_s = (uint32_t)j.sp.As;
         }

@@ -165,8 +165,12 @@ cudaError_t mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_gra
                      cudaStream_t s);
 cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, float* d_feat,
                          unsigned long long n_entries, cudaStream_t s);
+// from_live: score the compacted live entries (after the exact bound) and
+// mark cuts in the table only; otherwise score every entry and count the
+// live ones per compaction block.
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
-                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s);
+                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s,
+                              bool from_live);
 cudaError_t mlp_targets(const double* d_sums, unsigned long long n, double floor_v, float* d_t, cudaStream_t s);
 // Polls of a bounded tensor-core wait before it gives up (process-wide;
 // change it only while no scoring kernel is being launched).

@@ -399,6 +399,7 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
     double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    if (is_bottom(amp.x)) return make_double2(0.0, 0.0);   // cut after the compaction
     const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
     const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
     const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};

@@ -689,6 +689,7 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
     const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
     const uint4 sv = __ldg(ent);
     double2 amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
+    if (is_bottom(amp.x)) return make_double2(0.0, 0.0);   // cut after the compaction
     uint32_t st[W], bin[W];
     const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll

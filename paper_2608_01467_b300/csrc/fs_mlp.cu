@@ -629,15 +629,25 @@ __device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t parity, volati
 
 // PRUNE: rows are the entries of a job's checkpoint table, features computed
 // here, entries scoring below tau cut (amplitude set to NaN, counted in
-// stats[5]).  Otherwise rows are X [n][16] and y goes to Y.
+// stats[5]).  With from_live the rows are the job's compacted live entries
+// (row i = table entry live[i], stats[6] of them: the exact bound has cut
+// the others already); otherwise every table entry, and the entries left
+// live are counted per compaction block.  Without PRUNE rows are X [n][16]
+// and y goes to Y.
 template <bool PRUNE>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     mlp_tc_kernel(const float* __restrict__ P, const float* __restrict__ X, long long n_rows, float* __restrict__ Y,
                   const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err,
-                  uint32_t wait_limit)
+                  uint32_t wait_limit, int from_live)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, grp = tid >> 7, r = tid & 127, warp = tid >> 5;
+    const JobDev* J = PRUNE ? &jobs[job] : nullptr;
+    const long long n = PRUNE ? (from_live ? (long long)J->stats[6] : (long long)(J->n_pairs << J->Ap)) : n_rows;
+    const long long tiles = (n + 127) / 128;
+    // a CTA with no tile leaves before staging anything (the live count of a
+    // from_live launch is known only on the device)
+    if ((long long)blockIdx.x * 2 >= tiles) return;
     float* vb1 = (float*)(sm + SM_VEC);
     float* vb2 = vb1 + H;
     float* vw3 = vb2 + H;
@@ -712,24 +722,29 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const float b3 = vw3[H];
     uint32_t phase = 0;
     unsigned long long cuts = 0;
-    const JobDev* J = PRUNE ? &jobs[job] : nullptr;
-    const long long n = PRUNE ? (long long)(J->n_pairs << J->Ap) : n_rows;
-    const long long tiles = (n + 127) / 128;
     const long long tstride = (long long)gridDim.x * 2;
+    // table index of a row
+    auto entry_of = [&](long long row_) -> unsigned long long {
+        return from_live ? J->live[row_] : (unsigned long long)row_;
+    };
     // PRUNE: the entry of the next tile is loaded while this tile's MMAs run
     Entry cur;
+    unsigned long long cur_e = 0;
     {
         const long long row0 = ((long long)blockIdx.x * 2 + grp) * 128 + r;
-        if (PRUNE && row0 < n) cur = J->table[row0];
+        if (PRUNE && row0 < n) {
+            cur_e = entry_of(row0);
+            cur = J->table[cur_e];
+        }
     }
     // features of one row (bf16) into this group's X operand; false: the row
     // is outside the table or a bottom entry (zero features, never cut)
-    auto stage_x = [&](long long row_, const Entry& e) -> bool {
+    auto stage_x = [&](long long row_, const Entry& e, unsigned long long e_idx) -> bool {
         float fv[16];
         bool lv = false;
         if (row_ < n) {
             if (PRUNE) {
-                entry_features_of(*J, e, (unsigned long long)row_, sp, fv);
+                entry_features_of(*J, e, e_idx, sp, fv);
                 lv = !isnan(fv[0]);
             } else {
                 const float4* x4 = reinterpret_cast<const float4*>(X + row_ * F);
@@ -753,7 +768,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     };
     // the features of tile i + 1 are computed while tile i's layer-2 MMAs run
     long long tile = (long long)blockIdx.x * 2 + grp;
-    bool live = tile < tiles ? stage_x(tile * 128 + r, cur) : false;
+    bool live = tile < tiles ? stage_x(tile * 128 + r, cur, cur_e) : false;
+    unsigned long long row_e = cur_e;   // table index of this tile's row
     for (; tile < tiles; tile += tstride) {
         const long long row = tile * 128 + r;
         const long long nrow = row + tstride * 128;
@@ -764,7 +780,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             tc_mma(tmem, sdesc(sx, 256), sdesc(sw1, 256), 0u);
             tc_commit(bar);
         }
-        if (PRUNE && nrow < n) cur = J->table[nrow];
+        if (PRUNE && nrow < n) {
+            cur_e = entry_of(nrow);
+            cur = J->table[cur_e];
+        }
         if (!group_wait(bar, phase, abort_flag, r, grp, err, wait_limit)) break;
         phase ^= 1u;
         // epilogue 1: h1 = bf16(relu(x W1 + b1)) into the layer-2 A operand
@@ -796,7 +815,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             tc_commit(bar);
         }
         // next tile's X (the layer-1 MMA that read X has completed)
-        const bool live_next = tile + tstride < tiles ? stage_x(nrow, cur) : false;
+        const bool live_next = tile + tstride < tiles ? stage_x(nrow, cur, cur_e) : false;
         if (!group_wait(bar, phase, abort_flag, r, grp, err, wait_limit)) break;
         phase ^= 1u;
         // epilogue 2: y = relu(h1 W2 + b2) . bf16(w3) + b3
@@ -817,18 +836,21 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         if (PRUNE) {
             const bool cut = live && y < tau;
             if (cut) {
-                J->table[row].amp.x = __longlong_as_double(0x7ff8000000000000ll);
+                J->table[row_e].amp.x = __longlong_as_double(0x7ff8000000000000ll);
                 ++cuts;
             }
             // entries left live, counted per compaction block (the warp's 32
             // rows lie in one block); the compaction's own count pass is skipped
-            const unsigned keep = __ballot_sync(0xffffffffu, live && !cut);
-            if ((tid & 31) == 0 && keep)
-                atomicAdd(&J->blk[(unsigned long long)(tile * 128 + (r & ~31)) / COMPACT_BLOCK], (unsigned)__popc(keep));
+            if (!from_live) {
+                const unsigned keep = __ballot_sync(0xffffffffu, live && !cut);
+                if ((tid & 31) == 0 && keep)
+                    atomicAdd(&J->blk[(unsigned long long)(tile * 128 + (r & ~31)) / COMPACT_BLOCK], (unsigned)__popc(keep));
+            }
         } else if (row < n) {
             Y[row] = y;
         }
         live = live_next;
+        row_e = cur_e;
     }
     if (PRUNE) {
         cuts = warp_sum_cuts(cuts);
@@ -856,13 +878,14 @@ uint32_t g_wait_limit = TC_WAIT_LIMIT;
 
 template <bool PRUNE>
 cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y, const JobDev* jobs, int job,
-                      const FeatureSpec& sp, float tau, uint32_t* err, unsigned long long rows, cudaStream_t s)
+                      const FeatureSpec& sp, float tau, uint32_t* err, unsigned long long rows, cudaStream_t s,
+                      int from_live = 0)
 {
     const unsigned long long tiles = (rows + 127) / 128;
     unsigned long long blocks = (tiles + 1) / 2;
     if (blocks > 148 * 2) blocks = 148 * 2;
     mlp_tc_kernel<PRUNE><<<(unsigned)blocks, TC_THREADS, TC_SMEM, s>>>(P, X, n_rows, Y, jobs, job, sp, tau, err,
-                                                                       g_wait_limit);
+                                                                       g_wait_limit, from_live);
     return cudaGetLastError();
 }
 
@@ -918,10 +941,11 @@ cudaError_t mlp_targets(const double* d_sums, unsigned long long n, double floor
 }
 
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
-                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s)
+                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s, bool from_live)
 {
     if (n_entries == 0) return cudaSuccess;
-    return launch_tc<true>(d_params, nullptr, 0, nullptr, d_jobs, job, sp, tau, d_err, n_entries, s);
+    return launch_tc<true>(d_params, nullptr, 0, nullptr, d_jobs, job, sp, tau, d_err, n_entries, s,
+                           from_live ? 1 : 0);
 }
 
 void mlp_set_wait_limit(uint32_t polls) { g_wait_limit = polls; }

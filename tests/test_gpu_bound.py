@@ -60,3 +60,41 @@ def test_exact_bound_cuts_the_unreachable_entries_and_keeps_the_amplitudes(k_pre
     assert st["live_entries"] == st0["live_entries"] - expect
     assert st["valid"] == st0["valid"]
     assert st["completed"] < st0["completed"]
+
+
+def test_learned_pruner_on_top_of_the_exact_bound():
+    """With both, the table is compacted after the bound and the pruner
+    scores only the live entries, marking its cuts in place: with tau below
+    every score nothing more is cut and the amplitudes stay exact; with tau
+    above every score every live entry is cut and the amplitudes are zero."""
+    import torch
+    from workloads import mlp_init_params
+    from paper_2608_01467_b300 import learned
+    steps = 8
+    w = qw_workload(steps=steps, n_out=128)
+    G = len(w.circuit.gates)
+    c1 = 3 * (G // steps)
+    exact, st0 = _run(w, c1, False)
+    _, stb = _run(w, c1, True)
+    params = torch.from_numpy(np.asarray(mlp_init_params(3), np.float32)).cuda()
+    for tau, expect_cut in ((-1e30, False), (1e30, True)):
+        C = fs.Circuit(w.circuit)
+        C.set_input(w.inputs)
+        b = fs.Batch(split="fixed", c1=c1, c2=c1)
+        b.add(C, w.outputs)
+        b.set_exact_bound(0)
+        learned.attach(b, 0, params, tau)
+        b.plan()
+        b.allocate()
+        b.upload()
+        b.run()
+        st = b.finish()[0]
+        got = b.amp.cpu().numpy()[:len(w.outputs)]
+        assert st["bound_cuts"] == stb["bound_cuts"]
+        if expect_cut:
+            assert st["learned_cuts"] == stb["live_entries"] and st["live_entries"] == 0
+            assert np.all(got == 0) and st["completed"] == 0
+        else:
+            assert st["learned_cuts"] == 0 and st["live_entries"] == stb["live_entries"]
+            err = np.abs(got - exact)
+            assert np.all(err <= 1e-12 + 1e-10 * np.abs(exact)), err.max()
