@@ -1300,10 +1300,26 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
     return FS_OK;
 }
 
+// Whether some output of a planned batch can have more partial sums than a
+// warp of the reduction takes (then the block-per-output pass runs): S
+// pairs per output, per pair 2^log2_spp tile partials (exact jobs) or up to
+// 2^A_p live entries x 2^(A_r - 5 or A_r) subtree sums (compacted jobs).
+static bool big_outputs_possible(const fs_batch& b)
+{
+    for (const Job& j : b.jobs) {
+        if (j.outs.empty()) continue;
+        const int lg = j.compact ? j.sp.Ap + (j.sp.Ar >= 5 ? j.sp.Ar - 5 : j.sp.Ar) : j.log2_spp;
+        const long double per_out = std::ldexp((long double)j.ins.size(), lg);
+        if (per_out > (long double)fs::RED_BIG_ITEMS) return true;
+    }
+    return false;
+}
+
 int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
 {
     if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
-    uint32_t k = b->total_out ? 2 : 0;   // reduce: outputs by lane groups, then the listed large ones
+    // reduce: outputs by lane groups, then (when possible) the listed large ones
+    uint32_t k = b->total_out ? (big_outputs_possible(*b) ? 2 : 1) : 0;
     bool tiled = false, flat_prefix = false;
     for (const Job& j : b->jobs) {
         tiled |= !j.compact;
@@ -1453,7 +1469,7 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     if (b->timing) CUDA_TRY(record(b->ev[2], s));
     CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
                                (double2*)d_amp_out, (unsigned int*)(base + b->o_bigcount),
-                               (uint64_t*)(base + b->o_biglist), s));
+                               (uint64_t*)(base + b->o_biglist), big_outputs_possible(*b), s));
     if (b->timing) {
         CUDA_TRY(record(b->ev[3], s));
         b->ev_recorded = true;

@@ -211,9 +211,12 @@ cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cuda
 // Two launches: lane groups sum most outputs and list the large ones in
 // d_big_list (count in d_big_count, zeroed by the caller); one block per
 // listed output sums the rest.
+// big_possible = false skips the block-per-output launch when no output
+// can have more than RED_BIG_ITEMS items.
+constexpr uint64_t RED_BIG_ITEMS = 4096;
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, unsigned int* d_big_count, uint64_t* d_big_list,
-                          cudaStream_t s);
+                          bool big_possible, cudaStream_t s);
 int history_grid_size(int device);
 
 // Straight-line engine (fs_jit.cpp): one generated persistent kernel for the

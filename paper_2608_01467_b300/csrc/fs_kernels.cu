@@ -815,7 +815,7 @@ __device__ __forceinline__ double2 strided_sum(const double2* __restrict__ src, 
 
 constexpr int RED_LPO = 4;            // lanes per output in the common path
 constexpr uint64_t RED_SMALL = 64;    // outputs with more items take the whole warp
-constexpr uint64_t RED_WARP = 4096;   // outputs with more items go to reduce_big_kernel
+constexpr uint64_t RED_WARP = RED_BIG_ITEMS;   // outputs with more items go to reduce_big_kernel
 constexpr int RED_BIG_THREADS = 256;
 
 // FP64 is scarce on this part (about 2 FMA per clock per SM), so the
@@ -1152,7 +1152,7 @@ cudaError_t launch_bound_prune(const JobDev* d_jobs, int job, const BoundSpec& s
 
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, unsigned int* d_big_count, uint64_t* d_big_list,
-                          cudaStream_t s)
+                          bool big_possible, cudaStream_t s)
 {
     if (total_out == 0) return cudaSuccess;
     const uint64_t per_block = (REDUCE_THREADS / 32) * (32 / RED_LPO);   // outputs per block pass
@@ -1161,7 +1161,7 @@ cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_j
     reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp,
                                                               d_big_count, d_big_list);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !big_possible) return e;
     const uint64_t big_blocks = total_out < 148ull * 4 ? total_out : 148ull * 4;
     reduce_big_kernel<<<(unsigned)big_blocks, RED_BIG_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, d_big_count,
                                                                        d_big_list, d_amp);

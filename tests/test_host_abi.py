@@ -169,11 +169,13 @@ def test_plan_layout_and_fixed_split_errors():
     n = b2.plan()
     assert n > 0 and n % 256 == 0
     assert b2.total_outputs == 16
-    assert b2.launch_count() == 4      # prefix, history, reduce (lane groups + large outputs)
+    # prefix, history, reduce by lane groups (no output can exceed what a
+    # warp of the reduction sums, so the block-per-output pass is skipped)
+    assert b2.launch_count() == 3
     b3 = fs.Batch(prefix="levels")     # prefix expanded one level per source op
     b3.add(C, w.outputs)
     b3.plan()
-    st_levels = b3.launch_count() - 3  # levels + history + reduce (2)
+    st_levels = b3.launch_count() - 2  # levels + history + reduce
     assert st_levels >= 2
 
 
@@ -258,9 +260,10 @@ def test_work_model_counts_fused_incrementers_for_the_generated_engine():
             work[engine] = b.region_work(0)[0][1]   # root region integer ops
         if fused:
             # H deferred (3 + 1 class count) + its unit-phase class applied as a
-            # sign flip (3) + the cascade: common-control test on 1 word (2)
-            # and 5 per register word of the field (2 words)
-            assert work["straight"] == 4 + 3 + 2 + 10
+            # sign flip (3) + the cascade: common-control test on 1 word (2),
+            # 5 for the field's first register word and a vote (2) guarding
+            # the second word, which only a borrow reaches
+            assert work["straight"] == 4 + 3 + 2 + 5 + 2
             assert work["straight"] < work["interp"] / 4
         else:
             # gate by gate in both engines; they differ only in the H: 4 integer
