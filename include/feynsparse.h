@@ -326,6 +326,14 @@ FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
  * range) and the history over live entries). */
 FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
 
+/* Per-output cost (the paper's per-output distribution of work, Sec. V,
+ * Fig. 11): with d_counts set (device, 2 x n_out uint64 of the job, 8-byte
+ * aligned), every fs_batch_run zeroes it and adds each output's completed
+ * and valid leaves ({completed, valid} per output, in request order) as the
+ * history kernels finish its items; NULL turns it off.  Call before
+ * fs_batch_upload.  Summed over outputs the counts equal fs_stats. */
+FS_API int fs_batch_trace_outputs(fs_batch* b, uint32_t job, uint64_t* d_counts);
+
 /* Stage timing (the paper times its kernel per output, Fig. 11; here per
  * stage of Algorithm 2).  enable != 0 makes fs_batch_run record CUDA events
  * around its stages (as event nodes when the stream is being captured). */

@@ -108,6 +108,7 @@ SIGNATURES = {
     "fs_mlp_targets": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, vp, vp]),
     "fs_set_wait_limit": (ctypes.c_int, [ctypes.c_int64]),
     "fs_batch_set_exact_bound": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.c_int32]),
+    "fs_batch_trace_outputs": (ctypes.c_int, [vp, ctypes.c_uint32, vp]),
     "fs_source_placement": (ctypes.c_int, [vp, ctypes.c_uint32, P(ctypes.c_uint32), P(ctypes.c_uint32)]),
     "fs_lpt_assign": (ctypes.c_int, [P(ctypes.c_double), ctypes.c_size_t, ctypes.c_uint32, P(ctypes.c_uint32),
                                      P(ctypes.c_double)]),

@@ -190,6 +190,13 @@ class Batch:
         self._circuits.append(circuit)
         return jid.value
 
+    def trace_outputs(self, job: int, counts):
+        """Per-output {completed, valid} leaf counters of a job in a device
+        uint64 tensor of 2 x n_out elements (None: off); call before upload."""
+        ptr = None if counts is None else ctypes.c_void_p(counts.data_ptr())
+        check(_lib.load().fs_batch_trace_outputs(self._h, job, ptr))
+        self._trace = counts
+
     def set_exact_bound(self, job: int, enable: bool = True):
         """Cut checkpoint entries that provably cannot reach the input (exact)."""
         check(_lib.load().fs_batch_set_exact_bound(self._h, job, 1 if enable else 0))

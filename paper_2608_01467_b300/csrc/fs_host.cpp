@@ -417,6 +417,7 @@ struct Job {
     size_t o_ops = 0, o_masks = 0, o_fac = 0, o_outs = 0, o_ins = 0, o_coef = 0, o_table = 0, o_part = 0;
     // optional: per-item subtree sums (caller device buffer) and learned pruner
     double2* d_log = nullptr;
+    unsigned long long* d_trace = nullptr;   // per output {completed, valid} (caller device buffer)
     const float* d_pruner = nullptr;
     float tau = 0;
     fs::FeatureSpec fspec{};
@@ -720,6 +721,16 @@ int fs_batch_log_subtrees(fs_batch* b, uint32_t job, double* d_log)
     if (!b) return fail(FS_ERR_INVALID, "NULL batch");
     if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
     b->jobs[job].d_log = (double2*)d_log;
+    b->uploaded = false;
+    return FS_OK;
+}
+
+int fs_batch_trace_outputs(fs_batch* b, uint32_t job, uint64_t* d_counts)
+{
+    if (!b) return fail(FS_ERR_INVALID, "NULL batch");
+    if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
+    if (((uintptr_t)d_counts) & 7) return fail(FS_ERR_INVALID, "counters must be 8-byte aligned");
+    b->jobs[job].d_trace = (unsigned long long*)d_counts;
     b->uploaded = false;
     return FS_OK;
 }
@@ -1259,6 +1270,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.prange = j.compact ? (uint64_t*)(base + j.o_prange) : nullptr;
         d.n_entries = j.table_entries;
         d.scale = j.scale;
+        d.trace = j.d_trace;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
         if (j.levels.empty()) pacc += j.table_entries;
@@ -1394,6 +1406,9 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
     const int nj = (int)b->jobs.size();
     const fs::JobDev* jobs = (const fs::JobDev*)(base + b->o_jobs);
     CUDA_TRY(cudaMemsetAsync(base + b->o_stats, 0, b->o_err + sizeof(uint32_t) - b->o_stats, s));
+    for (const Job& j : b->jobs)
+        if (j.d_trace && !j.outs.empty())
+            CUDA_TRY(cudaMemsetAsync(j.d_trace, 0, 2 * j.outs.size() * sizeof(unsigned long long), s));
     // the generated prefix of a job with the exact bound counts the live
     // entries per compaction block as it writes them
     if (b->jit)

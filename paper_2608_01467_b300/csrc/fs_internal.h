@@ -113,7 +113,8 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     uint32_t* blk;             /* per compaction block: live count, then offset */       \
     uint64_t* prange;          /* per pair: [lo, hi) of its live entries */              \
     uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */                   \
-    double2 scale;             /* constant factor hoisted out of the root and suffix */
+    double2 scale;             /* constant factor hoisted out of the root and suffix */ \
+    unsigned long long* trace; /* optional: per output {completed, valid} leaves */
 
 struct JobDev {
     FS_JOBDEV_FIELDS

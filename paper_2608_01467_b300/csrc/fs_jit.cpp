@@ -277,6 +277,18 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
     return acc;
 }
 
+// Per-output leaf counts of a traced job (the paper's per-output cost
+// distribution, Fig. 11): the completed and valid leaves of one item added
+// to its output's counters.
+__device__ __forceinline__ void trace_counts(const JobDev& J, u64 pair, u64 dc, u64 dv)
+{
+    if (!(dc | dv)) return;
+    u64 s;
+    const u64 o = pair_split(pair, J, s);
+    if (dc) atomicAdd(&J.trace[2 * o], dc);
+    if (dv) atomicAdd(&J.trace[2 * o + 1], dv);
+}
+
 // The checkpoint entry and input bits of the item a lane is on: consecutive
 // items of a lane share them whenever they share (pair, h_p), so they are
 // loaded once per change instead of once per item.
@@ -325,7 +337,9 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
 #pragma unroll
     for (int j = 0; j < W; ++j) st[j] = c.st[j];
     double2 amp = c.amp;
+    const u64 c0 = completed, v0 = valid;
     if (T::root(st, amp, hr, c.bin, visits) < 0) acc = suffix_sum<T>(st, amp, c.bin, completed, valid, visits);
+    if (J.trace) trace_counts(J, pair, completed - c0, valid - v0);
     return acc;
 }
 
@@ -407,7 +421,9 @@ __device__ double2 compact_body(const JobDev& J, u64 i, u64& completed, u64& val
 #pragma unroll
     for (int j = 0; j < W; ++j) { st[j] = tmp[j]; bin[j] = btmp[j]; }
     double2 acc = make_double2(0.0, 0.0);
+    const u64 c0 = completed, v0 = valid;
     if (T::root(st, amp, hr, bin, visits) < 0) acc = suffix_sum<T>(st, amp, bin, completed, valid, visits);
+    if (J.trace) trace_counts(J, pair, completed - c0, valid - v0);
     return acc;
 }
 

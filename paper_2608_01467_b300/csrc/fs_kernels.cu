@@ -450,6 +450,18 @@ __global__ void __launch_bounds__(256) prefix_level_kernel(const JobDev* __restr
 
 // ---------------------------------------------------------------- history
 
+// Per-output leaf counts of a traced job: one item's completed and valid
+// leaves added to its output's counters.
+__device__ __forceinline__ void trace_counts(const JobDev& J, uint64_t pair, unsigned long long dc,
+                                             unsigned long long dv)
+{
+    if (!(dc | dv)) return;
+    uint64_t s;
+    const uint64_t o = pair_split(pair, J, s);
+    if (dc) atomicAdd(&J.trace[2 * o], dc);
+    if (dv) atomicAdd(&J.trace[2 * o + 1], dv);
+}
+
 // Sum over the valid leaves of one (prefix, root) item: the root once, the
 // suffix for every h_s (skipping cut subtrees), the chi test at the input.
 template <int W>
@@ -473,6 +485,7 @@ __device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, u
     for (int j = 0; j < W; ++j) st[j] = tmp[j];
     load_bits<W>(J.ins + 4 * s, bin);
     double2 amp = a0;
+    const unsigned long long c0 = completed, v0 = valid;
     if (run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err) < 0) {
         const uint64_t ns = 1ull << J.As;
         uint64_t hs = 0;
@@ -495,6 +508,7 @@ __device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, u
             }
         }
     }
+    if (J.trace) trace_counts(J, pair, completed - c0, valid - v0);
     return acc;
 }
 
@@ -696,6 +710,7 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
     for (int j = 0; j < W; ++j) st[j] = tmp[j];
     load_bits<W>(J.ins + 4 * s, bin);
     double2 acc = make_double2(0.0, 0.0);
+    const unsigned long long c0 = completed, v0 = valid;
     if (run_ops<W>(J, J.c1, J.c2, st, amp, hr, J.Ar, bin, visits, err) < 0) {
         const uint64_t ns = 1ull << J.As;
         uint64_t hs = 0;
@@ -718,6 +733,7 @@ __device__ double2 compact_item(const JobDev& J, uint64_t i, uint32_t* err, unsi
             }
         }
     }
+    if (J.trace) trace_counts(J, pair, completed - c0, valid - v0);
     return acc;
 }
 
