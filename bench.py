@@ -196,6 +196,14 @@ def oracle_sample(jobs, budget_s=15.0, max_outputs=None, threads=None):
     desc = []
     per_job_budget = budget_s / len(jobs)
     for w in jobs:
+        if w.eps == 0.0:
+            # exact mode enumerates 2^A histories per (output, input) pair:
+            # a job whose single output is far beyond the budget (at the
+            # oracle's rate of order 1e8 histories/s) is left out of the sample
+            A = feynman.analyze(w.circuit)["A"]
+            if float(2 ** A) * len(w.inputs) > 1e8 * 4 * per_job_budget:
+                desc.append(f"{w.name}: none (one output enumerates 2^{A} x {len(w.inputs)} histories)")
+                continue
         c1, c2, _ = feynman.autotune(w.circuit)
         k = max(1, threads)
         t_used = 0.0
@@ -218,6 +226,9 @@ def oracle_sample(jobs, budget_s=15.0, max_outputs=None, threads=None):
         tot_hist += hist
         tot_time += t_used
         desc.append(f"{w.name}: {done} of {len(w.outputs)} outputs")
+    if tot_time == 0.0:
+        return {"amplitudes_per_s": None, "histories_per_s": None, "seconds": 0.0, "cores": threads,
+                "sample": "; ".join(desc)}
     return {"amplitudes_per_s": tot_out / tot_time, "histories_per_s": tot_hist / tot_time,
             "seconds": tot_time, "cores": threads, "sample": "; ".join(desc)}
 
@@ -368,6 +379,10 @@ def run_reference(args):
     samp = None
     for _ in range(args.steps):
         samp = oracle_sample(jobs, budget_s=max(5.0, 60.0 / max(args.steps, 1)))
+        if samp["amplitudes_per_s"] is None:
+            print(json.dumps({"impl": "reference", "unavailable": "no bounded oracle sample: " + samp["sample"]}),
+                  flush=True)
+            return
         rates.append(samp["amplitudes_per_s"])
     v = statistics.mean(rates)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "amplitudes/s",
@@ -570,8 +585,10 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
       the generated code) times the executions of the step, as warp
       instructions (32 lanes each), against the issue rate of the part:
       SMs x 4 schedulers x one warp instruction per clock x the maximum SM
-      clock.  The model is calibrated against ncu's smsp__inst_executed of
-      the same kernel (ratio stated with the profile).
+      clock -- or, when its FP64 instructions are the larger share of their
+      pipe (threshold jobs), against the measured FP64 rate.  The model is
+      calibrated against ncu's instruction counts of the same kernel (ratio
+      stated with the profile).
     * prune (the scoring MLP on the tensor cores): its FLOPs per scored entry
       against the measured bf16 peak.
     Beside it, the checkpoint table's HBM rate: 32 B written per entry by the
@@ -589,8 +606,15 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
         work["prefix"][0] += iw[0] * entries
         work["prefix"][1] += fw[0] * entries
         root_runs = s0["live_entries"] << s0["A_r"]
-        work["history"][0] += iw[1] * root_runs + iw[2] * s0["completed"] + iw[3] * s0["completed"]
-        work["history"][1] += fw[1] * root_runs + fw[2] * s0["completed"] + fw[3] * s0["valid"]
+        if w.eps > 0.0:
+            # threshold jobs stop at every cut: the suffix work follows the
+            # gate visits (each visited op at the suffix region's mean cost)
+            G_s = max(1, len(w.circuit.gates) - s0["c2"])
+            work["history"][0] += iw[2] / G_s * s0["gate_visits"] + iw[3] * s0["completed"]
+            work["history"][1] += fw[2] / G_s * s0["gate_visits"] + fw[3] * s0["valid"]
+        else:
+            work["history"][0] += iw[1] * root_runs + iw[2] * s0["completed"] + iw[3] * s0["completed"]
+            work["history"][1] += fw[1] * root_runs + fw[2] * s0["completed"] + fw[3] * s0["valid"]
         if s0["learned_cuts"] or (b.pruned and b.pruned[ji]):
             work["prune"][1] += 2.0 * (2048 + 16384 + 128) * entries   # MLP FLOPs per scored entry
     dom = max(("prefix", "history", "prune"), key=lambda k: stage_ms.get(k, 0.0))
@@ -602,10 +626,20 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
              "peak_note": "bf16 cuBLAS burst of measured peaks; the scoring MLP runs tcgen05.mma (BF16, FP32 accumulate in tensor memory)"}
     else:
         warp_inst = (work[dom][0] + work[dom][1]) / 32.0
-        r = {"bound": "alu", "achieved": warp_inst / t / 1e9, "peak": issue_peak / 1e9,
-             "unit": "G warp-instructions/s", "frac": warp_inst / t / issue_peak,
-             "peak_note": "derived: SMs x 4 schedulers x 1 warp instruction per clock x max SM clock (issue slots)",
-             "fp64_pipe_frac": work[dom][1] / t / peaks["dfma_per_s"]}
+        issue_frac = warp_inst / t / issue_peak
+        fp64_frac = work[dom][1] / t / peaks["dfma_per_s"]
+        if fp64_frac > issue_frac:
+            # FP64-bound (threshold jobs multiply literally up to the last
+            # test): FP64 warp instructions against the measured DFMA rate
+            r = {"bound": "alu", "achieved": work[dom][1] / 32.0 / t / 1e9, "peak": peaks["dfma_per_s"] / 32.0 / 1e9,
+                 "unit": "G FP64 warp-instructions/s", "frac": fp64_frac,
+                 "peak_note": "measured FP64 FMA rate (fs_probe_peaks) / 32 lanes: the FP64 pipe",
+                 "issue_frac": issue_frac}
+        else:
+            r = {"bound": "alu", "achieved": warp_inst / t / 1e9, "peak": issue_peak / 1e9,
+                 "unit": "G warp-instructions/s", "frac": issue_frac,
+                 "peak_note": "derived: SMs x 4 schedulers x 1 warp instruction per clock x max SM clock (issue slots)",
+                 "fp64_pipe_frac": fp64_frac}
     r.update({"kernel": dom, "traffic": None, "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}})
     tp = stage_ms.get("prefix", 0.0) / 1000.0
     if tp > 0:

@@ -424,6 +424,8 @@ struct Job {
     // pruned jobs (eps > 0, a learned pruner or the exact bound) run over
     // compacted live entries
     bool compact = false;
+    bool direct = false;   // empty prefix region, exact: entries read as (b_out, 1), no table
+    std::vector<std::pair<int, fs::BoundSpec>> src_bounds;   // bound after each source op of root and suffix
     bool bound = false;                   // exact reachability bound at the checkpoint
     fs::BoundSpec bspec{};
     int fixed_c1 = -1, fixed_c2 = -1;     // per-job cuts overriding the batch split
@@ -785,6 +787,7 @@ int fs_batch_features(fs_batch* b, uint32_t job, void* d_ws, float* d_features, 
     if (!b->uploaded || b->uploaded_ws != d_ws) return fail(FS_ERR_STATE, "no run on this workspace");
     if (job >= b->jobs.size()) return fail(FS_ERR_INVALID, "job %u out of range", job);
     const Job& j = b->jobs[job];
+    if (j.direct) return fail(FS_ERR_UNSUPPORTED, "job %u has no checkpoint table (empty prefix region)", job);
     const fs::JobDev* jobs = (const fs::JobDev*)((unsigned char*)d_ws + b->o_jobs);
     CUDA_TRY(fs::mlp_features(jobs, (int)job, j.fspec, d_features, j.table_entries, (cudaStream_t)stream));
     return FS_OK;
@@ -994,12 +997,13 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
         j.log2_ipp = j.sp.Ap + j.sp.Ar;
         j.log2_spp = std::max(0, j.log2_ipp - fs::TILE_LOG2);
         j.table_entries = j.pairs << j.sp.Ap;
+        j.direct = j.sp.c1 == 0 && !j.compact && j.levels.empty();
         j.n_partials = j.compact ? 0 : (j.pairs << j.log2_spp);
         const uint64_t items = j.pairs << j.log2_ipp;
         j.n_tiles = j.compact ? 0 : (items + fs::TILE - 1) / fs::TILE;
         j.nblk = j.compact ? (j.table_entries + fs::COMPACT_BLOCK - 1) / fs::COMPACT_BLOCK : 0;
         if (j.n_tiles >= (1ull << 32)) return fail(FS_ERR_TOO_LARGE, "job %zu: too many tiles", ji);
-        if (j.levels.empty()) b->total_prefix += j.table_entries;
+        if (j.levels.empty() && !j.direct) b->total_prefix += j.table_entries;
         b->total_out += j.outs.size();
         // predicted cost of one tile (Eq. 8 per item): G_r + 2^As G_s
         const double tile_cost = (double)(j.sp.c2 - j.sp.c1) + std::ldexp((double)(G - j.sp.c2), j.sp.As);
@@ -1038,7 +1042,7 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     b->o_err = take(sizeof(uint32_t));   // last of the words zeroed at the start of every run
     b->o_biglist = take(b->total_out * sizeof(uint64_t));
     for (Job& j : b->jobs) {
-        j.o_table = take(j.table_entries * sizeof(fs::Entry));
+        j.o_table = take(j.direct ? 0 : j.table_entries * sizeof(fs::Entry));
         j.o_part = take(j.n_partials * sizeof(double2));
         if (!j.levels.empty()) j.o_lvscratch = take((j.table_entries / 2) * sizeof(fs::Entry));
         if (j.compact) {
@@ -1062,17 +1066,18 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     return FS_OK;
 }
 
-// The exact reachability bound of a planned job (cuts at sp.c1): qubits no
-// op in [c1, G) can change, and fields moved only by +-1 cascades with the
-// number of such cascades as the radius.
-static bool make_bound(Job& j, int n_qubits)
+// The exact reachability bound at evaluation position e0 of a job's
+// program: qubits no op in [e0, G) can change, and fields moved only by +-1
+// cascades with the number of such cascades as the radius.  False when the
+// ops after e0 hold more than MAX_BOUND_FIELDS cascade fields.
+static bool bound_at(const Job& j, int n_qubits, int e0, fs::BoundSpec& sp)
 {
     const int G = (int)j.prog.ops.size(), W = j.W;
     uint32_t freem[4] = {0, 0, 0, 0};
     struct F { int t0, len; uint32_t runs; bool ok; };
     std::vector<F> fields;
     auto setq = [&](int q) { freem[q >> 5] |= 1u << (q & 31); };
-    for (int e = j.sp.c1; e < G; ++e) {
+    for (int e = e0; e < G; ++e) {
         fs::CascadeRun run;
         if (fs::find_cascade(j.prog.ops.data(), j.prog.masks.data(), W, e, G, run)) {
             bool found = false;
@@ -1103,7 +1108,6 @@ static bool make_bound(Job& j, int n_qubits)
                 if (&g != &f && q >= g.t0 && q < g.t0 + g.len) f.ok = false;
         }
     }
-    fs::BoundSpec& sp = j.bspec;
     std::memset(&sp, 0, sizeof sp);
     for (F& f : fields) {
         for (int q = f.t0; q < f.t0 + f.len; ++q) fmask[q >> 5] |= 1u << (q & 31);
@@ -1125,6 +1129,28 @@ static bool make_bound(Job& j, int n_qubits)
     return true;
 }
 
+// The bound at the checkpoint (cuts at sp.c1), applied where the table is
+// written; and for the straight-line engine the bound after every op of the
+// root and suffix that carries an artificial source (a history whose state
+// there cannot reach b_in is cut with its subtree: all its leaves are
+// invalid, so the amplitude is unchanged).
+static bool make_bound(Job& j, int n_qubits)
+{
+    if (!bound_at(j, n_qubits, j.sp.c1, j.bspec)) return false;
+    j.src_bounds.clear();
+    const int G = (int)j.prog.ops.size();
+    for (int e = j.sp.c1; e < G; ++e) {
+        const fs::Op& op = j.prog.ops[e];
+        const bool br = op.code == fs::OP_H || op.code == fs::OP_BR1 || op.code == fs::OP_BR2;
+        if (!br || (op.s0 < 0 && !(op.code == fs::OP_BR2 && op.s1 >= 0))) continue;
+        fs::BoundSpec sp;
+        if (!bound_at(j, n_qubits, e + 1, sp)) continue;
+        if (!(sp.frozen[0] | sp.frozen[1] | sp.frozen[2] | sp.frozen[3]) && sp.n_fields == 0) continue;
+        j.src_bounds.push_back({e, sp});
+    }
+    return true;
+}
+
 static std::vector<fs::JitJobSpec> jit_specs(const fs_batch* b)
 {
     std::vector<fs::JitJobSpec> specs(b->jobs.size());
@@ -1138,6 +1164,7 @@ static std::vector<fs::JitJobSpec> jit_specs(const fs_batch* b)
         specs[ji].bound = j.bound;
         specs[ji].bound_counts = j.bound;
         specs[ji].bspec = j.bspec;
+        if (j.bound) specs[ji].src_bounds = j.src_bounds;
     }
     return specs;
 }
@@ -1235,7 +1262,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.outs = (const uint32_t*)(base + j.o_outs);
         d.ins = (const uint32_t*)(base + j.o_ins);
         d.coef = (const double2*)(base + j.o_coef);
-        d.table = (fs::Entry*)(base + j.o_table);
+        d.table = j.direct ? nullptr : (fs::Entry*)(base + j.o_table);
         d.partials = (double2*)(base + j.o_part);
         d.stats = (unsigned long long*)(base + b->o_stats) + fs::STATS_PER_JOB * ji;
         d.G = (int32_t)j.c->g.size();
@@ -1273,7 +1300,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.trace = j.d_trace;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
-        if (j.levels.empty()) pacc += j.table_entries;
+        if (j.levels.empty() && !j.direct) pacc += j.table_entries;
         oacc += j.outs.size();
         std::memcpy(&H[j.o_ops], j.prog.ops.data(), j.prog.ops.size() * sizeof(fs::Op));
         std::memcpy(&H[j.o_masks], j.prog.masks.data(), j.prog.masks.size() * sizeof(uint32_t));
@@ -1322,7 +1349,7 @@ static bool big_outputs_possible(const fs_batch& b)
         if (j.outs.empty()) continue;
         const int lg = j.compact ? j.sp.Ap + (j.sp.Ar >= 5 ? j.sp.Ar - 5 : j.sp.Ar) : j.log2_spp;
         const long double per_out = std::ldexp((long double)j.ins.size(), lg);
-        if (per_out > (long double)fs::RED_BIG_ITEMS) return true;
+        if (per_out > (long double)fs::RED_BIG_ITEMS || j.ins.size() >= (size_t)fs::RED_BIG_THREADS) return true;
     }
     return false;
 }
@@ -1335,7 +1362,7 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
     bool tiled = false, flat_prefix = false;
     for (const Job& j : b->jobs) {
         tiled |= !j.compact;
-        flat_prefix |= j.levels.empty();
+        flat_prefix |= j.levels.empty() && !j.direct;
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
         if (j.bound && b->opt.engine == 1) k += 1;   // exact bound (inside the generated prefix otherwise)
@@ -1542,10 +1569,10 @@ int fs_batch_finish(fs_batch* b, void* d_ws, void* stream, fs_stats* stats, size
             o.valid = q[1];
             o.gate_visits = q[2] + q[4];
             o.history_visits = q[2];
-            o.table_entries = q[3];
+            o.table_entries = j.direct ? j.pairs : q[3];
             o.learned_cuts = q[5];
             o.bound_cuts = q[8];
-            o.live_entries = j.compact ? q[6] : q[3];
+            o.live_entries = j.compact ? q[6] : o.table_entries;
             // with the bound, the pruner's cuts are marked in the compacted list
             if (j.bound && j.d_pruner) o.live_entries = q[6] - q[5];
             o.c1 = j.sp.c1; o.c2 = j.sp.c2;
@@ -1618,8 +1645,16 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
 {
     const int W = j.W;
     std::vector<std::pair<double2, double2>> classes;
+    bool phase = false;   // commensurate phases: one integer phase, one product per region
     auto defer = [&](double2 A, double2 B) {
         iops += 1;
+        uint32_t p;
+        const bool unit = (B.x == A.x && B.y == A.y) || (B.x == -A.x && B.y == -A.y) ||
+                          (B.x == -A.y && B.y == A.x) || (B.x == A.y && B.y == -A.x);
+        if (fs::phase_index(A, B, &p) && !(hoisted && unit)) {
+            phase = true;
+            return;
+        }
         for (auto& c : classes)
             if (same2(c.first, A) && same2(c.second, B)) return;
         classes.push_back({A, B});
@@ -1702,6 +1737,10 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
                           (B.x == -A.y && B.y == A.x) || (B.x == A.y && B.y == -A.x);
         if (hoisted && unit) iops += 3;   // select and sign flips
         else fops += 4;                   // one complex product per region
+    }
+    if (phase) {
+        iops += 2;   // shift and mask of the phase index
+        fops += 4;   // one complex product by the table entry
     }
 }
 

@@ -136,6 +136,12 @@ constexpr int MLP_PARAMS = 18817;
 // remaining cascades on it), so a state whose field value is farther than
 // that from b_in's (cyclically, modulo 2^len) has an exactly zero subtree
 // sum too.
+// A deferred two-valued factor (A, B) = (1, e^{2 pi i p / 2^16}) for an
+// integer p in (0, 2^16): the straight-line engine adds p to one integer
+// phase per region instead of counting a class (one table product per
+// region for all such factors).
+bool phase_index(double2 A, double2 B, uint32_t* p);
+
 constexpr int MAX_BOUND_FIELDS = 4;
 struct BoundSpec {
     uint32_t frozen[4];
@@ -213,8 +219,11 @@ cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cuda
 // d_big_list (count in d_big_count, zeroed by the caller); one block per
 // listed output sums the rest.
 // big_possible = false skips the block-per-output launch when no output
-// can have more than RED_BIG_ITEMS items.
+// can have more than RED_BIG_ITEMS items or RED_BIG_THREADS input states.
 constexpr uint64_t RED_BIG_ITEMS = 4096;
+// threads of the block-per-output pass; outputs whose input support has at
+// least this many states also go to it (one thread per input state)
+constexpr int RED_BIG_THREADS = 256;
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_job_out_begin, int n_jobs,
                           uint64_t total_out, double2* d_amp, unsigned int* d_big_count, uint64_t* d_big_list,
                           bool big_possible, cudaStream_t s);
@@ -236,6 +245,10 @@ struct JitJobSpec {
     // block (the job has no learned pruner to do it)
     bool bound = false, bound_counts = false;
     BoundSpec bspec{};
+    // with the bound: the bound after each op of the root and suffix that
+    // carries an artificial source (evaluation position, spec for the ops
+    // after it)
+    std::vector<std::pair<int, BoundSpec>> src_bounds;
 };
 // The generated source for these jobs (what jit_build compiles), without
 // compiling it.

@@ -322,10 +322,20 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
         for (int j = 0; j < W; ++j) c.bin[j] = btmp[j];
     }
     if (pair != c.pair || (u64)hp != c.hp) {
-        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
-        const uint4 sv = __ldg(ent);
-        c.amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
-        c.bottom = is_bottom(c.amp.x);
+        uint4 sv;
+        if (J.table) {
+            const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << T::Ap) + hp);
+            sv = __ldg(ent);
+            c.amp = __ldg(reinterpret_cast<const double2*>(ent + 1));
+            c.bottom = is_bottom(c.amp.x);
+        } else {
+            // an empty prefix region: the entry is (b_out, 1)
+            u64 s;
+            const u64 o = pair_split(pair, J, s);
+            sv = __ldg(reinterpret_cast<const uint4*>(J.outs + 4 * o));
+            c.amp = make_double2(1.0, 0.0);
+            c.bottom = false;
+        }
         const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
         for (int j = 0; j < W; ++j) c.st[j] = tmp[j];
@@ -466,6 +476,156 @@ __device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u6
             double2 acc = make_double2(0.0, 0.0);
             if (i < nlive) acc = compact_body<T>(J, i, completed, valid, visits);
             store_esum(J, i, acc, i < nlive);
+        }
+    }
+}
+
+// Level-by-level walk of a threshold job's suffix, a warp per live
+// checkpoint entry.  The partial histories of the entry's subtree wait in
+// per-level queues in shared memory: level L holds histories that passed
+// the suffix's first L sources, at most WALK_CAP of them.  Each step takes
+// up to 16 histories from the top of one level's queue and evaluates both
+// values of their next source in the 32 lanes (segment L of the suffix);
+// the histories that pass the threshold test are queued one level deeper,
+// or, after the last source, run through the tail and the chi test.  The
+// level is the one that fills the most lanes among those whose next level
+// has room for the children (the deepest on ties): the deepest non-empty
+// level always qualifies, since the level below it is empty, so no queue
+// ever exceeds WALK_CAP.  Every history is expanded exactly once, as in the
+// depth-first search, so the leaf counts and gate visits are the same; the
+// lanes stay busy whatever the shape of the subtree, where a lane-per-item
+// search leaves most of a warp idle.  The order of the additions into the
+// entry's sum depends on the entry alone, so an output's amplitude does not
+// depend on the other requested outputs.
+//
+// Shared memory per warp: amplitudes [As][WALK_CAP] (double2), then state
+// words [As][W][WALK_CAP] (u32).  The count of level L is held by lane
+// L % 32 (cnt0 for L < 32, cnt1 otherwise).
+#define WALK_CAP 40
+template <class T>
+__device__ __forceinline__ void walk_loop(const JobDev& J, unsigned char* smem, u64& completed, u64& valid,
+                                          u64& visits)
+{
+    constexpr int W = T::W, As = T::As, CAP = WALK_CAP;
+    constexpr u32 per_warp = (u32)As * CAP * (16u + 4u * (u32)W);
+    constexpr int sh = T::Ar >= 5 ? T::Ar - 5 : T::Ar;   // subtree sums per live entry: 2^sh
+    constexpr u32 n_root = 1u << T::Ar;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    double2* qa = reinterpret_cast<double2*>(smem + (threadIdx.x >> 5) * per_warp);
+    u32* qs = reinterpret_cast<u32*>(qa + As * CAP);
+    const u64 nlive = J.stats[6];
+    for (;;) {
+        u64 i = 0;
+        if (lane == 0) i = atomicAdd(&J.stats[7], 1ull);
+        i = __shfl_sync(full, i, 0);
+        if (i >= nlive) break;
+        const u64 e = J.live[i];
+        const u64 pair = e >> T::Ap;
+        u64 sidx;
+        pair_split(pair, J, sidx);
+        const uint4* ent = reinterpret_cast<const uint4*>(J.table + e);
+        const uint4 sv = __ldg(ent);
+        const double2 amp0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+        const bool bottom = is_bottom(amp0.x);   // cut after the compaction
+        const uint4 bv = __ldg(reinterpret_cast<const uint4*>(J.ins + 4 * sidx));
+        const u32 tmp[4] = {sv.x, sv.y, sv.z, sv.w};
+        const u32 btmp[4] = {bv.x, bv.y, bv.z, bv.w};
+        u32 bin[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) bin[j] = btmp[j];
+        const u64 c0 = completed, v0 = valid;
+        for (u32 r0 = 0; r0 < n_root; r0 += 32u) {
+            double2 acc = make_double2(0.0, 0.0);
+            if (!bottom) {
+                // the roots: lane l takes h_r = r0 + l; survivors form level 0
+                u32 st[W];
+#pragma unroll
+                for (int j = 0; j < W; ++j) st[j] = tmp[j];
+                double2 a = amp0;
+                const u32 hr = r0 + (u32)lane;
+                const bool live = hr < n_root && T::root(st, a, hr, bin, visits) < 0;
+                const unsigned m = __ballot_sync(full, live);
+                if (live) {
+                    const int pos = __popc(m & lt);
+                    qa[pos] = a;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) qs[j * CAP + pos] = st[j];
+                }
+                u32 cnt0 = lane == 0 ? (u32)__popc(m) : 0u, cnt1 = 0u;
+                __syncwarp();
+                for (;;) {
+                    // the level that fills the most lanes with room below it
+                    const u32 nx0 = __shfl_down_sync(full, cnt0, 1), nx1 = __shfl_down_sync(full, cnt1, 1);
+                    const u32 c32 = __shfl_sync(full, cnt1, 0);
+                    const u32 next0 = lane == 31 ? c32 : nx0, next1 = lane == 31 ? 0u : nx1;
+                    const u32 k0 = cnt0 < 16u ? cnt0 : 16u, k1 = cnt1 < 16u ? cnt1 : 16u;
+                    const u32 key0 = (k0 && next0 + 2u * k0 <= (u32)CAP) ? (k0 << 6) | (u32)lane : 0u;
+                    const u32 key1 = (k1 && next1 + 2u * k1 <= (u32)CAP) ? (k1 << 6) | (u32)(lane + 32) : 0u;
+                    const u32 best = __reduce_max_sync(full, key0 > key1 ? key0 : key1);
+                    if (best == 0u) break;
+                    const int L = (int)(best & 63u);
+                    const u32 k = best >> 6;
+                    const u32 n = __shfl_sync(full, L >= 32 ? cnt1 : cnt0, L & 31);
+                    const u32 base = n - k;
+                    if (lane == (L & 31)) {
+                        if (L >= 32) cnt1 = base;
+                        else cnt0 = base;
+                    }
+                    const u32 node = (u32)lane >> 1;
+                    const bool act = node < k;
+                    u32 s2[W];
+                    double2 a2 = make_double2(0.0, 0.0);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) s2[j] = 0u;
+                    int r = 1;
+                    if (act) {
+                        const int slot = (int)(base + node);
+                        a2 = qa[L * CAP + slot];
+#pragma unroll
+                        for (int j = 0; j < W; ++j) s2[j] = qs[(L * W + j) * CAP + slot];
+                        r = T::seg_step(L, s2, a2, (u32)lane & 1u, bin, visits);
+                    }
+                    const bool pass = act && r == 0;
+                    if (L + 1 < As) {
+                        const int L1 = L + 1;
+                        const unsigned m2 = __ballot_sync(full, pass);
+                        const u32 n1 = __shfl_sync(full, L1 >= 32 ? cnt1 : cnt0, L1 & 31);
+                        if (pass) {
+                            const int pos = (int)n1 + __popc(m2 & lt);
+                            qa[L1 * CAP + pos] = a2;
+#pragma unroll
+                            for (int j = 0; j < W; ++j) qs[(L1 * W + j) * CAP + pos] = s2[j];
+                        }
+                        if (lane == (L1 & 31)) {
+                            if (L1 >= 32) cnt1 = n1 + (u32)__popc(m2);
+                            else cnt0 = n1 + (u32)__popc(m2);
+                        }
+                    } else {
+                        bool ok = false;
+                        if (pass && T::tail(s2, a2, 0ull, bin, visits) < 0) {
+                            ++completed;
+                            u32 d = 0;
+#pragma unroll
+                            for (int j = 0; j < W; ++j) d |= s2[j] ^ bin[j];
+                            ok = d == 0u;
+                            valid += ok ? 1u : 0u;
+                        }
+                        add_kept(acc, a2, ok);
+                    }
+                    __syncwarp();
+                }
+            }
+            acc = group_sum(acc, 32);
+            if (lane == 0) J.esum[(i << sh) + (r0 >> 5)] = acc;
+            // with A_r < 5 the entry's other subtree sums are zero (its
+            // whole sum is in the first)
+            if (T::Ar < 5 && lane > 0 && (u32)lane < n_root) J.esum[(i << sh) + (u64)lane] = make_double2(0.0, 0.0);
+        }
+        if (J.trace) {
+            const u64 dc = warp_sum_u64(completed - c0), dv = warp_sum_u64(valid - v0);
+            if (lane == 0) trace_counts(J, pair, dc, dv);
         }
     }
 }
@@ -652,6 +812,34 @@ int class_of(std::vector<FactorClass>& cls, double2 A, double2 B)
     return (int)cls.size() - 1;
 }
 
+// Commensurate phases of the job being generated: the deferred factors
+// (1, e^{2 pi i p / 2^16}) of every region add p to one integer phase and
+// cost one table product per region in all (`bits`: the OR of the p used,
+// which sets the table's size).  Set by generate() for each job.
+struct PhaseAcc {
+    uint32_t bits = 0;
+    std::string table;   // name of the job's phase table
+};
+thread_local PhaseAcc* t_phase = nullptr;
+
+bool unit_phase_pair(double2 A, double2 B)
+{
+    return (B.x == A.x && B.y == A.y) || (B.x == -A.x && B.y == -A.y) || (B.x == -A.y && B.y == A.x) ||
+           (B.x == A.y && B.y == -A.x);
+}
+
+void emit_phase_table(std::string& globals, const std::string& name, int m)
+{
+    const int M = 1 << m;
+    globals += "__device__ const double2 " + name + "[" + std::to_string(M) + "] = {";
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int k = 0; k < M; ++k) {
+        const long double t = two_pi * (long double)k / (long double)M;
+        globals += (k ? ", " : "") + std::string("{") + hexd((double)cosl(t)) + ", " + hexd((double)sinl(t)) + "}";
+    }
+    globals += "};\n";
+}
+
 void emit_class_table(std::string& globals, const std::string& name, const FactorClass& f)
 {
     using cl = std::complex<long double>;
@@ -750,9 +938,15 @@ std::string mul_two_valued(double2 A, double2 B, const std::string& sel)
 // sst / sam, so that the next history can restart at the first source whose
 // bit changed.  `low` then starts at the bit of the last source before
 // `start`, and visits count the ops run in this call.
+// segswitch: the region's segments as the cases of a switch on L (segment L
+// alone, its source bit given as `bit`; 1 when the history is cut, 0
+// otherwise) -- the level-by-level walk of the suffix; the region must end
+// with its last source op (the ops after it form the separate tail).
+std::string bound_after(const JitJobSpec& J, int e, const std::string& visits_cut);
+
 void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
                  int e0, int e1, int nbits, bool chi_only = false, std::complex<long double>* hoist = nullptr,
-                 bool stacked = false)
+                 bool stacked = false, bool segswitch = false)
 {
     const int W = J.W;
     const int dfrom = defer_from(J);
@@ -760,7 +954,15 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
     std::string body;
     int seg = 0, seg_e0 = e0;   // current segment and its first op
     if (stacked) body += "    if (start <= 0) {\n";
+    if (segswitch) body += "    int low = 0;\n    (void)low;\n    switch (L) {\n    case 0: {\n";
+    bool ph_used = false;
     auto count = [&](double2 A, double2 B, const std::string& bexpr) {
+        uint32_t pidx = 0;
+        if (t_phase && phase_index(A, B, &pidx) && !(hoist && unit_phase_pair(A, B))) {
+            ph_used = true;
+            t_phase->bits |= pidx;
+            return "ph += (" + bexpr + ") ? " + std::to_string(pidx) + "u : 0u;";
+        }
         const int c = class_of(cls, A, B);
         return "k" + std::to_string(c) + " += (" + bexpr + ");";
     };
@@ -777,8 +979,10 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         const int q0 = op.q0, q1 = op.q1;
         const double2* F = J.fac + op.aux;
         const bool defer = e >= dfrom;
-        const std::string visits_cut = "{ visits += " + std::to_string(e - seg_e0 + 1) + "ull; return low; }";
+        const std::string visits_cut = "{ visits += " + std::to_string(e - seg_e0 + 1) + "ull; return " +
+                                       (segswitch ? "1" : "low") + "; }";
         auto srcbit = [&](int sidx, int q) {
+            if (segswitch && sidx >= 0) return std::string("bit");
             if (sidx >= 32) return "((u32)(h >> " + std::to_string(sidx) + ") & 1u)";
             return sidx >= 0 ? "((h32 >> " + std::to_string(sidx) + ") & 1u)"
                              : "((bin[" + std::to_string(q >> 5) + "] >> " + std::to_string(q & 31) + ") & 1u)";
@@ -847,6 +1051,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             if (op.s0 >= 0) {
                 c += " low = " + std::to_string(op.s0) + ";";
                 if (J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
+                c += bound_after(J, e, visits_cut);
             }
             break;
         }
@@ -867,6 +1072,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
                 c += " if (" + zc + ") " + visits_cut;
             }
             if (op.s0 >= 0 && J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
+            if (op.s0 >= 0) c += bound_after(J, e, visits_cut);
             c += " }";
             break;
         }
@@ -887,6 +1093,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
                 c += " if (" + zc + ") " + visits_cut;
             }
             if (lo != 99 && J.eps2 > 0) c += " if (cut(a, " + hexd(J.eps2) + ")) " + visits_cut;
+            if (lo != 99) c += bound_after(J, e, visits_cut);
             c += " }";
             break;
         }
@@ -897,6 +1104,12 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         if (!c.empty()) body += "    " + c + "\n";
         const bool carries = (op.code == OP_H || op.code == OP_BR1 || op.code == OP_BR2) &&
                              (op.s0 >= 0 || (op.code == OP_BR2 && op.s1 >= 0));
+        if (segswitch && carries) {
+            body += "    visits += " + std::to_string(e - seg_e0 + 1) + "ull;\n    return 0;\n    }\n";
+            ++seg;
+            seg_e0 = e + 1;
+            if (seg < nbits) body += "    case " + std::to_string(seg) + ": {\n";
+        }
         if (stacked && carries) {
             // close the segment: checkpoint after this source op
             const std::string k = std::to_string(seg);
@@ -909,14 +1122,20 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         }
     }
     if (stacked && seg < nbits) body += "    }\n";   // (a region whose last op carries no source)
+    if (segswitch) {
+        out += body + "    default: break;\n    }\n    (void)s; (void)a; (void)bin;\n    return 0;\n";
+        return;
+    }
     // 64-bit integer operations run through the FP64 pipe on this part:
     // the enumeration word is read as 32 bits wherever its bits allow
     out += "    const u32 h32 = (u32)h;\n    (void)h32;\n";
     out += stacked ? "    int low = " + std::to_string(nbits) + " - start;\n"
                    : "    int low = " + std::to_string(nbits) + ";\n";
     for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
+    if (ph_used) out += "    u32 ph = 0u;\n";
     out += body;
-    if (chi_only && !cls.empty()) {
+    const bool products = !cls.empty() || ph_used;
+    if (chi_only && products) {
         out += "    u32 dchi = 0u;\n";
         for (int j = 0; j < W; ++j) out += "    dchi |= s[" + std::to_string(j) + "] ^ bin[" + std::to_string(j) + "];\n";
         // the class products only for valid leaves, behind a vote so that
@@ -950,30 +1169,33 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         out += chi_only ? "    a = fs_cmul_ool(a, &" + name + "[" + kv + "]);\n"
                         : "    a = cmul(a, __ldg(&" + name + "[" + kv + "]));\n";
     }
-    if (chi_only && !cls.empty()) out += "    }\n";
+    if (ph_used) {
+        const std::string idx = "&" + t_phase->table + "[(ph >> PH_SHIFT) & PH_MASK]";
+        out += chi_only ? "    a = fs_cmul_ool(a, " + idx + ");\n" : "    a = cmul(a, __ldg(" + idx + "));\n";
+    }
+    if (chi_only && products) out += "    }\n";
     out += "    visits += " + std::to_string(e1 - seg_e0) + "ull;\n    (void)low;\n    return -1;\n";
 }
 
 // The exact reachability bound of a job as code (the BoundSpec as
 // immediates): true when the checkpoint state s cannot reach bin.
-std::string emit_bound(const JitJobSpec& J)
+std::string emit_bound_fn(const std::string& name, int W, bool enabled, const BoundSpec& B)
 {
-    const int W = J.W;
-    std::string c = "  static __device__ __forceinline__ bool bound_cut(const u32 (&s)[" + std::to_string(W) +
+    std::string c = "  static __device__ __forceinline__ bool " + name + "(const u32 (&s)[" + std::to_string(W) +
                     "], const u32 (&bin)[" + std::to_string(W) + "]) {\n";
-    if (!J.bound) return c + "    (void)s; (void)bin;\n    return false;\n  }\n";
+    if (!enabled) return c + "    (void)s; (void)bin;\n    return false;\n  }\n";
     c += "    u32 d = 0u;\n";
     for (int j = 0; j < W; ++j)
-        if (J.bspec.frozen[j]) {
+        if (B.frozen[j]) {
             char buf[96];
-            snprintf(buf, sizeof buf, "    d |= (s[%d] ^ bin[%d]) & 0x%08xu;\n", j, j, J.bspec.frozen[j]);
+            snprintf(buf, sizeof buf, "    d |= (s[%d] ^ bin[%d]) & 0x%08xu;\n", j, j, B.frozen[j]);
             c += buf;
         }
     c += "    if (d) return true;\n";
     // a field: its value in 32-bit words (funnel shifts at fixed offsets),
     // both cyclic differences by borrow chains, each compared with the radius
-    for (int f = 0; f < J.bspec.n_fields; ++f) {
-        const int t0 = J.bspec.t0[f], len = J.bspec.len[f], FW = (len + 31) / 32;
+    for (int f = 0; f < B.n_fields; ++f) {
+        const int t0 = B.t0[f], len = B.len[f], FW = (len + 31) / 32;
         const uint32_t top = (len % 32) ? ((1u << (len % 32)) - 1u) : 0xffffffffu;
         c += "    {\n";
         auto word = [&](const std::string& v, int k) {
@@ -1002,11 +1224,30 @@ std::string emit_bound(const JitJobSpec& J)
             std::string hiw = "0u";
             for (int k = 1; k < FW; ++k) hiw += " | " + std::string(dir) + std::to_string(k);
             c += "      const bool " + std::string(dir) + "far = (" + hiw + ") != 0u || " + dir + "0 > " +
-                 std::to_string(J.bspec.radius[f]) + "u;\n";
+                 std::to_string(B.radius[f]) + "u;\n";
         }
         c += "      if (ufar && vfar) return true;\n    }\n";
     }
     return c + "    return false;\n  }\n";
+}
+
+// The bound at the checkpoint (bound_cut) and after each source op of the
+// root and suffix (bound_after_<e>).
+std::string emit_bound(const JitJobSpec& J)
+{
+    std::string c = emit_bound_fn("bound_cut", J.W, J.bound, J.bspec);
+    if (J.bound)
+        for (const auto& pb : J.src_bounds) c += emit_bound_fn("bound_after_" + std::to_string(pb.first), J.W, true, pb.second);
+    return c;
+}
+
+// The per-source bound test after op e, or "" (none at e).
+std::string bound_after(const JitJobSpec& J, int e, const std::string& visits_cut)
+{
+    if (!J.bound) return "";
+    for (const auto& pb : J.src_bounds)
+        if (pb.first == e) return " if (bound_after_" + std::to_string(e) + "(s, bin)) " + visits_cut;
+    return "";
 }
 
 // Threshold jobs whose suffix carries at least two artificial sources, one
@@ -1024,6 +1265,22 @@ bool stacked_suffix(const JitJobSpec& J)
     return n == J.As;
 }
 
+// Threshold jobs whose suffix walks level by level (a warp per root
+// checkpoint, per-level queues of partial histories): the stacked ones with
+// at least 5 sources in the suffix.  Returns the evaluation position of the
+// suffix's last source op, or -1.
+int queue_last_source(const JitJobSpec& J)
+{
+    if (!stacked_suffix(J) || J.As < 5) return -1;
+    int last = -1;
+    for (int e = J.c2; e < J.G; ++e) {
+        const Op& op = J.ops[e];
+        const bool br = op.code == OP_H || op.code == OP_BR1 || op.code == OP_BR2;
+        if (br && (op.s0 >= 0 || op.s1 >= 0)) last = e;
+    }
+    return last;
+}
+
 std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* scales)
 {
     std::string src = kPrelude;
@@ -1032,13 +1289,18 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         const JitJobSpec& J = jobs[j];
         const std::string W = std::to_string(J.W), js = std::to_string(j);
         const bool stacked = stacked_suffix(J);
+        const int qlast = queue_last_source(J);   // >= 0: the suffix walks level by level
         structs += "struct J" + js + " {\n";
         structs += "  static constexpr int W = " + W + ", Ap = " + std::to_string(J.Ap) + ", Ar = " +
                    std::to_string(J.Ar) + ", As = " + std::to_string(J.As) + ";\n";
         structs += std::string("  static constexpr bool STACKED = ") + (stacked ? "true" : "false") + ";\n";
+        structs += std::string("  static constexpr bool QUEUE = ") + (qlast >= 0 ? "true" : "false") + ";\n";
         structs += std::string("  static constexpr bool BOUND = ") + (J.bound ? "true" : "false") +
                    ", COUNTB = " + (J.bound && J.bound_counts ? "true" : "false") + ";\n";
         structs += emit_bound(J);
+        PhaseAcc phase;
+        phase.table = "PH_J" + js;
+        t_phase = &phase;
         const std::string sig = "(u32 (&s)[" + W + "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits)";
         structs += "  static __device__ __forceinline__ int prefix" + sig + " {\n    (void)h; (void)bin;\n";
         if (J.levels.empty()) emit_region(structs, globals, js + "p", J, 0, J.c1, J.Ap);
@@ -1056,6 +1318,18 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         std::complex<long double> hoisted(1.0L, 0.0L);
         emit_region(structs, globals, js + "r", J, J.c1, J.c2, J.Ar, false, &hoisted);
         structs += "  }\n";
+        if (qlast >= 0) {
+            // the suffix as one switch case per source segment, and its tail
+            // (the ops after the last source: deferred classes, chi)
+            std::complex<long double> h3(1.0L, 0.0L);
+            structs += "  static __device__ __forceinline__ int seg_step(int L, u32 (&s)[" + W + "], double2& a, u32 bit, "
+                       "const u32 (&bin)[" + W + "], u64& visits) {\n    (void)bit;\n";
+            emit_region(structs, globals, js + "q", J, J.c2, qlast + 1, J.As, false, nullptr, false, true);
+            structs += "  }\n";
+            structs += "  static __device__ __forceinline__ int tail" + sig + " {\n    (void)h; (void)bin;\n";
+            emit_region(structs, globals, js + "u", J, qlast + 1, J.G, 0, true, &h3);
+            structs += "  }\n";
+        }
         if (stacked) {
             // the same suffix as per-source segments (its hoisted constant is
             // the one of `suffix` below: the same tail classes)
@@ -1073,7 +1347,18 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         if (scales) (*scales)[j] = sc;
         structs += "// J" + js + ": constant factor of the root and suffix, applied through c_in: (" + hexd(sc.x) +
                    ", " + hexd(sc.y) + ")\n";
-        structs += "  }\n};\n";
+        structs += "  }\n";
+        // the phase table: 2^m entries, m from the lowest phase bit used
+        t_phase = nullptr;
+        int m = 0;
+        if (phase.bits) {
+            m = 16;
+            while (m > 0 && !(phase.bits & (1u << (16 - m)))) --m;
+            emit_phase_table(globals, phase.table, m);
+        }
+        structs += "  static constexpr int PH_SHIFT = " + std::to_string(16 - m) + ";\n";
+        structs += "  static constexpr u32 PH_MASK = " + std::to_string((1u << m) - 1u) + "u;\n";
+        structs += "};\n";
     }
     src += globals;
     src += structs;
@@ -1101,6 +1386,22 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
            "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
            "    if (lane == 0 && (completed | valid | visits)) {\n"
            "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
+    bool any_queue = false;
+    for (const JitJobSpec& J : jobs) any_queue |= queue_last_source(J) >= 0;
+    if (any_queue) {
+        src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_walk(const JobDev* __restrict__ jobs, int job)\n{\n"
+               "    extern __shared__ __align__(16) unsigned char walk_smem[];\n"
+               "    const JobDev& J = jobs[job];\n    const int lane = threadIdx.x & 31;\n"
+               "    u64 completed = 0, valid = 0, visits = 0;\n    switch (job) {\n";
+        for (size_t j = 0; j < jobs.size(); ++j)
+            if (queue_last_source(jobs[j]) >= 0)
+                src += "    case " + std::to_string(j) + ": walk_loop<J" + std::to_string(j) +
+                       ">(J, walk_smem, completed, valid, visits); break;\n";
+        src += "    default: break;\n    }\n"
+               "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
+               "    if (lane == 0 && (completed | valid | visits)) {\n"
+               "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
+    }
     for (size_t j = 0; j < jobs.size(); ++j) {
         if (jobs[j].levels.empty()) continue;
         const std::string js = std::to_string(j), T = "J" + js;
@@ -1169,12 +1470,39 @@ struct JitModule {
     cudaKernel_t kernel = nullptr;
     cudaKernel_t prefix = nullptr;
     cudaKernel_t compact = nullptr;
+    cudaKernel_t walk = nullptr;      // level-by-level suffix walk (threshold jobs)
+    std::vector<int> walk_warps;      // per job: warps per block of the walk (0: not walked)
+    std::vector<int> walk_grid;       // per job: blocks of the walk
+    std::vector<size_t> walk_smem;    // per job: shared memory per block of the walk
     int compact_grid = 0;
     int grid = 0;
     int sms = 148;
 };
 
+// Shared memory of the walk: per warp, As x 40 queued histories (the
+// device's WALK_CAP) of 16 B (amplitude) plus 4 W bytes (state); warps per
+// block such that a block takes at most 220 KB (the SM's shared memory), at
+// most 8 warps.
+constexpr size_t WALK_BLOCK_BYTES = 220 * 1024;
+size_t walk_bytes_per_warp(const JitJobSpec& J) { return (size_t)J.As * 40u * (16u + 4u * (size_t)J.W); }
+
 }  // namespace
+
+bool phase_index(double2 A, double2 B, uint32_t* p)
+{
+    if (A.x != 1.0 || A.y != 0.0) return false;
+    const long double re = B.x, im = B.y;
+    if (fabsl(re * re + im * im - 1.0L) > 1e-12L) return false;
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    long double t = atan2l(im, re) / two_pi * 65536.0L;
+    if (t < 0) t += 65536.0L;
+    const long double r = roundl(t);
+    if (fabsl(t - r) > 1e-6L) return false;
+    const uint32_t q = (uint32_t)r & 0xffffu;
+    if (q == 0u) return false;
+    *p = q;
+    return true;
+}
 
 std::string jit_source(const std::vector<JitJobSpec>& jobs)
 {
@@ -1238,6 +1566,35 @@ int jit_build(const std::vector<JitJobSpec>& jobs, void** handle, std::string* e
     per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)m->compact, TILE, 0);
     m->compact_grid = m->sms * (per_sm > 0 ? per_sm : 1);
+    m->walk_warps.assign(jobs.size(), 0);
+    m->walk_grid.assign(jobs.size(), 0);
+    m->walk_smem.assign(jobs.size(), 0);
+    size_t walk_max = 0;
+    for (size_t j = 0; j < jobs.size() && e == cudaSuccess; ++j) {
+        if (queue_last_source(jobs[j]) < 0) continue;
+        if (!m->walk) e = cudaLibraryGetKernel(&m->walk, m->lib, "fs_jit_walk");
+        const size_t pw = walk_bytes_per_warp(jobs[j]);
+        size_t w = WALK_BLOCK_BYTES / pw;
+        w = w < 1 ? 1 : (w > 8 ? 8 : w);
+        m->walk_warps[j] = (int)w;
+        m->walk_smem[j] = w * pw;
+        if (m->walk_smem[j] > walk_max) walk_max = m->walk_smem[j];
+    }
+    if (e == cudaSuccess && m->walk)
+        e = cudaFuncSetAttribute((const void*)m->walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)walk_max);
+    for (size_t j = 0; j < jobs.size() && e == cudaSuccess; ++j) {
+        if (!m->walk_warps[j]) continue;
+        per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)m->walk, 32 * m->walk_warps[j],
+                                                          m->walk_smem[j]);
+        m->walk_grid[j] = m->sms * (per_sm > 0 ? per_sm : 1);
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("preparing the suffix walk kernel: ") + cudaGetErrorString(e);
+        cudaLibraryUnload(m->lib);
+        delete m;
+        return -2;
+    }
     *handle = m;
     return 0;
 }
@@ -1282,6 +1639,9 @@ cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cuda
 {
     JitModule* m = (JitModule*)handle;
     void* args[] = {(void*)&d_jobs, (void*)&job};
+    if (job >= 0 && job < (int)m->walk_warps.size() && m->walk_warps[job])
+        return cudaLaunchKernel((const void*)m->walk, dim3(m->walk_grid[job]), dim3(32 * m->walk_warps[job]), args,
+                                m->walk_smem[job], s);
     return cudaLaunchKernel((const void*)m->compact, dim3(m->compact_grid), dim3(TILE), args, 0, s);
 }
 

@@ -474,11 +474,18 @@ __device__ double2 history_item(const JobDev& J, uint64_t item, uint32_t* err, u
     const uint64_t hp = local >> J.Ar;
     const uint64_t hr = local & ((1ull << J.Ar) - 1ull);
     uint64_t s;
-    pair_split(pair, J, s);
-    const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << J.Ap) + hp);
-    const uint4 sv = __ldg(ent);
-    const double2 a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
-    if (is_bottom(a0.x)) return acc;
+    const uint64_t o = pair_split(pair, J, s);
+    uint4 sv;
+    double2 a0 = make_double2(1.0, 0.0);
+    if (J.table) {
+        const uint4* ent = reinterpret_cast<const uint4*>(J.table + (pair << J.Ap) + hp);
+        sv = __ldg(ent);
+        a0 = __ldg(reinterpret_cast<const double2*>(ent + 1));
+        if (is_bottom(a0.x)) return acc;
+    } else {
+        // an empty prefix region: the entry is (b_out, 1)
+        sv = __ldg(reinterpret_cast<const uint4*>(J.outs + 4 * o));
+    }
     uint32_t st[W], bin[W];
     const uint32_t tmp[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
@@ -829,17 +836,40 @@ __device__ __forceinline__ double2 strided_sum(const double2* __restrict__ src, 
     return make_double2((a[0].x + a[1].x) + (a[2].x + a[3].x), (a[0].y + a[1].y) + (a[2].y + a[3].y));
 }
 
+// c_in * alpha summed over the pairs s = t, t + stride, ... of output o,
+// each pair's items added in order (the thread's share of a wide input
+// support, Eq. 2).
+__device__ __forceinline__ double2 pairs_by_lane(const JobDev& J, uint64_t o, int t, int stride)
+{
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = t; s < J.S; s += stride) {
+        uint64_t lo, hi;
+        const double2* src = pair_items(J, o * (uint64_t)J.S + (uint64_t)s, lo, hi);
+        if (hi == lo) continue;
+        double2 p = src[lo];
+        for (uint64_t k = lo + 1; k < hi; ++k) {
+            const double2 v = src[k];
+            p.x += v.x;
+            p.y += v.y;
+        }
+        const double2 w = cmul(__ldg(J.coef + s), p);
+        acc.x += w.x;
+        acc.y += w.y;
+    }
+    return acc;
+}
+
 constexpr int RED_LPO = 4;            // lanes per output in the common path
 constexpr uint64_t RED_SMALL = 64;    // outputs with more items take the whole warp
 constexpr uint64_t RED_WARP = RED_BIG_ITEMS;   // outputs with more items go to reduce_big_kernel
-constexpr int RED_BIG_THREADS = 256;
 
 // FP64 is scarce on this part (about 2 FMA per clock per SM), so the
 // reduction keeps FP64 instructions per output low: each warp takes 8
 // outputs, 4 lanes each (lane-strided sums, a 2-level butterfly), then adds
 // c_in * alpha over the input support in order (Eq. 2).  An output with more
 // than RED_SMALL items is summed by the whole warp, one with more than
-// RED_WARP is listed for reduce_big_kernel.  The order of every sum depends
+// RED_WARP items or an input support of RED_BIG_THREADS or more is listed
+// for reduce_big_kernel.  The order of every sum depends
 // only on the item counts, so results are run-to-run identical.
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __restrict__ jobs,
                                                                 const uint64_t* __restrict__ begin,
@@ -860,12 +890,15 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
         const int S = have ? J.S : 0;
         const uint64_t o = have ? g - J.out_begin : 0;
         uint64_t n = 0;
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < (S < RED_BIG_THREADS ? S : 0); ++s) {
             uint64_t lo, hi;
             pair_items(J, o * (uint64_t)S + (uint64_t)s, lo, hi);
             n += hi - lo;
         }
-        const bool small = n <= RED_SMALL;
+        // wide input supports (S >= 256) go to the block-per-output pass,
+        // whose threads take the pairs in parallel
+        const bool small = n <= RED_SMALL && S < 32;
+        const bool big = n > RED_WARP || S >= RED_BIG_THREADS;
         const int s_max = (int)__reduce_max_sync(0xffffffffu, small ? (unsigned)S : 0u);
         double2 amp = make_double2(0.0, 0.0);
         for (int s = 0; s < s_max; ++s) {
@@ -891,7 +924,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
         }
         // medium outputs: the whole warp, one output at a time (32-lane
         // stride, 5-level butterfly); larger ones go to reduce_big_kernel
-        unsigned mid = __ballot_sync(0xffffffffu, have && !small && n <= RED_WARP && sub == 0);
+        unsigned mid = __ballot_sync(0xffffffffu, have && !small && !big && sub == 0);
         while (mid) {
             const int b = __ffs(mid) - 1;
             mid &= mid - 1u;
@@ -899,26 +932,39 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
             const int jb = __shfl_sync(0xffffffffu, j, b);
             const JobDev& JB = jobs[jb];
             const uint64_t ob = gb - JB.out_begin;
+            const uint64_t nb = __shfl_sync(0xffffffffu, n, b);
             double2 ab = make_double2(0.0, 0.0);
-            for (int s = 0; s < JB.S; ++s) {
-                uint64_t lo, hi;
-                const double2* src = pair_items(JB, ob * (uint64_t)JB.S + (uint64_t)s, lo, hi);
-                if (hi == lo) continue;   // warp-uniform: the same pair for every lane
-                double2 t = strided_sum(src, lo + (uint64_t)lane, hi, 32);
+            if (JB.S >= 32 && nb <= 8u * (uint64_t)JB.S) {
+                // a wide input support with few items per pair: lane l
+                // takes the pairs s = l, l + 32, ... (c_in * alpha of each
+                // added in order), then a 5-level butterfly
+                ab = pairs_by_lane(JB, ob, lane, 32);
 #pragma unroll
                 for (int off = 16; off >= 1; off >>= 1) {
-                    t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
-                    t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+                    ab.x += __shfl_xor_sync(0xffffffffu, ab.x, off);
+                    ab.y += __shfl_xor_sync(0xffffffffu, ab.y, off);
                 }
-                const double2 w = cmul(__ldg(JB.coef + s), t);
-                ab.x += w.x;
-                ab.y += w.y;
+            } else {
+                for (int s = 0; s < JB.S; ++s) {
+                    uint64_t lo, hi;
+                    const double2* src = pair_items(JB, ob * (uint64_t)JB.S + (uint64_t)s, lo, hi);
+                    if (hi == lo) continue;   // warp-uniform: the same pair for every lane
+                    double2 t = strided_sum(src, lo + (uint64_t)lane, hi, 32);
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) {
+                        t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+                        t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+                    }
+                    const double2 w = cmul(__ldg(JB.coef + s), t);
+                    ab.x += w.x;
+                    ab.y += w.y;
+                }
             }
             if (lane == b) amp_out[gb] = ab;
         }
         if (have && sub == 0) {
             if (small) amp_out[g] = amp;
-            else if (n > RED_WARP) big_list[atomicAdd(big_count, 1u)] = g;
+            else if (big) big_list[atomicAdd(big_count, 1u)] = g;
         }
     }
 }
@@ -940,6 +986,28 @@ __global__ void __launch_bounds__(RED_BIG_THREADS) reduce_big_kernel(const JobDe
         const JobDev& J = jobs[find_job(begin, n_jobs, g)];
         const uint64_t o = g - J.out_begin;
         double2 amp = make_double2(0.0, 0.0);
+        if (J.S >= RED_BIG_THREADS) {
+            // a wide input support: thread t takes the pairs s = t, t + 256,
+            // ...; then a butterfly per warp and the warps added in order
+            double2 t = pairs_by_lane(J, o, threadIdx.x, RED_BIG_THREADS);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+            }
+            if (lane == 0) s_w[warp] = t;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double2 a = s_w[0];
+                for (int w = 1; w < RED_BIG_THREADS / 32; ++w) {
+                    a.x += s_w[w].x;
+                    a.y += s_w[w].y;
+                }
+                amp_out[g] = a;
+            }
+            __syncthreads();
+            continue;
+        }
         for (int s = 0; s < J.S; ++s) {
             uint64_t lo, hi;
             const double2* src = pair_items(J, o * (uint64_t)J.S + (uint64_t)s, lo, hi);

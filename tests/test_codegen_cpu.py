@@ -212,6 +212,57 @@ SUFFIX_STACKED = """
                     }"""
 
 
+# the device's level-by-level walk of a threshold suffix (its 32 lanes in
+# turn): per-level queues of partial histories (at most 40 each); a step
+# takes up to 16 histories from the top of the level that fills the most
+# lanes among those whose next level has room for their children (the
+# deepest on ties) and evaluates both values of their next source; the
+# passing ones are queued one level deeper or, after the last source, run
+# through the tail and the chi test
+SUFFIX_QUEUE = """
+                    {
+                        static u32 qs[J0::As][40][W];
+                        static double2 qa[J0::As][40];
+                        u32 cnt[J0::As + 1];
+                        for (int l = 0; l <= J0::As; ++l) cnt[l] = 0;
+                        for (int j = 0; j < W; ++j) qs[0][0][j] = st2[j];
+                        qa[0][0] = a2;
+                        cnt[0] = 1;
+                        for (;;) {
+                            int L = -1;
+                            u32 k = 0;
+                            for (int l = J0::As - 1; l >= 0; --l) {
+                                const u32 kl = cnt[l] < 16 ? cnt[l] : 16;
+                                if (kl > k && cnt[l + 1] + 2 * kl <= 40) { L = l; k = kl; }
+                            }
+                            if (L < 0) break;
+                            const u32 n = cnt[L], base = n - k;
+                            cnt[L] = base;
+                            u32 np = cnt[L + 1];
+                            for (int lane = 0; lane < 32; ++lane) {
+                                const u32 node = lane >> 1;
+                                if (node >= k) continue;
+                                u32 s3[W];
+                                for (int j = 0; j < W; ++j) s3[j] = qs[L][base + node][j];
+                                double2 a3 = qa[L][base + node];
+                                if (J0::seg_step(L, s3, a3, (u32)lane & 1u, bin, visits) != 0) continue;
+                                if (L + 1 < J0::As) {
+                                    if (np >= 40) { std::printf("queue overflow\\n"); return 1; }
+                                    for (int j = 0; j < W; ++j) qs[L + 1][np][j] = s3[j];
+                                    qa[L + 1][np] = a3;
+                                    ++np;
+                                } else if (J0::tail(s3, a3, 0ull, bin, visits) < 0) {
+                                    ++completed;
+                                    bool ok = true;
+                                    for (int j = 0; j < W; ++j) ok = ok && s3[j] == bin[j];
+                                    if (ok) { sr += a3.x; si += a3.y; ++valid; }
+                                }
+                            }
+                            if (L + 1 < J0::As) cnt[L + 1] = np;
+                        }
+                    }"""
+
+
 def _words(v, W):
     return "{" + ", ".join(f"{(v >> (32 * j)) & 0xffffffff}u" for j in range(4)) + "}"
 
@@ -221,7 +272,8 @@ def _extract(src):
     j = src.index("__device__ __forceinline__ double2 sel2")
     j = src.index("\n", j) + 1
     helpers = src[i:j]
-    k = min(x for x in (src.find("__device__ const double2 T_"), src.find("struct J0 {")) if x >= 0)
+    k = min(x for x in (src.find("__device__ const double2 T_"), src.find("__device__ const double2 PH_"),
+                        src.find("struct J0 {")) if x >= 0)
     e = src.index('extern "C"', k)
     body = src[k:e]
     scale_line = [l for l in body.splitlines() if "J0: constant factor" in l][0]
@@ -229,11 +281,13 @@ def _extract(src):
     return helpers, body, sx.strip(), sy.strip()
 
 
-def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
+def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single", walk=False, bound=False):
     C = fs.Circuit(circ)
     C.set_input(inputs)
     b = fs.Batch(split="fixed", c1=c1, c2=c2, prefix=prefix)
     b.add(C, outputs, eps)
+    if bound:
+        b.set_exact_bound(0)
     b.plan()
     src = b.generated_source()
     helpers, body, sx, sy = _extract(src)
@@ -244,7 +298,8 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
                   cre=", ".join(repr(complex(c).real) for _, c in inputs),
                   cim=", ".join(repr(complex(c).imag) for _, c in inputs), sx=sx, sy=sy)
     stacked = "STACKED = true" in src
-    fields["suffix_loop"] = SUFFIX_STACKED if stacked else SUFFIX_PLAIN
+    queue = "QUEUE = true" in src
+    fields["suffix_loop"] = (SUFFIX_QUEUE if walk and queue else SUFFIX_STACKED if stacked else SUFFIX_PLAIN)
     levels = [l.split("sources [")[1].rstrip(")").split(", ") for l in src.splitlines() if "  // level " in l]
     if levels:
         fields.update(L=len(levels), aprev=", ".join(a for a, _ in levels), anext=", ".join(b_ for _, b_ in levels),
@@ -261,6 +316,7 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single"):
     rows = [l.split() for l in subprocess.check_output([exe]).decode().splitlines()]
     amp = np.array([float(r[0]) + 1j * float(r[1]) for r in rows])
     _host_amplitudes.stacked = stacked
+    _host_amplitudes.queue = queue
     return amp, np.array([int(r[2]) for r in rows]), np.array([int(r[3]) for r in rows])
 
 
@@ -404,6 +460,12 @@ def test_stacked_suffix_matches_the_oracle(family, eps, tmp_path):
     _close(got, want)
     assert np.array_equal(completed, cnt["completed"].astype(np.int64))
     assert np.array_equal(valid, cnt["valid"].astype(np.int64))
+    if _host_amplitudes.queue:
+        # the same suffix walked level by level (seg_step / tail)
+        got, completed, valid = _host_amplitudes(circ, inputs, outputs, c1, c2, eps, str(tmp_path), walk=True)
+        _close(got, want)
+        assert np.array_equal(completed, cnt["completed"].astype(np.int64))
+        assert np.array_equal(valid, cnt["valid"].astype(np.int64))
 
 
 def test_generated_exact_bound_matches_the_reachability_rule(tmp_path):
@@ -459,3 +521,31 @@ def test_generated_exact_bound_matches_the_reachability_rule(tmp_path):
             want.append(int(dist > radius or (((s ^ b_in) >> (pos_bits + 3)) & 1) == 1))
         assert got == want
         assert 0 < sum(want) < len(want)
+
+
+@pytest.mark.parametrize("case", ["walk", "cascade_inc", "cascade_dec"])
+def test_generated_bound_after_each_source_keeps_every_valid_leaf(case, tmp_path):
+    """With the exact bound, the generated root and suffix also test the
+    bound after every op that carries an artificial source (bound_after_<e>)
+    and cut the subtree of a history that can no longer reach the input.
+    Driven on the host by Algorithm 2's loop: the valid leaves and the
+    amplitudes are the oracle's (only invalid histories are cut), and on the
+    walk the checks are present and fewer leaves complete."""
+    spec = CASES[case]()
+    circ, inputs, outputs = spec
+    G = len(circ.gates)
+    c1, c2 = G // 3, (2 * G) // 3
+    got, completed, valid = _host_amplitudes(circ, inputs, outputs, c1, c2, 0.0, str(tmp_path), bound=True)
+    want, cnt = feynman.run(circ, inputs, outputs, c1=c1, c2=c2)
+    _close(got, want)
+    assert np.array_equal(valid, cnt["valid"].astype(np.int64))
+    assert np.all(completed <= cnt["completed"].astype(np.int64))
+    if case == "walk":
+        C = fs.Circuit(circ)
+        C.set_input(inputs)
+        b = fs.Batch(split="fixed", c1=c1, c2=c2)
+        b.add(C, outputs)
+        b.set_exact_bound(0)
+        b.plan()
+        assert "if (bound_after_" in b.generated_source()
+        assert completed.sum() < cnt["completed"].sum()

@@ -130,3 +130,46 @@ def test_threshold_request_exercises_large_tables_and_the_block_reduction():
     entries = len(w.outputs) << st["A_p"]
     assert entries // 1024 > 1024                  # compaction blocks > scan threads
     assert st["A_r"] <= 5 and st["live_entries"] // len(w.outputs) > 4096
+
+
+def _cut_after_sources(circuit, k):
+    """Evaluation position just after the op carrying artificial source
+    k - 1 (the first k sources of the backward sweep lie before it)."""
+    bv = fs.Circuit(circuit).branch_vars()
+    srcs = {s: g for g, q, s in bv if s >= 0}
+    return 0 if k <= 0 else len(circuit.gates) - srcs[k - 1]
+
+
+@pytest.mark.parametrize("ap,ar", [(4, 2), (3, 6)])
+@pytest.mark.parametrize("eps", [1e-3, 3e-4])
+def test_level_walk_of_the_suffix_matches_the_oracle(ap, ar, eps):
+    """Threshold jobs with five or more sources in the suffix walk it level
+    by level, a warp per live checkpoint entry, with per-level queues of
+    partial histories in shared memory.  With A_r = 2 the entry's roots fill
+    part of one warp and its sum lands in the first of its subtree slots;
+    with A_r = 6 the roots come in two chunks of 32 with one sum each.
+    Amplitudes within 1e-12 / 1e-10 of the oracle at the same cuts, leaf
+    counts exactly the oracle's, and fewer gate visits than Algorithm 2's
+    (no cut subtree is entered)."""
+    from oracle import feynman
+    w = qaoa_workload(10, 2, n_out=24, seed=9)
+    c1 = _cut_after_sources(w.circuit, ap)
+    c2 = _cut_after_sources(w.circuit, ap + ar)
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    b = fs.Batch(split="fixed", c1=c1, c2=c2)
+    b.add(C, w.outputs, eps)
+    b.plan()
+    assert "QUEUE = true" in b.generated_source()
+    b.allocate()
+    b.upload()
+    b.run()
+    st = b.finish()[0]
+    assert (st["A_p"], st["A_r"], st["A_s"]) == (ap, ar, 20 - ap - ar)
+    amp = b.amp.cpu().numpy()[:len(w.outputs)]
+    want, cnt = feynman.run(w.circuit, w.inputs, w.outputs, eps=eps, c1=c1, c2=c2)
+    err = np.abs(amp - want)
+    assert np.all(err <= ATOL + RTOL * np.abs(want)), err.max()
+    assert st["completed"] == int(cnt["completed"].sum()) and st["valid"] == int(cnt["valid"].sum())
+    assert st["gate_visits"] < int(cnt["visits"].sum())
+    assert np.abs(want).max() > 1e-3
