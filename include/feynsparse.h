@@ -361,9 +361,11 @@ FS_API int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* coun
  * 2 suffix) of a planned job, as integer instructions on the register state
  * and FP64 instructions, from the job's program (control-mask words that are
  * not all zero, factor forms); index 3 is the work per completed leaf (chi
- * test, integer) and per valid leaf (accumulation, FP64).  Arrays of 4
- * doubles (host).  Used to state kernel throughput against the issue and
- * FP64 rooflines. */
+ * test, integer) and per valid leaf (accumulation, FP64).  For the
+ * straight-line engine the root's figure includes the item loop around it
+ * (24 integer instructions: indices, entry cache, sums) and the leaf figure
+ * the suffix loop's control (12).  Arrays of 4 doubles (host).  Used to
+ * state kernel throughput against the issue and FP64 rooflines. */
 FS_API int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, double* fp64_ops);
 
 /* Register width (32-bit words: 1, 2 or 4) of a planned job's state (the

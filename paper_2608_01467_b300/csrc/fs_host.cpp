@@ -1776,6 +1776,15 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
     // per completed leaf: the chi test (2W); per valid leaf: two FP64 adds
     int_ops[3] = 2.0 * j.W;
     fp64_ops[3] = 2.0;
+    if (b->opt.engine == 0) {
+        // loop control of the generated engine, read off its item and leaf
+        // loops: per item the pair / h_p / h_r indices, the entry-cache
+        // tests, the nonzero test and vote of the item's sum, the loop
+        // counter (24); per leaf the enumeration word's update and compare,
+        // the restart test, the counters and the vote of the valid add (12)
+        int_ops[1] += 24.0;
+        int_ops[3] += 12.0;
+    }
     return FS_OK;
 }
 

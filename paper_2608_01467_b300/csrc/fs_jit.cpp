@@ -902,12 +902,19 @@ std::string emit_cascade(const CascadeRun& r, int W)
 // power (sign flips and swaps on the integer pipe) and its constant A^n is
 // multiplied into *hoist, to be applied once per (output, input) pair.
 // First evaluation position from which factors may be deferred: 0 in exact
-// mode; with a threshold, the position after the last op that tests |beta|
+// mode; with a threshold, the position after the last op carrying a source
 // (no later test reads the running amplitude, so the remaining factors may
 // be reassociated).
+// Threshold jobs test |beta| after every op carrying a source: their
+// factors are multiplied literally up to the last such op, and their suffix
+// keeps a checkpoint per source.  (The exact bound's tests after source ops
+// read only the state, so bound jobs keep the deferred factors and the
+// region-at-a-time suffix.)
+bool tests_sources(const JitJobSpec& J) { return J.eps2 > 0.0; }
+
 int defer_from(const JitJobSpec& J)
 {
-    if (J.eps2 == 0.0) return 0;
+    if (!tests_sources(J)) return 0;
     int last = -1;
     for (int e = 0; e < J.G; ++e) {
         const Op& op = J.ops[e];
@@ -1254,7 +1261,7 @@ std::string bound_after(const JitJobSpec& J, int e, const std::string& visits_cu
 // per op, run the stacked suffix (a checkpoint after every source op).
 bool stacked_suffix(const JitJobSpec& J)
 {
-    if (J.eps2 == 0.0 || J.As < 2) return false;
+    if (!tests_sources(J) || J.As < 2) return false;
     int n = 0;
     for (int e = J.c2; e < J.G; ++e) {
         const Op& op = J.ops[e];
