@@ -265,6 +265,36 @@ void jit_release(void* handle);
 
 // Sets the thread-local message read by fs_last_error and returns code.
 int set_error(int code, const char* msg);
+
+// Programmatic dependent launch.  The kernels of a run are launched so that
+// each may be scheduled while the previous kernel on the stream finishes
+// (its launch and block setup overlap the previous kernel's last blocks);
+// every such kernel first waits for the previous grid to complete and its
+// memory to be visible (griddepcontrol.wait) and then lets the next kernel
+// be scheduled (griddepcontrol.launch_dependents).  FS_NO_PDL=1 in the
+// environment launches them plainly.
+#define FS_GRID_DEP() asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
+bool pdl_enabled();
+// cudaLaunchKernelExC with the programmatic-serialization attribute (when
+// enabled); args as for cudaLaunchKernel.
+cudaError_t launch_ex(const void* func, dim3 grid, dim3 block, size_t smem, cudaStream_t s, void** args);
+#ifdef __CUDACC__
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+#endif
 cudaError_t probe_peaks(double* dfma_per_s, double* int_ops_per_s, int* sms);
 
 }  // namespace fs

@@ -49,6 +49,9 @@ struct Entry { u32 st[4]; double2 amp; };
 R"PRE(
 #define TILE_LOG2 8
 #define TILE 256
+// programmatic dependent launch: wait for the previous grid, then let the
+// next one be scheduled
+#define FS_GRID_DEP() asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
@@ -1373,6 +1376,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
     // while the current tile runs
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_history(const JobDev* __restrict__ jobs, "
            "const uint2* __restrict__ tiles, u64 n_tiles, unsigned int* counter)\n{\n"
+           "    FS_GRID_DEP();\n"
            "    const int lane = threadIdx.x & 31;\n    unsigned int t = 0u, next = 0u;\n"
            "    if (lane == 0) t = atomicAdd(counter, 1u);\n    t = __shfl_sync(0xffffffffu, t, 0);\n"
            "    while ((u64)t < n_tiles) {\n"
@@ -1383,6 +1387,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
                std::to_string(j) + "], td.y); break;\n";
     src += "        default: break;\n        }\n        t = __shfl_sync(0xffffffffu, next, 0);\n    }\n}\n";
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job)\n{\n"
+           "    FS_GRID_DEP();\n"
            "    const JobDev& J = jobs[job];\n    const int lane = threadIdx.x & 31;\n"
            "    u64 completed = 0, valid = 0, visits = 0;\n    switch (job) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
@@ -1397,6 +1402,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
     for (const JitJobSpec& J : jobs) any_queue |= queue_last_source(J) >= 0;
     if (any_queue) {
         src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_walk(const JobDev* __restrict__ jobs, int job)\n{\n"
+               "    FS_GRID_DEP();\n"
                "    extern __shared__ __align__(16) unsigned char walk_smem[];\n"
                "    const JobDev& J = jobs[job];\n    const int lane = threadIdx.x & 31;\n"
                "    u64 completed = 0, valid = 0, visits = 0;\n    switch (job) {\n";
@@ -1415,6 +1421,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_lv_" + js +
                "(const JobDev* __restrict__ jobs, int level, int a_prev, int a_next, const Entry* __restrict__ src, "
                "Entry* __restrict__ dst, u64 n, int last)\n{\n"
+               "    FS_GRID_DEP();\n"
                "    const JobDev& J = jobs[" + js + "];\n    u64 visits = 0, entries = 0, bcuts = 0;\n"
                "    for (u64 base = (u64)blockIdx.x * blockDim.x; base < n; base += (u64)gridDim.x * blockDim.x) {\n"
                "        const u64 idx = base + threadIdx.x;\n"
@@ -1443,6 +1450,7 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
     for (const JitJobSpec& J : jobs) any_count |= J.bound && J.bound_counts && J.levels.empty();
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_prefix(const JobDev* __restrict__ jobs, "
            "const u64* __restrict__ begin, int n_jobs, u64 total)\n{\n"
+           "    FS_GRID_DEP();\n"
            "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (u64)gridDim.x * blockDim.x) {\n"
            "        if (!__any_sync(0xffffffffu, idx < total)) break;\n"
            "        u64 visits = 0, entries = 0, bcuts = 0, local = 0;\n        int j = 0;\n"
@@ -1614,7 +1622,7 @@ cudaError_t jit_launch_history(void* handle, const JobDev* d_jobs, const uint2* 
     int grid = m->grid;
     if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
     void* args[] = {(void*)&d_jobs, (void*)&d_tiles, (void*)&n_tiles, (void*)&d_counter};
-    return cudaLaunchKernel((const void*)m->kernel, dim3(grid), dim3(TILE), args, 0, s);
+    return launch_ex((const void*)m->kernel, dim3(grid), dim3(TILE), 0, s, args);
 }
 
 cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
@@ -1625,7 +1633,7 @@ cudaError_t jit_launch_prefix(void* handle, const JobDev* d_jobs, const uint64_t
     uint64_t blocks = (total + 255) / 256;
     if (blocks > (uint64_t)m->sms * 64) blocks = (uint64_t)m->sms * 64;
     void* args[] = {(void*)&d_jobs, (void*)&d_begin, (void*)&n_jobs, (void*)&total};
-    return cudaLaunchKernel((const void*)m->prefix, dim3((unsigned)blocks), dim3(256), args, 0, s);
+    return launch_ex((const void*)m->prefix, dim3((unsigned)blocks), dim3(256), 0, s, args);
 }
 
 cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job, int level, const PrefixLevel& L,
@@ -1639,7 +1647,7 @@ cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job,
     int a_prev = L.a_prev, a_next = L.a_next, lst = last ? 1 : 0;
     void* args[] = {(void*)&d_jobs, (void*)&level, (void*)&a_prev, (void*)&a_next, (void*)&src, (void*)&dst,
                     (void*)&n_dst, (void*)&lst};
-    return cudaLaunchKernel((const void*)m->lv[job], dim3((unsigned)blocks), dim3(TILE), args, 0, s);
+    return launch_ex((const void*)m->lv[job], dim3((unsigned)blocks), dim3(TILE), 0, s, args);
 }
 
 cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s)
@@ -1647,9 +1655,9 @@ cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cuda
     JitModule* m = (JitModule*)handle;
     void* args[] = {(void*)&d_jobs, (void*)&job};
     if (job >= 0 && job < (int)m->walk_warps.size() && m->walk_warps[job])
-        return cudaLaunchKernel((const void*)m->walk, dim3(m->walk_grid[job]), dim3(32 * m->walk_warps[job]), args,
-                                m->walk_smem[job], s);
-    return cudaLaunchKernel((const void*)m->compact, dim3(m->compact_grid), dim3(TILE), args, 0, s);
+        return launch_ex((const void*)m->walk, dim3(m->walk_grid[job]), dim3(32 * m->walk_warps[job]),
+                         m->walk_smem[job], s, args);
+    return launch_ex((const void*)m->compact, dim3(m->compact_grid), dim3(TILE), 0, s, args);
 }
 
 void jit_release(void* handle)

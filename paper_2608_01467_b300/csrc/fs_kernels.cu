@@ -17,6 +17,7 @@
 // explicit round-to-nearest intrinsics, so every history's amplitude is the
 // same double the host-side definition gives when it multiplies the same
 // factors in the same (backward) order.
+#include <cstdlib>
 #include "fs_internal.h"
 
 namespace fs {
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(256) prefix_kernel(const JobDev* __restrict__ 
                                                      const uint64_t* __restrict__ begin, int n_jobs,
                                                      uint64_t total, uint32_t* err)
 {
+    FS_GRID_DEP();
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (uint64_t)gridDim.x * blockDim.x) {
         const bool any = __any_sync(0xffffffffu, idx < total);
         if (!any) break;
@@ -433,6 +435,7 @@ __global__ void __launch_bounds__(256) prefix_level_kernel(const JobDev* __restr
                                                            const Entry* __restrict__ src, Entry* __restrict__ dst,
                                                            uint64_t n, int last, uint32_t* err)
 {
+    FS_GRID_DEP();
     const JobDev& J = *jobp;
     unsigned long long visits = 0, entries = 0;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (uint64_t)gridDim.x * blockDim.x) {
@@ -573,6 +576,7 @@ __global__ void __launch_bounds__(TILE) history_kernel(const JobDev* __restrict_
                                                        const uint2* __restrict__ tiles, uint64_t n_tiles,
                                                        unsigned int* counter, uint32_t* err)
 {
+    FS_GRID_DEP();
     const int lane = threadIdx.x & 31;
     unsigned int t = 0u, next = 0u;
     if (lane == 0) t = atomicAdd(counter, 1u);
@@ -599,6 +603,7 @@ __device__ __forceinline__ bool entry_live(const JobDev& J, uint64_t e)
 
 __global__ void __launch_bounds__(256) compact_count_kernel(const JobDev* __restrict__ jobp)
 {
+    FS_GRID_DEP();
     const JobDev& J = *jobp;
     const uint64_t base = (uint64_t)blockIdx.x * COMPACT_BLOCK;
     unsigned c = 0;
@@ -620,6 +625,7 @@ __global__ void __launch_bounds__(256) compact_count_kernel(const JobDev* __rest
 
 __global__ void __launch_bounds__(1024) compact_scan_kernel(const JobDev* __restrict__ jobp, uint32_t nblk)
 {
+    FS_GRID_DEP();
     const JobDev& J = *jobp;
     __shared__ unsigned long long s_carry;
     __shared__ unsigned s_w[32];
@@ -656,6 +662,7 @@ __global__ void __launch_bounds__(1024) compact_scan_kernel(const JobDev* __rest
 
 __global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __restrict__ jobp)
 {
+    FS_GRID_DEP();
     const JobDev& J = *jobp;
     const uint64_t base = (uint64_t)blockIdx.x * COMPACT_BLOCK;
     bool lv[4];
@@ -759,6 +766,7 @@ __device__ __forceinline__ void store_esum(const JobDev& J, uint64_t i, double2 
 
 __global__ void __launch_bounds__(256) history_compact_kernel(const JobDev* __restrict__ jobp, uint32_t* err)
 {
+    FS_GRID_DEP();
     const JobDev& J = *jobp;
     const uint64_t n_items = J.stats[6] << J.Ar;
     const int lane = threadIdx.x & 31;
@@ -876,6 +884,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
                                                                 int n_jobs, uint64_t total, double2* amp_out,
                                                                 unsigned int* big_count, uint64_t* big_list)
 {
+    FS_GRID_DEP();
     constexpr int OPW = 32 / RED_LPO;
     const int lane = threadIdx.x & 31, sub = lane & (RED_LPO - 1), slot = lane / RED_LPO;
     const uint64_t warp = ((uint64_t)blockIdx.x * REDUCE_THREADS + threadIdx.x) >> 5;
@@ -978,6 +987,7 @@ __global__ void __launch_bounds__(RED_BIG_THREADS) reduce_big_kernel(const JobDe
                                                                      const uint64_t* __restrict__ big_list,
                                                                      double2* amp_out)
 {
+    FS_GRID_DEP();
     __shared__ double2 s_w[RED_BIG_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned int count = *big_count;
@@ -1041,6 +1051,7 @@ __global__ void __launch_bounds__(RED_BIG_THREADS) reduce_big_kernel(const JobDe
 __global__ void __launch_bounds__(256) bound_prune_kernel(const JobDev* __restrict__ jobs, int job, BoundSpec sp,
                                                           unsigned long long n, int count_blocks)
 {
+    FS_GRID_DEP();
     const JobDev& J = jobs[job];
     unsigned long long cuts = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -1161,14 +1172,37 @@ cudaError_t probe_peaks(double* dfma_per_s, double* int_ops_per_s, int* sms)
     return e;
 }
 
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char* v = getenv("FS_NO_PDL");
+        return !(v && v[0] == '1');
+    }();
+    return on;
+}
+
+cudaError_t launch_ex(const void* func, dim3 grid, dim3 block, size_t smem, cudaStream_t s, void** args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, func, args);
+}
+
 cudaError_t launch_prefix(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
                           uint64_t total, uint32_t* d_err, cudaStream_t s)
 {
     if (total == 0) return cudaSuccess;
     uint64_t blocks = (total + 255) / 256;
     if (blocks > 148ull * 64) blocks = 148ull * 64;
-    prefix_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_begin, n_jobs, total, d_err);
-    return cudaGetLastError();
+    return launch_pdl(prefix_kernel, dim3((unsigned)blocks), dim3(256), 0, s, d_jobs, d_begin, n_jobs, total, d_err);
 }
 
 int history_grid_size(int device)
@@ -1186,8 +1220,7 @@ cudaError_t launch_history(const JobDev* d_jobs, const uint2* d_tiles, uint64_t 
 {
     if (n_tiles == 0) return cudaSuccess;
     if ((uint64_t)grid > n_tiles) grid = (int)n_tiles;
-    history_kernel<<<grid, TILE, 0, s>>>(d_jobs, d_tiles, n_tiles, d_counter, d_err);
-    return cudaGetLastError();
+    return launch_pdl(history_kernel, dim3(grid), dim3(TILE), 0, s, d_jobs, d_tiles, n_tiles, d_counter, d_err);
 }
 
 cudaError_t launch_prefix_level(const JobDev* d_job, const PrefixLevel& L, const Entry* src, Entry* dst,
@@ -1196,18 +1229,19 @@ cudaError_t launch_prefix_level(const JobDev* d_job, const PrefixLevel& L, const
     if (n_dst == 0) return cudaSuccess;
     uint64_t blocks = (n_dst + 255) / 256;
     if (blocks > 148ull * 64) blocks = 148ull * 64;
-    prefix_level_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_job, L, src, dst, n_dst, last ? 1 : 0, d_err);
-    return cudaGetLastError();
+    return launch_pdl(prefix_level_kernel, dim3((unsigned)blocks), dim3(256), 0, s, d_job, L, src, dst, n_dst,
+                      last ? 1 : 0, d_err);
 }
 
 cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, bool counted, cudaStream_t s)
 {
     const uint64_t nblk = (n_entries + COMPACT_BLOCK - 1) / COMPACT_BLOCK;
     if (nblk == 0) return cudaSuccess;
-    if (!counted) compact_count_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
-    compact_scan_kernel<<<1, 1024, 0, s>>>(d_job, (uint32_t)nblk);
-    compact_write_kernel<<<(unsigned)nblk, 256, 0, s>>>(d_job);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (!counted) e = launch_pdl(compact_count_kernel, dim3((unsigned)nblk), dim3(256), 0, s, d_job);
+    if (e == cudaSuccess) e = launch_pdl(compact_scan_kernel, dim3(1), dim3(1024), 0, s, d_job, (uint32_t)nblk);
+    if (e == cudaSuccess) e = launch_pdl(compact_write_kernel, dim3((unsigned)nblk), dim3(256), 0, s, d_job);
+    return e;
 }
 
 int compact_grid_size(int device)
@@ -1220,8 +1254,7 @@ int compact_grid_size(int device)
 
 cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s)
 {
-    history_compact_kernel<<<grid, 256, 0, s>>>(d_job, d_err);
-    return cudaGetLastError();
+    return launch_pdl(history_compact_kernel, dim3(grid), dim3(256), 0, s, d_job, d_err);
 }
 
 cudaError_t launch_bound_prune(const JobDev* d_jobs, int job, const BoundSpec& sp, unsigned long long n_entries,
@@ -1230,8 +1263,8 @@ cudaError_t launch_bound_prune(const JobDev* d_jobs, int job, const BoundSpec& s
     if (n_entries == 0) return cudaSuccess;
     unsigned long long blocks = (n_entries + 255) / 256;
     if (blocks > 148ull * 16) blocks = 148ull * 16;
-    bound_prune_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, job, sp, n_entries, count_blocks ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(bound_prune_kernel, dim3((unsigned)blocks), dim3(256), 0, s, d_jobs, job, sp, n_entries,
+                      count_blocks ? 1 : 0);
 }
 
 cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_jobs,
@@ -1242,14 +1275,12 @@ cudaError_t launch_reduce(const JobDev* d_jobs, const uint64_t* d_begin, int n_j
     const uint64_t per_block = (REDUCE_THREADS / 32) * (32 / RED_LPO);   // outputs per block pass
     uint64_t blocks = (total_out + per_block - 1) / per_block;
     if (blocks > 148ull * 16) blocks = 148ull * 16;
-    reduce_kernel<<<(unsigned)blocks, REDUCE_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, total_out, d_amp,
-                                                              d_big_count, d_big_list);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(reduce_kernel, dim3((unsigned)blocks), dim3(REDUCE_THREADS), 0, s, d_jobs, d_begin,
+                               n_jobs, total_out, d_amp, d_big_count, d_big_list);
     if (e != cudaSuccess || !big_possible) return e;
     const uint64_t big_blocks = total_out < 148ull * 4 ? total_out : 148ull * 4;
-    reduce_big_kernel<<<(unsigned)big_blocks, RED_BIG_THREADS, 0, s>>>(d_jobs, d_begin, n_jobs, d_big_count,
-                                                                       d_big_list, d_amp);
-    return cudaGetLastError();
+    return launch_pdl(reduce_big_kernel, dim3((unsigned)big_blocks), dim3(RED_BIG_THREADS), 0, s, d_jobs, d_begin,
+                      n_jobs, (const unsigned int*)d_big_count, (const uint64_t*)d_big_list, d_amp);
 }
 
 }  // namespace fs

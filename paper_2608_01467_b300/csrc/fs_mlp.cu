@@ -640,6 +640,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                   const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err,
                   uint32_t wait_limit, int from_live)
 {
+    FS_GRID_DEP();
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, grp = tid >> 7, r = tid & 127, warp = tid >> 5;
     const JobDev* J = PRUNE ? &jobs[job] : nullptr;
@@ -884,9 +885,8 @@ cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y
     const unsigned long long tiles = (rows + 127) / 128;
     unsigned long long blocks = (tiles + 1) / 2;
     if (blocks > 148 * 2) blocks = 148 * 2;
-    mlp_tc_kernel<PRUNE><<<(unsigned)blocks, TC_THREADS, TC_SMEM, s>>>(P, X, n_rows, Y, jobs, job, sp, tau, err,
-                                                                       g_wait_limit, from_live);
-    return cudaGetLastError();
+    return launch_pdl(mlp_tc_kernel<PRUNE>, dim3((unsigned)blocks), dim3(TC_THREADS), TC_SMEM, s, P, X, n_rows, Y,
+                      jobs, job, sp, tau, err, g_wait_limit, from_live);
 }
 
 
