@@ -284,8 +284,10 @@ FS_API int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* strea
  * expansion (checkpoint table), persistent history kernel over the atomic
  * tile queue, fixed-order reduction into d_amp_out (device, 2 * total
  * outputs doubles).  Asynchronous and free of host synchronisation, so it
- * can be captured into a CUDA graph.  Requires fs_batch_upload on the same
- * workspace first. */
+ * can be captured into a CUDA graph.  Its kernels are launched with
+ * programmatic dependent launch (each waits for the previous grid before
+ * touching memory); FS_NO_PDL=1 in the environment launches them plainly.
+ * Requires fs_batch_upload on the same workspace first. */
 FS_API int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream);
 
 /* Waits for stream, reads the device error word and the per-job counters
