@@ -606,12 +606,16 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
         work["prefix"][0] += iw[0] * entries
         work["prefix"][1] += fw[0] * entries
         root_runs = s0["live_entries"] << s0["A_r"]
-        if w.eps > 0.0:
-            # threshold jobs stop at every cut: the suffix work follows the
-            # gate visits (each visited op at the suffix region's mean cost)
-            G_s = max(1, len(w.circuit.gates) - s0["c2"])
-            work["history"][0] += iw[2] / G_s * s0["gate_visits"] + iw[3] * s0["completed"]
-            work["history"][1] += fw[2] / G_s * s0["gate_visits"] + fw[3] * s0["valid"]
+        if w.eps > 0.0 or s0["bound_cuts"] > 0:
+            # jobs whose histories stop at cuts inside the root and suffix
+            # (threshold, exact bound): the work follows the history stage's
+            # gate visits, each visited op at the root and suffix's mean cost,
+            # plus the item loop (24) per root execution
+            G_rs = max(1, len(w.circuit.gates) - s0["c1"])
+            loop = 24.0 if b.engine == "straight" else 0.0
+            work["history"][0] += ((iw[1] - loop + iw[2]) / G_rs * s0["history_visits"] + loop * root_runs +
+                                   iw[3] * s0["completed"])
+            work["history"][1] += (fw[1] + fw[2]) / G_rs * s0["history_visits"] + fw[3] * s0["valid"]
         else:
             work["history"][0] += iw[1] * root_runs + iw[2] * s0["completed"] + iw[3] * s0["completed"]
             work["history"][1] += fw[1] * root_runs + fw[2] * s0["completed"] + fw[3] * s0["valid"]
