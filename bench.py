@@ -612,7 +612,7 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
             # gate visits, each visited op at the root and suffix's mean cost,
             # plus the item loop (24) per root execution
             G_rs = max(1, len(w.circuit.gates) - s0["c1"])
-            loop = 24.0 if b.engine == "straight" else 0.0
+            loop = 24.0 if b.engine_name == "straight" else 0.0
             work["history"][0] += ((iw[1] - loop + iw[2]) / G_rs * s0["history_visits"] + loop * root_runs +
                                    iw[3] * s0["completed"])
             work["history"][1] += (fw[1] + fw[2]) / G_rs * s0["history_visits"] + fw[3] * s0["valid"]

@@ -164,7 +164,7 @@ class Batch:
         opt.engine = {"straight": 0, "interp": 1}[engine]
         opt.prefix_mode = {"auto": 0, "single": 1, "levels": 2}[prefix]
         check(L.fs_batch_set_options(self._h, ctypes.byref(opt)))
-        self.engine = engine
+        self.engine_name = engine
         self.jobs = []
         self.ws = None
         self.amp = None
