@@ -602,7 +602,8 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
         s0 = stats[ji]
         pairs = len(w.outputs) * len(w.inputs)
         entries = pairs << s0["A_p"]
-        table_bytes += 32.0 * entries
+        if s0["c1"] > 0:   # (an empty prefix region keeps no table)
+            table_bytes += 32.0 * entries
         work["prefix"][0] += iw[0] * entries
         work["prefix"][1] += fw[0] * entries
         root_runs = s0["live_entries"] << s0["A_r"]
@@ -646,7 +647,7 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
                  "fp64_pipe_frac": fp64_frac}
     r.update({"kernel": dom, "traffic": None, "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}})
     tp = stage_ms.get("prefix", 0.0) / 1000.0
-    if tp > 0:
+    if tp > 0 and table_bytes > 0:
         hbm = peaks.get("hbm_gbs", 6497.4)
         r["table"] = {"bound": "hbm", "achieved": table_bytes / tp / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": table_bytes / tp / 1e9 / hbm, "bytes": table_bytes,
