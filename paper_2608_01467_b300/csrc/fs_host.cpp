@@ -1730,6 +1730,14 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
         case fs::OP_BR2: iops += 10; fops += 4; break;
         default: break;
         }
+        // with a threshold, |beta|^2 after every op carrying a source: a
+        // multiply and a fused multiply-add, an integer compare and branch
+        const bool src_op = (op.code == fs::OP_H || op.code == fs::OP_BR1 || op.code == fs::OP_BR2) &&
+                            (op.s0 >= 0 || (op.code == fs::OP_BR2 && op.s1 >= 0));
+        if (j.eps > 0.0 && src_op) {
+            iops += 2;
+            fops += 2;
+        }
     }
     for (const auto& c : classes) {
         const double2 A = c.first, B = c.second;
