@@ -1738,6 +1738,21 @@ static void region_work(const Job& j, int e0, int e1, double& iops, double& fops
             iops += 2;
             fops += 2;
         }
+        // the exact bound after a source op (straight-line engine): the
+        // frozen-qubit test (xor, and, or per word) and per cascade field
+        // its words (two funnel shifts and masks each for state and input)
+        // and both borrow chains (four ops per word each), two compares
+        if (fused && j.bound && src_op)
+            for (const auto& pb : j.src_bounds) {
+                if (pb.first != e) continue;
+                double c = 1;
+                for (int w = 0; w < 4; ++w) c += pb.second.frozen[w] ? 3 : 0;
+                for (int f = 0; f < pb.second.n_fields; ++f) {
+                    const int fw = (pb.second.len[f] + 31) / 32;
+                    c += 4.0 * fw + 8.0 * fw + 4.0;
+                }
+                iops += c;
+            }
     }
     for (const auto& c : classes) {
         const double2 A = c.first, B = c.second;
