@@ -175,6 +175,11 @@ __device__ __noinline__ double2 fs_add_ool(double2 a, double2 b)
     return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
 }
 
+// A logged item's sum times the job's constant, out of line: inlined, the
+// product would be if-converted into FP64 instructions that every item of a
+// run without logging issues with no lane active.
+__device__ __noinline__ void fs_log_ool(double2* dst, double2 scale, double2 v) { *dst = cmul(scale, v); }
+
 // acc += v in the lanes where keep holds.  Most leaves are invalid and most
 // items zero, so the adds run only when some active lane keeps its value.
 __device__ __forceinline__ void add_kept(double2& acc, double2 v, bool keep)
@@ -381,10 +386,7 @@ __device__ void tile_body(const JobDev& J, u64 tile)
 #pragma unroll 1
     for (int k = 0; k < kn; ++k) {
         const double2 v = item_sum<T>(J, pair, local, cache, completed, valid, visits);
-        if (J.log) {   // logging runs only: keep the product out of the common path
-            asm volatile("" ::: "memory");
-            J.log[first + (u64)k] = cmul(J.scale, v);
-        }
+        if (J.log) fs_log_ool(J.log + first + (u64)k, J.scale, v);   // logging runs only
         add_kept(acc, v, nonzero(v));
         ++local;
         if (lg < 3 && local == ((loc_t)1 << (lg < 3 ? lg : 0))) {

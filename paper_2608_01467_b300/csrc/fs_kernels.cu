@@ -110,6 +110,11 @@ __device__ __forceinline__ double2 group_sum(double2 acc, int seg)
     return acc;
 }
 
+// A logged item's sum times the job's constant, out of line: inlined, the
+// product would be if-converted into FP64 instructions that every item of a
+// run without logging issues with no lane active.
+__device__ __noinline__ void fs_log_ool(double2* dst, double2 scale, double2 v) { *dst = cmul(scale, v); }
+
 // The FP64 adds of add_kept, out of line: a call that no lane makes issues
 // none of the callee's instructions, where an inlined add would be
 // if-converted into FP64 instructions predicated off in every lane -- and
@@ -541,10 +546,7 @@ __device__ void history_tile(const JobDev& J, uint64_t tile, uint32_t* err)
         const uint64_t item = first + (uint64_t)k;
         if (item >= n_items) break;
         const double2 v = history_item<W>(J, item, err, completed, valid, visits);
-        if (J.log) {   // logging runs only: keep the product out of the common path
-            asm volatile("" ::: "memory");
-            J.log[item] = cmul(J.scale, v);
-        }
+        if (J.log) fs_log_ool(J.log + item, J.scale, v);   // logging runs only
         add_kept(acc, v, nonzero(v));
         if (lg < 3 && ((item + 1ull) & ((1ull << lg) - 1ull)) == 0ull) {
             J.partials[item >> lg] = acc;   // a pair of at most 4 items ends here
