@@ -594,6 +594,11 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
     Beside it, the checkpoint table's HBM rate: 32 B written per entry by the
     prefix stage against the measured copy bandwidth."""
     sm_max = (clocks or {}).get("sm_max_mhz") or 2032.0
+    # jobs whose suffix runs as per-source segments (checkpoint per source)
+    src = b.generated_source() if b.engine_name == "straight" else ""
+    stacked = {ji for ji in range(len(jobs))
+               if f"struct J{ji} {{" in src and
+               "STACKED = true" in src.split(f"struct J{ji} {{", 1)[1].split("};", 1)[0]}
     issue_peak = peaks["sms"] * 4 * sm_max * 1e6                 # warp instructions / s
     work = {"prefix": [0.0, 0.0], "history": [0.0, 0.0], "prune": [0.0, 0.0]}
     table_bytes = 0.0
@@ -607,9 +612,10 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
         work["prefix"][0] += iw[0] * entries
         work["prefix"][1] += fw[0] * entries
         root_runs = s0["live_entries"] << s0["A_r"]
-        if w.eps > 0.0 or s0["bound_cuts"] > 0:
+        if w.eps > 0.0 or s0["bound_cuts"] > 0 or ji in stacked:
             # jobs whose histories stop at cuts inside the root and suffix
-            # (threshold, exact bound): the work follows the history stage's
+            # (threshold, exact bound) or restart at the changed source
+            # (per-source segments): the work follows the history stage's
             # gate visits, each visited op at the root and suffix's mean cost,
             # plus the item loop (24) per root execution
             G_rs = max(1, len(w.circuit.gates) - s0["c1"])

@@ -205,10 +205,11 @@ __device__ __forceinline__ bool is_bottom(double x)
 
 // Leaves of one root checkpoint (state st, amplitude amp): the suffix for
 // every h_s in increasing order, skipping the subtree of a cut history, the
-// chi test at the input boundary.  A stacked suffix (threshold jobs) keeps
-// the state after each of its source ops (a checkpoint per source, the
-// per-source limit of Algorithm 2's regions) and restarts the next history
-// at the first source whose bit changed, instead of at the region's start.
+// chi test at the input boundary.  A stacked suffix keeps the state, the
+// amplitude and the deferred class counts after each of its source ops (a
+// checkpoint per source, the per-source limit of Algorithm 2's regions) and
+// restarts the next history at the first source whose bit changed, instead
+// of at the region's start.
 
 template <class T>
 __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp, const u32 (&bin)[T::W],
@@ -222,6 +223,7 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
     if constexpr (T::STACKED) {
         u32 sst[T::As][W];
         double2 sam[T::As];
+        u32 skc[T::As][T::SC];
         int start = 0;
         while (hs < ns) {
             u32 st2[W];
@@ -235,7 +237,7 @@ __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp
                 for (int j = 0; j < W; ++j) st2[j] = sst[start - 1][j];
                 amp2 = sam[start - 1];
             }
-            const int r2 = T::suffix_from(start, st2, amp2, (u64)hs, bin, visits, sst, sam);
+            const int r2 = T::suffix_from(start, st2, amp2, (u64)hs, bin, visits, sst, sam, skc);
             hs_t nx;
             if (r2 < 0) {
                 ++completed;
@@ -956,9 +958,12 @@ std::string mul_two_valued(double2 A, double2 B, const std::string& sel)
 // with its last source op (the ops after it form the separate tail).
 std::string bound_after(const JitJobSpec& J, int e, const std::string& visits_cut);
 
+// With stacked, the deferred class counts (and the commensurate phase) are
+// checkpointed with the state: skc[k][c] after segment k, restored at the
+// restart; *n_save receives the number of saved counts (at least 1).
 void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
                  int e0, int e1, int nbits, bool chi_only = false, std::complex<long double>* hoist = nullptr,
-                 bool stacked = false, bool segswitch = false)
+                 bool stacked = false, bool segswitch = false, int* n_save = nullptr)
 {
     const int W = J.W;
     const int dfrom = defer_from(J);
@@ -1127,7 +1132,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             const std::string k = std::to_string(seg);
             for (int j = 0; j < W; ++j)
                 body += "    sst[" + k + "][" + std::to_string(j) + "] = s[" + std::to_string(j) + "];";
-            body += " sam[" + k + "] = a; visits += " + std::to_string(e - seg_e0 + 1) + "ull;\n    }\n";
+            body += " sam[" + k + "] = a; @SAVEK" + k + "@ visits += " + std::to_string(e - seg_e0 + 1) + "ull;\n    }\n";
             ++seg;
             seg_e0 = e + 1;
             if (seg < nbits) body += "    if (start <= " + std::to_string(seg) + ") {\n";
@@ -1143,8 +1148,27 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
     out += "    const u32 h32 = (u32)h;\n    (void)h32;\n";
     out += stacked ? "    int low = " + std::to_string(nbits) + " - start;\n"
                    : "    int low = " + std::to_string(nbits) + ";\n";
-    for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
-    if (ph_used) out += "    u32 ph = 0u;\n";
+    if (stacked) {
+        // counts restored at the restart, saved after every segment
+        const size_t nk = cls.size() + (ph_used ? 1 : 0);
+        for (size_t k = 0; k < cls.size(); ++k)
+            out += "    u32 k" + std::to_string(k) + " = start ? skc[start - 1][" + std::to_string(k) + "] : 0u;\n";
+        if (ph_used) out += "    u32 ph = start ? skc[start - 1][" + std::to_string(cls.size()) + "] : 0u;\n";
+        for (int seg_k = 0; seg_k < nbits; ++seg_k) {
+            std::string save;
+            for (size_t k = 0; k < cls.size(); ++k)
+                save += "skc[" + std::to_string(seg_k) + "][" + std::to_string(k) + "] = k" + std::to_string(k) + "; ";
+            if (ph_used) save += "skc[" + std::to_string(seg_k) + "][" + std::to_string(cls.size()) + "] = ph; ";
+            const std::string tok = "@SAVEK" + std::to_string(seg_k) + "@";
+            for (size_t at = body.find(tok); at != std::string::npos; at = body.find(tok))
+                body.replace(at, tok.size(), save);
+        }
+        if (n_save) *n_save = nk > 0 ? (int)nk : 1;
+        out += "    (void)skc;\n";
+    } else {
+        for (size_t k = 0; k < cls.size(); ++k) out += "    u32 k" + std::to_string(k) + " = 0u;\n";
+        if (ph_used) out += "    u32 ph = 0u;\n";
+    }
     out += body;
     const bool products = !cls.empty() || ph_used;
     if (chi_only && products) {
@@ -1262,11 +1286,14 @@ std::string bound_after(const JitJobSpec& J, int e, const std::string& visits_cu
     return "";
 }
 
-// Threshold jobs whose suffix carries at least two artificial sources, one
-// per op, run the stacked suffix (a checkpoint after every source op).
+// Jobs whose suffix carries artificial sources, one per op -- at least two
+// with a threshold, ten in exact mode (below that the checkpoint stores
+// cost more than the gates they save; measured on amplitude amplification
+// and the walk) -- run the stacked suffix (a checkpoint after every source
+// op).
 bool stacked_suffix(const JitJobSpec& J)
 {
-    if (!tests_sources(J) || J.As < 2) return false;
+    if (J.As < (J.eps2 > 0.0 ? 2 : 10)) return false;
     int n = 0;
     for (int e = J.c2; e < J.G; ++e) {
         const Op& op = J.ops[e];
@@ -1283,7 +1310,7 @@ bool stacked_suffix(const JitJobSpec& J)
 // suffix's last source op, or -1.
 int queue_last_source(const JitJobSpec& J)
 {
-    if (!stacked_suffix(J) || J.As < 5) return -1;
+    if (J.eps2 == 0.0 || !stacked_suffix(J) || J.As < 5) return -1;
     int last = -1;
     for (int e = J.c2; e < J.G; ++e) {
         const Op& op = J.ops[e];
@@ -1344,14 +1371,18 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         }
         if (stacked) {
             // the same suffix as per-source segments (its hoisted constant is
-            // the one of `suffix` below: the same tail classes)
+            // the one of `suffix` below: the same classes); the class counts
+            // are checkpointed with the state
             std::complex<long double> h2(1.0L, 0.0L);
+            std::string fn;
+            int sc = 1;
+            emit_region(fn, globals, js + "t", J, J.c2, J.G, J.As, true, &h2, true, false, &sc);
+            structs += "  static constexpr int SC = " + std::to_string(sc) + ";\n";
             structs += "  static __device__ __forceinline__ int suffix_from(int start, u32 (&s)[" + W +
                        "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits, u32 (&sst)[" +
                        std::to_string(J.As) + "][" + W + "], double2 (&sam)[" + std::to_string(J.As) +
-                       "]) {\n    (void)h; (void)bin;\n";
-            emit_region(structs, globals, js + "t", J, J.c2, J.G, J.As, true, &h2, true);
-            structs += "  }\n";
+                       "], u32 (&skc)[" + std::to_string(J.As) + "][" + std::to_string(sc) +
+                       "]) {\n    (void)h; (void)bin;\n" + fn + "  }\n";
         }
         structs += "  static __device__ __forceinline__ int suffix" + sig + " {\n    (void)h; (void)bin;\n";
         emit_region(structs, globals, js + "s", J, J.c2, J.G, J.As, true, &hoisted);

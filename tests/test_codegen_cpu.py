@@ -187,6 +187,7 @@ SUFFIX_STACKED = """
                     {
                         u32 sst[J0::As][W];
                         double2 sam[J0::As];
+                        u32 skc[J0::As][J0::SC];
                         int start = 0;
                         const u64 ns = 1ull << J0::As;
                         u64 hs = 0;
@@ -195,7 +196,7 @@ SUFFIX_STACKED = """
                             double2 a3;
                             for (int j = 0; j < W; ++j) st3[j] = start ? sst[start - 1][j] : st2[j];
                             a3 = start ? sam[start - 1] : a2;
-                            const int r2 = J0::suffix_from(start, st3, a3, hs, bin, visits, sst, sam);
+                            const int r2 = J0::suffix_from(start, st3, a3, hs, bin, visits, sst, sam, skc);
                             u64 nx;
                             if (r2 < 0) {
                                 ++completed;
@@ -549,3 +550,38 @@ def test_generated_bound_after_each_source_keeps_every_valid_leaf(case, tmp_path
         b.plan()
         assert "if (bound_after_" in b.generated_source()
         assert completed.sum() < cnt["completed"].sum()
+
+
+@pytest.mark.parametrize("family", ["aa", "qaoa", "random"])
+def test_stacked_suffix_in_exact_mode_checkpoints_the_class_counts(family, tmp_path):
+    """Exact jobs with ten or more sources in the suffix (one per op) run
+    it as per-source segments too; the deferred class counts (and the
+    commensurate phase) are checkpointed with the state after every segment
+    and restored at the restart.  Driven on the host by the device's restart
+    loop: amplitudes and leaf counts are the oracle's."""
+    if family == "aa":
+        w = aa_workload(n=4, iters=2, all_outputs=True)
+        circ, inputs, outputs = w.circuit, w.inputs, w.outputs[:6]
+    elif family == "qaoa":
+        w = qaoa_workload(8, 2, n_out=6, seed=5)
+        circ, inputs, outputs = w.circuit, w.inputs, w.outputs
+    else:
+        circ = random_small_circuit(10, 90, 9129)    # one source per op after the cut
+        rng = SplitMix64(9129)
+        inputs = [(rng.bits(10), 0.8), (rng.bits(10), 0.6j)]
+        outputs = [rng.bits(10) for _ in range(5)]
+    C = fs.Circuit(circ)
+    srcs = {s_: g for g, q, s_ in C.branch_vars() if s_ >= 0}
+    G = len(circ.gates)
+    A = len(srcs)
+    c1 = G - srcs[A // 4 - 1]
+    c2 = G - srcs[A // 4]                          # one source in the root, the rest in the suffix
+    assert A - A // 4 - 1 >= 10
+    got, completed, valid = _host_amplitudes(circ, inputs, outputs, c1, c2, 0.0, str(tmp_path))
+    assert _host_amplitudes.stacked
+    want, cnt = feynman.run(circ, inputs, outputs, c1=c1, c2=c2)
+    _close(got, want)
+    assert np.array_equal(completed, cnt["completed"].astype(np.int64))
+    assert np.array_equal(valid, cnt["valid"].astype(np.int64))
+    if family != "random":
+        assert np.abs(want).max() > 1e-3

@@ -148,10 +148,14 @@ def test_aa_fig8_ablation_rows_agree():
         close(a, want)
         assert st[0]["valid"] == 10 * (1 << 24)
         res[name] = st[0]
-    # gate visits follow Eq. 8 at the chosen cuts
+    # gate visits follow Eq. 8 at the chosen cuts, or fewer where the
+    # suffix runs as per-source segments (the interpreter follows Eq. 8)
     for name, st in res.items():
         (_, cost) = feynman.region_counts(w.circuit, st["c1"], st["c2"])
-        assert st["gate_visits"] == 10 * cost
+        assert st["gate_visits"] <= 10 * cost
+    (_,), st_i, _ = run_batch([(w.circuit, w.inputs, outs, 0.0)], split="fixed", c1=res["auto"]["c1"],
+                              c2=res["auto"]["c2"], prefix="single", engine="interp")
+    assert st_i[0]["gate_visits"] == 10 * feynman.region_counts(w.circuit, res["auto"]["c1"], res["auto"]["c2"])[1]
 
 
 def test_aa12x1_config_all_outputs_vs_dense():
@@ -174,7 +178,7 @@ def test_qaoa8_exact_vs_dense_and_oracle_counts():
     close(a, dense.amplitudes(w.circuit, w.inputs, w.outputs))
     assert st[0]["completed"] == 64 * (1 << 16) == st[0]["valid"]
     cost = feynman.region_counts(w.circuit, st[0]["c1"], st[0]["c2"])[1]
-    assert st[0]["gate_visits"] == 64 * cost
+    assert st[0]["gate_visits"] <= 64 * cost      # Eq. 8, or fewer with per-source segments
 
 
 def test_qaoa16_full_size_sampled_outputs():
@@ -349,8 +353,9 @@ def test_incrementer_cascades_match_oracle(n, f0, L, common, inc, msb):
     close(a1[0], o)
     close(a2[0], o)
     assert np.abs(o).max() > 0.1
-    for k in ("completed", "valid", "gate_visits"):
+    for k in ("completed", "valid"):
         assert s1[0][k] == s2[0][k], k
+    assert s1[0]["gate_visits"] <= s2[0]["gate_visits"]
     assert s1[0]["valid"] == int(cnt["valid"].sum())
 
 
@@ -458,12 +463,9 @@ def test_engines_bitwise_equal(case):
     for x, y in zip(s1, s2):
         for k in ("completed", "valid", "table_entries"):
             assert x[k] == y[k], k
-        # a threshold job's stacked suffix restarts at the changed source
-        # instead of the region start: it evaluates fewer gates
-        if jobs[0][3] > 0:
-            assert x["gate_visits"] <= y["gate_visits"]
-        else:
-            assert x["gate_visits"] == y["gate_visits"]
+        # a stacked suffix (per-source segments) restarts at the changed
+        # source instead of the region start: it evaluates no more gates
+        assert x["gate_visits"] <= y["gate_visits"]
     o, _ = oracle_counts(*jobs[0][:3], eps=jobs[0][3])
     close(a1[0], o)
 
