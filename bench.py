@@ -612,10 +612,16 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
         work["prefix"][0] += iw[0] * entries
         work["prefix"][1] += fw[0] * entries
         root_runs = s0["live_entries"] << s0["A_r"]
-        if w.eps > 0.0 or s0["bound_cuts"] > 0 or ji in stacked:
+        if ji in stacked and w.eps == 0.0 and s0["bound_cuts"] == 0:
+            # exact per-source segments: every root runs whole; the suffix's
+            # work follows its gate visits (the history visits less the roots')
+            G_r, G_s = s0["c2"] - s0["c1"], max(1, len(w.circuit.gates) - s0["c2"])
+            suffix_visits = max(0, s0["history_visits"] - root_runs * G_r)
+            work["history"][0] += iw[1] * root_runs + iw[2] / G_s * suffix_visits + iw[3] * s0["completed"]
+            work["history"][1] += fw[1] * root_runs + fw[2] / G_s * suffix_visits + fw[3] * s0["valid"]
+        elif w.eps > 0.0 or s0["bound_cuts"] > 0:
             # jobs whose histories stop at cuts inside the root and suffix
-            # (threshold, exact bound) or restart at the changed source
-            # (per-source segments): the work follows the history stage's
+            # (threshold, exact bound): the work follows the history stage's
             # gate visits, each visited op at the root and suffix's mean cost,
             # plus the item loop (24) per root execution
             G_rs = max(1, len(w.circuit.gates) - s0["c1"])

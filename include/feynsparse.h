@@ -366,7 +366,9 @@ FS_API int fs_batch_op_histogram(const fs_batch* b, uint32_t job, uint32_t* coun
  * test, integer) and per valid leaf (accumulation, FP64).  For the
  * straight-line engine the root's figure includes the item loop around it
  * (24 integer instructions: indices, entry cache, sums) and the leaf figure
- * the suffix loop's control (12).  Arrays of 4 doubles (host).  Used to
+ * the suffix loop's control (12); where the engine counts a unit-phase
+ * suffix's valid leaves by phase, a valid leaf costs 4 integer instructions
+ * and no FP64, a root one product.  Arrays of 4 doubles (host).  Used to
  * state kernel throughput against the issue and FP64 rooflines. */
 FS_API int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, double* fp64_ops);
 

@@ -1807,6 +1807,13 @@ int fs_batch_region_work(const fs_batch* b, uint32_t job, double* int_ops, doubl
         // the restart test, the counters and the vote of the valid add (12)
         int_ops[1] += 24.0;
         int_ops[3] += 12.0;
+        // the phase census: per valid leaf four compares and adds instead
+        // of the FP64 adds; per root one product (2 conversions, 4 FP64)
+        if (fs::jit_census(jit_specs(b)[job])) {
+            int_ops[3] += 4.0;
+            fp64_ops[3] = 0.0;
+            fp64_ops[1] += 6.0;
+        }
     }
     return FS_OK;
 }

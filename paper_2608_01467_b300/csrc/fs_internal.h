@@ -250,6 +250,9 @@ struct JitJobSpec {
     // after it)
     std::vector<std::pair<int, BoundSpec>> src_bounds;
 };
+// Whether the generated engine counts this job's valid leaves by phase (an
+// exact suffix whose factors are all unit phases): no FP64 add per leaf.
+bool jit_census(const JitJobSpec& J);
 // The generated source for these jobs (what jit_build compiles), without
 // compiling it.
 std::string jit_source(const std::vector<JitJobSpec>& jobs);

@@ -211,12 +211,91 @@ __device__ __forceinline__ bool is_bottom(double x)
 // restarts the next history at the first source whose bit changed, instead
 // of at the region's start.
 
+// amp * (re + i im), out of line (a call no lane makes issues none of its
+// FP64 instructions)
+__device__ __noinline__ double2 fs_census_ool(double2 amp, int re, int im)
+{
+    return cmul(amp, make_double2((double)re, (double)im));
+}
+
+// Phase census (exact suffixes whose factors are all unit phases): every
+// valid leaf's amplitude is amp * i^q, so the leaves are counted by q and
+// the root's sum is amp * ((n0 - n2) + i (n1 - n3)), one product per root
+// instead of an FP64 add per valid leaf.
+template <class T>
+__device__ __forceinline__ double2 suffix_census(const u32 (&st)[T::W], double2 amp, const u32 (&bin)[T::W],
+                                                 u64& completed, u64& valid, u64& visits)
+{
+    constexpr int W = T::W;
+    u32 n0 = 0u, n1 = 0u, n2 = 0u, n3 = 0u;
+    const u32 ns = 1u << T::As;
+    u32 hs = 0u;
+    auto leaf = [&](const u32 (&s2)[W], u32 q) {
+        ++completed;
+        u32 d = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) d |= s2[j] ^ bin[j];
+        const u32 ok = d == 0u ? 1u : 0u;
+        valid += ok;
+        n0 += ok & (q == 0u ? 1u : 0u);
+        n1 += ok & (q == 1u ? 1u : 0u);
+        n2 += ok & (q == 2u ? 1u : 0u);
+        n3 += ok & (q == 3u ? 1u : 0u);
+    };
+    if constexpr (T::STACKED) {
+        u32 sst[T::As][W];
+        double2 sam[T::As];
+        u32 skc[T::As][T::SCQ];
+        int start = 0;
+        while (hs < ns) {
+            u32 st2[W];
+            double2 amp2 = amp;
+#pragma unroll
+            for (int j = 0; j < W; ++j) st2[j] = start == 0 ? st[j] : sst[start - 1][j];
+            u32 q = 0u;
+            const int r2 = T::suffix_from_q(start, st2, amp2, (u64)hs, bin, visits, sst, sam, skc, q);
+            u32 nx;
+            if (r2 < 0) {
+                leaf(st2, q);
+                nx = hs + 1u;
+            } else {
+                nx = ((hs >> r2) + 1u) << r2;
+            }
+            if (nx < ns) start = T::As - 1 - (31 - __clz(hs ^ nx));
+            hs = nx;
+        }
+    } else {
+        while (hs < ns) {
+            u32 st2[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) st2[j] = st[j];
+            double2 amp2 = amp;
+            u32 q = 0u;
+            const int r2 = T::suffix_q(st2, amp2, (u64)hs, bin, visits, q);
+            if (r2 < 0) {
+                leaf(st2, q);
+                ++hs;
+            } else {
+                hs = ((hs >> r2) + 1u) << r2;
+            }
+        }
+    }
+    const int re = (int)(n0 - n2), im = (int)(n1 - n3);
+    double2 acc = make_double2(0.0, 0.0);
+    if (__any_sync(__activemask(), (re | im) != 0)) {
+        const double2 t = fs_census_ool(amp, re, im);
+        if ((re | im) != 0) acc = t;
+    }
+    return acc;
+}
+
 template <class T>
 __device__ __forceinline__ double2 suffix_sum(const u32 (&st)[T::W], double2 amp, const u32 (&bin)[T::W],
                                               u64& completed, u64& valid, u64& visits)
 {
     constexpr int W = T::W;
     double2 acc = make_double2(0.0, 0.0);
+    if constexpr (T::CENSUS) return suffix_census<T>(st, amp, bin, completed, valid, visits);
     typedef typename CounterType<(T::As < 32)>::type hs_t;   // 32-bit when it fits
     const hs_t ns = (hs_t)1 << T::As;
     hs_t hs = 0;
@@ -961,10 +1040,19 @@ std::string bound_after(const JitJobSpec& J, int e, const std::string& visits_cu
 // With stacked, the deferred class counts (and the commensurate phase) are
 // checkpointed with the state: skc[k][c] after segment k, restored at the
 // restart; *n_save receives the number of saved counts (at least 1).
+// census (in/out, with chi_only): the phase census of an exact suffix whose
+// every factor is a unit phase -- deferred classes whose two factors differ
+// by +-1 or +-i, and signs (NEG ops counted as the class (1, -1)).  A leaf's
+// amplitude is then the suffix's starting amplitude times i^q; the
+// generated function returns q (quarter turns) through `q` instead of
+// applying the classes.  *census is cleared when the suffix has any other
+// factor (a literal product, a table class, a commensurate phase).
 void emit_region(std::string& out, std::string& globals, const std::string& tag, const JitJobSpec& J,
                  int e0, int e1, int nbits, bool chi_only = false, std::complex<long double>* hoist = nullptr,
-                 bool stacked = false, bool segswitch = false, int* n_save = nullptr)
+                 bool stacked = false, bool segswitch = false, int* n_save = nullptr, int* census = nullptr)
 {
+    const bool cen = census && *census && chi_only && J.eps2 == 0.0;
+    bool literal = false;   // census mode: an op multiplied the amplitude
     const int W = J.W;
     const int dfrom = defer_from(J);
     std::vector<FactorClass> cls;
@@ -1039,7 +1127,10 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             }
             break;
         }
-        case OP_NEG1: c = "if (" + bitexpr(q0) + ") a = cneg(a);"; break;
+        case OP_NEG1:
+            if (cen) c = count(make_double2(1.0, 0.0), make_double2(-1.0, 0.0), bitexpr(q0));
+            else c = "if (" + bitexpr(q0) + ") a = cneg(a);";
+            break;
         case OP_MCPH: {
             if (defer) {
                 if (!is_one(F[0])) c = count(make_double2(1.0, 0.0), F[0], "(" + match_expr(J.masks + op.aux2, W) + ") ? 1u : 0u");
@@ -1049,7 +1140,11 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             }
             break;
         }
-        case OP_MCNEG: c = "if (" + match_expr(J.masks + op.aux2, W) + ") a = cneg(a);"; break;
+        case OP_MCNEG:
+            if (cen) c = count(make_double2(1.0, 0.0), make_double2(-1.0, 0.0),
+                               "(" + match_expr(J.masks + op.aux2, W) + ") ? 1u : 0u");
+            else c = "if (" + match_expr(J.masks + op.aux2, W) + ") a = cneg(a);";
+            break;
         case OP_DIAG2: {
             const bool parity = same_d2(F[0], F[3]) && same_d2(F[1], F[2]);
             if (parity && defer)
@@ -1118,6 +1213,7 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
             c = "/* unknown op */";
             break;
         }
+        if (cen && c.find("a = ") != std::string::npos) literal = true;
         if (!c.empty()) body += "    " + c + "\n";
         const bool carries = (op.code == OP_H || op.code == OP_BR1 || op.code == OP_BR2) &&
                              (op.s0 >= 0 || (op.code == OP_BR2 && op.s1 >= 0));
@@ -1170,6 +1266,35 @@ void emit_region(std::string& out, std::string& globals, const std::string& tag,
         if (ph_used) out += "    u32 ph = 0u;\n";
     }
     out += body;
+    if (cen) {
+        // the leaf's phase in quarter turns; the classes' constants A^n go
+        // to *hoist like the applied ones
+        bool ok = !literal && !ph_used && hoist;
+        std::string qs = "    u32 qq = 0u;\n";
+        for (size_t k = 0; k < cls.size() && ok; ++k) {
+            const FactorClass& f = cls[k];
+            const double2 A = f.A, B = f.B;
+            int kind = -1;
+            if (B.x == A.x && B.y == A.y) kind = 0;
+            else if (B.x == -A.x && B.y == -A.y) kind = 1;
+            else if (B.x == -A.y && B.y == A.x) kind = 2;
+            else if (B.x == A.y && B.y == -A.x) kind = 3;
+            if (kind < 0) { ok = false; break; }
+            using cl = std::complex<long double>;
+            cl An(1.0L, 0.0L);
+            const cl Al((long double)A.x, (long double)A.y);
+            for (int i = 0; i < f.n; ++i) An *= Al;
+            *hoist *= An;
+            const std::string kv = "k" + std::to_string(k);
+            if (kind == 1) qs += "    qq += (" + kv + " & 1u) << 1;\n";
+            else if (kind == 2) qs += "    qq += " + kv + ";\n";
+            else if (kind == 3) qs += "    qq += 3u * " + kv + ";\n";
+        }
+        *census = ok ? 1 : 0;
+        out += qs + "    q = qq & 3u;\n";
+        out += "    visits += " + std::to_string(e1 - seg_e0) + "ull;\n    (void)low;\n    return -1;\n";
+        return;
+    }
     const bool products = !cls.empty() || ph_used;
     if (chi_only && products) {
         out += "    u32 dchi = 0u;\n";
@@ -1369,6 +1494,35 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
             emit_region(structs, globals, js + "u", J, qlast + 1, J.G, 0, true, &h3);
             structs += "  }\n";
         }
+        // the phase census of a unit-phase exact suffix (4 or more sources,
+        // up to 30): suffix_q / suffix_from_q return each leaf's quarter
+        // turns, and the leaves of a root are counted by phase
+        bool census = false;
+        if (J.eps2 == 0.0 && J.As >= 4 && J.As <= 30) {
+            PhaseAcc* keep = t_phase;
+            t_phase = nullptr;
+            std::string fq, fsq;
+            std::complex<long double> hq(1.0L, 0.0L), hsq(1.0L, 0.0L);
+            int ok1 = 1, ok2 = 1, scq = 1;
+            emit_region(fq, globals, js + "c", J, J.c2, J.G, J.As, true, &hq, false, false, nullptr, &ok1);
+            if (stacked)
+                emit_region(fsq, globals, js + "d", J, J.c2, J.G, J.As, true, &hsq, true, false, &scq, &ok2);
+            t_phase = keep;
+            census = ok1 && ok2;
+            if (census) {
+                structs += "  static __device__ __forceinline__ int suffix_q(u32 (&s)[" + W + "], double2& a, u64 h, "
+                           "const u32 (&bin)[" + W + "], u64& visits, u32& q) {\n    (void)h; (void)bin;\n" + fq + "  }\n";
+                if (stacked)
+                    structs += "  static constexpr int SCQ = " + std::to_string(scq) + ";\n"
+                               "  static __device__ __forceinline__ int suffix_from_q(int start, u32 (&s)[" + W +
+                               "], double2& a, u64 h, const u32 (&bin)[" + W + "], u64& visits, u32 (&sst)[" +
+                               std::to_string(J.As) + "][" + W + "], double2 (&sam)[" + std::to_string(J.As) +
+                               "], u32 (&skc)[" + std::to_string(J.As) + "][" + std::to_string(scq) +
+                               "], u32& q) {\n    (void)h; (void)bin;\n" + fsq + "  }\n";
+            }
+        }
+        structs += std::string("  static constexpr bool CENSUS = ") + (census ? "true" : "false") + ";\n";
+        if (!(census && stacked)) structs += "  static constexpr int SCQ = 1;\n";
         if (stacked) {
             // the same suffix as per-source segments (its hoisted constant is
             // the one of `suffix` below: the same classes); the class counts
@@ -1550,6 +1704,20 @@ bool phase_index(double2 A, double2 B, uint32_t* p)
     if (q == 0u) return false;
     *p = q;
     return true;
+}
+
+bool jit_census(const JitJobSpec& J)
+{
+    if (J.eps2 != 0.0 || J.As < 4 || J.As > 30) return false;
+    std::string g, f;
+    std::complex<long double> h(1.0L, 0.0L);
+    int ok1 = 1, ok2 = 1, sc = 1;
+    PhaseAcc* keep = t_phase;
+    t_phase = nullptr;
+    emit_region(f, g, "x", J, J.c2, J.G, J.As, true, &h, false, false, nullptr, &ok1);
+    if (stacked_suffix(J)) emit_region(f, g, "y", J, J.c2, J.G, J.As, true, &h, true, false, &sc, &ok2);
+    t_phase = keep;
+    return ok1 && ok2;
 }
 
 std::string jit_source(const std::vector<JitJobSpec>& jobs)

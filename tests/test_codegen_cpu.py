@@ -264,6 +264,63 @@ SUFFIX_QUEUE = """
                     }"""
 
 
+# the device's phase census (exact suffixes whose factors are unit phases):
+# each valid leaf is the root's amplitude times i^q; the leaves are counted
+# by q and the root adds amp * ((n0 - n2) + i (n1 - n3))
+SUFFIX_CENSUS = """
+                    {
+                        long long n[4] = {0, 0, 0, 0};
+                        for (u64 hs = 0; hs < (1ull << J0::As); ++hs) {
+                            u32 st3[W];
+                            for (int j = 0; j < W; ++j) st3[j] = st2[j];
+                            double2 a3 = a2;
+                            u32 q = 0;
+                            if (J0::suffix_q(st3, a3, hs, bin, visits, q) >= 0) continue;
+                            ++completed;
+                            bool ok = true;
+                            for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
+                            if (ok) { ++n[q & 3u]; ++valid; }
+                        }
+                        const double re = (double)(n[0] - n[2]), im = (double)(n[1] - n[3]);
+                        sr += a2.x * re - a2.y * im;
+                        si += a2.x * im + a2.y * re;
+                    }"""
+
+
+SUFFIX_CENSUS_STACKED = """
+                    {
+                        long long n[4] = {0, 0, 0, 0};
+                        u32 sst[J0::As][W];
+                        double2 sam[J0::As];
+                        u32 skc[J0::As][J0::SCQ];
+                        int start = 0;
+                        const u64 ns = 1ull << J0::As;
+                        u64 hs = 0;
+                        while (hs < ns) {
+                            u32 st3[W];
+                            double2 a3 = a2;
+                            for (int j = 0; j < W; ++j) st3[j] = start ? sst[start - 1][j] : st2[j];
+                            u32 q = 0;
+                            const int r2 = J0::suffix_from_q(start, st3, a3, hs, bin, visits, sst, sam, skc, q);
+                            u64 nx;
+                            if (r2 < 0) {
+                                ++completed;
+                                bool ok = true;
+                                for (int j = 0; j < W; ++j) ok = ok && st3[j] == bin[j];
+                                if (ok) { ++n[q & 3u]; ++valid; }
+                                nx = hs + 1;
+                            } else {
+                                nx = ((hs >> r2) + 1) << r2;
+                            }
+                            if (nx < ns) start = J0::As - 1 - (63 - __builtin_clzll(hs ^ nx));
+                            hs = nx;
+                        }
+                        const double re = (double)(n[0] - n[2]), im = (double)(n[1] - n[3]);
+                        sr += a2.x * re - a2.y * im;
+                        si += a2.x * im + a2.y * re;
+                    }"""
+
+
 def _words(v, W):
     return "{" + ", ".join(f"{(v >> (32 * j)) & 0xffffffff}u" for j in range(4)) + "}"
 
@@ -282,7 +339,8 @@ def _extract(src):
     return helpers, body, sx.strip(), sy.strip()
 
 
-def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single", walk=False, bound=False):
+def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single", walk=False, bound=False,
+                     census=False):
     C = fs.Circuit(circ)
     C.set_input(inputs)
     b = fs.Batch(split="fixed", c1=c1, c2=c2, prefix=prefix)
@@ -300,7 +358,11 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single", w
                   cim=", ".join(repr(complex(c).imag) for _, c in inputs), sx=sx, sy=sy)
     stacked = "STACKED = true" in src
     queue = "QUEUE = true" in src
-    fields["suffix_loop"] = (SUFFIX_QUEUE if walk and queue else SUFFIX_STACKED if stacked else SUFFIX_PLAIN)
+    has_census = "CENSUS = true" in src
+    if census and has_census:
+        fields["suffix_loop"] = SUFFIX_CENSUS_STACKED if stacked else SUFFIX_CENSUS
+    else:
+        fields["suffix_loop"] = SUFFIX_QUEUE if walk and queue else SUFFIX_STACKED if stacked else SUFFIX_PLAIN
     levels = [l.split("sources [")[1].rstrip(")").split(", ") for l in src.splitlines() if "  // level " in l]
     if levels:
         fields.update(L=len(levels), aprev=", ".join(a for a, _ in levels), anext=", ".join(b_ for _, b_ in levels),
@@ -318,6 +380,7 @@ def _host_amplitudes(circ, inputs, outputs, c1, c2, eps, tmp, prefix="single", w
     amp = np.array([float(r[0]) + 1j * float(r[1]) for r in rows])
     _host_amplitudes.stacked = stacked
     _host_amplitudes.queue = queue
+    _host_amplitudes.census = has_census
     return amp, np.array([int(r[2]) for r in rows]), np.array([int(r[3]) for r in rows])
 
 
@@ -585,3 +648,28 @@ def test_stacked_suffix_in_exact_mode_checkpoints_the_class_counts(family, tmp_p
     assert np.array_equal(valid, cnt["valid"].astype(np.int64))
     if family != "random":
         assert np.abs(want).max() > 1e-3
+
+
+@pytest.mark.parametrize("iters,a_s", [(1, 4), (2, 8), (2, 12)])
+def test_phase_census_of_unit_phase_suffixes(iters, a_s, tmp_path):
+    """Exact suffixes whose factors are all unit phases (amplitude
+    amplification: H, Toffoli, the marking and diffusion signs) count their
+    valid leaves by phase: suffix_q returns each leaf's quarter turns q and
+    the root adds amp * ((n0 - n2) + i (n1 - n3)).  Driven on the host by
+    Algorithm 2's loop: amplitudes within 1e-12 / 1e-10 of the oracle, leaf
+    counts exact."""
+    w = aa_workload(n=4, iters=iters, all_outputs=True)
+    circ, inputs, outputs = w.circuit, w.inputs, w.outputs[:8]
+    C = fs.Circuit(circ)
+    srcs = {s_: g for g, q, s_ in C.branch_vars() if s_ >= 0}
+    G = len(circ.gates)
+    A = len(srcs)
+    c1 = c2 = G - srcs[A - a_s - 1]              # a_s sources in the suffix
+    got, completed, valid = _host_amplitudes(circ, inputs, outputs, c1, c2, 0.0, str(tmp_path), census=True)
+    assert _host_amplitudes.census
+    assert _host_amplitudes.stacked == (a_s >= 10)
+    want, cnt = feynman.run(circ, inputs, outputs, c1=c1, c2=c2)
+    _close(got, want)
+    assert np.array_equal(completed, cnt["completed"].astype(np.int64))
+    assert np.array_equal(valid, cnt["valid"].astype(np.int64))
+    assert np.abs(want).max() > 0.05
