@@ -576,7 +576,17 @@ def timed_steps(b, steps, stream, flush, name, graph=None):
     return step_ms, mean_stage, completed, st
 
 
-def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
+# DRAM bytes (read + written) per launch of a step's dominant kernel, from
+# one ncu capture of the same kernel on the same request (dram__bytes_read.sum
+# + dram__bytes_write.sum; commands in profiles/); valid while that kernel's
+# code is unchanged.  Key: (workload, arm, learned cut or None).
+NCU_TRAFFIC = {
+    ("qw100", "plain", None): 270624512 + 5695232,      # fs_jit_history, history_kernel_qw100_4096out.md
+    ("qw100", "learned", (4, 8)): 86016 + 0,            # fs_jit_compact, history_compact_kernel_qw100_bound.md
+}
+
+
+def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks, traffic=None):
     """Roofline of the dominant stage of a step: algorithmic work per launch
     over the stage's mean device time (CUDA events on the launch stream).
 
@@ -657,7 +667,8 @@ def stage_roofline(fs, b, jobs, stats, stage_ms, peaks, clocks):
                  "unit": "G warp-instructions/s", "frac": issue_frac,
                  "peak_note": "derived: SMs x 4 schedulers x 1 warp instruction per clock x max SM clock (issue slots)",
                  "fp64_pipe_frac": fp64_frac}
-    r.update({"kernel": dom, "traffic": None, "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}})
+    r.update({"kernel": dom, "traffic": traffic if dom == "history" else None,
+              "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}})
     tp = stage_ms.get("prefix", 0.0) / 1000.0
     if tp > 0 and table_bytes > 0:
         hbm = peaks.get("hbm_gbs", 6497.4)
@@ -779,12 +790,17 @@ def run_ours(args):
     if learned_info:
         value, hist_rate, step = rates(learned_ms, learned_completed)
         F = fidelity(plain_amp[:n_out], learned_amp[:n_out])
-        roof = stage_roofline(fs, bl, jobs, stats_learned, learned_stage, peaks, clocks)
+        cut = learned_info[0]["cut"] if len(jobs) == 1 and learned_info[0] else None
+        key = (args.workload, "learned", tuple(cut) if cut else None)
+        roof = stage_roofline(fs, bl, jobs, stats_learned, learned_stage, peaks, clocks,
+                              NCU_TRAFFIC.get(key) if args.engine == "straight" and not args.no_bound else None)
     else:
         value, hist_rate, step = plain_value, plain_hist, plain_step
         F = 1.0
-        roof = stage_roofline(fs, bp, jobs, stats_plain, plain_stage, peaks, clocks)
-    roof_plain = stage_roofline(fs, bp, jobs, stats_plain, plain_stage, peaks, clocks)
+        roof = stage_roofline(fs, bp, jobs, stats_plain, plain_stage, peaks, clocks,
+                              NCU_TRAFFIC.get((args.workload, "plain", None)) if args.engine == "straight" else None)
+    roof_plain = stage_roofline(fs, bp, jobs, stats_plain, plain_stage, peaks, clocks,
+                                NCU_TRAFFIC.get((args.workload, "plain", None)) if args.engine == "straight" else None)
 
     # end to end through the public API with host buffers: every step the
     # request (programs, bit strings, descriptors) goes host-to-device, the
