@@ -793,10 +793,15 @@ __device__ __forceinline__ bool prefix_body(const JobDev& J, u64 local, u64& vis
             ++bcuts;
         }
     }
-    if (!live) amp.x = __longlong_as_double(0x7ff8000000000000ll);
     uint4* dst = reinterpret_cast<uint4*>(J.table + local);
-    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    reinterpret_cast<double2*>(dst + 1)[0] = amp;
+    if (live) {
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<double2*>(dst + 1)[0] = amp;
+    } else {
+        // a cut entry is only its bottom mark (NaN real part): no reader
+        // looks at the rest of it, and the table writes drain faster
+        reinterpret_cast<double*>(dst + 1)[0] = __longlong_as_double(0x7ff8000000000000ll);
+    }
     return live;
 }
 
