@@ -135,6 +135,44 @@ def test_random_circuit_nonzero_outputs_wide_registers():
         assert abs(np.sum(np.abs(a) ** 2) - 1) < 1e-12
 
 
+@pytest.mark.parametrize("family,a_s", [("aa", 6), ("aa", 12), ("qaoa", 12)])
+def test_suffix_census_and_per_source_segments_vs_dense(family, a_s):
+    """Exact suffixes on the generated engine: amplitude amplification's
+    unit-phase suffix counts its leaves by phase (6 sources), with 12 it
+    also runs as per-source segments with the class counts checkpointed;
+    QAOA's RZZ classes are not unit phases, so 12 sources run as segments
+    with table classes.  Against the dense state vector; every history is
+    valid in these circuits, so the leaf counts are 2^A per pair."""
+    if family == "aa":
+        w = aa_workload(n=4, iters=3, seed=7, all_outputs=True)
+        outs = w.outputs[:12]
+    else:
+        w = qaoa_workload(8, 2, n_out=12, seed=13)
+        outs = w.outputs
+    C = fs.Circuit(w.circuit)
+    srcs = {s_: g for g, q, s_ in C.branch_vars() if s_ >= 0}
+    G = len(w.circuit.gates)
+    A = len(srcs)
+    c1 = c2 = G - srcs[A - a_s - 1]
+    C.set_input(w.inputs)
+    b = fs.Batch(split="fixed", c1=c1, c2=c2, prefix="single")
+    b.add(C, outs)
+    b.plan()
+    src = b.generated_source()
+    assert ("CENSUS = true" in src) == (family == "aa")
+    assert ("STACKED = true" in src) == (a_s >= 10)
+    b.allocate()
+    b.upload()
+    b.run()
+    st = b.finish()[0]
+    amp = b.amp.cpu().numpy()[:len(outs)]
+    close(amp, dense.amplitudes(w.circuit, w.inputs, outs))
+    # no factor of these circuits is zero and every history reaches the input
+    # bits: all 2^A histories of every pair complete and are valid
+    assert st["valid"] == st["completed"] == len(outs) << A
+    assert st["A_s"] == a_s
+
+
 def test_aa_fig8_ablation_rows_agree():
     w = aa_workload(n=4, iters=3, seed=11, all_outputs=True)
     outs = w.outputs[:10]
