@@ -245,9 +245,8 @@ struct JitJobSpec {
     // block (the job has no learned pruner to do it)
     bool bound = false, bound_counts = false;
     BoundSpec bspec{};
-    // with the bound: the bound after each op of the root and suffix that
-    // carries an artificial source (evaluation position, spec for the ops
-    // after it)
+    // with the bound: the bound after each op of the suffix that carries an
+    // artificial source (evaluation position, spec for the ops after it)
     std::vector<std::pair<int, BoundSpec>> src_bounds;
 };
 // Whether the generated engine counts this job's valid leaves by phase (an
