@@ -393,8 +393,11 @@ FS_API int fs_probe_peaks(double* dfma_per_s, double* int_ops_per_s, int32_t* sm
  * left, so a field value farther than that (cyclically) from b_in's is
  * unreachable.  Cut entries are counted in fs_stats.bound_cuts; the job runs
  * the history over the compacted live entries, so amplitudes are the exact
- * ones.  Call before fs_batch_plan; FS_ERR_UNSUPPORTED from the plan when
- * more than 4 disjoint cascade fields follow the cut. */
+ * ones.  The straight-line engine also tests the bound after every op of
+ * the suffix that carries an artificial source (the cut histories' leaves
+ * are all invalid: fewer leaves complete, the amplitudes are unchanged).
+ * Call before fs_batch_plan; FS_ERR_UNSUPPORTED from the plan when more
+ * than 4 disjoint cascade fields follow the cut. */
 FS_API int fs_batch_set_exact_bound(fs_batch* b, uint32_t job, int32_t enable);
 
 /* ---- learned pruning at the checkpoint boundary ---------------------------
