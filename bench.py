@@ -582,7 +582,7 @@ def timed_steps(b, steps, stream, flush, name, graph=None):
 # code is unchanged.  Key: (workload, arm, learned cut or None).
 NCU_TRAFFIC = {
     ("qw100", "plain", None): 270624512 + 5695232,      # fs_jit_history, history_kernel_qw100_4096out.md
-    ("qw100", "learned", (4, 8)): 86016 + 0,            # fs_jit_compact, history_compact_kernel_qw100_bound.md
+    ("qw100", "learned", (4, 8)): 80384 + 0,            # fs_jit_compact, history_compact_kernel_qw100_bound.md
 }
 
 
