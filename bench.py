@@ -538,21 +538,44 @@ def fidelity(a, b):
     return float(abs(np.vdot(a, b)) ** 2 / (na * nb))
 
 
-def capture(b, stream):
+class StepGraph:
     """The step's launches (counter reset, prefix levels, pruner, compaction,
-    history, reduction) captured once into a CUDA graph."""
-    import torch
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        b.run(stream)
-    torch.cuda.synchronize()
-    return g
+    history, reduction) captured twice into CUDA graphs: once as a user runs
+    them (no events inside: the timed replays) and once with the library's
+    stage events as graph nodes (the per-stage breakdown, from replays of
+    their own: an event node between two kernels stops the second one from
+    launching early, so it would lengthen the timed step)."""
+
+    def __init__(self, b, stream):
+        import torch
+        self.graphs = {}
+        # the timed capture last: the batch keeps its stage events on (and
+        # marked as recorded, which switching the timing would clear)
+        for timing in (False, True):
+            b.time_kernels(timing)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                b.run(stream)
+            torch.cuda.synchronize()
+            self.graphs[timing] = g
+
+    def replay(self):
+        self.graphs[False].replay()
+
+    def replay_stages(self):
+        self.graphs[True].replay()
+
+
+def capture(b, stream):
+    return StepGraph(b, stream)
 
 
 def timed_steps(b, steps, stream, flush, name, graph=None):
     """Device time of each step (CUDA events on the launch stream, L2 flushed
-    between steps) and the per-stage times of the library (its events are
-    nodes of the captured graph).  Each step is an NVTX range `name`."""
+    between steps) and the per-stage times of the library (from as many
+    replays of the graph that holds its stage events; without a graph the
+    stage events sit inside the timed steps).  Each timed step is an NVTX
+    range `name`."""
     import torch
     step_ms, stages, completed, valid = [], [], 0, 0
     for _ in range(steps):
@@ -569,9 +592,16 @@ def timed_steps(b, steps, stream, flush, name, graph=None):
         torch.cuda.nvtx.range_pop()
         st = b.finish(stream)
         step_ms.append(e0.elapsed_time(e1))
-        stages.append(b.stage_ms())
+        if graph is None:
+            stages.append(b.stage_ms())
         completed += sum(x["completed"] for x in st)
         valid += sum(x["valid"] for x in st)
+    if graph is not None:
+        for _ in range(steps):
+            flush.zero_()
+            graph.replay_stages()
+            b.finish(stream)
+            stages.append(b.stage_ms())
     mean_stage = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
     return step_ms, mean_stage, completed, st
 

@@ -283,7 +283,12 @@ FS_API int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* strea
  * output by Eq. 2.  Enqueues one evaluation of every job on stream: counter reset, prefix
  * expansion (checkpoint table), persistent history kernel over the atomic
  * tile queue, fixed-order reduction into d_amp_out (device, 2 * total
- * outputs doubles).  Asynchronous and free of host synchronisation, so it
+ * outputs doubles).  An exact job with the exact bound or a learned pruner
+ * on the straight-line engine, with at least 5 sources in the root, fewer
+ * than 32 input states and at most 4096 subtree sums per output, has its
+ * outputs reduced by its compacted history kernel (the warp that stores an
+ * output's last sum adds them, in the reduction kernel's order) and leaves
+ * none to the reduction kernels.  Asynchronous and free of host synchronisation, so it
  * can be captured into a CUDA graph.  Its kernels are launched with
  * programmatic dependent launch (each waits for the previous grid before
  * touching memory); FS_NO_PDL=1 in the environment launches them plainly.
@@ -322,10 +327,13 @@ FS_API int fs_batch_total_outputs(const fs_batch* b, size_t* n);
 
 /* Launch accounting of Algorithm 2's stages: the number of kernel launches
  * fs_batch_run enqueues (prefix levels or the
- * flat prefix, the two reduction kernels, the tiled history kernel when any
- * job is exact, and per pruned job a learned-prune launch if attached plus
- * count/scan/write compaction (the write also records each pair's live
- * range) and the history over live entries). */
+ * flat prefix, the reduction kernels unless every job with outputs reduces
+ * them itself (see fs_batch_run), the tiled history kernel when any job is
+ * exact, and per pruned job a learned-prune launch if attached plus the
+ * compaction: a count pass unless the bound or the pruner counted, a scan
+ * when the table has more than 1024 compaction blocks of 1024 entries, and
+ * the write (it also records each pair's live range), then the history
+ * over live entries). */
 FS_API int fs_batch_launch_count(const fs_batch* b, uint32_t* n);
 
 /* Per-output cost (the paper's per-output distribution of work, Sec. V,

@@ -434,9 +434,24 @@ struct Job {
     size_t o_lvscratch = 0;
     size_t o_live = 0, o_esum = 0, o_blk = 0, o_prange = 0;
     uint64_t nblk = 0;
+    bool fused = false;    // outputs reduced by the generated compacted history (no reduction launch)
+    size_t o_odone = 0;    // per output: subtree sums stored so far (zeroed at the start of every run)
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// An exact compacted job of the straight-line engine whose warps of 32
+// (live entry, h_r) items each store one subtree sum (A_r >= 5) reduces its
+// own outputs: the warp that stores an output's last sum adds them (Eq. 2),
+// with a warp per output, when an output has at most RED_BIG_ITEMS sums and
+// fewer than 32 input states.
+template <class B, class J> bool fused_reduction_of(const B& b, const J& j)
+{
+    if (b.opt.engine != 0 || !j.compact || j.eps != 0.0 || j.sp.Ar < 5 || j.outs.empty() || j.ins.size() >= 32)
+        return false;
+    const long double per_out = std::ldexp((long double)j.ins.size(), j.sp.Ap + j.sp.Ar - 5);
+    return per_out <= (long double)fs::RED_BIG_ITEMS;
+}
 
 // Makes a device current for the lifetime of the guard and restores the
 // caller's device afterwards (no-op for device < 0 or when it already is).
@@ -1037,6 +1052,10 @@ int fs_batch_plan(fs_batch* b, size_t* workspace_bytes)
     b->static_bytes = off;
     b->dyn_begin = off;
     b->o_stats = take(nj * fs::STATS_PER_JOB * sizeof(unsigned long long));
+    for (Job& j : b->jobs) {
+        j.fused = fused_reduction_of(*b, j);
+        j.o_odone = j.fused ? take(j.outs.size() * sizeof(uint32_t)) : 0;
+    }
     b->o_counter = take(sizeof(unsigned int));
     b->o_bigcount = take(sizeof(unsigned int));
     b->o_err = take(sizeof(uint32_t));   // last of the words zeroed at the start of every run
@@ -1300,6 +1319,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
         d.n_entries = j.table_entries;
         d.scale = j.scale;
         d.trace = j.d_trace;
+        d.odone = j.fused ? (uint32_t*)(base + j.o_odone) : nullptr;
         pbegin[ji] = pacc;
         obegin[ji] = oacc;
         if (j.levels.empty() && !j.direct) pacc += j.table_entries;
@@ -1348,7 +1368,7 @@ int fs_batch_upload(fs_batch* b, void* d_ws, size_t ws_bytes, void* stream)
 static bool big_outputs_possible(const fs_batch& b)
 {
     for (const Job& j : b.jobs) {
-        if (j.outs.empty()) continue;
+        if (j.outs.empty() || j.fused) continue;
         const int lg = j.compact ? j.sp.Ap + (j.sp.Ar >= 5 ? j.sp.Ar - 5 : j.sp.Ar) : j.log2_spp;
         const long double per_out = std::ldexp((long double)j.ins.size(), lg);
         if (per_out > (long double)fs::RED_BIG_ITEMS || j.ins.size() >= (size_t)fs::RED_BIG_THREADS) return true;
@@ -1356,11 +1376,20 @@ static bool big_outputs_possible(const fs_batch& b)
     return false;
 }
 
+// Whether some job with outputs leaves them to the reduction kernels.
+static bool reduce_needed(const fs_batch& b)
+{
+    for (const Job& j : b.jobs)
+        if (!j.outs.empty() && !j.fused) return true;
+    return false;
+}
+
 int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
 {
     if (!b || !n) return fail(FS_ERR_INVALID, "NULL argument");
-    // reduce: outputs by lane groups, then (when possible) the listed large ones
-    uint32_t k = b->total_out ? (big_outputs_possible(*b) ? 2 : 1) : 0;
+    // reduce: outputs by lane groups, then (when possible) the listed large
+    // ones; none when every job with outputs reduces them in its history
+    uint32_t k = reduce_needed(*b) ? (big_outputs_possible(*b) ? 2 : 1) : 0;
     bool tiled = false, flat_prefix = false;
     for (const Job& j : b->jobs) {
         tiled |= !j.compact;
@@ -1368,7 +1397,9 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         k += (uint32_t)j.levels.size();
         if (j.d_pruner) k += 1;                 // learned prune
         if (j.bound && b->opt.engine == 1) k += 1;   // exact bound (inside the generated prefix otherwise)
-        if (j.compact) k += (j.d_pruner || j.bound) ? 3 : 4;   // [count,] scan, write (with pair ranges), history over live entries
+        // [count,] [scan,] write (with pair ranges), history over live entries
+        if (j.compact)
+            k += ((j.d_pruner || j.bound) ? 2 : 3) + (j.nblk > (uint64_t)fs::COMPACT_DIRECT_BLOCKS ? 1 : 0);
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
@@ -1507,13 +1538,14 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
                                     (unsigned int*)(base + b->o_counter), (uint32_t*)(base + b->o_err), b->grid, s));
     for (int ji = 0; ji < nj; ++ji) {
         if (!b->jobs[ji].compact) continue;
-        if (b->jit) CUDA_TRY(fs::jit_launch_compact(b->jit, jobs, ji, s));
+        if (b->jit) CUDA_TRY(fs::jit_launch_compact(b->jit, jobs, ji, (double2*)d_amp_out, s));
         else CUDA_TRY(fs::launch_history_compact(jobs + ji, (uint32_t*)(base + b->o_err), b->compact_grid, s));
     }
     if (b->timing) CUDA_TRY(record(b->ev[2], s));
-    CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
-                               (double2*)d_amp_out, (unsigned int*)(base + b->o_bigcount),
-                               (uint64_t*)(base + b->o_biglist), big_outputs_possible(*b), s));
+    if (reduce_needed(*b))
+        CUDA_TRY(fs::launch_reduce(jobs, (const uint64_t*)(base + b->o_obegin), nj, b->total_out,
+                                   (double2*)d_amp_out, (unsigned int*)(base + b->o_bigcount),
+                                   (uint64_t*)(base + b->o_biglist), big_outputs_possible(*b), s));
     if (b->timing) {
         CUDA_TRY(record(b->ev[3], s));
         b->ev_recorded = true;

@@ -114,7 +114,8 @@ static_assert(sizeof(Entry) == 32, "Entry must be 32 bytes");
     uint64_t* prange;          /* per pair: [lo, hi) of its live entries */              \
     uint64_t n_entries;        /* checkpoint entries (pairs << Ap) */                   \
     double2 scale;             /* constant factor hoisted out of the root and suffix */ \
-    unsigned long long* trace; /* optional: per output {completed, valid} leaves */
+    unsigned long long* trace; /* optional: per output {completed, valid} leaves */ \
+    uint32_t* odone;           /* optional: per output, subtree sums stored (reduction fused into the compacted history) */
 
 struct JobDev {
     FS_JOBDEV_FIELDS
@@ -126,6 +127,7 @@ constexpr int REDUCE_THREADS = 128;
 constexpr int STATS_PER_JOB = 9;   // completed, valid, hist visits, entries, prefix visits, learned cuts,
                                    // live entries after compaction, compact work counter, bound cuts
 constexpr int COMPACT_BLOCK = 1024;   // entries per compaction block (256 threads x 4)
+constexpr int COMPACT_DIRECT_BLOCKS = 1024;   // up to this many blocks the write pass adds the counts itself
 constexpr int MLP_PARAMS = 18817;
 
 // Exact reachability bound at the checkpoint: what the ops after the cut can
@@ -214,7 +216,7 @@ cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job,
 cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, bool counted, cudaStream_t s);
 cudaError_t launch_history_compact(const JobDev* d_job, uint32_t* d_err, int grid, cudaStream_t s);
 int compact_grid_size(int device);
-cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s);
+cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, double2* d_amp, cudaStream_t s);
 // Two launches: lane groups sum most outputs and list the large ones in
 // d_big_list (count in d_big_count, zeroed by the caller); one block per
 // listed output sums the rest.

@@ -99,6 +99,48 @@ __device__ __forceinline__ u64 warp_sum_u64(u64 v)
     return v;
 }
 
+// Adds three per-thread counts into stats[k0], stats[k1], stats[k2] of job j
+// (this thread's job; -1 or all-zero counts: nothing to add) at a kernel's
+// end.  When every counting thread of the block has the same job, the block
+// adds its sums with one atomic per counter: the counters of a job share a
+// cache line, and thousands of warps adding to it one by one at the end of
+// a short kernel queue up behind each other in L2.  Otherwise every thread
+// adds its own counts.  Every thread of the block calls it.
+__device__ __noinline__ void flush_stats3(const JobDev* jobs, int j, int k0, int k1, int k2, u64 a, u64 b, u64 c)
+{
+    __shared__ u64 s_red[32][3];
+    __shared__ int s_job;
+    const bool has = (a | b | c) != 0ull;
+    if (threadIdx.x == 0) s_job = -1;
+    __syncthreads();
+    if (has) s_job = j;   // any one counting thread's job
+    __syncthreads();
+    const int jb = s_job;
+    if (!__syncthreads_and(!has || j == jb)) {
+        if (has) {
+            if (a) atomicAdd(&jobs[j].stats[k0], a);
+            if (b) atomicAdd(&jobs[j].stats[k1], b);
+            if (c) atomicAdd(&jobs[j].stats[k2], c);
+        }
+        return;   // the same branch for the whole block
+    }
+    a = warp_sum_u64(a);
+    b = warp_sum_u64(b);
+    c = warp_sum_u64(c);
+    if ((threadIdx.x & 31) == 0) {
+        s_red[threadIdx.x >> 5][0] = a;
+        s_red[threadIdx.x >> 5][1] = b;
+        s_red[threadIdx.x >> 5][2] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && jb >= 0) {
+        u64 t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w][threadIdx.x];
+        const int k = threadIdx.x == 0 ? k0 : (threadIdx.x == 1 ? k1 : k2);
+        if (t) atomicAdd(&jobs[jb].stats[k], t);
+    }
+}
+
 // (output, input) of a pair index, pair = o * S + s.  Integer division by a
 // runtime value goes through the scarce FP64 pipe on this part, so the
 // quotient comes from the job's precomputed multiplier (division by an
@@ -447,14 +489,13 @@ __device__ __forceinline__ double2 item_sum(const JobDev& J, u64 pair,
 // across lanes (group_sum) into one partial per (pair, 256-item block).  No
 // block-wide barrier: warps run their tiles independently.
 template <class T>
-__device__ void tile_body(const JobDev& J, u64 tile)
+__device__ void tile_body(const JobDev& J, u64 tile, u64& completed, u64& valid, u64& visits)
 {
     const int lane = threadIdx.x & 31;
     constexpr int lg = T::Ap + T::Ar;   // items per pair: 2^lg
     typedef typename CounterType<(lg <= 32)>::type loc_t;
     const u64 n_items = J.n_pairs << lg;
     const u64 first = tile * TILE + (u64)lane * 8u;
-    u64 completed = 0, valid = 0, visits = 0;
     double2 acc = make_double2(0.0, 0.0);
     // the lane's items as (pair, index within the pair), advanced in place
     // (the index stays 32-bit where it fits)
@@ -486,14 +527,21 @@ __device__ void tile_body(const JobDev& J, u64 tile)
             J.partials[(p << J.log2_spp) + (l >> TILE_LOG2)] = acc;
         }
     }
+}
+
+// Adds a warp's counts of one job into its stats (lane 0, one atomic each),
+// then clears them.
+__device__ __forceinline__ void warp_flush3(const JobDev& J, u64& completed, u64& valid, u64& visits)
+{
     completed = warp_sum_u64(completed);
     valid = warp_sum_u64(valid);
     visits = warp_sum_u64(visits);
-    if (lane == 0 && (completed | valid | visits)) {
+    if ((threadIdx.x & 31) == 0 && (completed | valid | visits)) {
         atomicAdd(&J.stats[0], completed);
         atomicAdd(&J.stats[1], valid);
         atomicAdd(&J.stats[2], visits);
     }
+    completed = valid = visits = 0;
 }
 
 template <class T>
@@ -536,13 +584,98 @@ __device__ __forceinline__ void store_esum(const JobDev& J, u64 i, double2 acc, 
     }
 }
 
+// Output reduction of a job that does it in its compacted history (odone
+// set): the sums of an output are added in the order of the separate
+// reduction kernel, so the amplitudes are the same doubles.  Items
+// src[k], src[k + stride], ... below hi, the i-th into accumulator i mod 4,
+// combined as (a0 + a1) + (a2 + a3), read from L2 (other SMs stored them
+// during this kernel).
+__device__ __forceinline__ double2 strided_sum_l2(const double2* src, u64 k, u64 hi, u32 stride)
+{
+    double2 a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = make_double2(0.0, 0.0);
+    for (; k + 7 * (u64)stride < hi; k += 8 * (u64)stride) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(src + k + (u64)u * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            a[u & 3].x += v[u].x;
+            a[u & 3].y += v[u].y;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 7; ++u) {
+        if (k < hi) {
+            const double2 v = __ldcg(src + k);
+            a[u & 3].x += v.x;
+            a[u & 3].y += v.y;
+        }
+        k += stride;
+    }
+    return make_double2((a[0].x + a[1].x) + (a[2].x + a[3].x), (a[0].y + a[1].y) + (a[2].y + a[3].y));
+}
+
+// An output none of whose pairs kept a live entry has amplitude 0 (nothing
+// else writes it when the job reduces its own outputs).
+__device__ __noinline__ void zero_empty_outputs(const JobDev& J, double2* amp_out)
+{
+    const u64 S = (u64)J.S;
+    for (u64 o = (u64)blockIdx.x * blockDim.x + threadIdx.x; o < (u64)J.M; o += (u64)gridDim.x * blockDim.x)
+        if (__ldg(J.prange + 2 * o * S) == __ldg(J.prange + 2 * (o * S + S - 1) + 1))
+            amp_out[J.out_begin + o] = make_double2(0.0, 0.0);
+}
+
+// Called by a whole warp after it stored the subtree sum of its 32 items of
+// live entry L: counts the sum for the entry's output (the store is made
+// visible device-wide first).  The warp that stores an output's last sum
+// adds the output's sums, pair by pair, times c_in of the pair's input
+// (Eq. 2): four lanes for at most 64 sums, else the whole warp, as the
+// reduction kernel does.
+__device__ __noinline__ void sum_done(const JobDev& J, u64 L, double2* amp_out)
+{
+    const int lane = threadIdx.x & 31;
+    u64 s0;
+    const u64 o = pair_split(__ldg(J.live + L) >> J.Ap, J, s0);
+    const u64 p0 = o * (u64)J.S;
+    const int sh = J.Ar - 5;
+    const u64 need = (__ldg(J.prange + 2 * (p0 + (u64)J.S - 1) + 1) - __ldg(J.prange + 2 * p0)) << sh;
+    u32 done = 0;
+    if (lane == 0) {
+        __threadfence();
+        done = atomicAdd(J.odone + o, 1u) + 1u;
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if ((u64)done != need) return;
+    __threadfence();
+    double2 amp = make_double2(0.0, 0.0);
+    const bool small = need <= 64u;
+    const int lanes = small ? 4 : 32;
+    for (int s = 0; s < J.S; ++s) {
+        const u64 lo = __ldg(J.prange + 2 * (p0 + (u64)s)) << sh;
+        const u64 hi = __ldg(J.prange + 2 * (p0 + (u64)s) + 1) << sh;
+        if (hi == lo) continue;   // the same pair for every lane
+        double2 t = strided_sum_l2(J.esum, lo + (u64)(lane & (lanes - 1)), hi, (u32)lanes);
+        for (int off = lanes / 2; off >= 1; off >>= 1) {
+            t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+            t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+        }
+        const double2 w = cmul(__ldg(J.coef + s), t);
+        amp.x += w.x;
+        amp.y += w.y;
+    }
+    if (lane == 0) amp_out[J.out_begin + o] = amp;
+}
+
 // History over the compacted live entries of one job.  With A_r < 5 every
 // (live entry, h_r) item keeps its own subtree sum, and each lane takes its
 // next item on its own: the subtrees of a threshold job differ widely in
 // size, and a lane never waits for the rest of its warp.  Otherwise a warp
 // takes 32 consecutive items (one live entry) and adds their sums.
 template <class T>
-__device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u64& valid, u64& visits)
+__device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u64& valid, u64& visits,
+                                             double2* amp_out)
 {
     const u64 nlive = J.stats[6] << T::Ar;
     if constexpr (T::Ar < 5) {
@@ -562,6 +695,7 @@ __device__ __forceinline__ void compact_loop(const JobDev& J, u64& completed, u6
             double2 acc = make_double2(0.0, 0.0);
             if (i < nlive) acc = compact_body<T>(J, i, completed, valid, visits);
             store_esum(J, i, acc, i < nlive);
+            if (J.odone) sum_done(J, base >> T::Ar, amp_out);
         }
     }
 }
@@ -1566,46 +1700,52 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
     src += structs;
     // persistent warps pull tiles off the queue; the next index is fetched
     // while the current tile runs
+    // a warp keeps its counts while its tiles are of one job and adds them
+    // to that job's stats when the job changes and at the end
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_history(const JobDev* __restrict__ jobs, "
            "const uint2* __restrict__ tiles, u64 n_tiles, unsigned int* counter)\n{\n"
            "    FS_GRID_DEP();\n"
            "    const int lane = threadIdx.x & 31;\n    unsigned int t = 0u, next = 0u;\n"
+           "    u64 completed = 0, valid = 0, visits = 0;\n    int cj = -1;\n"
            "    if (lane == 0) t = atomicAdd(counter, 1u);\n    t = __shfl_sync(0xffffffffu, t, 0);\n"
            "    while ((u64)t < n_tiles) {\n"
            "        if (lane == 0) next = atomicAdd(counter, 1u);\n        const uint2 td = tiles[t];\n"
+           "        if ((int)td.x != cj) {\n"
+           "            if (cj >= 0) warp_flush3(jobs[cj], completed, valid, visits);\n"
+           "            cj = (int)td.x;\n        }\n"
            "        switch (td.x) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
         src += "        case " + std::to_string(j) + "u: tile_body<J" + std::to_string(j) + ">(jobs[" +
-               std::to_string(j) + "], td.y); break;\n";
-    src += "        default: break;\n        }\n        t = __shfl_sync(0xffffffffu, next, 0);\n    }\n}\n";
-    src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job)\n{\n"
+               std::to_string(j) + "], td.y, completed, valid, visits); break;\n";
+    src += "        default: break;\n        }\n        t = __shfl_sync(0xffffffffu, next, 0);\n    }\n"
+           "    flush_stats3(jobs, cj, 0, 1, 2, completed, valid, visits);\n}\n";
+    src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job, "
+           "double2* amp_out)\n{\n"
            "    FS_GRID_DEP();\n"
-           "    const JobDev& J = jobs[job];\n    const int lane = threadIdx.x & 31;\n"
+           "    const JobDev& J = jobs[job];\n"
+           "    if (J.odone) zero_empty_outputs(J, amp_out);\n"
            "    u64 completed = 0, valid = 0, visits = 0;\n    switch (job) {\n";
     for (size_t j = 0; j < jobs.size(); ++j)
         if (jobs[j].compact)
             src += "    case " + std::to_string(j) + ": compact_loop<J" + std::to_string(j) +
-                   ">(J, completed, valid, visits); break;\n";
+                   ">(J, completed, valid, visits, amp_out); break;\n";
     src += "    default: break;\n    }\n"
-           "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
-           "    if (lane == 0 && (completed | valid | visits)) {\n"
-           "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
+           "    flush_stats3(jobs, job, 0, 1, 2, completed, valid, visits);\n}\n";
     bool any_queue = false;
     for (const JitJobSpec& J : jobs) any_queue |= queue_last_source(J) >= 0;
     if (any_queue) {
-        src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_walk(const JobDev* __restrict__ jobs, int job)\n{\n"
+        src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_walk(const JobDev* __restrict__ jobs, int job, "
+               "double2*)\n{\n"
                "    FS_GRID_DEP();\n"
                "    extern __shared__ __align__(16) unsigned char walk_smem[];\n"
-               "    const JobDev& J = jobs[job];\n    const int lane = threadIdx.x & 31;\n"
+               "    const JobDev& J = jobs[job];\n"
                "    u64 completed = 0, valid = 0, visits = 0;\n    switch (job) {\n";
         for (size_t j = 0; j < jobs.size(); ++j)
             if (queue_last_source(jobs[j]) >= 0)
                 src += "    case " + std::to_string(j) + ": walk_loop<J" + std::to_string(j) +
                        ">(J, walk_smem, completed, valid, visits); break;\n";
         src += "    default: break;\n    }\n"
-               "    completed = warp_sum_u64(completed);\n    valid = warp_sum_u64(valid);\n    visits = warp_sum_u64(visits);\n"
-               "    if (lane == 0 && (completed | valid | visits)) {\n"
-               "        atomicAdd(&J.stats[0], completed);\n        atomicAdd(&J.stats[1], valid);\n        atomicAdd(&J.stats[2], visits);\n    }\n}\n";
+               "    flush_stats3(jobs, job, 0, 1, 2, completed, valid, visits);\n}\n";
     }
     for (size_t j = 0; j < jobs.size(); ++j) {
         if (jobs[j].levels.empty()) continue;
@@ -1634,15 +1774,14 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
         if (jobs[j].bound && jobs[j].bound_counts)
             src += "        if (last) count_live(J, idx, live, true);\n";
         src += "    }\n"
-               "    visits = warp_sum_u64(visits);\n    entries = warp_sum_u64(entries);\n    bcuts = warp_sum_u64(bcuts);\n"
-               "    if ((threadIdx.x & 31) == 0) {\n        if (visits) atomicAdd(&J.stats[4], visits);\n"
-               "        if (entries) atomicAdd(&J.stats[3], entries);\n        if (bcuts) atomicAdd(&J.stats[8], bcuts);\n    }\n}\n";
+               "    flush_stats3(jobs, " + js + ", 4, 3, 8, visits, entries, bcuts);\n}\n";
     }
     bool any_count = false;
     for (const JitJobSpec& J : jobs) any_count |= J.bound && J.bound_counts && J.levels.empty();
     src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_prefix(const JobDev* __restrict__ jobs, "
            "const u64* __restrict__ begin, int n_jobs, u64 total)\n{\n"
            "    FS_GRID_DEP();\n"
+           "    u64 dv = 0, den = 0, dbc = 0;\n    int cj = -1;\n"
            "    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; ; idx += (u64)gridDim.x * blockDim.x) {\n"
            "        if (!__any_sync(0xffffffffu, idx < total)) break;\n"
            "        u64 visits = 0, entries = 0, bcuts = 0, local = 0;\n        int j = 0;\n"
@@ -1659,7 +1798,12 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
            "        const bool uniform = act == 0xffffffffu && same == 0xffffffffu;\n";
     if (any_count)
         src += "        if (__any_sync(0xffffffffu, counts)) count_live(jobs[j], local, live && counts, uniform && counts);\n";
-    src += "        if (uniform) {\n"
+    // a warp whose lanes all ran entries of its first job keeps those
+    // counts for the block-wide flush at the end; other iterations add
+    // theirs as they go
+    src += "        if (uniform && (cj < 0 || j == cj)) {\n"
+           "            cj = j;\n            dv += visits;\n            den += entries;\n            dbc += bcuts;\n"
+           "        } else if (uniform) {\n"
            "            const u64 v = warp_sum_u64(visits), en = warp_sum_u64(entries), bc = warp_sum_u64(bcuts);\n"
            "            if ((threadIdx.x & 31) == 0) { atomicAdd(&jobs[j].stats[4], v); atomicAdd(&jobs[j].stats[3], en);\n"
            "                                           if (bc) atomicAdd(&jobs[j].stats[8], bc); }\n"
@@ -1667,7 +1811,8 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
            "            if (visits) atomicAdd(&jobs[j].stats[4], visits);\n"
            "            if (entries) atomicAdd(&jobs[j].stats[3], entries);\n"
            "            if (bcuts) atomicAdd(&jobs[j].stats[8], bcuts);\n"
-           "        }\n    }\n}\n";
+           "        }\n    }\n"
+           "    flush_stats3(jobs, cj, 4, 3, 8, dv, den, dbc);\n}\n";
     return src;
 }
 
@@ -1856,10 +2001,10 @@ cudaError_t jit_launch_prefix_level(void* handle, const JobDev* d_jobs, int job,
     return launch_ex((const void*)m->lv[job], dim3((unsigned)blocks), dim3(TILE), 0, s, args);
 }
 
-cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, cudaStream_t s)
+cudaError_t jit_launch_compact(void* handle, const JobDev* d_jobs, int job, double2* d_amp, cudaStream_t s)
 {
     JitModule* m = (JitModule*)handle;
-    void* args[] = {(void*)&d_jobs, (void*)&job};
+    void* args[] = {(void*)&d_jobs, (void*)&job, (void*)&d_amp};
     if (job >= 0 && job < (int)m->walk_warps.size() && m->walk_warps[job])
         return launch_ex((const void*)m->walk, dim3(m->walk_grid[job]), dim3(32 * m->walk_warps[job]),
                          m->walk_smem[job], s, args);

@@ -662,10 +662,25 @@ __global__ void __launch_bounds__(1024) compact_scan_kernel(const JobDev* __rest
     if (threadIdx.x == 0) J.stats[6] = s_carry;
 }
 
-__global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __restrict__ jobp)
+// scanned: J.blk holds each block's exclusive offset (compact_scan_kernel
+// ran); otherwise it holds the blocks' counts, and each block adds those of
+// the blocks before it (at most COMPACT_DIRECT_BLOCKS of them, a few loads
+// per thread, so the scan needs no launch of its own) and the last block
+// writes the live total (stats[6]).
+__global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __restrict__ jobp, int scanned)
 {
     FS_GRID_DEP();
     const JobDev& J = *jobp;
+    __shared__ unsigned s_pre[8];
+    unsigned before = 0;
+    if (!scanned) {
+        unsigned t = 0;
+        for (unsigned k = threadIdx.x; k < blockIdx.x; k += 256) t += J.blk[k];
+        t = __reduce_add_sync(0xffffffffu, t);
+        if ((threadIdx.x & 31) == 0) s_pre[threadIdx.x >> 5] = t;
+        __syncthreads();
+        for (int w = 0; w < 8; ++w) before += s_pre[w];
+    }
     const uint64_t base = (uint64_t)blockIdx.x * COMPACT_BLOCK;
     bool lv[4];
     unsigned c = 0;
@@ -685,7 +700,12 @@ __global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __rest
     __syncthreads();
     unsigned woff = 0;
     for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) woff += s_w[w];
-    uint64_t pos = (uint64_t)J.blk[blockIdx.x] + woff + x - c;
+    if (!scanned && blockIdx.x + 1 == gridDim.x && threadIdx.x == 0) {
+        unsigned mine = 0;
+        for (int w = 0; w < 8; ++w) mine += s_w[w];
+        J.stats[6] = (unsigned long long)before + mine;
+    }
+    uint64_t pos = (scanned ? (uint64_t)J.blk[blockIdx.x] : (uint64_t)before) + woff + x - c;
     // pos is the number of live entries before e: at the first entry of a
     // pair it opens that pair's range and closes the previous one's
     const uint64_t pmask = (1ull << J.Ap) - 1ull;
@@ -895,9 +915,10 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const JobDev* __
     // (requests list the likely ones first) spread over warps
     for (uint64_t g0 = warp; g0 < total; g0 += nwarp * OPW) {
         const uint64_t g = g0 + (uint64_t)slot * nwarp;
-        const bool have = g < total;
+        bool have = g < total;
         const int j = have ? find_job(begin, n_jobs, g) : 0;
         const JobDev& J = jobs[j];
+        have = have && J.odone == nullptr;   // (a job with odone reduces its outputs in its history)
         const int S = have ? J.S : 0;
         const uint64_t o = have ? g - J.out_begin : 0;
         uint64_t n = 0;
@@ -1240,9 +1261,12 @@ cudaError_t launch_compact(const JobDev* d_job, uint64_t n_entries, bool counted
     const uint64_t nblk = (n_entries + COMPACT_BLOCK - 1) / COMPACT_BLOCK;
     if (nblk == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
+    const bool scan = nblk > (uint64_t)COMPACT_DIRECT_BLOCKS;
     if (!counted) e = launch_pdl(compact_count_kernel, dim3((unsigned)nblk), dim3(256), 0, s, d_job);
-    if (e == cudaSuccess) e = launch_pdl(compact_scan_kernel, dim3(1), dim3(1024), 0, s, d_job, (uint32_t)nblk);
-    if (e == cudaSuccess) e = launch_pdl(compact_write_kernel, dim3((unsigned)nblk), dim3(256), 0, s, d_job);
+    if (e == cudaSuccess && scan)
+        e = launch_pdl(compact_scan_kernel, dim3(1), dim3(1024), 0, s, d_job, (uint32_t)nblk);
+    if (e == cudaSuccess)
+        e = launch_pdl(compact_write_kernel, dim3((unsigned)nblk), dim3(256), 0, s, d_job, scan ? 1 : 0);
     return e;
 }
 

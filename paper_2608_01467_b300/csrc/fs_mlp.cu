@@ -640,15 +640,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                   const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err,
                   uint32_t wait_limit, int from_live)
 {
-    FS_GRID_DEP();
+    // The weights of a learned pruner are uploaded once, before any step,
+    // and no kernel writes them: a pruning launch stages them (and sets up
+    // its barriers) while the kernel before it finishes, and waits for that
+    // kernel only before it reads the rows' count.  A plain forward pass
+    // (training) waits first.
+    if (!PRUNE) FS_GRID_DEP();
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, grp = tid >> 7, r = tid & 127, warp = tid >> 5;
     const JobDev* J = PRUNE ? &jobs[job] : nullptr;
-    const long long n = PRUNE ? (from_live ? (long long)J->stats[6] : (long long)(J->n_pairs << J->Ap)) : n_rows;
-    const long long tiles = (n + 127) / 128;
-    // a CTA with no tile leaves before staging anything (the live count of a
-    // from_live launch is known only on the device)
-    if ((long long)blockIdx.x * 2 >= tiles) return;
+    if (!PRUNE && ((long long)blockIdx.x * 2 >= (n_rows + 127) / 128)) return;
     float* vb1 = (float*)(sm + SM_VEC);
     float* vb2 = vb1 + H;
     float* vw3 = vb2 + H;
@@ -702,6 +703,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < 2) ((volatile uint32_t*)(sm + SM_BAR + 20))[tid] = 0u;
+    if (PRUNE) FS_GRID_DEP();
+    const long long n = PRUNE ? (from_live ? (long long)J->stats[6] : (long long)(J->n_pairs << J->Ap)) : n_rows;
+    const long long tiles = (n + 127) / 128;
+    // a CTA with no tile leaves before it takes tensor memory (the live
+    // count of a from_live launch is known only on the device)
+    if ((long long)blockIdx.x * 2 >= tiles) return;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(TC_COLS)

@@ -98,3 +98,63 @@ def test_learned_pruner_on_top_of_the_exact_bound():
             assert st["learned_cuts"] == 0 and st["live_entries"] == stb["live_entries"]
             err = np.abs(got - exact)
             assert np.all(err <= 1e-12 + 1e-10 * np.abs(exact)), err.max()
+
+
+def _cut_run(w, c1, c2, engine="straight", bound=True, tau=None, outputs=None):
+    import torch
+    from workloads import mlp_init_params
+    from paper_2608_01467_b300 import learned
+    outs = w.outputs if outputs is None else outputs
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    b = fs.Batch(engine=engine, prefix="single")
+    b.add(C, outs)
+    if bound:
+        b.set_exact_bound(0)
+    if tau is not None:
+        params = torch.from_numpy(np.asarray(mlp_init_params(3), np.float32)).cuda()
+        learned.attach(b, 0, params, tau)
+    b.set_cuts(0, c1, c2)
+    b.plan()
+    b.allocate()
+    b.upload()
+    b.amp.fill_(complex(float("nan"), float("nan")))   # every output must be written
+    b.run()
+    st = b.finish()[0]
+    return b.amp.cpu().numpy()[:len(outs)], st, b.launch_count()
+
+
+def test_compacted_history_reduces_its_own_outputs():
+    """An exact compacted job on the generated engine with A_r >= 5 leaves
+    no reduction launch: the warp that stores an output's last subtree sum
+    adds the output's sums (Eq. 2).  Outputs without a live entry come out
+    as exact zeros, outputs with up to 64 sums (the exact bound leaves a few
+    entries per output) and with more (a pruner that cuts nothing leaves
+    all 32 entries x 8 sums) agree with the interpreter's separate
+    reduction and with the plain exact run, every output is written, and a
+    sub-request gives the same doubles as the full request."""
+    w = qw_workload(steps=16, n_out=512)
+    G = len(w.circuit.gates)
+    src = {s: g for g, q, s in fs.Circuit(w.circuit).branch_vars() if s >= 0}
+    c1, c2 = G - src[3], G - src[11]            # A_p = 4, A_r = 8
+    exact, _, _ = _cut_run(w, c1, c2, bound=False)
+    tol = lambda x, y: np.all(np.abs(x - y) <= 1e-12 + 1e-10 * np.abs(y))
+    got, st, n = _cut_run(w, c1, c2)
+    assert n == 3 and np.all(np.isfinite(got.view(np.float64)))
+    assert tol(got, exact), np.abs(got - exact).max()
+    zero = got == 0
+    assert zero.sum() > 0 and np.all(np.abs(exact[zero]) <= 1e-12)
+    ref, st_i, n_i = _cut_run(w, c1, c2, engine="interp")
+    assert n_i == 5 and tol(got, ref) and st["live_entries"] == st_i["live_entries"]
+    # the pruner alone, cutting nothing: 256 sums for every output
+    allv, st_a, n_a = _cut_run(w, c1, c2, bound=False, tau=-1e30)
+    assert n_a == 4 and st_a["learned_cuts"] == 0    # prune, write, history (+ the prefix)
+    assert np.all(np.isfinite(allv.view(np.float64))) and tol(allv, exact)
+    ref_a, _, _ = _cut_run(w, c1, c2, engine="interp", bound=False, tau=-1e30)
+    assert tol(allv, ref_a)
+    # outputs alone: the same doubles
+    idx = list(range(0, 512, 7))
+    sub, _, _ = _cut_run(w, c1, c2, outputs=[w.outputs[i] for i in idx])
+    assert np.array_equal(sub, got[idx])
+    sub_a, _, _ = _cut_run(w, c1, c2, bound=False, tau=-1e30, outputs=[w.outputs[i] for i in idx])
+    assert np.array_equal(sub_a, allv[idx])

@@ -406,3 +406,37 @@ def test_source_placement_matches_the_oracle():
     with pytest.raises(_lib.FsError) as e:
         C.source_placement("greedy")
     assert e.value.code == -2
+
+
+def test_compacted_exact_job_launches():
+    """An exact job with the reachability bound, on the generated engine:
+    the prefix (bound applied, live entries counted per compaction block),
+    the compaction's write pass (it adds the block counts before its own
+    when there are at most 1024 blocks: no scan launch) and the compacted
+    history, which also reduces the outputs (A_r >= 5, at most 4096 sums
+    per output): three launches.  The interpreter keeps its bound pass and
+    the reduction kernel; a table of more than 1024 compaction blocks adds
+    the scan."""
+    w = qw_workload(n_out=1024)
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    G = len(w.circuit.gates)
+    src = {s: g for g, q, s in C.branch_vars() if s >= 0}
+
+    def count(engine, ap, ar):
+        # evaluation positions after the first ap and ap + ar backward
+        # sources; the prefix as one region (no per-source levels)
+        b = fs.Batch(engine=engine, prefix="single")
+        b.add(C, w.outputs, 0.0)
+        b.set_exact_bound(0)
+        b.set_cuts(0, G - src[ap - 1], G - src[ap + ar - 1])
+        b.plan()
+        return b.launch_count()
+
+    assert count("straight", 4, 8) == 3        # 2048 pairs x 16 entries: 32 blocks
+    assert count("interp", 4, 8) == 5          # bound pass, prefix, write, history, reduction
+    # 2048 pairs x 1024 entries: 2048 blocks (scan); A_r < 5: the reduction,
+    # and its pass for outputs of more than 4096 sums
+    assert count("straight", 10, 4) == 6
+    assert count("straight", 9, 5) == 3        # 1024 blocks
+    assert count("straight", 4, 3) == 4        # A_r = 3: the reduction kernel sums per item
