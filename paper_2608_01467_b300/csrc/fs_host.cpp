@@ -1376,6 +1376,15 @@ static bool big_outputs_possible(const fs_batch& b)
     return false;
 }
 
+// A learned pruner on top of the exact bound whose table has at most
+// COMPACT_DIRECT_BLOCKS compaction blocks: the scoring kernel writes the
+// compaction (a CTA per block, the bound's per-block counts) and scores
+// each block's live entries, one launch instead of two.
+static bool scorer_compacts(const Job& j)
+{
+    return j.bound && j.d_pruner && j.nblk <= (uint64_t)fs::COMPACT_DIRECT_BLOCKS;
+}
+
 // Whether some job with outputs leaves them to the reduction kernels.
 static bool reduce_needed(const fs_batch& b)
 {
@@ -1399,7 +1408,8 @@ int fs_batch_launch_count(const fs_batch* b, uint32_t* n)
         if (j.bound && b->opt.engine == 1) k += 1;   // exact bound (inside the generated prefix otherwise)
         // [count,] [scan,] write (with pair ranges), history over live entries
         if (j.compact)
-            k += ((j.d_pruner || j.bound) ? 2 : 3) + (j.nblk > (uint64_t)fs::COMPACT_DIRECT_BLOCKS ? 1 : 0);
+            k += ((j.d_pruner || j.bound) ? 2 : 3) + (j.nblk > (uint64_t)fs::COMPACT_DIRECT_BLOCKS ? 1 : 0) -
+                 (scorer_compacts(j) ? 1 : 0);
     }
     *n = k + (tiled ? 1 : 0) + (flat_prefix ? 1 : 0);
     return FS_OK;
@@ -1514,11 +1524,12 @@ int fs_batch_run(fs_batch* b, void* d_ws, double* d_amp_out, void* stream)
             CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
             CUDA_TRY(fs::launch_bound_prune(jobs, ji, j.bspec, j.table_entries, true, s));
         }
-        if (j.bound) CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, true, s));
+        const bool scorer_writes = scorer_compacts(j);
+        if (j.bound && !scorer_writes) CUDA_TRY(fs::launch_compact(jobs + ji, j.table_entries, true, s));
         if (j.d_pruner) {
             if (!j.bound) CUDA_TRY(cudaMemsetAsync(base + j.o_blk, 0, j.nblk * sizeof(uint32_t), s));
             CUDA_TRY(fs::mlp_learned_prune(j.d_pruner, jobs, ji, j.fspec, j.tau, j.table_entries,
-                                           (uint32_t*)(base + b->o_err), s, j.bound));
+                                           (uint32_t*)(base + b->o_err), s, j.bound ? (scorer_writes ? 2 : 1) : 0));
         }
     }
     if (b->timing) CUDA_TRY(record(b->ev[5], s));

@@ -174,12 +174,14 @@ cudaError_t mlp_adam(float* d_params, float* d_m, float* d_v, const float* d_gra
                      cudaStream_t s);
 cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, float* d_feat,
                          unsigned long long n_entries, cudaStream_t s);
-// from_live: score the compacted live entries (after the exact bound) and
-// mark cuts in the table only; otherwise score every entry and count the
-// live ones per compaction block.
+// rows = 0: score every entry and count the live ones per compaction block;
+// 1: score the compacted live entries (after the exact bound) and mark cuts
+// in the table only; 2: as 1, with the compaction's write pass done by the
+// scoring kernel (a CTA per compaction block, its live entries scored by
+// it; the bound's per-block counts, at most COMPACT_DIRECT_BLOCKS blocks).
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
                               float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s,
-                              bool from_live);
+                              int rows);
 cudaError_t mlp_targets(const double* d_sums, unsigned long long n, double floor_v, float* d_t, cudaStream_t s);
 // Polls of a bounded tensor-core wait before it gives up (process-wide;
 // change it only while no scoring kernel is being launched).
@@ -297,6 +299,78 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.attrs = at;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
+// Compaction write of table block b (COMPACT_BLOCK entries, 256 threads x 4;
+// every thread of the block calls it): each live entry (amplitude not the
+// bottom NaN) goes to J.live at its rank among the live entries in table
+// order, a pair's range of live ranks is recorded at its first entry (and
+// closes the previous pair's), and the last table entry closes the last
+// pair's.  scanned: J.blk holds each block's exclusive offset; otherwise
+// it holds the blocks' counts, the block adds those before it (nblk is at
+// most COMPACT_DIRECT_BLOCKS), and the last block writes the live total
+// (stats[6]).  list (shared memory, optional): the block's live entries as
+// offsets within the block, in table order.  Returns the block's live count.
+__device__ __forceinline__ unsigned compact_block_write(const JobDev& J, unsigned b, unsigned nblk, int scanned,
+                                                        uint16_t* list)
+{
+    __shared__ unsigned s_pre[8], s_w[8];
+    unsigned before = 0;
+    if (!scanned) {
+        unsigned t = 0;
+        for (unsigned k = threadIdx.x; k < b; k += 256) t += J.blk[k];
+        t = __reduce_add_sync(0xffffffffu, t);
+        if ((threadIdx.x & 31) == 0) s_pre[threadIdx.x >> 5] = t;
+        __syncthreads();
+        for (int w = 0; w < 8; ++w) before += s_pre[w];
+    }
+    const uint64_t base = (uint64_t)b * COMPACT_BLOCK;
+    bool lv[4];
+    unsigned c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
+        bool live = false;
+        if (e < J.n_entries) {
+            const double x = J.table[e].amp.x;
+            const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+            live = !(hi > 0x7ff00000u || (hi == 0x7ff00000u && (unsigned)__double2loint(x) != 0u));
+        }
+        lv[k] = live;
+        c += live;
+    }
+    unsigned x = c;   // inclusive warp scan of the per-thread counts
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+        if ((threadIdx.x & 31) >= (unsigned)off) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned woff = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < (int)(threadIdx.x >> 5)) woff += s_w[w];
+        total += s_w[w];
+    }
+    if (!scanned && b + 1 == nblk && threadIdx.x == 0) J.stats[6] = (unsigned long long)before + total;
+    const uint64_t first = (scanned ? (uint64_t)J.blk[b] : (uint64_t)before);
+    uint64_t pos = first + woff + x - c;
+    const uint64_t pmask = (1ull << J.Ap) - 1ull;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
+        if (e < J.n_entries && (e & pmask) == 0ull) {
+            const uint64_t p = e >> J.Ap;
+            J.prange[2 * p] = pos;
+            if (p) J.prange[2 * p - 1] = pos;
+        }
+        if (lv[k]) {
+            J.live[pos] = e;
+            if (list) list[pos - first] = (uint16_t)(e - base);
+            ++pos;
+        }
+        if (e + 1ull == J.n_entries) J.prange[2 * (e >> J.Ap) + 1] = pos;
+    }
+    return total;
 }
 #endif
 cudaError_t probe_peaks(double* dfma_per_s, double* int_ops_per_s, int* sms);

@@ -1719,7 +1719,10 @@ std::string generate(const std::vector<JitJobSpec>& jobs, std::vector<double2>* 
                std::to_string(j) + "], td.y, completed, valid, visits); break;\n";
     src += "        default: break;\n        }\n        t = __shfl_sync(0xffffffffu, next, 0);\n    }\n"
            "    flush_stats3(jobs, cj, 0, 1, 2, completed, valid, visits);\n}\n";
-    src += "extern \"C\" __global__ void __launch_bounds__(256) fs_jit_compact(const JobDev* __restrict__ jobs, int job, "
+    // four blocks per SM (64 registers): the items of a live entry are
+    // short chains, and the warps of a fourth block hide their latency
+    // better than the registers a few spilled values would take
+    src += "extern \"C\" __global__ void __launch_bounds__(256, 4) fs_jit_compact(const JobDev* __restrict__ jobs, int job, "
            "double2* amp_out)\n{\n"
            "    FS_GRID_DEP();\n"
            "    const JobDev& J = jobs[job];\n"

@@ -662,64 +662,11 @@ __global__ void __launch_bounds__(1024) compact_scan_kernel(const JobDev* __rest
     if (threadIdx.x == 0) J.stats[6] = s_carry;
 }
 
-// scanned: J.blk holds each block's exclusive offset (compact_scan_kernel
-// ran); otherwise it holds the blocks' counts, and each block adds those of
-// the blocks before it (at most COMPACT_DIRECT_BLOCKS of them, a few loads
-// per thread, so the scan needs no launch of its own) and the last block
-// writes the live total (stats[6]).
+// One block per compaction block (see compact_block_write).
 __global__ void __launch_bounds__(256) compact_write_kernel(const JobDev* __restrict__ jobp, int scanned)
 {
     FS_GRID_DEP();
-    const JobDev& J = *jobp;
-    __shared__ unsigned s_pre[8];
-    unsigned before = 0;
-    if (!scanned) {
-        unsigned t = 0;
-        for (unsigned k = threadIdx.x; k < blockIdx.x; k += 256) t += J.blk[k];
-        t = __reduce_add_sync(0xffffffffu, t);
-        if ((threadIdx.x & 31) == 0) s_pre[threadIdx.x >> 5] = t;
-        __syncthreads();
-        for (int w = 0; w < 8; ++w) before += s_pre[w];
-    }
-    const uint64_t base = (uint64_t)blockIdx.x * COMPACT_BLOCK;
-    bool lv[4];
-    unsigned c = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
-        lv[k] = e < J.n_entries && entry_live(J, e);
-        c += lv[k];
-    }
-    unsigned x = c;
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
-        if ((threadIdx.x & 31) >= (unsigned)off) x += y;
-    }
-    __shared__ unsigned s_w[8];
-    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = x;
-    __syncthreads();
-    unsigned woff = 0;
-    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) woff += s_w[w];
-    if (!scanned && blockIdx.x + 1 == gridDim.x && threadIdx.x == 0) {
-        unsigned mine = 0;
-        for (int w = 0; w < 8; ++w) mine += s_w[w];
-        J.stats[6] = (unsigned long long)before + mine;
-    }
-    uint64_t pos = (scanned ? (uint64_t)J.blk[blockIdx.x] : (uint64_t)before) + woff + x - c;
-    // pos is the number of live entries before e: at the first entry of a
-    // pair it opens that pair's range and closes the previous one's
-    const uint64_t pmask = (1ull << J.Ap) - 1ull;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint64_t e = base + (uint64_t)threadIdx.x * 4 + k;
-        if (e < J.n_entries && (e & pmask) == 0ull) {
-            const uint64_t p = e >> J.Ap;
-            J.prange[2 * p] = pos;
-            if (p) J.prange[2 * p - 1] = pos;
-        }
-        if (lv[k]) J.live[pos++] = e;
-        if (e + 1ull == J.n_entries) J.prange[2 * (e >> J.Ap) + 1] = pos;
-    }
+    compact_block_write(*jobp, blockIdx.x, gridDim.x, scanned, nullptr);
 }
 
 // History over the compacted live entries: items are (live entry, h_r)

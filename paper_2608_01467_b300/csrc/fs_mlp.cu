@@ -483,9 +483,10 @@ constexpr int SM_X = SM_W2 + 32768;           // per warpgroup: 128 rows x 16 k
 constexpr int SM_H1 = SM_X + 2 * 4096;        // per warpgroup: 128 rows x 128 k
 constexpr int SM_VEC = SM_H1 + 2 * 32768;     // b1, b2, bf16(w3) (FP32), b3
 constexpr int SM_BAR = SM_VEC + (3 * H + 4) * 4;   // 2 mbarriers, TMEM address, 2 abort flags
-constexpr int TC_SMEM = SM_BAR + 64;
+constexpr int SM_LIST = SM_BAR + 64;          // one compaction block's live entries (from_live = 2)
+constexpr int TC_SMEM = SM_LIST + 2 * COMPACT_BLOCK;
 static_assert(SM_BAR % 8 == 0, "mbarrier alignment");
-static_assert(2 * (TC_SMEM + 1024) <= 233472, "two CTAs per SM");
+static_assert(2 * (TC_SMEM + 128 + 1024) <= 233472, "two CTAs per SM (dynamic, static and reserved shared memory)");
 
 // instruction descriptor of kind::f16: FP32 D (bits 4-5 = 1), bf16 A and B
 // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
@@ -629,27 +630,39 @@ __device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t parity, volati
 
 // PRUNE: rows are the entries of a job's checkpoint table, features computed
 // here, entries scoring below tau cut (amplitude set to NaN, counted in
-// stats[5]).  With from_live the rows are the job's compacted live entries
-// (row i = table entry live[i], stats[6] of them: the exact bound has cut
-// the others already); otherwise every table entry, and the entries left
-// live are counted per compaction block.  Without PRUNE rows are X [n][16]
-// and y goes to Y.
+// stats[5]).  With from_live = 1 the rows are the job's compacted live
+// entries (row i = table entry live[i], stats[6] of them: the exact bound
+// has cut the others already); with from_live = 2 CTA b first writes the
+// compaction of table block b (the bound counted its live entries) and
+// then scores that block's live entries, listed in shared memory (one launch
+// less; the history reads the same live list); otherwise every table entry,
+// and the entries left live are counted per compaction block.  Without
+// PRUNE rows are X [n][16] and y goes to Y.
 template <bool PRUNE>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     mlp_tc_kernel(const float* __restrict__ P, const float* __restrict__ X, long long n_rows, float* __restrict__ Y,
                   const JobDev* __restrict__ jobs, int job, FeatureSpec sp, float tau, uint32_t* err,
                   uint32_t wait_limit, int from_live)
 {
-    // The weights of a learned pruner are uploaded once, before any step,
-    // and no kernel writes them: a pruning launch stages them (and sets up
-    // its barriers) while the kernel before it finishes, and waits for that
-    // kernel only before it reads the rows' count.  A plain forward pass
-    // (training) waits first.
-    if (!PRUNE) FS_GRID_DEP();
+    FS_GRID_DEP();
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, grp = tid >> 7, r = tid & 127, warp = tid >> 5;
     const JobDev* J = PRUNE ? &jobs[job] : nullptr;
-    if (!PRUNE && ((long long)blockIdx.x * 2 >= (n_rows + 127) / 128)) return;
+    uint16_t* blist = (uint16_t*)(sm + SM_LIST);   // from_live = 2: the block's live entries
+    long long n, t_first, tstride;
+    if (PRUNE && from_live == 2) {
+        n = (long long)compact_block_write(*J, blockIdx.x, gridDim.x, 0, blist);
+        t_first = grp;
+        tstride = 2;
+    } else {
+        n = PRUNE ? (from_live ? (long long)J->stats[6] : (long long)(J->n_pairs << J->Ap)) : n_rows;
+        t_first = (long long)blockIdx.x * 2 + grp;
+        tstride = (long long)gridDim.x * 2;
+    }
+    const long long tiles = (n + 127) / 128;
+    // a CTA with no tile leaves before staging anything (the live count of a
+    // from_live launch is known only on the device)
+    if (t_first - grp >= tiles) return;
     float* vb1 = (float*)(sm + SM_VEC);
     float* vb2 = vb1 + H;
     float* vw3 = vb2 + H;
@@ -657,29 +670,35 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     uint32_t* tmem_slot = (uint32_t*)(sm + SM_BAR + 16);
     volatile uint32_t* abort_flag = (volatile uint32_t*)(sm + SM_BAR + 20) + grp;
 
-    // weights as the B operands (B[n][k] = W[k][n]), biases, bf16-rounded w3;
-    // 16-byte loads, eight in flight per thread (the staging is on every
-    // CTA's critical path)
+    // weights as the B operands (B[n][k] = W[k][n]), biases, bf16-rounded w3.
+    // A thread takes 8 k x 4 n of W (eight 16-byte loads along n, coalesced
+    // over the warp) and writes each of its 4 columns' 8 k values as one
+    // 16-byte row segment of a core matrix: the staging is on every CTA's
+    // critical path, and element-wise 2-byte shared stores queue up in the
+    // shared-memory pipe.
     if (((uintptr_t)P & 15u) == 0u) {
         const float4* P4 = reinterpret_cast<const float4*>(P);
+        auto stage_w = [&](int off, int unit, int sbo, int dst) {
+            const int kg = unit / (H / 4), n0 = 4 * (unit % (H / 4));
+            float4 v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __ldg(P4 + (off + (8 * kg + e) * H + n0) / 4);
+            *(uint4*)(sm + dst + kmajor_off(n0, 8 * kg, sbo)) =
+                make_uint4(pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x), pack_bf16(v[4].x, v[5].x),
+                           pack_bf16(v[6].x, v[7].x));
+            *(uint4*)(sm + dst + kmajor_off(n0 + 1, 8 * kg, sbo)) =
+                make_uint4(pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y), pack_bf16(v[4].y, v[5].y),
+                           pack_bf16(v[6].y, v[7].y));
+            *(uint4*)(sm + dst + kmajor_off(n0 + 2, 8 * kg, sbo)) =
+                make_uint4(pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z), pack_bf16(v[4].z, v[5].z),
+                           pack_bf16(v[6].z, v[7].z));
+            *(uint4*)(sm + dst + kmajor_off(n0 + 3, 8 * kg, sbo)) =
+                make_uint4(pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w), pack_bf16(v[4].w, v[5].w),
+                           pack_bf16(v[6].w, v[7].w));
+        };
+        for (int u = tid; u < (F / 8) * (H / 4); u += TC_THREADS) stage_w(OFF_W1, u, 256, SM_W1);
 #pragma unroll 2
-        for (int i = tid; i < F * H / 4; i += TC_THREADS) {
-            const float4 v = __ldg(P4 + OFF_W1 / 4 + i);
-            const int k = (4 * i) / H, n = (4 * i) % H;
-            const float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                *(__nv_bfloat16*)(sm + SM_W1 + kmajor_off(n + u, k, 256)) = __float2bfloat16_rn(f[u]);
-        }
-#pragma unroll 8
-        for (int i = tid; i < H * H / 4; i += TC_THREADS) {
-            const float4 v = __ldg(P4 + OFF_W2 / 4 + i);
-            const int k = (4 * i) / H, n = (4 * i) % H;
-            const float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                *(__nv_bfloat16*)(sm + SM_W2 + kmajor_off(n + u, k, 2048)) = __float2bfloat16_rn(f[u]);
-        }
+        for (int u = tid; u < (H / 8) * (H / 4); u += TC_THREADS) stage_w(OFF_W2, u, 2048, SM_W2);
     } else {
         for (int i = tid; i < F * H; i += TC_THREADS) {
             const int k = i / H, n = i % H;
@@ -703,12 +722,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < 2) ((volatile uint32_t*)(sm + SM_BAR + 20))[tid] = 0u;
-    if (PRUNE) FS_GRID_DEP();
-    const long long n = PRUNE ? (from_live ? (long long)J->stats[6] : (long long)(J->n_pairs << J->Ap)) : n_rows;
-    const long long tiles = (n + 127) / 128;
-    // a CTA with no tile leaves before it takes tensor memory (the live
-    // count of a from_live launch is known only on the device)
-    if ((long long)blockIdx.x * 2 >= tiles) return;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(TC_COLS)
@@ -730,16 +743,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const float b3 = vw3[H];
     uint32_t phase = 0;
     unsigned long long cuts = 0;
-    const long long tstride = (long long)gridDim.x * 2;
     // table index of a row
     auto entry_of = [&](long long row_) -> unsigned long long {
+        if (from_live == 2) return (unsigned long long)blockIdx.x * COMPACT_BLOCK + blist[row_];
         return from_live ? J->live[row_] : (unsigned long long)row_;
     };
     // PRUNE: the entry of the next tile is loaded while this tile's MMAs run
     Entry cur;
     unsigned long long cur_e = 0;
     {
-        const long long row0 = ((long long)blockIdx.x * 2 + grp) * 128 + r;
+        const long long row0 = t_first * 128 + r;
         if (PRUNE && row0 < n) {
             cur_e = entry_of(row0);
             cur = J->table[cur_e];
@@ -775,7 +788,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         return lv;
     };
     // the features of tile i + 1 are computed while tile i's layer-2 MMAs run
-    long long tile = (long long)blockIdx.x * 2 + grp;
+    long long tile = t_first;
     bool live = tile < tiles ? stage_x(tile * 128 + r, cur, cur_e) : false;
     unsigned long long row_e = cur_e;   // table index of this tile's row
     for (; tile < tiles; tile += tstride) {
@@ -892,6 +905,7 @@ cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y
     const unsigned long long tiles = (rows + 127) / 128;
     unsigned long long blocks = (tiles + 1) / 2;
     if (blocks > 148 * 2) blocks = 148 * 2;
+    if (from_live == 2) blocks = (rows + COMPACT_BLOCK - 1) / COMPACT_BLOCK;   // a CTA per compaction block
     return launch_pdl(mlp_tc_kernel<PRUNE>, dim3((unsigned)blocks), dim3(TC_THREADS), TC_SMEM, s, P, X, n_rows, Y,
                       jobs, job, sp, tau, err, g_wait_limit, from_live);
 }
@@ -948,11 +962,12 @@ cudaError_t mlp_targets(const double* d_sums, unsigned long long n, double floor
 }
 
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
-                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s, bool from_live)
+                              float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s, int rows)
 {
     if (n_entries == 0) return cudaSuccess;
-    return launch_tc<true>(d_params, nullptr, 0, nullptr, d_jobs, job, sp, tau, d_err, n_entries, s,
-                           from_live ? 1 : 0);
+    if (rows == 2 && (n_entries + COMPACT_BLOCK - 1) / COMPACT_BLOCK > (unsigned long long)COMPACT_DIRECT_BLOCKS)
+        return cudaErrorInvalidValue;   // the fused compaction adds the block counts itself
+    return launch_tc<true>(d_params, nullptr, 0, nullptr, d_jobs, job, sp, tau, d_err, n_entries, s, rows);
 }
 
 void mlp_set_wait_limit(uint32_t polls) { g_wait_limit = polls; }

@@ -132,7 +132,10 @@ def test_compacted_history_reduces_its_own_outputs():
     entries per output) and with more (a pruner that cuts nothing leaves
     all 32 entries x 8 sums) agree with the interpreter's separate
     reduction and with the plain exact run, every output is written, and a
-    sub-request gives the same doubles as the full request."""
+    sub-request gives the same doubles as the full request.  A pruner on top
+    of the bound scores the live entries in the kernel that writes the
+    compaction; cutting nothing, it leaves the amplitudes bitwise as they
+    are."""
     w = qw_workload(steps=16, n_out=512)
     G = len(w.circuit.gates)
     src = {s: g for g, q, s in fs.Circuit(w.circuit).branch_vars() if s >= 0}
@@ -146,6 +149,13 @@ def test_compacted_history_reduces_its_own_outputs():
     assert zero.sum() > 0 and np.all(np.abs(exact[zero]) <= 1e-12)
     ref, st_i, n_i = _cut_run(w, c1, c2, engine="interp")
     assert n_i == 5 and tol(got, ref) and st["live_entries"] == st_i["live_entries"]
+    # a pruner on top of the bound that cuts nothing: its kernel also writes
+    # the compaction (prefix, scorer, history), the same doubles
+    bp, st_bp, n_bp = _cut_run(w, c1, c2, tau=-1e30)
+    assert n_bp == 3 and st_bp["learned_cuts"] == 0 and st_bp["live_entries"] == st["live_entries"]
+    assert np.array_equal(bp, got)
+    bp_i, _, n_bpi = _cut_run(w, c1, c2, engine="interp", tau=-1e30)
+    assert n_bpi == 5 and np.array_equal(bp_i, ref)
     # the pruner alone, cutting nothing: 256 sums for every output
     allv, st_a, n_a = _cut_run(w, c1, c2, bound=False, tau=-1e30)
     assert n_a == 4 and st_a["learned_cuts"] == 0    # prune, write, history (+ the prefix)
