@@ -128,6 +128,10 @@ constexpr int STATS_PER_JOB = 9;   // completed, valid, hist visits, entries, pr
                                    // live entries after compaction, compact work counter, bound cuts
 constexpr int COMPACT_BLOCK = 1024;   // entries per compaction block (256 threads x 4)
 constexpr int COMPACT_DIRECT_BLOCKS = 1024;   // up to this many blocks the write pass adds the counts itself
+// The learned scorer's cut mark in an entry's amplitude: a NaN (every reader
+// treats it as a cut entry) with its own payload, told apart from the other
+// cut marks only by a compaction written beside the scorer.
+constexpr unsigned long long LEARNED_CUT_BITS = 0x7ff8000000000001ull;
 constexpr int MLP_PARAMS = 18817;
 
 // Exact reachability bound at the checkpoint: what the ops after the cut can
@@ -310,13 +314,18 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // it holds the blocks' counts, the block adds those before it (nblk is at
 // most COMPACT_DIRECT_BLOCKS), and the last block writes the live total
 // (stats[6]).  list (shared memory, optional): the block's live entries as
-// offsets within the block, in table order.  Returns the block's live count.
+// offsets within the block, in table order.  write = false: only the list
+// and the count (another CTA of the same block writes the compaction).
+// learned_live: an entry carrying the scorer's cut mark counts as live (the
+// scorer cutting this block's entries while its CTAs list them: every CTA
+// then sees the same list, whichever cuts it reads).  Returns the block's
+// live count.
 __device__ __forceinline__ unsigned compact_block_write(const JobDev& J, unsigned b, unsigned nblk, int scanned,
-                                                        uint16_t* list)
+                                                        uint16_t* list, bool write = true, bool learned_live = false)
 {
     __shared__ unsigned s_pre[8], s_w[8];
     unsigned before = 0;
-    if (!scanned) {
+    if (!scanned && write) {
         unsigned t = 0;
         for (unsigned k = threadIdx.x; k < b; k += 256) t += J.blk[k];
         t = __reduce_add_sync(0xffffffffu, t);
@@ -334,7 +343,8 @@ __device__ __forceinline__ unsigned compact_block_write(const JobDev& J, unsigne
         if (e < J.n_entries) {
             const double x = J.table[e].amp.x;
             const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
-            live = !(hi > 0x7ff00000u || (hi == 0x7ff00000u && (unsigned)__double2loint(x) != 0u));
+            live = !(hi > 0x7ff00000u || (hi == 0x7ff00000u && (unsigned)__double2loint(x) != 0u)) ||
+                   (learned_live && (unsigned long long)__double_as_longlong(x) == LEARNED_CUT_BITS);
         }
         lv[k] = live;
         c += live;
@@ -350,6 +360,13 @@ __device__ __forceinline__ unsigned compact_block_write(const JobDev& J, unsigne
     for (int w = 0; w < 8; ++w) {
         if (w < (int)(threadIdx.x >> 5)) woff += s_w[w];
         total += s_w[w];
+    }
+    if (!write) {   // the block's list only
+        uint64_t pos = woff + x - c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (lv[k]) list[pos++] = (uint16_t)(threadIdx.x * 4 + k);
+        return total;
     }
     if (!scanned && b + 1 == nblk && threadIdx.x == 0) J.stats[6] = (unsigned long long)before + total;
     const uint64_t first = (scanned ? (uint64_t)J.blk[b] : (uint64_t)before);

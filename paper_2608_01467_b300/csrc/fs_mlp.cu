@@ -474,6 +474,12 @@ __global__ void features_kernel(const JobDev* __restrict__ jobs, int job, Featur
 // matrices along K (128 here), SBO = between 8-row groups along M or N.
 
 constexpr int TC_THREADS = 256;
+// CTAs per compaction block when the scorer writes the compaction: a
+// block's (at most 8) tiles of 128 live entries go one per warpgroup, so a
+// block that holds most of the live entries is not scored tile after tile
+// by one CTA; part 0 writes the block's compaction, every part lists the
+// block's live entries in its own shared memory.
+constexpr int TC_SPLIT = 4;
 constexpr uint32_t TC_COLS = 256;             // TMEM columns per CTA, 128 per warpgroup
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;  // default mbarrier polls before a wait gives up
 constexpr uint32_t TC_DRAIN_LIMIT = 1u << 24; // polls for the commit left pending by a give-up
@@ -650,10 +656,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const JobDev* J = PRUNE ? &jobs[job] : nullptr;
     uint16_t* blist = (uint16_t*)(sm + SM_LIST);   // from_live = 2: the block's live entries
     long long n, t_first, tstride;
+    const unsigned blk = blockIdx.x / TC_SPLIT, part = blockIdx.x % TC_SPLIT;   // from_live = 2
     if (PRUNE && from_live == 2) {
-        n = (long long)compact_block_write(*J, blockIdx.x, gridDim.x, 0, blist);
-        t_first = grp;
-        tstride = 2;
+        n = (long long)compact_block_write(*J, blk, gridDim.x / TC_SPLIT, 0, blist, part == 0, true);
+        t_first = 2 * part + grp;
+        tstride = 2 * TC_SPLIT;
     } else {
         n = PRUNE ? (from_live ? (long long)J->stats[6] : (long long)(J->n_pairs << J->Ap)) : n_rows;
         t_first = (long long)blockIdx.x * 2 + grp;
@@ -745,7 +752,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     unsigned long long cuts = 0;
     // table index of a row
     auto entry_of = [&](long long row_) -> unsigned long long {
-        if (from_live == 2) return (unsigned long long)blockIdx.x * COMPACT_BLOCK + blist[row_];
+        if (from_live == 2) return (unsigned long long)blk * COMPACT_BLOCK + blist[row_];
         return from_live ? J->live[row_] : (unsigned long long)row_;
     };
     // PRUNE: the entry of the next tile is loaded while this tile's MMAs run
@@ -857,7 +864,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         if (PRUNE) {
             const bool cut = live && y < tau;
             if (cut) {
-                J->table[row_e].amp.x = __longlong_as_double(0x7ff8000000000000ll);
+                J->table[row_e].amp.x = __longlong_as_double((long long)LEARNED_CUT_BITS);
                 ++cuts;
             }
             // entries left live, counted per compaction block (the warp's 32
@@ -905,7 +912,7 @@ cudaError_t launch_tc(const float* P, const float* X, long long n_rows, float* Y
     const unsigned long long tiles = (rows + 127) / 128;
     unsigned long long blocks = (tiles + 1) / 2;
     if (blocks > 148 * 2) blocks = 148 * 2;
-    if (from_live == 2) blocks = (rows + COMPACT_BLOCK - 1) / COMPACT_BLOCK;   // a CTA per compaction block
+    if (from_live == 2) blocks = TC_SPLIT * ((rows + COMPACT_BLOCK - 1) / COMPACT_BLOCK);   // TC_SPLIT per compaction block
     return launch_pdl(mlp_tc_kernel<PRUNE>, dim3((unsigned)blocks), dim3(TC_THREADS), TC_SMEM, s, P, X, n_rows, Y,
                       jobs, job, sp, tau, err, g_wait_limit, from_live);
 }
