@@ -35,7 +35,7 @@ GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "qaoa_
 N_EVAL = 64                       # outputs of the QAOA-24 p = 3 request evaluated
 EPS_SWEEP = (2e-4, 1e-4, 7e-5)    # threshold alone
 EPS_LEARNED = 7e-5                # threshold in the suffix under the pruner
-TAUS = (-1e30, -9.0, -8.0, -7.0, -6.0)
+TAUS = (-1e30, -9.0, -8.0, -7.0, -6.0, -5.0, -4.0, -3.0)
 
 
 def _cut_after_sources(circuit, k):
