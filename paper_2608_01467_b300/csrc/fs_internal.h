@@ -181,8 +181,8 @@ cudaError_t mlp_features(const JobDev* d_jobs, int job, const FeatureSpec& sp, f
 // rows = 0: score every entry and count the live ones per compaction block;
 // 1: score the compacted live entries (after the exact bound) and mark cuts
 // in the table only; 2: as 1, with the compaction's write pass done by the
-// scoring kernel (a CTA per compaction block, its live entries scored by
-// it; the bound's per-block counts, at most COMPACT_DIRECT_BLOCKS blocks).
+// scoring kernel (four CTAs per compaction block share its live entries;
+// the bound's per-block counts, at most COMPACT_DIRECT_BLOCKS blocks).
 cudaError_t mlp_learned_prune(const float* d_params, const JobDev* d_jobs, int job, const FeatureSpec& sp,
                               float tau, unsigned long long n_entries, uint32_t* d_err, cudaStream_t s,
                               int rows);

@@ -638,10 +638,11 @@ __device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t parity, volati
 // here, entries scoring below tau cut (amplitude set to NaN, counted in
 // stats[5]).  With from_live = 1 the rows are the job's compacted live
 // entries (row i = table entry live[i], stats[6] of them: the exact bound
-// has cut the others already); with from_live = 2 CTA b first writes the
-// compaction of table block b (the bound counted its live entries) and
-// then scores that block's live entries, listed in shared memory (one launch
-// less; the history reads the same live list); otherwise every table entry,
+// has cut the others already); with from_live = 2 the TC_SPLIT CTAs of
+// table block b list its live entries in shared memory (the bound counted
+// them per block), the first also writes the block's compaction, and each
+// scores its share of the list (one launch less; the history reads the same
+// live list); otherwise every table entry,
 // and the entries left live are counted per compaction block.  Without
 // PRUNE rows are X [n][16] and y goes to Y.
 template <bool PRUNE>
