@@ -168,3 +168,60 @@ def test_compacted_history_reduces_its_own_outputs():
     assert np.array_equal(sub, got[idx])
     sub_a, _, _ = _cut_run(w, c1, c2, bound=False, tau=-1e30, outputs=[w.outputs[i] for i in idx])
     assert np.array_equal(sub_a, allv[idx])
+
+
+def test_scorer_cuts_on_the_bound_are_those_of_the_network_and_repeat_bitwise():
+    """A pruner on top of the bound that cuts about half of the live
+    entries.  The scoring kernel spreads a compaction block's live entries
+    over several CTAs, each listing the block's entries while the others may
+    already be cutting some: every CTA must list the same entries.  The cuts
+    are exactly the live entries the same network scores below tau (its
+    forward pass over the job's features), the entries left are the bound's
+    live ones minus those, repeated runs give the same doubles and counts,
+    and the generated and interpreted histories over the same compaction
+    agree."""
+    import ctypes
+    import torch
+    from workloads import mlp_init_params
+    from paper_2608_01467_b300 import _lib, learned
+    w = qw_workload(steps=16, n_out=512)
+    G = len(w.circuit.gates)
+    src = {s: g for g, q, s in fs.Circuit(w.circuit).branch_vars() if s >= 0}
+    c1, c2 = G - src[3], G - src[11]            # A_p = 4, A_r = 8
+    params = torch.from_numpy(np.asarray(mlp_init_params(3), np.float32)).cuda()
+    # the bound alone: its live entries and their scores
+    C = fs.Circuit(w.circuit)
+    C.set_input(w.inputs)
+    b = fs.Batch(prefix="single")
+    b.add(C, w.outputs)
+    b.set_exact_bound(0)
+    b.set_cuts(0, c1, c2)
+    b.plan()
+    b.allocate()
+    b.upload()
+    b.run()
+    st_b = b.finish()[0]
+    n_ent = len(w.outputs) * len(w.inputs) << st_b["A_p"]
+    feat = torch.empty((n_ent, 16), dtype=torch.float32, device="cuda")
+    _lib.check(_lib.load().fs_batch_features(b._h, 0, ctypes.c_void_p(b.ws_ptr), ctypes.c_void_p(feat.data_ptr()),
+                                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    live = ~torch.isnan(feat[:, 0])
+    assert int(live.sum()) == st_b["live_entries"]
+    # a compaction block holds more live entries than one CTA scores (256)
+    assert n_ent % 1024 == 0 and int(live.view(-1, 1024).sum(1).max()) > 256
+    score = learned.forward(params, feat[live].contiguous()).cpu().numpy()
+    tau = float(np.median(score))
+    below = int((score < tau).sum())
+    assert 0 < below < len(score)
+    runs = [_cut_run(w, c1, c2, tau=tau) for _ in range(3)]
+    amp, st, n = runs[0]
+    assert n == 3 and st["learned_cuts"] == below
+    assert st["live_entries"] == st_b["live_entries"] - below
+    for a2, s2, _ in runs[1:]:
+        assert np.array_equal(a2, amp)
+        assert all(s2[k] == st[k] for k in ("learned_cuts", "live_entries", "completed", "valid"))
+    # (the interpreter does not test the bound inside the suffix, so its
+    # completed count is larger; the live entries and amplitudes agree)
+    ref, st_i, _ = _cut_run(w, c1, c2, engine="interp", tau=tau)
+    assert st_i["learned_cuts"] == below and st_i["live_entries"] == st["live_entries"]
+    assert np.all(np.abs(amp - ref) <= 1e-12 + 1e-10 * np.abs(ref))
