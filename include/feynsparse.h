@@ -484,7 +484,11 @@ FS_API int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items);
  * checkpoint entries between the prefix and history kernels.  Call before
  * fs_batch_plan (it changes the job's layout); NULL detaches it.  Jobs with a
  * pruner or eps > 0 run the history over the compacted list of live
- * checkpoint entries, so cut entries cost nothing downstream. */
+ * checkpoint entries, so cut entries cost nothing downstream.  With the
+ * exact bound also set (fs_batch_set_exact_bound) the bound cuts first and
+ * the pruner scores only the entries it leaves live; up to 1024 compaction
+ * blocks (2^20 table entries) the scoring kernel also writes the compaction,
+ * so the step is three launches (prefix, scorer, history). */
 FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau);
 
 /* ---- output sharding across devices or processes -----------------------
