@@ -487,8 +487,9 @@ FS_API int fs_batch_log_items(const fs_batch* b, uint32_t job, uint64_t* items);
  * checkpoint entries, so cut entries cost nothing downstream.  With the
  * exact bound also set (fs_batch_set_exact_bound) the bound cuts first and
  * the pruner scores only the entries it leaves live; up to 1024 compaction
- * blocks (2^20 table entries) the scoring kernel also writes the compaction,
- * so the step is three launches (prefix, scorer, history). */
+ * blocks (2^20 table entries) the scoring kernel also writes the compaction
+ * (on the generated engine an exact job with A_r >= 5 then runs in three
+ * launches: prefix, scorer, history; fs_batch_launch_count gives the count). */
 FS_API int fs_batch_set_pruner(fs_batch* b, uint32_t job, const float* d_params, float tau);
 
 /* ---- output sharding across devices or processes -----------------------
